@@ -1,0 +1,314 @@
+"""Throughput benchmark of the 2LPT f(R) forward path on GB300.
+
+One step = one full forward pass over one realisation: Philox white noise ->
+delta(k) -> the six phi_ij and the source term -> Psi1 + Psi2 (summed in k
+space) -> particle positions -> CIC deposit -> 32-shell P(k).  The growth
+tables D1(k,a), D2(k,a) depend only on the cosmology and are computed when the
+plan is made; their time is reported separately ("growth_ms").
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+N > 1 runs under torchrun: every rank makes its own realisation (seed 1 + rank),
+no data-path collective (weak scaling); the time is the max over ranks.
+--impl reference times the FP64 CPU oracle as it stands on a bounded sample.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = dict(name="fwd_512", n=512, box=1024.0, fr0=1e-5, seed=1, n_shells=32)
+SAMPLE_N = 64                      # oracle sample: same cell size (2 Mpc/h), 64^3 grid
+SAMPLE_BOX = WORKLOAD["box"] * SAMPLE_N / WORKLOAD["n"]
+
+
+def workload_desc():
+    return (f"{WORKLOAD['n']}^3 grid, {WORKLOAD['n']}^3 particles, L={WORKLOAD['box']:g} Mpc/h, "
+            f"|fR0|={WORKLOAD['fr0']:g}, z=0: Philox noise -> 2LPT (T1) positions -> CIC -> "
+            f"{WORKLOAD['n_shells']}-shell P(k)")
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        self.lines = []
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in getattr(self, "lines", []):
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_peak_gbs():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+ORACLE_SAMPLE_CODE = r"""
+import json, sys, time
+sys.path.insert(0, {root!r})
+import workloads as W
+from oracle import growth, lpt2
+n, box, reps = {n}, {box}, {reps}
+c = W.COSMO.replace(fr0_abs={fr0})
+tables = growth.growth_tables(c, 1.0, n_steps=1024)
+t0 = time.perf_counter()
+for r in range(reps):
+    out = lpt2.run(n, box, c, seed=1 + r, tables=tables, n_shells={ns})
+dt = time.perf_counter() - t0
+print(json.dumps(dict(seconds=dt, particles=reps * n ** 3)))
+"""
+
+
+def run_oracle_sample(reps, n=SAMPLE_N, box=SAMPLE_BOX):
+    """Runs the oracle in a fresh single-threaded process (spawned, never forked)."""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               CUDA_VISIBLE_DEVICES="")
+    code = ORACLE_SAMPLE_CODE.format(root=ROOT, n=n, box=box, reps=reps, fr0=WORKLOAD["fr0"],
+                                     ns=WORKLOAD["n_shells"])
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=900)
+    if r.returncode != 0:
+        raise RuntimeError("oracle sample failed: " + r.stderr[-2000:])
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+def bench_reference(args):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return
+    per = []
+    for i in range(args.warmup + args.steps):
+        res = run_oracle_sample(1)
+        if i >= args.warmup:
+            per.append(res["seconds"])
+    sec = sum(per) / len(per)
+    value = SAMPLE_N ** 3 / sec
+    line = {
+        "impl": "reference", "metric": "particles_per_s", "value": value, "unit": "particles/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": workload_desc(), "sample": f"{SAMPLE_N}^3 grid, L={SAMPLE_BOX:g} Mpc/h "
+                   "(same cell size), one realisation per step, growth tables precomputed"},
+        "cpu_baseline": {"value": value, "unit": "particles/s", "cores": 1, "kind": "oracle",
+                         "sample": f"{SAMPLE_N}^3 sub-box at the workload's cell size, per step"},
+        "e2e": {"value": value, "unit": "particles/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def bench_ours(args):
+    import numpy as np
+    import torch
+
+    import paper_1909_06282_gb300 as L
+    import workloads as W
+
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    n, box = WORKLOAD["n"], WORKLOAD["box"]
+    inst = W.Instance(n, box, WORKLOAD["seed"] + rank, W.COSMO.replace(fr0_abs=WORKLOAD["fr0"]))
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        t0 = time.perf_counter()
+        plan = L.Plan(inst, n_steps=1024, stream=stream)
+        g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        g0.record(stream)
+        L.lpt2_growth_tables(plan)
+        g1.record(stream)
+        stream.synchronize()
+        growth_ms = g0.elapsed_time(g1)
+
+        pos = torch.empty((3, n, n, n), dtype=torch.float32, device="cuda")
+        pk = dict(pk=torch.empty(32, dtype=torch.float64, device="cuda"))
+
+        def step():
+            L.lpt2_displace(plan, psi1=False, psi2=False, pos=pos)
+            return L.lpt2_cic_pk(plan, pos=None, n_shells=WORKLOAD["n_shells"])
+
+        for _ in range(args.warmup):
+            step()
+        stream.synchronize()
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        L.lpt2_timing(plan, True)
+        c0 = L.lpt2_launch_count(plan)
+        with ClockSampler(local) as clk:
+            e0.record(stream)
+            for _ in range(args.steps):
+                res = step()
+            e1.record(stream)
+            stream.synchronize()
+        launches = L.lpt2_launch_count(plan) - c0
+        kstats = L.lpt2_timing_report(plan)
+        L.lpt2_timing(plan, False)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / args.steps
+
+        # end to end through the public API: pinned host noise in, positions + P(k) out
+        noise_h = torch.from_numpy(W.white_noise(n, 1000 + rank)).pin_memory()
+        pos_h = torch.empty((3, n, n, n), dtype=torch.float32).pin_memory()
+        pk_h = torch.empty(32, dtype=torch.float64).pin_memory()
+        noise_d = torch.empty((n, n, n), dtype=torch.float32, device="cuda")
+
+        def e2e_step():
+            noise_d.copy_(noise_h, non_blocking=True)
+            L.lpt2_displace(plan, noise=noise_d, psi1=False, psi2=False, pos=pos)
+            r = L.lpt2_cic_pk(plan, pos=None, n_shells=WORKLOAD["n_shells"])
+            pos_h.copy_(pos, non_blocking=True)
+            pk_h.copy_(r["pk"], non_blocking=True)
+
+        for _ in range(max(1, args.warmup)):
+            e2e_step()
+        stream.synchronize()
+        if dist:
+            dist.barrier()
+        e2 = torch.cuda.Event(enable_timing=True)
+        e3 = torch.cuda.Event(enable_timing=True)
+        e2.record(stream)
+        for _ in range(args.steps):
+            e2e_step()
+        e3.record(stream)
+        stream.synchronize()
+        ms_e2e = e2.elapsed_time(e3) / args.steps
+
+    if dist:
+        t = torch.tensor([ms, ms_e2e], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms, ms_e2e = float(t[0]), float(t[1])
+
+    if rank == 0:
+        parts = n ** 3 * world
+        value = parts / (ms / 1e3)
+        peak, peak_kind = measured_peak_gbs()
+        total_ms = sum(v["total_ms"] for v in kstats.values())
+        dom = max(kstats.items(), key=lambda kv: kv[1]["total_ms"])
+        dname, dv = dom
+        achieved = dv["bytes"] / (dv["total_ms"] / 1e3) / 1e9
+        kernels = {k: {"launches": v["launches"], "ms_per_launch": v["total_ms"] / v["launches"],
+                       "share": v["total_ms"] / total_ms,
+                       "gbs": (v["bytes"] / (v["total_ms"] / 1e3) / 1e9) if v["bytes"] else None}
+                   for k, v in sorted(kstats.items(), key=lambda kv: -kv[1]["total_ms"])}
+        all_bytes = sum(v["bytes"] for v in kstats.values())
+        line = {
+            "metric": "particles_per_s", "value": value, "unit": "particles/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": workload_desc(), "grid": n, "box_mpc_h": box, "fr0_abs": WORKLOAD["fr0"],
+                       "outputs": "positions, CIC density (in workspace), P(k)",
+                       "l2": "inputs larger than L2 (every field 537 MB > 129 MB L2); no flush",
+                       "parallelism": f"{world} independent realisation(s), one per GPU"},
+            "roofline": {"bound": "hbm", "kernel": dname, "achieved": achieved, "peak": peak,
+                         "peak_kind": f"hbm_gbs of {peak_kind}", "unit": "GB/s", "frac": achieved / peak,
+                         "traffic": None},
+            "path_roofline": {"algorithmic_gb_per_step": all_bytes / args.steps / 1e9,
+                              "achieved_gbs": all_bytes / (total_ms / 1e3) / 1e9,
+                              "frac": all_bytes / (total_ms / 1e3) / 1e9 / peak},
+            "kernels": kernels,
+            "growth_ms": growth_ms,
+            "gpu_launches": launches,
+            "e2e": {"value": parts / (ms_e2e / 1e3), "unit": "particles/s",
+                    "h2d_bytes_per_step": n ** 3 * 4, "d2h_bytes_per_step": 3 * n ** 3 * 4 + 32 * 8},
+            "clocks": clk.summary(),
+        }
+        if not args.no_cpu_baseline:
+            reps = 3
+            res = run_oracle_sample(reps)
+            line["cpu_baseline"] = {"value": res["particles"] / res["seconds"], "unit": "particles/s",
+                                    "cores": 1, "kind": "oracle",
+                                    "sample": f"{reps} realisations of a {SAMPLE_N}^3 grid at the workload's "
+                                              f"cell size (L={SAMPLE_BOX:g} Mpc/h), growth tables precomputed, "
+                                              f"{res['seconds']:.1f} s"}
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        args.warmup = 3
+    if args.impl == "reference":
+        bench_reference(args)
+    else:
+        bench_ours(args)
+
+
+if __name__ == "__main__":
+    main()

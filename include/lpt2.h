@@ -1,0 +1,180 @@
+/*
+ * lpt2.h - C ABI of the GB300 (sm_103a) library for second-order Lagrangian
+ * perturbation theory (2LPT) displacements in Hu-Sawicki f(R) gravity, after
+ * Moretti, Mozzon, Monaco, Munari & Baldi (2019), "Fast numerical method to
+ * generate halo catalogs in modified gravity (part I): second-order Lagrangian
+ * Perturbation Theory".
+ *
+ * Every function returns an int status: LPT2_OK (0) or a negative error code.
+ * Arguments are validated on the host before any launch; on error nothing is
+ * launched and lpt2_last_error() gives a message (thread-local).  No C++
+ * exception crosses this boundary.
+ *
+ * Memory: all field pointers are DEVICE pointers owned by the caller.  The
+ * plan owns only small tables (twiddles, growth tables, cosmology constants).
+ * Large scratch ("workspace") is caller-owned too: query lpt2_workspace_size()
+ * and hand a device buffer to lpt2_set_workspace() before lpt2_displace /
+ * lpt2_cic_pk / lpt2_displace_vjp / lpt2_fft_*.  No call after lpt2_plan
+ * allocates device memory.  All launches go to the stream given to lpt2_plan
+ * and are asynchronous with respect to the host; results are ready after the
+ * caller synchronises that stream.
+ *
+ * Layouts.  Grid side N (16, 32, 64, 128, 256, 512 or 1024), box side L in
+ * Mpc/h.  A real field is float[N][N][N] (x, y, z; z fastest), cell (ix,iy,iz)
+ * at Lagrangian position q = (ix, iy, iz) L / N (cell corner).  Vector fields
+ * and particle positions are SoA float[3][N^3].  A spectrum ("half spectrum")
+ * is float2[N][N][N/2]: modes (kx, ky, kz) with kz in [0, N/2); index i maps to
+ * mode number n = i for i < N/2 and i - N otherwise, k = 2 pi n / L.  The
+ * kz = N/2 plane is not stored: the method zeroes every Nyquist plane.
+ *
+ * Threading: a plan is not thread-safe; distinct plans are independent.
+ */
+#ifndef LPT2_H
+#define LPT2_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  LPT2_OK = 0,
+  LPT2_EINVAL = -1,       /* bad argument (pointer, size, parameter range)      */
+  LPT2_ENOMEM = -2,       /* plan-time device allocation failed                  */
+  LPT2_ECUDA = -3,        /* a CUDA runtime call or kernel launch failed         */
+  LPT2_EUNSUPPORTED = -4, /* valid but not supported (grid size, hs_n != 1, ...) */
+  LPT2_ETIMEOUT = -5,     /* a bounded device-side wait gave up                  */
+  LPT2_ENOWORKSPACE = -6  /* workspace missing or smaller than required          */
+};
+
+/* D2 variants (the triangle configuration of the second-order growth, Sec. 3). */
+enum { LPT2_D2_T1 = 0 /* k1 = k2 = k/sqrt2, theta = 90 deg: the paper's choice */ };
+
+/* Background cosmology and f(R) parameters. fr0_abs = |f_R0|; 0 selects GR
+ * (mu = 1).  Flat: omega_m + omega_l must equal 1 to 1e-6.  hs_n must be 1
+ * (Eq. mihusawicki is given for n = 1). a_init is the start of the growth
+ * integration (Einstein-de Sitter growing mode there, Sec. 2.4). */
+typedef struct {
+  double omega_m, omega_l, omega_b, h, n_s, sigma8, t_cmb;
+  double fr0_abs;
+  int hs_n;
+  double a_init;
+  int d2_variant;
+} lpt2_cosmo;
+
+/* One realisation: grid side n, box side (Mpc/h), Philox seed, output scale
+ * factor a_out (0 < a_init < a_out <= 1). */
+typedef struct {
+  int n;
+  double box;
+  uint64_t seed;
+  double a_out;
+  lpt2_cosmo cosmo;
+} lpt2_instance;
+
+typedef struct lpt2_plan_s* lpt2_plan_t;
+
+/* lpt2_plan: create a plan for n_inst instances (n_inst must be 1 in this
+ * version) with growth tables on n_k log-spaced wavenumbers in [k_min, k_max]
+ * h/Mpc (Sec. 2.4: D1(k,a) is solved per k and interpolated), integrated with
+ * n_steps classical RK4 steps in ln a.  cuda_stream is a cudaStream_t (NULL =
+ * legacy default stream).  flags: reserved, pass 0.  Allocates the plan's small
+ * device tables and computes the P(k) normalisation (sigma_8) and the growth
+ * tables on the stream.  Errors: LPT2_EINVAL (null pointers, n_k < 2,
+ * k_min <= 0, k_max <= k_min, box <= 0, a range, non-flat cosmology,
+ * fr0_abs < 0, n_steps < 1), LPT2_EUNSUPPORTED (n not in the list above,
+ * hs_n != 1, d2_variant != T1, n_inst != 1), LPT2_ENOMEM, LPT2_ECUDA. */
+int lpt2_plan(lpt2_plan_t* out, const lpt2_instance* inst, int n_inst, int n_k,
+              double k_min, double k_max, int n_steps, void* cuda_stream,
+              unsigned flags);
+
+int lpt2_plan_destroy(lpt2_plan_t plan);
+
+/* Bytes of caller-owned device scratch the plan needs (about 14 N^3 floats). */
+int lpt2_workspace_size(lpt2_plan_t plan, size_t* bytes);
+
+/* Attach scratch: dev_ptr must be 256-byte aligned and >= lpt2_workspace_size
+ * bytes; it must stay valid while calls using this plan are in flight. */
+int lpt2_set_workspace(lpt2_plan_t plan, void* dev_ptr, size_t bytes);
+
+/* lpt2_growth_tables: D1(k,a_out), D2(k,a_out) of the T1 configuration and
+ * their derivatives with respect to ln|f_R0| (Eq. d1, Eq. full-d2 at k1 = k2 =
+ * k/sqrt2, theta = 90 deg; D2 sign such that GR gives -3/7 D1^2), recomputed
+ * on the plan's stream by the batched FP64 RK4 kernel and copied into the
+ * caller's device arrays double[n_k] (each pointer may be NULL). */
+int lpt2_growth_tables(lpt2_plan_t plan, double* d1, double* d2,
+                       double* dd1_dlogf, double* dd2_dlogf);
+
+/* lpt2_white_noise: the unit Gaussian white noise the plan draws (Philox4x32-10
+ * keyed by the seed, counter = flat cell index; Box-Muller on words 0 and 1),
+ * written to float[N^3]. */
+int lpt2_white_noise(lpt2_plan_t plan, float* noise);
+
+/* lpt2_philox_words: raw Philox4x32-10 output for counters (c, 0) with
+ * c in [first, first + count): uint32 out[count][4].  count <= 2^31. */
+int lpt2_philox_words(uint64_t seed, uint64_t first, int64_t count,
+                      uint32_t* out, void* cuda_stream);
+
+/* lpt2_displace: the forward 2LPT map (Sec. 2.1 Eq. second-ini, Sec. 2.4).
+ *   noise : float[N^3] unit white noise, or NULL to draw it with Philox
+ *   psi1  : float[3][N^3] first-order displacement Psi1 = i k D1 delta/k^2, or NULL
+ *   psi2  : float[3][N^3] second-order displacement Psi2 = i k D2 (-S(k)/k^2), or NULL
+ *   pos   : float[3][N^3] particle positions q + Psi1 + Psi2 wrapped into [0, L), or NULL
+ *   dk    : float2 half spectrum of the linear density delta(k), or NULL
+ * When psi1 and psi2 are both NULL the two potentials are summed in k space
+ * and only the total displacement is transformed.  The CIC density of the
+ * displaced particles is always deposited into the workspace, for
+ * lpt2_cic_pk(plan, NULL, ...).  Needs the workspace. */
+int lpt2_displace(lpt2_plan_t plan, const float* noise, float* psi1, float* psi2,
+                  float* pos, void* dk);
+
+/* lpt2_cic_pk: cloud-in-cell density contrast of N^3 unit-mass particles and
+ * its power spectrum P(k) = V |delta(k)|^2 / N^6 averaged over n_shells linear
+ * shells of width k_Ny / n_shells in [0, k_Ny) (DC excluded).
+ *   pos     : float[3][N^3] positions in [0, L), or NULL to use the density
+ *             deposited by the last lpt2_displace on this plan
+ *   density : float[N^3] density contrast output, or NULL
+ *   pk, k_mean : double[n_shells] shell mean of P and of |k| (0 if empty)
+ *   n_modes : int64[n_shells] number of modes per shell (full spectrum count)
+ * 1 <= n_shells <= 256.  Needs the workspace. */
+int lpt2_cic_pk(lpt2_plan_t plan, const float* pos, float* density, double* pk,
+                double* k_mean, int64_t* n_modes, int n_shells);
+
+/* lpt2_fft_r2c: forward 3-D transform of a real field (unnormalised,
+ * exp(-i k.x)) into the half spectrum; in and out may not alias.
+ * lpt2_fft_c2r: inverse (exp(+i k.x), unnormalised: the result is N^3 times the
+ * inverse DFT), treating the missing kz = N/2 plane as zero.  `in` is not
+ * modified.  Both need the workspace. */
+int lpt2_fft_r2c(lpt2_plan_t plan, const float* in, void* out);
+int lpt2_fft_c2r(lpt2_plan_t plan, const void* in, float* out);
+
+/* Per-kernel timing.  lpt2_timing(plan, 1) clears the record and brackets each
+ * later kernel launch of this plan with CUDA events on the plan's stream (up to
+ * 4096 launches); lpt2_timing(plan, 0) stops recording.  lpt2_timing_report
+ * waits for the recorded events and aggregates them by kernel name: launches,
+ * total device time (ms, from the events) and the algorithmic bytes those
+ * launches move (the reads and writes each pass needs at minimum).  Up to `max`
+ * entries are written to `out`; *n_out gets their number. */
+typedef struct {
+  char name[32];
+  int64_t launches;
+  double total_ms;
+  double bytes;
+} lpt2_kernel_stat;
+int lpt2_timing(lpt2_plan_t plan, int enable);
+int lpt2_timing_report(lpt2_plan_t plan, lpt2_kernel_stat* out, int max, int* n_out);
+
+/* Message of the last failing call on this thread ("" if none). */
+const char* lpt2_last_error(void);
+
+/* Number of kernel launches issued by this plan since creation (counter kept on
+ * the host; used to report launch counts). */
+int64_t lpt2_launch_count(lpt2_plan_t plan);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LPT2_H */

@@ -1,0 +1,265 @@
+"""ctypes marshalling for liblpt2.so (the C ABI of include/lpt2.h).
+
+Tensors are PyTorch CUDA tensors; their data pointers and the current CUDA
+stream are handed to the library.  Nothing here computes any part of the method.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import re
+
+import torch
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(HERE)
+HEADER = os.path.join(ROOT, "include", "lpt2.h")
+
+_ERRORS = {-1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "EUNSUPPORTED", -5: "ETIMEOUT",
+           -6: "ENOWORKSPACE"}
+
+
+def _header_functions():
+    txt = open(HEADER).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(lpt2_[a-z0-9_]+)\s*\(", txt)))
+
+
+HEADER_FUNCTIONS = _header_functions()
+
+
+class LPT2Error(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"lpt2 error {code} ({_ERRORS.get(code, '?')}): {msg}")
+        self.code = code
+
+
+class _Cosmo(C.Structure):
+    _fields_ = [("omega_m", C.c_double), ("omega_l", C.c_double), ("omega_b", C.c_double),
+                ("h", C.c_double), ("n_s", C.c_double), ("sigma8", C.c_double),
+                ("t_cmb", C.c_double), ("fr0_abs", C.c_double), ("hs_n", C.c_int),
+                ("a_init", C.c_double), ("d2_variant", C.c_int)]
+
+
+class _Instance(C.Structure):
+    _fields_ = [("n", C.c_int), ("box", C.c_double), ("seed", C.c_uint64), ("a_out", C.c_double),
+                ("cosmo", _Cosmo)]
+
+
+class _KernelStat(C.Structure):
+    _fields_ = [("name", C.c_char * 32), ("launches", C.c_int64), ("total_ms", C.c_double),
+                ("bytes", C.c_double)]
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return os.path.join(HERE, "lib", "liblpt2.so")
+
+
+def load_library():
+    """Loads liblpt2.so; raises if it has not been built (no fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = library_path()
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with __graft_entry__.build() "
+                           "or python paper_1909_06282_gb300/build.py")
+    lib = C.CDLL(path)
+    vp, i, d, u64, i64 = C.c_void_p, C.c_int, C.c_double, C.c_uint64, C.c_int64
+    sig = {
+        "lpt2_plan": (i, [C.POINTER(vp), C.POINTER(_Instance), i, i, d, d, i, vp, C.c_uint]),
+        "lpt2_plan_destroy": (i, [vp]),
+        "lpt2_workspace_size": (i, [vp, C.POINTER(C.c_size_t)]),
+        "lpt2_set_workspace": (i, [vp, vp, C.c_size_t]),
+        "lpt2_growth_tables": (i, [vp, vp, vp, vp, vp]),
+        "lpt2_white_noise": (i, [vp, vp]),
+        "lpt2_philox_words": (i, [u64, u64, i64, vp, vp]),
+        "lpt2_displace": (i, [vp, vp, vp, vp, vp, vp]),
+        "lpt2_cic_pk": (i, [vp, vp, vp, vp, vp, vp, i]),
+        "lpt2_fft_r2c": (i, [vp, vp, vp]),
+        "lpt2_fft_c2r": (i, [vp, vp, vp]),
+        "lpt2_last_error": (C.c_char_p, []),
+        "lpt2_launch_count": (i64, [vp]),
+        "lpt2_timing": (i, [vp, i]),
+        "lpt2_timing_report": (i, [vp, C.POINTER(_KernelStat), i, C.POINTER(C.c_int)]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def lpt2_last_error() -> str:
+    return load_library().lpt2_last_error().decode()
+
+
+def _check(rc):
+    if rc != 0:
+        raise LPT2Error(rc, lpt2_last_error())
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if not t.is_cuda or not t.is_contiguous():
+        raise ValueError("expected a contiguous CUDA tensor")
+    return C.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+class Plan:
+    """Owns an lpt2 plan handle and its workspace (a torch uint8 CUDA tensor)."""
+
+    def __init__(self, inst, n_k=512, k_min=1e-4, k_max=10.0, n_steps=1024, stream=None,
+                 workspace=True):
+        lib = load_library()
+        c = inst.cosmo
+        cs = _Cosmo(c.omega_m, c.omega_l, c.omega_b, c.h, c.n_s, c.sigma8, c.t_cmb, c.fr0_abs,
+                    int(c.hs_n), c.a_init, 0)
+        self.inst = inst
+        self.n = int(inst.n)
+        self.n_k = int(n_k)
+        self.n_steps = int(n_steps)
+        self._cinst = _Instance(int(inst.n), float(inst.box), int(inst.seed) & (2 ** 64 - 1),
+                                float(getattr(inst, "a_out", 1.0)), cs)
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        h = C.c_void_p()
+        _check(lib.lpt2_plan(C.byref(h), C.byref(self._cinst), 1, self.n_k, float(k_min),
+                             float(k_max), self.n_steps, _stream(self.stream), 0))
+        self.handle = h
+        self.workspace = None
+        if workspace:
+            nb = C.c_size_t()
+            _check(lib.lpt2_workspace_size(h, C.byref(nb)))
+            self.workspace = torch.empty(nb.value, dtype=torch.uint8, device="cuda")
+            _check(lib.lpt2_set_workspace(h, _ptr(self.workspace), nb.value))
+
+    def close(self):
+        if getattr(self, "handle", None) is not None and self.handle.value:
+            load_library().lpt2_plan_destroy(self.handle)
+            self.handle = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def lpt2_plan(inst, **kw) -> Plan:
+    return Plan(inst, **kw)
+
+
+def lpt2_plan_destroy(plan: Plan):
+    plan.close()
+
+
+def lpt2_workspace_size(plan: Plan) -> int:
+    nb = C.c_size_t()
+    _check(load_library().lpt2_workspace_size(plan.handle, C.byref(nb)))
+    return nb.value
+
+
+def lpt2_launch_count(plan: Plan) -> int:
+    return int(load_library().lpt2_launch_count(plan.handle))
+
+
+def lpt2_growth_tables(plan: Plan):
+    """Returns (D1, D2, dD1/dln|fR0|, dD2/dln|fR0|), float64 CUDA tensors [n_k]."""
+    out = [torch.empty(plan.n_k, dtype=torch.float64, device="cuda") for _ in range(4)]
+    _check(load_library().lpt2_growth_tables(plan.handle, *[_ptr(t) for t in out]))
+    return tuple(out)
+
+
+def lpt2_white_noise(plan: Plan, out=None):
+    n = plan.n
+    out = torch.empty((n, n, n), dtype=torch.float32, device="cuda") if out is None else out
+    _check(load_library().lpt2_white_noise(plan.handle, _ptr(out)))
+    return out
+
+
+def lpt2_philox_words(seed: int, first: int, count: int, stream=None):
+    """Raw Philox4x32-10 words for counters first..first+count-1: int32 tensor (count, 4)
+    holding the uint32 bit patterns."""
+    out = torch.empty((count, 4), dtype=torch.int32, device="cuda")
+    _check(load_library().lpt2_philox_words(int(seed) & (2 ** 64 - 1), int(first), int(count),
+                                            _ptr(out), _stream(stream)))
+    return out
+
+
+def lpt2_displace(plan: Plan, noise=None, psi1=True, psi2=True, pos=True, dk=False):
+    """Forward 2LPT map. Returns dict with the requested outputs ('psi1', 'psi2' and 'pos'
+    as float32 (3, N, N, N) tensors, 'dk' as complex64 (N, N, N/2) tensor)."""
+    n = plan.n
+    f3 = lambda: torch.empty((3, n, n, n), dtype=torch.float32, device="cuda")
+    out = {}
+    if psi1:
+        out["psi1"] = psi1 if torch.is_tensor(psi1) else f3()
+    if psi2:
+        out["psi2"] = psi2 if torch.is_tensor(psi2) else f3()
+    if pos:
+        out["pos"] = pos if torch.is_tensor(pos) else f3()
+    if dk:
+        out["dk"] = dk if torch.is_tensor(dk) else torch.empty((n, n, n // 2), dtype=torch.complex64,
+                                                               device="cuda")
+    if noise is not None and (noise.dtype != torch.float32 or noise.numel() != n ** 3):
+        raise ValueError("noise must be float32 with N^3 elements")
+    _check(load_library().lpt2_displace(plan.handle, _ptr(noise), _ptr(out.get("psi1")),
+                                        _ptr(out.get("psi2")), _ptr(out.get("pos")),
+                                        _ptr(out.get("dk"))))
+    return out
+
+
+def lpt2_cic_pk(plan: Plan, pos=None, density=False, n_shells=32):
+    """CIC density contrast and shell P(k). pos None uses the density deposited by the
+    last lpt2_displace on this plan."""
+    n = plan.n
+    res = dict(pk=torch.empty(n_shells, dtype=torch.float64, device="cuda"),
+               k_mean=torch.empty(n_shells, dtype=torch.float64, device="cuda"),
+               n_modes=torch.empty(n_shells, dtype=torch.int64, device="cuda"))
+    if density:
+        res["density"] = density if torch.is_tensor(density) else torch.empty(
+            (n, n, n), dtype=torch.float32, device="cuda")
+    if pos is not None and (pos.dtype != torch.float32 or pos.numel() != 3 * n ** 3):
+        raise ValueError("pos must be float32 with 3 N^3 elements")
+    _check(load_library().lpt2_cic_pk(plan.handle, _ptr(pos), _ptr(res.get("density")),
+                                      _ptr(res["pk"]), _ptr(res["k_mean"]), _ptr(res["n_modes"]),
+                                      int(n_shells)))
+    return res
+
+
+def lpt2_fft_r2c(plan: Plan, x, out=None):
+    n = plan.n
+    out = torch.empty((n, n, n // 2), dtype=torch.complex64, device="cuda") if out is None else out
+    _check(load_library().lpt2_fft_r2c(plan.handle, _ptr(x), _ptr(out)))
+    return out
+
+
+def lpt2_fft_c2r(plan: Plan, X, out=None):
+    n = plan.n
+    out = torch.empty((n, n, n), dtype=torch.float32, device="cuda") if out is None else out
+    _check(load_library().lpt2_fft_c2r(plan.handle, _ptr(X), _ptr(out)))
+    return out
+
+
+def lpt2_timing(plan: Plan, enable: bool):
+    _check(load_library().lpt2_timing(plan.handle, 1 if enable else 0))
+
+
+def lpt2_timing_report(plan: Plan):
+    """{kernel name: dict(launches, total_ms, bytes)} of the launches recorded since
+    lpt2_timing(plan, True) (waits for them)."""
+    arr = (_KernelStat * 64)()
+    n = C.c_int()
+    _check(load_library().lpt2_timing_report(plan.handle, arr, 64, C.byref(n)))
+    return {arr[i].name.decode(): dict(launches=int(arr[i].launches), total_ms=float(arr[i].total_ms),
+                                       bytes=float(arr[i].bytes)) for i in range(n.value)}

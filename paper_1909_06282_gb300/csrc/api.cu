@@ -1,0 +1,584 @@
+// Host side of the C ABI declared in include/lpt2.h: argument validation, plan
+// tables, workspace layout and the launch sequence of each entry point.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/lpt2.h"
+#include "passes.h"
+
+using namespace lpt2;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return code;
+}
+
+bool supported_n(int n) {
+  return n == 16 || n == 32 || n == 64 || n == 128 || n == 256 || n == 512 || n == 1024;
+}
+
+// Workspace slots, each N^3 floats (= a half spectrum of N^3/2 complex).
+enum Slot { S_A = 0, S_DELTA = 1, S_X0 = 2, S_Y0 = 7, S_RHO = 16, N_SLOTS = 17 };
+constexpr int kMaxShells = 256;
+constexpr int kMaxRec = 4096;
+
+}  // namespace
+
+struct lpt2_plan_s {
+  int n;
+  double box;
+  uint64_t seed;
+  double a_out;
+  lpt2_cosmo cosmo;
+  int nk;
+  double k_min, k_max;
+  int n_steps;
+  cudaStream_t stream;
+  float2* tw;
+  DevCosmo* cosmo_dev;
+  double* partials;
+  double* tab;    // [4][nk]
+  float* tabf;    // [2][nk]
+  char* ws;
+  size_t ws_bytes;
+  int64_t launches;
+  // per-launch CUDA-event timing (lpt2_timing)
+  bool timing_on;
+  int n_rec;
+  cudaEvent_t* ev;            // 2 * kMaxRec events, created on first enable
+  const char* rec_name[kMaxRec];
+  double rec_bytes[kMaxRec];
+};
+
+namespace {
+
+double V3(const lpt2_plan_s* p) { return (double)p->n * p->n * p->n; }
+
+size_t slot_bytes(const lpt2_plan_s* p) { return (size_t)p->n * p->n * p->n * sizeof(float); }
+
+int x_blocks(int n) {
+  switch (n) {
+    case 16: return x_blocks_16();
+    case 32: return x_blocks_32();
+    case 64: return x_blocks_64();
+    case 128: return x_blocks_128();
+    case 256: return x_blocks_256();
+    case 512: return x_blocks_512();
+    default: return x_blocks_1024();
+  }
+}
+
+size_t ws_need(const lpt2_plan_s* p) {
+  return N_SLOTS * slot_bytes(p) + (size_t)x_blocks(p->n) * 3 * kMaxShells * sizeof(double);
+}
+
+float2* slot(const lpt2_plan_s* p, int i) { return reinterpret_cast<float2*>(p->ws + i * slot_bytes(p)); }
+double* pk_part(const lpt2_plan_s* p) { return reinterpret_cast<double*>(p->ws + N_SLOTS * slot_bytes(p)); }
+
+Geo make_geo(const lpt2_plan_s* p) {
+  Geo g;
+  const double n = p->n;
+  g.n = p->n;
+  g.kf = (float)(2.0 * M_PI / p->box);
+  g.box = (float)p->box;
+  g.cell = (float)(p->box / n);
+  g.inv_cell = (float)(n / p->box);
+  g.inv_n3 = (float)(1.0 / (n * n * n));
+  g.sqrt_n3_over_v = (float)sqrt(n * n * n / (p->box * p->box * p->box));
+  return g;
+}
+
+GrowthParams growth_params(const lpt2_plan_s* p) {
+  GrowthParams g;
+  g.omega_m = p->cosmo.omega_m;
+  g.omega_l = p->cosmo.omega_l;
+  g.omega_b = p->cosmo.omega_b;
+  g.h = p->cosmo.h;
+  g.n_s = p->cosmo.n_s;
+  g.sigma8 = p->cosmo.sigma8;
+  g.t_cmb = p->cosmo.t_cmb;
+  g.fr0_abs = p->cosmo.fr0_abs;
+  g.a_init = p->cosmo.a_init;
+  g.a_out = p->a_out;
+  g.k_min = p->k_min;
+  g.k_max = p->k_max;
+  g.nk = p->nk;
+  g.n_steps = p->n_steps;
+  return g;
+}
+
+#define DISPATCH(NAME, n, args, s)          \
+  switch (n) {                              \
+    case 16: return NAME##_16(args, s);     \
+    case 32: return NAME##_32(args, s);     \
+    case 64: return NAME##_64(args, s);     \
+    case 128: return NAME##_128(args, s);   \
+    case 256: return NAME##_256(args, s);   \
+    case 512: return NAME##_512(args, s);   \
+    default: return NAME##_1024(args, s);   \
+  }
+
+cudaError_t z_r2c(int n, const ZR2CArgs& a, cudaStream_t s) { DISPATCH(launch_z_r2c, n, a, s) }
+cudaError_t z_c2r(int n, const ZC2RArgs& a, cudaStream_t s) { DISPATCH(launch_z_c2r, n, a, s) }
+cudaError_t z_source(int n, const ZSourceArgs& a, cudaStream_t s) { DISPATCH(launch_z_source, n, a, s) }
+cudaError_t z_final(int n, const ZFinalArgs& a, cudaStream_t s) { DISPATCH(launch_z_final, n, a, s) }
+cudaError_t y_pass(int n, const YArgs& a, cudaStream_t s) { DISPATCH(launch_y, n, a, s) }
+cudaError_t x_pass(int n, const XArgs& a, cudaStream_t s) { DISPATCH(launch_x, n, a, s) }
+
+void timing_begin(lpt2_plan_s* p) {
+  if (!p->timing_on || p->n_rec >= kMaxRec) return;
+  cudaEventRecord(p->ev[2 * p->n_rec], p->stream);
+}
+
+void timing_end(lpt2_plan_s* p, const char* name, double bytes) {
+  if (!p->timing_on || p->n_rec >= kMaxRec) return;
+  cudaEventRecord(p->ev[2 * p->n_rec + 1], p->stream);
+  p->rec_name[p->n_rec] = name;
+  p->rec_bytes[p->n_rec] = bytes;
+  p->n_rec++;
+}
+
+// Every kernel launch goes through LAUNCH(plan, name, algorithmic bytes, call):
+// counts it and, when timing is on, brackets it with CUDA events on the plan's stream.
+#define LAUNCH(plan, name, bytes, expr)                                               \
+  do {                                                                                \
+    timing_begin((plan));                                                             \
+    cudaError_t e_ = (expr);                                                          \
+    (plan)->launches++;                                                               \
+    timing_end((plan), (name), (double)(bytes));                                      \
+    if (e_ != cudaSuccess)                                                            \
+      return fail(LPT2_ECUDA, "%s: %s", #expr, cudaGetErrorString(e_));               \
+  } while (0)
+
+bool aligned(const void* p, size_t a) { return ((uintptr_t)p % a) == 0; }
+
+int check_plan_ws(lpt2_plan_t p) {
+  if (!p) return fail(LPT2_EINVAL, "null plan");
+  if (!p->ws) return fail(LPT2_ENOWORKSPACE, "no workspace attached (lpt2_set_workspace)");
+  return LPT2_OK;
+}
+
+// forward r2c of a real field (or the Philox noise) into `out`, z -> y -> x (plain)
+int forward_zy(lpt2_plan_t p, int src, const float* in, float2* out) {
+  ZR2CArgs z{};
+  z.g = make_geo(p);
+  z.tw = p->tw;
+  z.src = src;
+  z.in = in;
+  z.seed_lo = (uint32_t)p->seed;
+  z.seed_hi = (uint32_t)(p->seed >> 32);
+  z.out = out;
+  LAUNCH(p, src == Z_NOISE ? "z_r2c_noise" : (src == Z_DENSITY ? "z_r2c_density" : "z_r2c"),
+         (src == Z_NOISE ? 4.0 : 8.0) * V3(p), z_r2c(p->n, z, p->stream));
+  YArgs y{};
+  y.g = z.g;
+  y.tw = p->tw;
+  y.inverse = 0;
+  y.job.n_in = 1;
+  y.job.n_out = 1;
+  y.job.in[0] = out;
+  y.job.out[0] = out;
+  y.job.src[0] = 0;
+  y.job.ord[0] = 0;
+  LAUNCH(p, "y_fwd", 8.0 * V3(p), y_pass(p->n, y, p->stream));
+  return LPT2_OK;
+}
+
+int run_growth(lpt2_plan_t p) {
+  const GrowthParams gp = growth_params(p);
+  LAUNCH(p, "growth", 0.0, launch_growth(gp, p->tab, p->tabf, p->stream));
+  return LPT2_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* lpt2_last_error(void) { return g_err.c_str(); }
+
+int64_t lpt2_launch_count(lpt2_plan_t plan) { return plan ? plan->launches : -1; }
+
+int lpt2_plan(lpt2_plan_t* out, const lpt2_instance* inst, int n_inst, int n_k, double k_min,
+              double k_max, int n_steps, void* cuda_stream, unsigned flags) {
+  g_err.clear();
+  if (!out || !inst) return fail(LPT2_EINVAL, "null out/inst pointer");
+  *out = nullptr;
+  if (n_inst != 1) return fail(LPT2_EUNSUPPORTED, "n_inst must be 1 (got %d)", n_inst);
+  if (flags != 0) return fail(LPT2_EINVAL, "flags must be 0");
+  const lpt2_cosmo& c = inst->cosmo;
+  if (!supported_n(inst->n)) return fail(LPT2_EUNSUPPORTED, "grid size %d not supported", inst->n);
+  if (!(inst->box > 0) || !isfinite(inst->box)) return fail(LPT2_EINVAL, "box must be > 0");
+  if (n_k < 2 || n_k > 4096) return fail(LPT2_EINVAL, "n_k must be in [2, 4096]");
+  if (!(k_min > 0) || !(k_max > k_min)) return fail(LPT2_EINVAL, "need 0 < k_min < k_max");
+  if (n_steps < 1 || n_steps > 2800) return fail(LPT2_EINVAL, "n_steps must be in [1, 2800]");
+  if (!(c.a_init > 0) || !(inst->a_out > c.a_init) || !(inst->a_out <= 1.0))
+    return fail(LPT2_EINVAL, "need 0 < a_init < a_out <= 1");
+  if (!(c.omega_m > 0) || !(c.omega_l >= 0) || fabs(c.omega_m + c.omega_l - 1.0) > 1e-6)
+    return fail(LPT2_EINVAL, "cosmology must be flat with omega_m > 0");
+  if (!(c.h > 0) || !(c.sigma8 > 0) || !(c.omega_b > 0) || !(c.omega_b < c.omega_m) || !(c.t_cmb > 0))
+    return fail(LPT2_EINVAL, "bad h / sigma8 / omega_b / t_cmb");
+  if (!(c.fr0_abs >= 0) || !isfinite(c.fr0_abs)) return fail(LPT2_EINVAL, "fr0_abs must be >= 0");
+  if (c.hs_n != 1) return fail(LPT2_EUNSUPPORTED, "only Hu-Sawicki n = 1 is supported");
+  if (c.d2_variant != LPT2_D2_T1) return fail(LPT2_EUNSUPPORTED, "only the T1 D2 variant is supported");
+
+  lpt2_plan_s* p = new lpt2_plan_s();
+  p->n = inst->n;
+  p->box = inst->box;
+  p->seed = inst->seed;
+  p->a_out = inst->a_out;
+  p->cosmo = c;
+  p->nk = n_k;
+  p->k_min = k_min;
+  p->k_max = k_max;
+  p->n_steps = n_steps;
+  p->stream = (cudaStream_t)cuda_stream;
+  const int n = p->n;
+  cudaError_t e = cudaSuccess;
+  e = cudaMalloc(&p->tw, n * sizeof(float2));
+  if (e == cudaSuccess) e = cudaMalloc(&p->cosmo_dev, sizeof(DevCosmo));
+  if (e == cudaSuccess) e = cudaMalloc(&p->partials, cosmo_partial_blocks() * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&p->tab, 4 * n_k * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&p->tabf, 2 * n_k * sizeof(float));
+  if (e != cudaSuccess) {
+    lpt2_plan_destroy(p);
+    return fail(LPT2_ENOMEM, "plan allocation failed: %s", cudaGetErrorString(e));
+  }
+  // twiddles exp(-2 pi i m / N), FP64 then rounded once
+  std::vector<float2> tw(n);
+  for (int m = 0; m < n; ++m) {
+    const double ang = 2.0 * M_PI * (double)m / (double)n;
+    tw[m] = make_float2((float)cos(ang), (float)(-sin(ang)));
+  }
+  e = cudaMemcpy(p->tw, tw.data(), n * sizeof(float2), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    lpt2_plan_destroy(p);
+    return fail(LPT2_ECUDA, "twiddle upload: %s", cudaGetErrorString(e));
+  }
+  const GrowthParams gp = growth_params(p);
+  e = launch_cosmo_setup(gp, p->partials, p->cosmo_dev, p->stream);
+  p->launches += 2;   // partial sums + final
+  if (e == cudaSuccess) {
+    e = launch_growth(gp, p->tab, p->tabf, p->stream);
+    p->launches += 1;
+  }
+  if (e != cudaSuccess) {
+    lpt2_plan_destroy(p);
+    return fail(LPT2_ECUDA, "set-up kernels: %s", cudaGetErrorString(e));
+  }
+  *out = p;
+  return LPT2_OK;
+}
+
+int lpt2_plan_destroy(lpt2_plan_t p) {
+  if (!p) return LPT2_OK;
+  cudaFree(p->tw);
+  cudaFree(p->cosmo_dev);
+  cudaFree(p->partials);
+  cudaFree(p->tab);
+  cudaFree(p->tabf);
+  if (p->ev) {
+    for (int i = 0; i < 2 * kMaxRec; ++i) cudaEventDestroy(p->ev[i]);
+    delete[] p->ev;
+  }
+  delete p;
+  return LPT2_OK;
+}
+
+int lpt2_workspace_size(lpt2_plan_t p, size_t* bytes) {
+  if (!p || !bytes) return fail(LPT2_EINVAL, "null argument");
+  *bytes = ws_need(p);
+  return LPT2_OK;
+}
+
+int lpt2_set_workspace(lpt2_plan_t p, void* dev_ptr, size_t bytes) {
+  if (!p || !dev_ptr) return fail(LPT2_EINVAL, "null argument");
+  if (!aligned(dev_ptr, 256)) return fail(LPT2_EINVAL, "workspace must be 256-byte aligned");
+  if (bytes < ws_need(p)) return fail(LPT2_ENOWORKSPACE, "workspace too small: %zu < %zu", bytes, ws_need(p));
+  p->ws = (char*)dev_ptr;
+  p->ws_bytes = bytes;
+  return LPT2_OK;
+}
+
+int lpt2_growth_tables(lpt2_plan_t p, double* d1, double* d2, double* dd1, double* dd2) {
+  if (!p) return fail(LPT2_EINVAL, "null plan");
+  int rc = run_growth(p);
+  if (rc) return rc;
+  double* dst[4] = {d1, d2, dd1, dd2};
+  for (int i = 0; i < 4; ++i) {
+    if (!dst[i]) continue;
+    cudaError_t e = cudaMemcpyAsync(dst[i], p->tab + (size_t)i * p->nk, p->nk * sizeof(double),
+                                    cudaMemcpyDeviceToDevice, p->stream);
+    if (e != cudaSuccess) return fail(LPT2_ECUDA, "table copy: %s", cudaGetErrorString(e));
+  }
+  return LPT2_OK;
+}
+
+int lpt2_white_noise(lpt2_plan_t p, float* noise) {
+  if (!p || !noise) return fail(LPT2_EINVAL, "null argument");
+  if (!aligned(noise, 4)) return fail(LPT2_EINVAL, "misaligned output");
+  LAUNCH(p, "noise", 4.0 * V3(p), launch_noise(make_geo(p), (uint32_t)p->seed, (uint32_t)(p->seed >> 32), noise, p->stream));
+  return LPT2_OK;
+}
+
+int lpt2_philox_words(uint64_t seed, uint64_t first, int64_t count, uint32_t* out, void* stream) {
+  if (!out || count < 0 || count > (1LL << 31)) return fail(LPT2_EINVAL, "bad philox arguments");
+  if (!aligned(out, 16)) return fail(LPT2_EINVAL, "output must be 16-byte aligned");
+  if (count == 0) return LPT2_OK;
+  cudaError_t e = launch_philox_words((uint32_t)seed, (uint32_t)(seed >> 32), first, count, out,
+                                      (cudaStream_t)stream);
+  if (e != cudaSuccess) return fail(LPT2_ECUDA, "philox: %s", cudaGetErrorString(e));
+  return LPT2_OK;
+}
+
+int lpt2_displace(lpt2_plan_t p, const float* noise, float* psi1, float* psi2, float* pos, void* dk) {
+  int rc = check_plan_ws(p);
+  if (rc) return rc;
+  if (dk && !aligned(dk, 16)) return fail(LPT2_EINVAL, "dk must be 16-byte aligned");
+  const int n = p->n;
+  const Geo g = make_geo(p);
+  const bool split = psi1 || psi2;
+  float2* A = slot(p, S_A);
+  float2* D = slot(p, S_DELTA);
+  float2* X[5];
+  float2* Y[9];
+  for (int i = 0; i < 5; ++i) X[i] = slot(p, S_X0 + i);
+  for (int i = 0; i < 9; ++i) Y[i] = slot(p, S_Y0 + i);
+  float* rho = reinterpret_cast<float*>(slot(p, S_RHO));
+
+  // 1. delta(k): noise -> z, y passes; x pass with sqrt(P) and the phi / Psi1 potentials
+  rc = forward_zy(p, noise ? Z_REAL : Z_NOISE, noise, A);
+  if (rc) return rc;
+  XArgs x{};
+  x.g = g;
+  x.tw = p->tw;
+  x.mode = X_DELTA;
+  x.split = split;
+  x.in = A;
+  x.delta_out = D;
+  for (int i = 0; i < 5; ++i) x.out[i] = X[i];
+  x.cosmo = p->cosmo_dev;
+  x.d1f = p->tabf;
+  x.d2f = p->tabf + p->nk;
+  LAUNCH(p, "x_delta", (split ? 28.0 : 20.0) * V3(p), x_pass(n, x, p->stream));
+
+  // 2. y inverse with y derivatives: the six phi_ij (+ Psi1)
+  YArgs y{};
+  y.g = g;
+  y.tw = p->tw;
+  y.inverse = 1;
+  y.job.n_in = split ? 5 : 3;
+  for (int i = 0; i < 5; ++i) y.job.in[i] = X[i];
+  const int src[9] = {0, 0, 0, 1, 1, 2, 3, 3, 4};
+  const int ord[9] = {0, 1, 2, 0, 1, 0, 0, 1, 0};
+  y.job.n_out = split ? 9 : 6;
+  for (int o = 0; o < 9; ++o) {
+    y.job.out[o] = Y[o];
+    y.job.src[o] = src[o];
+    y.job.ord[o] = ord[o];
+  }
+  LAUNCH(p, "y_phi", (split ? 56.0 : 36.0) * V3(p), y_pass(n, y, p->stream));
+
+  // 3. z inverse of phi_ij, source term, z forward of S
+  ZSourceArgs zs{};
+  zs.g = g;
+  zs.tw = p->tw;
+  const float2* phi[6] = {Y[5], Y[2], Y[0], Y[4], Y[3], Y[1]};   // xx yy zz xy xz yz
+  const int zord[6] = {0, 0, 2, 0, 1, 1};
+  for (int i = 0; i < 6; ++i) {
+    zs.in[i] = phi[i];
+    zs.ord[i] = zord[i];
+  }
+  zs.out = A;
+  LAUNCH(p, "z_source", 28.0 * V3(p), z_source(n, zs, p->stream));
+  YArgs yf{};
+  yf.g = g;
+  yf.tw = p->tw;
+  yf.inverse = 0;
+  yf.job.n_in = 1;
+  yf.job.n_out = 1;
+  yf.job.in[0] = A;
+  yf.job.out[0] = A;
+  LAUNCH(p, "y_fwd", 8.0 * V3(p), y_pass(n, yf, p->stream));
+
+  // 4. x pass: S(k) -> phi2 = -S D2/k^2 (+ D1 delta/k^2 when not split), x inverse
+  XArgs xs = x;
+  xs.mode = X_SOURCE;
+  xs.in = A;
+  xs.delta_out = nullptr;
+  xs.delta_in = D;
+  xs.out[0] = X[0];
+  xs.out[1] = X[1];
+  LAUNCH(p, "x_source", (split ? 12.0 : 16.0) * V3(p), x_pass(n, xs, p->stream));
+
+  // 5. y inverse: (x0 y0), (x0 y1), (x1 y0)
+  YArgs y2{};
+  y2.g = g;
+  y2.tw = p->tw;
+  y2.inverse = 1;
+  y2.job.n_in = 2;
+  y2.job.in[0] = X[0];
+  y2.job.in[1] = X[1];
+  y2.job.n_out = 3;
+  const int src2[3] = {0, 0, 1}, ord2[3] = {0, 1, 0};
+  for (int o = 0; o < 3; ++o) {
+    y2.job.out[o] = Y[o];
+    y2.job.src[o] = src2[o];
+    y2.job.ord[o] = ord2[o];
+  }
+  LAUNCH(p, "y_psi", 20.0 * V3(p), y_pass(n, y2, p->stream));
+
+  // 6. z inverse, positions, CIC
+  LAUNCH(p, "fill0", 4.0 * V3(p), launch_fill0(rho, (size_t)n * n * n, p->stream));
+  ZFinalArgs zf{};
+  zf.g = g;
+  zf.tw = p->tw;
+  zf.split = split;
+  for (int i = 0; i < 3; ++i) {
+    zf.a[i] = split ? Y[6 + i] : Y[i];
+    zf.b[i] = Y[i];
+  }
+  zf.psi1 = psi1;
+  zf.psi2 = psi2;
+  zf.pos = pos;
+  zf.rho = rho;
+  LAUNCH(p, "z_final",
+         ((split ? 24.0 : 12.0) + (pos ? 12.0 : 0.0) + (psi1 ? 12.0 : 0.0) + (psi2 ? 12.0 : 0.0) + 8.0) * V3(p),
+         z_final(n, zf, p->stream));
+  if (dk) {
+    cudaError_t e = cudaMemcpyAsync(dk, D, slot_bytes(p), cudaMemcpyDeviceToDevice, p->stream);
+    if (e != cudaSuccess) return fail(LPT2_ECUDA, "dk copy: %s", cudaGetErrorString(e));
+  }
+  return LPT2_OK;
+}
+
+int lpt2_cic_pk(lpt2_plan_t p, const float* pos, float* density, double* pk, double* k_mean,
+                int64_t* n_modes, int n_shells) {
+  int rc = check_plan_ws(p);
+  if (rc) return rc;
+  if (!pk) return fail(LPT2_EINVAL, "pk must not be null");
+  if (n_shells < 1 || n_shells > kMaxShells) return fail(LPT2_EINVAL, "n_shells must be in [1, 256]");
+  const int n = p->n;
+  const Geo g = make_geo(p);
+  float* rho = reinterpret_cast<float*>(slot(p, S_RHO));
+  float2* A = slot(p, S_A);
+  if (pos) {
+    LAUNCH(p, "fill0", 4.0 * V3(p), launch_fill0(rho, (size_t)n * n * n, p->stream));
+    CicArgs c{g, pos, rho};
+    LAUNCH(p, "cic", 20.0 * V3(p), launch_cic(c, p->stream));
+  }
+  rc = forward_zy(p, Z_DENSITY, rho, A);   // rho - 1 is formed in the z pass; rho is kept
+  if (rc) return rc;
+  if (density) LAUNCH(p, "contrast", 8.0 * V3(p), launch_contrast(rho, density, (size_t)n * n * n, p->stream));
+  XArgs x{};
+  x.g = g;
+  x.tw = p->tw;
+  x.mode = X_PK;
+  x.in = A;
+  x.cosmo = p->cosmo_dev;
+  x.pk_part = pk_part(p);
+  x.n_shells = n_shells;
+  LAUNCH(p, "x_pk", 4.0 * V3(p), x_pass(n, x, p->stream));
+  LAUNCH(p, "pk_finalize", 0.0, launch_pk_finalize(pk_part(p), x_blocks(n), n_shells, pk, k_mean, n_modes, p->stream));
+  return LPT2_OK;
+}
+
+int lpt2_fft_r2c(lpt2_plan_t p, const float* in, void* out) {
+  int rc = check_plan_ws(p);
+  if (rc) return rc;
+  if (!in || !out || !aligned(out, 16)) return fail(LPT2_EINVAL, "bad in/out");
+  float2* o = reinterpret_cast<float2*>(out);
+  rc = forward_zy(p, Z_REAL, in, o);
+  if (rc) return rc;
+  XArgs x{};
+  x.g = make_geo(p);
+  x.tw = p->tw;
+  x.mode = X_FWD;
+  x.in = o;
+  x.out[0] = o;
+  LAUNCH(p, "x_fwd", 8.0 * V3(p), x_pass(p->n, x, p->stream));
+  return LPT2_OK;
+}
+
+int lpt2_fft_c2r(lpt2_plan_t p, const void* in, float* out) {
+  int rc = check_plan_ws(p);
+  if (rc) return rc;
+  if (!in || !out || !aligned(in, 16)) return fail(LPT2_EINVAL, "bad in/out");
+  const Geo g = make_geo(p);
+  float2* A = slot(p, S_A);
+  XArgs x{};
+  x.g = g;
+  x.tw = p->tw;
+  x.mode = X_INV;
+  x.in = reinterpret_cast<const float2*>(in);
+  x.out[0] = A;
+  LAUNCH(p, "x_inv", 8.0 * V3(p), x_pass(p->n, x, p->stream));
+  YArgs y{};
+  y.g = g;
+  y.tw = p->tw;
+  y.inverse = 1;
+  y.job.n_in = 1;
+  y.job.n_out = 1;
+  y.job.in[0] = A;
+  y.job.out[0] = A;
+  LAUNCH(p, "y_inv", 8.0 * V3(p), y_pass(p->n, y, p->stream));
+  ZC2RArgs z{g, p->tw, A, out};
+  LAUNCH(p, "z_c2r", 8.0 * V3(p), z_c2r(p->n, z, p->stream));
+  return LPT2_OK;
+}
+
+int lpt2_timing(lpt2_plan_t p, int enable) {
+  if (!p) return fail(LPT2_EINVAL, "null plan");
+  if (enable && !p->ev) {
+    p->ev = new cudaEvent_t[2 * kMaxRec];
+    for (int i = 0; i < 2 * kMaxRec; ++i) {
+      cudaError_t e = cudaEventCreate(&p->ev[i]);
+      if (e != cudaSuccess) return fail(LPT2_ECUDA, "event create: %s", cudaGetErrorString(e));
+    }
+  }
+  p->timing_on = enable != 0;
+  if (enable) p->n_rec = 0;
+  return LPT2_OK;
+}
+
+int lpt2_timing_report(lpt2_plan_t p, lpt2_kernel_stat* out, int max, int* n_out) {
+  if (!p || !n_out || (max > 0 && !out)) return fail(LPT2_EINVAL, "null argument");
+  *n_out = 0;
+  if (p->n_rec == 0) return LPT2_OK;
+  cudaError_t e = cudaEventSynchronize(p->ev[2 * p->n_rec - 1]);
+  if (e != cudaSuccess) return fail(LPT2_ECUDA, "event sync: %s", cudaGetErrorString(e));
+  int n = 0;
+  for (int r = 0; r < p->n_rec; ++r) {
+    float ms = 0.f;
+    e = cudaEventElapsedTime(&ms, p->ev[2 * r], p->ev[2 * r + 1]);
+    if (e != cudaSuccess) return fail(LPT2_ECUDA, "event time: %s", cudaGetErrorString(e));
+    int j = 0;
+    while (j < n && strcmp(out[j].name, p->rec_name[r]) != 0) ++j;
+    if (j == n) {
+      if (n >= max) continue;
+      memset(&out[n], 0, sizeof(out[n]));
+      strncpy(out[n].name, p->rec_name[r], sizeof(out[n].name) - 1);
+      ++n;
+    }
+    out[j].launches += 1;
+    out[j].total_ms += ms;
+    out[j].bytes += p->rec_bytes[r];
+  }
+  *n_out = n;
+  return LPT2_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,240 @@
+// FP64 set-up kernels: Eisenstein-Hu constants and sigma_8 normalisation of
+// P(k), and the batched RK4 integration of the growth tables D1(k,a), D2(k,a)
+// (T1 triangle) with their ln|f_R0| tangents.
+//
+// Equations (units h/Mpc, s = ln a, flat E^2 = Om a^-3 + OL):
+//   D1_ss + (2 - 1.5 Om(a)) D1_s = 1.5 Om(a) mu(k,a) D1                    (Eq. d1)
+//   D2_ss + (2 - 1.5 Om(a)) D2_s - 1.5 Om(a) mu(k) D2
+//       = -1.5 Om(a) D1(k/sqrt2)^2 [mu(k) - B(k,a)],                     (Eq. full-d2, T1)
+//   B = (2/27) 4 pi G rho (k^2/a^2) M2(a) / (Pi(k) Pi(k/sqrt2)^2),
+//   mu = 1 + (k^2/a^2) / (3 Pi), Pi = k^2/a^2 + m^2, m^2 = M1/3    (Eq. mihusawicki, Sec. 2.4)
+// with D2 taken with the sign that gives -3/7 D1^2 in GR, the EdS growing mode at
+// a_init and D1 normalised to the GR solution at a = 1.  Tangents use
+// dm^2/dln|fR0| = -m^2 and dM2/dln|fR0| = -2 M2.
+#include <math.h>
+
+#include "passes.h"
+
+namespace lpt2 {
+
+static constexpr double kH0c = 1.0 / 2997.92458;   // H0 / c in h/Mpc
+static constexpr int kSigmaPts = 20001;            // Simpson points in ln k on [1e-5, 1e3]
+static constexpr int kPartBlocks = 64;
+
+struct EhConst { double theta2, omh, alpha, s; };
+
+__device__ EhConst eh_constants(const GrowthParams& p) {
+  const double h = p.h, wm = p.omega_m * h * h, wb = p.omega_b * h * h, fb = p.omega_b / p.omega_m;
+  const double theta = p.t_cmb / 2.7;
+  EhConst c;
+  c.theta2 = theta * theta;
+  c.s = 44.5 * log(9.83 / wm) / sqrt(1.0 + 10.0 * pow(wb, 0.75));                 // EH Eq. 26
+  c.alpha = 1.0 - 0.328 * log(431.0 * wm) * fb + 0.38 * log(22.3 * wm) * fb * fb;   // EH Eq. 31
+  c.omh = p.omega_m * h;
+  return c;
+}
+
+__device__ double eh_T64(const EhConst& c, double k, double h) {
+  const double sk = 0.43 * k * h * c.s;
+  const double gamma = c.omh * (c.alpha + (1.0 - c.alpha) / (1.0 + sk * sk * sk * sk));  // Eq. 30
+  const double q = k * c.theta2 / gamma;                                                  // Eq. 28
+  const double L0 = log(2.0 * 2.718281828459045 + 1.8 * q);                              // Eq. 29
+  const double C0 = 14.2 + 731.0 / (1.0 + 62.5 * q);
+  return L0 / (L0 + C0 * q * q);
+}
+
+__global__ void k_sigma_partial(GrowthParams p, double* part) {
+  const EhConst c = eh_constants(p);
+  const double lo = log(1e-5), hi = log(1e3), dl = (hi - lo) / (kSigmaPts - 1);
+  double acc = 0.0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < kSigmaPts; i += gridDim.x * blockDim.x) {
+    const double k = exp(lo + i * dl);
+    const double T = eh_T64(c, k, p.h);
+    const double x = 8.0 * k;
+    const double W = 3.0 * (sin(x) - x * cos(x)) / (x * x * x);
+    const double f = k * k * k * pow(k, p.n_s) * T * T * W * W / (2.0 * M_PI * M_PI);
+    const double w = (i == 0 || i == kSigmaPts - 1) ? 1.0 : ((i & 1) ? 4.0 : 2.0);
+    acc += w * f;
+  }
+  __shared__ double s[256];
+  s[threadIdx.x] = acc;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) s[threadIdx.x] += s[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[blockIdx.x] = s[0] * dl / 3.0;
+}
+
+__global__ void k_sigma_final(GrowthParams p, const double* part, DevCosmo* out) {
+  if (threadIdx.x != 0) return;
+  double s2 = 0.0;
+  for (int b = 0; b < kPartBlocks; ++b) s2 += part[b];
+  const EhConst c = eh_constants(p);
+  DevCosmo d;
+  d.sigma_sq = s2;
+  d.amp = p.sigma8 * p.sigma8 / s2;
+  d.sqrt_amp = (float)sqrt(d.amp);
+  d.ns_half = (float)(0.5 * p.n_s);
+  d.theta2 = (float)c.theta2;
+  d.omh = (float)c.omh;
+  d.alpha = (float)c.alpha;
+  d.s043h = (float)(0.43 * c.s * p.h);
+  d.lnkmin = (float)log(p.k_min);
+  d.inv_dlnk = (float)((p.nk - 1) / (log(p.k_max) - log(p.k_min)));
+  d.nk = p.nk;
+  *out = d;
+}
+
+int cosmo_partial_blocks() { return kPartBlocks; }
+
+cudaError_t launch_cosmo_setup(const GrowthParams& p, double* partials, DevCosmo* out, cudaStream_t s) {
+  k_sigma_partial<<<kPartBlocks, 256, 0, s>>>(p, partials);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_sigma_final<<<1, 32, 0, s>>>(p, partials, out);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ growth RK4
+// Background at every half step, shared by the block: 1/a^2, 1.5 Om(a),
+// 2 - 1.5 Om(a), m^2(a), (2/27) 4 pi G rho M2(a).
+struct Bg { double inv_a2, cc, damp, m2, bfac; };
+
+__device__ Bg background(const GrowthParams& p, double s, bool gr) {
+  const double a = exp(s);
+  const double a3 = 1.0 / (a * a * a);
+  const double e2 = p.omega_m * a3 + p.omega_l;
+  const double om = p.omega_m * a3 / e2;
+  Bg b;
+  b.inv_a2 = 1.0 / (a * a);
+  b.cc = 1.5 * om;
+  b.damp = 2.0 - 1.5 * om;
+  if (gr) {
+    b.m2 = 0.0;
+    b.bfac = 0.0;
+  } else {
+    const double x = p.omega_m * a3 + 4.0 * p.omega_l, x0 = p.omega_m + 4.0 * p.omega_l;
+    const double x2 = x * x, x02 = x0 * x0;
+    b.m2 = 0.5 * kH0c * kH0c * x2 * x / (p.fr0_abs * x02);
+    const double M2 = 2.25 * kH0c * kH0c * x2 * x2 * x / (p.fr0_abs * p.fr0_abs * x02 * x02);
+    b.bfac = (2.0 / 27.0) * 1.5 * p.omega_m * a3 * kH0c * kH0c * M2;
+  }
+  return b;
+}
+
+template <bool TAN>
+struct State {
+  double v[TAN ? 12 : 6];
+};
+
+// right-hand side: y = [D1, D1s, D1h, D1hs, D2, D2s (, tangents of each)]
+template <bool TAN>
+__device__ __forceinline__ void rhs(const Bg& b, double k2, bool gr, const double* y, double* dy) {
+  const double q = k2 * b.inv_a2, qh = 0.5 * q;
+  double mu_k = 1.0, mu_h = 1.0, mu_kt = 0.0, mu_ht = 0.0, B = 0.0, Bt = 0.0;
+  if (!gr) {
+    const double rpk = 1.0 / (q + b.m2), rph = 1.0 / (qh + b.m2);
+    mu_k = 1.0 + q * rpk * (1.0 / 3.0);
+    mu_h = 1.0 + qh * rph * (1.0 / 3.0);
+    B = b.bfac * q * rpk * rph * rph;
+    if (TAN) {
+      mu_kt = q * b.m2 * rpk * rpk * (1.0 / 3.0);
+      mu_ht = qh * b.m2 * rph * rph * (1.0 / 3.0);
+      Bt = B * (-2.0 + b.m2 * rpk + 2.0 * b.m2 * rph);
+    }
+  }
+  const double src = mu_k - B;
+  dy[0] = y[1];
+  dy[1] = -b.damp * y[1] + b.cc * mu_k * y[0];
+  dy[2] = y[3];
+  dy[3] = -b.damp * y[3] + b.cc * mu_h * y[2];
+  dy[4] = y[5];
+  dy[5] = -b.damp * y[5] + b.cc * mu_k * y[4] - b.cc * y[2] * y[2] * src;
+  if (TAN) {
+    dy[6] = y[7];
+    dy[7] = -b.damp * y[7] + b.cc * (mu_k * y[6] + mu_kt * y[0]);
+    dy[8] = y[9];
+    dy[9] = -b.damp * y[9] + b.cc * (mu_h * y[8] + mu_ht * y[2]);
+    dy[10] = y[11];
+    dy[11] = -b.damp * y[11] + b.cc * (mu_k * y[10] + mu_kt * y[4]) -
+             b.cc * (2.0 * y[2] * y[8] * src + y[2] * y[2] * (mu_kt - Bt));
+  }
+}
+
+template <int NY, bool TAN>
+__device__ void rk4(const Bg* tab, int n_steps, double h, double k2, bool gr, double* y) {
+  double k1[NY], k2v[NY], k3[NY], k4[NY], t[NY];
+  for (int i = 0; i < n_steps; ++i) {
+    const Bg& b0 = tab[2 * i];
+    const Bg& bm = tab[2 * i + 1];
+    const Bg& b1 = tab[2 * i + 2];
+    rhs<TAN>(b0, k2, gr, y, k1);
+#pragma unroll
+    for (int j = 0; j < NY; ++j) t[j] = y[j] + 0.5 * h * k1[j];
+    rhs<TAN>(bm, k2, gr, t, k2v);
+#pragma unroll
+    for (int j = 0; j < NY; ++j) t[j] = y[j] + 0.5 * h * k2v[j];
+    rhs<TAN>(bm, k2, gr, t, k3);
+#pragma unroll
+    for (int j = 0; j < NY; ++j) t[j] = y[j] + h * k3[j];
+    rhs<TAN>(b1, k2, gr, t, k4);
+#pragma unroll
+    for (int j = 0; j < NY; ++j) y[j] = y[j] + (h / 6.0) * (k1[j] + 2.0 * k2v[j] + 2.0 * k3[j] + k4[j]);
+  }
+}
+
+__device__ void fill_bg(Bg* tab, const GrowthParams& p, double s0, double h, int n_steps, bool gr) {
+  for (int j = threadIdx.x; j <= 2 * n_steps; j += blockDim.x) {
+    const int i = j >> 1;
+    const double s = (j & 1) ? (s0 + i * h) + 0.5 * h : s0 + i * h;
+    tab[j] = background(p, s, gr);
+  }
+}
+
+template <bool TAN>
+__global__ void k_growth(GrowthParams p, double* tab, float* tabf) {
+  extern __shared__ Bg s_bg[];
+  const bool gr = (p.fr0_abs == 0.0);
+  const double s0 = log(p.a_init);
+  // GR normalisation D1_GR(a = 1)
+  const double hg = (0.0 - s0) / p.n_steps;
+  fill_bg(s_bg, p, s0, hg, p.n_steps, true);
+  __syncthreads();
+  double g[6] = {p.a_init, p.a_init, p.a_init, p.a_init, 0.0, 0.0};
+  rk4<6, false>(s_bg, p.n_steps, hg, 1.0, true, g);
+  const double norm = g[0];
+  __syncthreads();
+  const double h = (log(p.a_out) - s0) / p.n_steps;
+  fill_bg(s_bg, p, s0, h, p.n_steps, gr);
+  __syncthreads();
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= p.nk) return;
+  const double k = p.k_min * pow(p.k_max / p.k_min, (double)t / (double)(p.nk - 1));
+  constexpr int NY = TAN ? 12 : 6;
+  double y[NY];
+#pragma unroll
+  for (int j = 0; j < NY; ++j) y[j] = 0.0;
+  y[0] = y[1] = y[2] = y[3] = p.a_init;
+  y[4] = -3.0 / 7.0 * p.a_init * p.a_init;
+  y[5] = -6.0 / 7.0 * p.a_init * p.a_init;
+  rk4<NY, TAN>(s_bg, p.n_steps, h, k * k, gr, y);
+  const int nk = p.nk;
+  tab[t] = y[0] / norm;
+  tab[nk + t] = y[4] / (norm * norm);
+  tab[2 * nk + t] = TAN ? y[6] / norm : 0.0;
+  tab[3 * nk + t] = TAN ? y[10] / (norm * norm) : 0.0;
+  tabf[t] = (float)(y[0] / norm);
+  tabf[nk + t] = (float)(y[4] / (norm * norm));
+}
+
+cudaError_t launch_growth(const GrowthParams& p, double* tab, float* tabf, cudaStream_t s) {
+  const int threads = 32;
+  const int blocks = (p.nk + threads - 1) / threads;
+  const size_t smem = (size_t)(2 * p.n_steps + 1) * sizeof(Bg);
+  cudaFuncSetAttribute(k_growth<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  k_growth<true><<<blocks, threads, smem, s>>>(p, tab, tabf);
+  return cudaGetLastError();
+}
+
+}  // namespace lpt2

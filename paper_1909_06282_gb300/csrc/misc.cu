@@ -1,0 +1,122 @@
+// Size-independent kernels: CIC deposit from positions, zero fill, P(k) shell
+// finalisation, white noise and raw Philox words.
+#include "passes.h"
+#include "philox.cuh"
+
+namespace lpt2 {
+
+// Periodic cloud-in-cell deposit of unit-mass particles (one thread per particle).
+__global__ void k_cic(CicArgs a) {
+  const int n = a.g.n;
+  const size_t n3 = (size_t)n * n * n;
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n3) return;
+  float u[3];
+  for (int c = 0; c < 3; ++c) {
+    float x = __ldg(a.pos + c * n3 + i) * a.g.inv_cell;
+    x = x - (float)n * floorf(x / (float)n);
+    u[c] = (x >= (float)n) ? x - (float)n : x;
+  }
+  const float fx = floorf(u[0]), fy = floorf(u[1]), fz = floorf(u[2]);
+  const float dx = u[0] - fx, dy = u[1] - fy, dz = u[2] - fz;
+  const int ix = (int)fx % n, iy = (int)fy % n, iz = (int)fz % n;
+  const int jx = (ix + 1) % n, jy = (iy + 1) % n, jz = (iz + 1) % n;
+  const float wx[2] = {1.f - dx, dx}, wy[2] = {1.f - dy, dy}, wz[2] = {1.f - dz, dz};
+  const int cx[2] = {ix, jx}, cy[2] = {iy, jy}, cz[2] = {iz, jz};
+  for (int ox = 0; ox < 2; ++ox)
+    for (int oy = 0; oy < 2; ++oy)
+      for (int oz = 0; oz < 2; ++oz)
+        atomicAdd(a.rho + ((size_t)cx[ox] * n + cy[oy]) * n + cz[oz], wx[ox] * wy[oy] * wz[oz]);
+}
+
+cudaError_t launch_cic(const CicArgs& a, cudaStream_t s) {
+  const size_t n3 = (size_t)a.g.n * a.g.n * a.g.n;
+  k_cic<<<(unsigned)((n3 + 255) / 256), 256, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+__global__ void k_fill0(float4* p, size_t n4) {
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += (size_t)gridDim.x * blockDim.x)
+    p[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+}
+
+cudaError_t launch_fill0(float* p, size_t n, cudaStream_t s) {
+  // n is a multiple of 4 for every buffer of this library (N >= 16)
+  k_fill0<<<152 * 8, 256, 0, s>>>(reinterpret_cast<float4*>(p), n / 4);
+  return cudaGetLastError();
+}
+
+// density contrast delta = rho N^3 / N_p - 1 with one particle per cell
+__global__ void k_contrast(const float* __restrict__ rho, float* __restrict__ out, size_t n) {
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    out[i] = rho[i] - 1.0f;
+}
+
+cudaError_t launch_contrast(const float* rho, float* out, size_t n, cudaStream_t s) {
+  k_contrast<<<152 * 8, 256, 0, s>>>(rho, out, n);
+  return cudaGetLastError();
+}
+
+// One block per shell: fixed-order strided sums then a tree (deterministic).
+__global__ void k_pk_finalize(const double* part, int n_blocks, int ns, double* pk, double* kmean,
+                              int64_t* nmodes) {
+  const int b = blockIdx.x;
+  double sp = 0.0, sk = 0.0, sc = 0.0;
+  for (int i = threadIdx.x; i < n_blocks; i += blockDim.x) {
+    const double* q = part + (size_t)i * 3 * ns;
+    sp += q[b];
+    sk += q[ns + b];
+    sc += q[2 * ns + b];
+  }
+  __shared__ double s[3][256];
+  s[0][threadIdx.x] = sp;
+  s[1][threadIdx.x] = sk;
+  s[2][threadIdx.x] = sc;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) {
+      s[0][threadIdx.x] += s[0][threadIdx.x + o];
+      s[1][threadIdx.x] += s[1][threadIdx.x + o];
+      s[2][threadIdx.x] += s[2][threadIdx.x + o];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const double c = s[2][0];
+    pk[b] = c > 0 ? s[0][0] / c : 0.0;
+    if (kmean) kmean[b] = c > 0 ? s[1][0] / c : 0.0;
+    if (nmodes) nmodes[b] = (int64_t)(c + 0.5);
+  }
+}
+
+cudaError_t launch_pk_finalize(const double* part, int n_blocks, int n_shells, double* pk, double* k_mean,
+                               int64_t* n_modes, cudaStream_t s) {
+  k_pk_finalize<<<n_shells, 256, 0, s>>>(part, n_blocks, n_shells, pk, k_mean, n_modes);
+  return cudaGetLastError();
+}
+
+__global__ void k_noise(int n, uint32_t k0, uint32_t k1, float* out) {
+  const size_t n3 = (size_t)n * n * n;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n3; i += (size_t)gridDim.x * blockDim.x)
+    out[i] = philox_gauss(i, k0, k1);
+}
+
+cudaError_t launch_noise(const Geo& g, uint32_t k0, uint32_t k1, float* out, cudaStream_t s) {
+  k_noise<<<152 * 8, 256, 0, s>>>(g.n, k0, k1, out);
+  return cudaGetLastError();
+}
+
+__global__ void k_philox_words(uint32_t k0, uint32_t k1, uint64_t first, int64_t count, uint4* out) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x) {
+    const uint64_t c = first + (uint64_t)i;
+    out[i] = philox4x32_10(make_uint4((uint32_t)c, (uint32_t)(c >> 32), 0u, 0u), k0, k1);
+  }
+}
+
+cudaError_t launch_philox_words(uint32_t k0, uint32_t k1, uint64_t first, int64_t count, uint32_t* out,
+                                cudaStream_t s) {
+  k_philox_words<<<152 * 4, 256, 0, s>>>(k0, k1, first, count, reinterpret_cast<uint4*>(out));
+  return cudaGetLastError();
+}
+
+}  // namespace lpt2

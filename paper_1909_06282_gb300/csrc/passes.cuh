@@ -1,0 +1,509 @@
+// Pass kernels of the 2LPT pipeline, templated on the grid side N.
+//
+// Spectral arrays are half spectra float2[N][N][N/2] (kx, ky, kz; kz fastest,
+// the kz = N/2 plane dropped because the method zeroes every Nyquist plane).
+// A 3-D transform is three passes: z (contiguous pencils, real <-> half
+// complex, two real rows packed as one complex pencil), y and x (strided
+// pencils, W consecutive kz handled per CTA so every load/store is a 128-byte
+// row segment).  The k-space multiplications of the method are fused into the
+// x pass, which sees full (kx, ky, kz) and runs the forward transform, the
+// multiplier and the first inverse transform back to back in registers.
+#pragma once
+#include "fft_core.cuh"
+#include "passes.h"
+#include "philox.cuh"
+
+namespace lpt2 {
+
+template <int N> struct PassCfg {
+  static constexpr int RMAX = Cfg<N>::RMAX;
+  static constexpr int TPP = N / RMAX;
+  static constexpr int H = N / 2;
+  static constexpr int ZP = (256 / TPP) < 1 ? 1 : (256 / TPP);       // pencil pairs per z CTA
+  static constexpr int ZT = ZP * TPP;                                 // z CTA threads
+  static constexpr int W = (N <= 16) ? 8 : (N >= 1024 ? 8 : 16);       // pencils per y/x CTA
+  static constexpr int XT = TPP * W;                                  // y/x CTA threads
+  static constexpr int ZSMEM = (N + ZP * SmemRow::words(N)) * 8;
+  static constexpr int XSMEM = (N + N * W) * 8;
+};
+
+// (i k)^m v for m = 0, 1, 2
+__device__ __forceinline__ float2 deriv(float2 v, float k, int m) {
+  if (m == 0) return v;
+  if (m == 1) return cscale(mul_i(v), k);
+  return cscale(v, -k * k);
+}
+
+// ===================================================================== z pass
+// Thread layout: tid = p * TPP + t (pencil pair p, lane t within the pencil).
+
+template <int N>
+__device__ __forceinline__ void z_store_pair(const float2 (&v)[Cfg<N>::RMAX], int t, const SmemRow& sm,
+                                             float2* __restrict__ outa, float2* __restrict__ outb) {
+  // v holds Z = FFT(fa + i fb) at n = t + r TPP. Split into the two real spectra.
+  constexpr int RMAX = Cfg<N>::RMAX, TPP = N / RMAX, H = N / 2;
+#pragma unroll
+  for (int r = 0; r < RMAX; ++r) sm.st(t + r * TPP, v[r]);
+  __syncthreads();
+#pragma unroll
+  for (int r = 0; r < RMAX / 2; ++r) {
+    const int k = t + r * TPP;                      // < H
+    const float2 zk = sm.ld(k);
+    const float2 zm = cconj(sm.ld((N - k) & (N - 1)));
+    outa[k] = cscale(cadd(zk, zm), 0.5f);
+    outb[k] = cscale(mul_mi(csub(zk, zm)), 0.5f);
+  }
+  (void)H;
+}
+
+// Z value at element n of the Hermitian extension of two half-spectrum rows,
+// each multiplied by (i k_z)^m first: Z = A + i B.
+template <int N>
+__device__ __forceinline__ float2 z_assemble(const float2* __restrict__ ra, const float2* __restrict__ rb,
+                                             int n, float kf, int ma, int mb) {
+  constexpr int H = N / 2;
+  if (n == H) return make_float2(0.f, 0.f);
+  const bool lo = n < H;
+  const int m = lo ? n : N - n;
+  const float kz = kf * (float)m;
+  float2 A = deriv(__ldg(ra + m), kz, ma);
+  float2 B = deriv(__ldg(rb + m), kz, mb);
+  if (!lo) { A = cconj(A); B = cconj(B); }
+  return make_float2(A.x - B.y, A.y + B.x);
+}
+
+template <int N>
+__global__ void __launch_bounds__(PassCfg<N>::ZT) k_z_r2c(ZR2CArgs a) {
+  using C = PassCfg<N>;
+  extern __shared__ float2 smem[];
+  float2* s_tw = smem;
+  load_twiddles(s_tw, a.tw, N);
+  const int p = threadIdx.x / C::TPP, t = threadIdx.x % C::TPP;
+  const SmemRow sm{smem + N + p * SmemRow::words(N)};
+  const int pair = blockIdx.x * C::ZP + p;
+  const int rowa = 2 * pair, rowb = rowa + 1;
+  float2 v[C::RMAX];
+#pragma unroll
+  for (int r = 0; r < C::RMAX; ++r) {
+    const int n = t + r * C::TPP;
+    float fa, fb;
+    if (a.src == Z_NOISE) {
+      const uint64_t ca = (uint64_t)rowa * N + n, cb = (uint64_t)rowb * N + n;
+      fa = philox_gauss(ca, a.seed_lo, a.seed_hi);
+      fb = philox_gauss(cb, a.seed_lo, a.seed_hi);
+    } else {
+      fa = __ldg(a.in + (size_t)rowa * N + n);
+      fb = __ldg(a.in + (size_t)rowb * N + n);
+      if (a.src == Z_DENSITY) { fa -= 1.0f; fb -= 1.0f; }
+    }
+    v[r] = make_float2(fa, fb);
+  }
+  __syncthreads();   // twiddles visible
+  fft<N, false>(v, t, sm, s_tw);
+  z_store_pair<N>(v, t, sm, a.out + (size_t)rowa * C::H, a.out + (size_t)rowb * C::H);
+}
+
+template <int N>
+__global__ void __launch_bounds__(PassCfg<N>::ZT) k_z_c2r(ZC2RArgs a) {
+  using C = PassCfg<N>;
+  extern __shared__ float2 smem[];
+  float2* s_tw = smem;
+  load_twiddles(s_tw, a.tw, N);
+  const int p = threadIdx.x / C::TPP, t = threadIdx.x % C::TPP;
+  const SmemRow sm{smem + N + p * SmemRow::words(N)};
+  const int pair = blockIdx.x * C::ZP + p;
+  const int rowa = 2 * pair, rowb = rowa + 1;
+  const float2* ra = a.in + (size_t)rowa * C::H;
+  const float2* rb = a.in + (size_t)rowb * C::H;
+  float2 v[C::RMAX];
+#pragma unroll
+  for (int r = 0; r < C::RMAX; ++r) v[r] = z_assemble<N>(ra, rb, t + r * C::TPP, 0.f, 0, 0);
+  __syncthreads();
+  fft<N, true>(v, t, sm, s_tw);
+#pragma unroll
+  for (int r = 0; r < C::RMAX; ++r) {
+    const int n = t + r * C::TPP;
+    a.out[(size_t)rowa * N + n] = v[r].x;
+    a.out[(size_t)rowb * N + n] = v[r].y;
+  }
+}
+
+// Six phi_ij -> S = sum_{i<j} (phi_ii phi_jj - phi_ij^2)  (Eq. second-ini) -> forward z.
+template <int N>
+__global__ void __launch_bounds__(PassCfg<N>::ZT) k_z_source(ZSourceArgs a) {
+  using C = PassCfg<N>;
+  extern __shared__ float2 smem[];
+  float2* s_tw = smem;
+  load_twiddles(s_tw, a.tw, N);
+  const int p = threadIdx.x / C::TPP, t = threadIdx.x % C::TPP;
+  const SmemRow sm{smem + N + p * SmemRow::words(N)};
+  const int pair = blockIdx.x * C::ZP + p;
+  const int rows[2] = {2 * pair, 2 * pair + 1};
+  float S[2][C::RMAX];
+  __syncthreads();
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const size_t off = (size_t)rows[h] * C::H;
+    float T[C::RMAX];
+#pragma unroll
+    for (int pr = 0; pr < 3; ++pr) {
+      float2 v[C::RMAX];
+#pragma unroll
+      for (int r = 0; r < C::RMAX; ++r)
+        v[r] = z_assemble<N>(a.in[2 * pr] + off, a.in[2 * pr + 1] + off, t + r * C::TPP, a.g.kf,
+                             a.ord[2 * pr], a.ord[2 * pr + 1]);
+      fft<N, true>(v, t, sm, s_tw);
+#pragma unroll
+      for (int r = 0; r < C::RMAX; ++r) {
+        const float e = v[r].x, f = v[r].y;
+        if (pr == 0) {          // phi_xx, phi_yy
+          S[h][r] = e * f;
+          T[r] = e + f;
+        } else if (pr == 1) {   // phi_zz, phi_xy
+          S[h][r] = fmaf(T[r], e, fmaf(-f, f, S[h][r]));
+        } else {                // phi_xz, phi_yz
+          S[h][r] = fmaf(-e, e, fmaf(-f, f, S[h][r]));
+        }
+      }
+    }
+  }
+  float2 v[C::RMAX];
+#pragma unroll
+  for (int r = 0; r < C::RMAX; ++r) v[r] = make_float2(S[0][r], S[1][r]);
+  fft<N, false>(v, t, sm, s_tw);
+  z_store_pair<N>(v, t, sm, a.out + (size_t)rows[0] * C::H, a.out + (size_t)rows[1] * C::H);
+}
+
+// Periodic CIC deposit of one unit-mass particle at grid coordinates u (cells).
+template <int N>
+__device__ __forceinline__ void cic_deposit(float* __restrict__ rho, float ux, float uy, float uz) {
+  const float fx = floorf(ux), fy = floorf(uy), fz = floorf(uz);
+  const float dx = ux - fx, dy = uy - fy, dz = uz - fz;
+  const int ix = ((int)fx) & (N - 1), iy = ((int)fy) & (N - 1), iz = ((int)fz) & (N - 1);
+  const int jx = (ix + 1) & (N - 1), jy = (iy + 1) & (N - 1), jz = (iz + 1) & (N - 1);
+  const float wx0 = 1.f - dx, wy0 = 1.f - dy, wz0 = 1.f - dz;
+  const size_t b00 = ((size_t)ix * N + iy) * N, b01 = ((size_t)ix * N + jy) * N;
+  const size_t b10 = ((size_t)jx * N + iy) * N, b11 = ((size_t)jx * N + jy) * N;
+  atomicAdd(rho + b00 + iz, wx0 * wy0 * wz0);
+  atomicAdd(rho + b00 + jz, wx0 * wy0 * dz);
+  atomicAdd(rho + b01 + iz, wx0 * dy * wz0);
+  atomicAdd(rho + b01 + jz, wx0 * dy * dz);
+  atomicAdd(rho + b10 + iz, dx * wy0 * wz0);
+  atomicAdd(rho + b10 + jz, dx * wy0 * dz);
+  atomicAdd(rho + b11 + iz, dx * dy * wz0);
+  atomicAdd(rho + b11 + jz, dx * dy * dz);
+}
+
+// wrap grid coordinate into [0, N)
+template <int N>
+__device__ __forceinline__ float wrapN(float u) {
+  u = u - (float)N * floorf(u * (1.0f / N));
+  return (u >= (float)N) ? u - (float)N : u;
+}
+
+// Psi inputs (z order 1 -> Psi_z, 0 -> Psi_y, 0 -> Psi_x), positions, CIC.
+template <int N>
+__global__ void __launch_bounds__(PassCfg<N>::ZT) k_z_final(ZFinalArgs a) {
+  using C = PassCfg<N>;
+  extern __shared__ float2 smem[];
+  float2* s_tw = smem;
+  load_twiddles(s_tw, a.tw, N);
+  const int p = threadIdx.x / C::TPP, t = threadIdx.x % C::TPP;
+  const SmemRow sm{smem + N + p * SmemRow::words(N)};
+  const int pair = blockIdx.x * C::ZP + p;
+  const int rows[2] = {2 * pair, 2 * pair + 1};
+  const size_t n3 = (size_t)N * N * N;
+  const float kf = a.g.kf;
+  float px[2][C::RMAX], py[2][C::RMAX], pz[2][C::RMAX];
+  __syncthreads();
+  const int nsets = a.split ? 2 : 1;
+  for (int set = 0; set < nsets; ++set) {
+    const float2* const* in = set == 0 ? a.a : a.b;
+    float* outp = a.split ? (set == 0 ? a.psi1 : a.psi2) : nullptr;
+    // (Psi_x, Psi_y) of each row
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const size_t off = (size_t)rows[h] * C::H;
+      float2 v[C::RMAX];
+#pragma unroll
+      for (int r = 0; r < C::RMAX; ++r)
+        v[r] = z_assemble<N>(in[2] + off, in[1] + off, t + r * C::TPP, kf, 0, 0);
+      fft<N, true>(v, t, sm, s_tw);
+#pragma unroll
+      for (int r = 0; r < C::RMAX; ++r) {
+        if (set == 0) { px[h][r] = v[r].x; py[h][r] = v[r].y; }
+        else { px[h][r] += v[r].x; py[h][r] += v[r].y; }
+        if (outp) {
+          const size_t e = (size_t)rows[h] * N + t + r * C::TPP;
+          outp[e] = v[r].x;
+          outp[n3 + e] = v[r].y;
+        }
+      }
+    }
+    // Psi_z of both rows
+    {
+      float2 v[C::RMAX];
+#pragma unroll
+      for (int r = 0; r < C::RMAX; ++r)
+        v[r] = z_assemble<N>(in[0] + (size_t)rows[0] * C::H, in[0] + (size_t)rows[1] * C::H,
+                             t + r * C::TPP, kf, 1, 1);
+      fft<N, true>(v, t, sm, s_tw);
+#pragma unroll
+      for (int r = 0; r < C::RMAX; ++r) {
+        if (set == 0) { pz[0][r] = v[r].x; pz[1][r] = v[r].y; }
+        else { pz[0][r] += v[r].x; pz[1][r] += v[r].y; }
+        if (outp) {
+          outp[2 * n3 + (size_t)rows[0] * N + t + r * C::TPP] = v[r].x;
+          outp[2 * n3 + (size_t)rows[1] * N + t + r * C::TPP] = v[r].y;
+        }
+      }
+    }
+  }
+  // positions x = q + Psi (Eq. position), wrapped; CIC deposit
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int ix = rows[h] / N, iy = rows[h] % N;
+#pragma unroll
+    for (int r = 0; r < C::RMAX; ++r) {
+      const int iz = t + r * C::TPP;
+      const float ux = wrapN<N>((float)ix + px[h][r] * a.g.inv_cell);
+      const float uy = wrapN<N>((float)iy + py[h][r] * a.g.inv_cell);
+      const float uz = wrapN<N>((float)iz + pz[h][r] * a.g.inv_cell);
+      if (a.pos) {
+        const size_t e = (size_t)rows[h] * N + iz;
+        a.pos[e] = ux * a.g.cell;
+        a.pos[n3 + e] = uy * a.g.cell;
+        a.pos[2 * n3 + e] = uz * a.g.cell;
+      }
+      if (a.rho) cic_deposit<N>(a.rho, ux, uy, uz);
+    }
+  }
+}
+
+// ===================================================================== y pass
+// CTA = (kz block of W, fixed x). Thread tid = t * W + w.
+template <int N>
+__global__ void __launch_bounds__(PassCfg<N>::XT) k_y(YArgs a) {
+  using C = PassCfg<N>;
+  extern __shared__ float2 smem[];
+  float2* s_tw = smem;
+  load_twiddles(s_tw, a.tw, N);
+  const int w = threadIdx.x % C::W, t = threadIdx.x / C::W;
+  const SmemCol<C::W> sm{smem + N + w};
+  const int kz = blockIdx.x * C::W + w;
+  const int x = blockIdx.y;
+  const size_t base = (size_t)x * N * C::H + kz;     // element (x, y, kz) = base + y * H
+  __syncthreads();
+  for (int i = 0; i < a.job.n_in; ++i) {
+    float2 in[C::RMAX];
+#pragma unroll
+    for (int r = 0; r < C::RMAX; ++r) in[r] = a.job.in[i][base + (size_t)(t + r * C::TPP) * C::H];
+    for (int o = 0; o < a.job.n_out; ++o) {
+      if (a.job.src[o] != i) continue;
+      const int m = a.job.ord[o];
+      float2 v[C::RMAX];
+#pragma unroll
+      for (int r = 0; r < C::RMAX; ++r) {
+        const int n = t + r * C::TPP;
+        const int my = mode_of(n, N);
+        v[r] = (m != 0 && n == C::H) ? make_float2(0.f, 0.f) : deriv(in[r], a.g.kf * (float)my, m);
+      }
+      if (a.inverse) fft<N, true>(v, t, sm, s_tw);
+      else fft<N, false>(v, t, sm, s_tw);
+      float2* dst = a.job.out[o];
+#pragma unroll
+      for (int r = 0; r < C::RMAX; ++r) dst[base + (size_t)(t + r * C::TPP) * C::H] = v[r];
+    }
+  }
+}
+
+// ===================================================================== x pass
+__device__ __forceinline__ float interp_table(const float* __restrict__ tab, const DevCosmo& c, float k) {
+  float x = (logf(k) - c.lnkmin) * c.inv_dlnk;
+  x = fminf(fmaxf(x, 0.f), (float)(c.nk - 1));
+  int i = (int)x;
+  i = i > c.nk - 2 ? c.nk - 2 : i;
+  const float f = x - (float)i;
+  const float d0 = __ldg(tab + i), d1 = __ldg(tab + i + 1);
+  return fmaf(f, d1 - d0, d0);
+}
+
+// sqrt(P_lin(k)) with the Eisenstein-Hu no-wiggle transfer function (their
+// Eqs. 28-30) in FP32; constants from the set-up kernel.
+__device__ __forceinline__ float sqrt_pk(const DevCosmo& c, float k) {
+  const float sk = c.s043h * k;
+  const float sk2 = sk * sk;
+  const float gamma = c.omh * (c.alpha + (1.f - c.alpha) / (1.f + sk2 * sk2));
+  const float q = k * c.theta2 / gamma;
+  const float L0 = logf(2.f * 2.718281828459045f + 1.8f * q);
+  const float C0 = 14.2f + 731.f / (1.f + 62.5f * q);
+  const float T = L0 / fmaf(C0 * q, q, L0);
+  return c.sqrt_amp * expf(c.ns_half * logf(k)) * T;
+}
+
+// CTA = (kz block of W, fixed ky). Thread tid = t * W + w; kx = t + r TPP.
+template <int N>
+__global__ void __launch_bounds__(PassCfg<N>::XT) k_x(XArgs a) {
+  using C = PassCfg<N>;
+  extern __shared__ float2 smem[];
+  float2* s_tw = smem;
+  load_twiddles(s_tw, a.tw, N);
+  __shared__ double s_pk[3 * 256];
+  const int w = threadIdx.x % C::W, t = threadIdx.x / C::W;
+  const SmemCol<C::W> sm{smem + N + w};
+  const int kz = blockIdx.x * C::W + w;
+  const int ky = blockIdx.y;
+  const size_t base = (size_t)ky * C::H + kz;      // element (kx, ky, kz) = base + kx * N * H
+  const size_t stride = (size_t)N * C::H;
+  const int my = mode_of(ky, N), mz = kz;
+  const bool ny_nyq = (ky == C::H);
+  if (a.mode == X_PK) {
+    for (int i = threadIdx.x; i < 3 * a.n_shells; i += blockDim.x) s_pk[i] = 0.0;
+  }
+  __syncthreads();
+
+  float2 v[C::RMAX];
+#pragma unroll
+  for (int r = 0; r < C::RMAX; ++r) v[r] = a.in[base + (size_t)(t + r * C::TPP) * stride];
+
+  if (a.mode == X_INV) {
+    fft<N, true>(v, t, sm, s_tw);
+#pragma unroll
+    for (int r = 0; r < C::RMAX; ++r) a.out[0][base + (size_t)(t + r * C::TPP) * stride] = v[r];
+    return;
+  }
+  fft<N, false>(v, t, sm, s_tw);
+  if (a.mode == X_FWD) {
+#pragma unroll
+    for (int r = 0; r < C::RMAX; ++r) a.out[0][base + (size_t)(t + r * C::TPP) * stride] = v[r];
+    return;
+  }
+
+  const DevCosmo cz = *a.cosmo;
+  const float kf = a.g.kf;
+  if (a.mode == X_PK) {
+    // P(k) shells: b = floor(2 ns |n| / N) for 0 < |n| < N/2, exact integer test.
+    const float pnorm = a.g.box * a.g.box * a.g.box * a.g.inv_n3 * a.g.inv_n3;
+    const int ns = a.n_shells;
+#pragma unroll
+    for (int r = 0; r < C::RMAX; ++r) {
+      const int kx = t + r * C::TPP;
+      const int mx = mode_of(kx, N);
+      const long long n2 = (long long)mx * mx + (long long)my * my + (long long)mz * mz;
+      if (n2 == 0 || 4 * n2 >= (long long)N * N) continue;
+      const long long M = 4LL * ns * ns * n2;
+      long long s = (long long)sqrtf((float)M);
+      while ((s + 1) * (s + 1) <= M) ++s;
+      while (s * s > M) --s;
+      const int b = (int)(s / N);
+      const double wgt = (mz == 0) ? 1.0 : 2.0;
+      const float p = (v[r].x * v[r].x + v[r].y * v[r].y) * pnorm;
+      atomicAdd(&s_pk[b], wgt * (double)p);
+      atomicAdd(&s_pk[ns + b], wgt * (double)(kf * sqrtf((float)n2)));
+      atomicAdd(&s_pk[2 * ns + b], wgt);
+    }
+    __syncthreads();
+    const size_t blk = (size_t)blockIdx.y * gridDim.x + blockIdx.x;
+    for (int i = threadIdx.x; i < 3 * ns; i += blockDim.x) a.pk_part[blk * 3 * ns + i] = s_pk[i];
+    return;
+  }
+
+  // k-space multipliers. g = potential to transform back along x.
+  float2 g[C::RMAX], hpot[C::RMAX];
+#pragma unroll
+  for (int r = 0; r < C::RMAX; ++r) {
+    const int kx = t + r * C::TPP;
+    const int mx = mode_of(kx, N);
+    const bool zero = ny_nyq || kx == C::H || (mx == 0 && my == 0 && mz == 0);
+    const float k2 = kf * kf * (float)(mx * mx + my * my + mz * mz);
+    const float k = sqrtf(k2);
+    const float inv = zero ? 0.f : a.g.inv_n3 / k2;
+    if (a.mode == X_DELTA) {
+      const float sc = zero ? 0.f : sqrt_pk(cz, k) * a.g.sqrt_n3_over_v;
+      const float2 d = cscale(v[r], sc);
+      if (a.delta_out) a.delta_out[base + (size_t)kx * stride] = d;
+      g[r] = cscale(d, inv);                                // phi1 = delta / k^2 (1/N^3 folded)
+      if (a.split) hpot[r] = cscale(g[r], zero ? 0.f : interp_table(a.d1f, cz, k));
+    } else {  // X_SOURCE: v = S(k)
+      const float d2 = zero ? 0.f : interp_table(a.d2f, cz, k);
+      float2 u = cscale(v[r], -d2 * inv);                   // phi2 = -S D2 / k^2
+      if (!a.split) {
+        const float d1 = zero ? 0.f : interp_table(a.d1f, cz, k);
+        const float2 dl = a.delta_in[base + (size_t)kx * stride];
+        u = cadd(u, cscale(dl, d1 * inv));                  // + phi1 D1 (total potential)
+      }
+      g[r] = u;
+    }
+  }
+  // x-inverse transforms with x-derivative orders
+  const int nout = (a.mode == X_DELTA) ? (a.split ? 5 : 3) : 2;
+  for (int o = 0; o < nout; ++o) {
+    const bool fromh = (a.mode == X_DELTA) && o >= 3;
+    const int m = (a.mode == X_DELTA) ? (o < 3 ? o : o - 3) : o;
+    float2 u[C::RMAX];
+#pragma unroll
+    for (int r = 0; r < C::RMAX; ++r) {
+      const int kx = t + r * C::TPP;
+      u[r] = deriv(fromh ? hpot[r] : g[r], kf * (float)mode_of(kx, N), m);
+    }
+    fft<N, true>(u, t, sm, s_tw);
+#pragma unroll
+    for (int r = 0; r < C::RMAX; ++r) a.out[o][base + (size_t)(t + r * C::TPP) * stride] = u[r];
+  }
+}
+
+// ================================================================ launchers
+template <int N> cudaError_t launch_z_r2c_t(const ZR2CArgs& a, cudaStream_t s) {
+  using C = PassCfg<N>;
+  cudaFuncSetAttribute(k_z_r2c<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::ZSMEM);
+  k_z_r2c<N><<<N * N / 2 / C::ZP, C::ZT, C::ZSMEM, s>>>(a);
+  return cudaGetLastError();
+}
+template <int N> cudaError_t launch_z_c2r_t(const ZC2RArgs& a, cudaStream_t s) {
+  using C = PassCfg<N>;
+  cudaFuncSetAttribute(k_z_c2r<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::ZSMEM);
+  k_z_c2r<N><<<N * N / 2 / C::ZP, C::ZT, C::ZSMEM, s>>>(a);
+  return cudaGetLastError();
+}
+template <int N> cudaError_t launch_z_source_t(const ZSourceArgs& a, cudaStream_t s) {
+  using C = PassCfg<N>;
+  cudaFuncSetAttribute(k_z_source<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::ZSMEM);
+  k_z_source<N><<<N * N / 2 / C::ZP, C::ZT, C::ZSMEM, s>>>(a);
+  return cudaGetLastError();
+}
+template <int N> cudaError_t launch_z_final_t(const ZFinalArgs& a, cudaStream_t s) {
+  using C = PassCfg<N>;
+  cudaFuncSetAttribute(k_z_final<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::ZSMEM);
+  k_z_final<N><<<N * N / 2 / C::ZP, C::ZT, C::ZSMEM, s>>>(a);
+  return cudaGetLastError();
+}
+template <int N> cudaError_t launch_y_t(const YArgs& a, cudaStream_t s) {
+  using C = PassCfg<N>;
+  cudaFuncSetAttribute(k_y<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::XSMEM);
+  k_y<N><<<dim3(C::H / C::W, N), C::XT, C::XSMEM, s>>>(a);
+  return cudaGetLastError();
+}
+template <int N> cudaError_t launch_x_t(const XArgs& a, cudaStream_t s) {
+  using C = PassCfg<N>;
+  cudaFuncSetAttribute(k_x<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::XSMEM);
+  k_x<N><<<dim3(C::H / C::W, N), C::XT, C::XSMEM, s>>>(a);
+  return cudaGetLastError();
+}
+template <int N> int x_blocks_t() { return (PassCfg<N>::H / PassCfg<N>::W) * N; }
+
+}  // namespace lpt2
+
+#define LPT2_INSTANTIATE(N)                                                                          \
+  namespace lpt2 {                                                                                   \
+  cudaError_t launch_z_r2c_##N(const ZR2CArgs& a, cudaStream_t s) { return launch_z_r2c_t<N>(a, s); } \
+  cudaError_t launch_z_c2r_##N(const ZC2RArgs& a, cudaStream_t s) { return launch_z_c2r_t<N>(a, s); } \
+  cudaError_t launch_z_source_##N(const ZSourceArgs& a, cudaStream_t s) {                            \
+    return launch_z_source_t<N>(a, s);                                                               \
+  }                                                                                                  \
+  cudaError_t launch_z_final_##N(const ZFinalArgs& a, cudaStream_t s) {                              \
+    return launch_z_final_t<N>(a, s);                                                                \
+  }                                                                                                  \
+  cudaError_t launch_y_##N(const YArgs& a, cudaStream_t s) { return launch_y_t<N>(a, s); }           \
+  cudaError_t launch_x_##N(const XArgs& a, cudaStream_t s) { return launch_x_t<N>(a, s); }           \
+  int x_blocks_##N() { return x_blocks_t<N>(); }                                                     \
+  }

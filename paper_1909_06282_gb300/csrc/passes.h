@@ -1,0 +1,147 @@
+// Host/device shared declarations of the pass kernels' argument blocks and the
+// per-grid-size launcher entry points (instantiated in inst_<N>.cu).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace lpt2 {
+
+// Written by the cosmology set-up kernels (FP64 in, FP32 constants out).
+struct DevCosmo {
+  double amp;        // P(k) amplitude A (sigma_8 normalisation), (Mpc/h)^(3+n_s)
+  double sigma_sq;   // sigma^2(8 Mpc/h) of the unnormalised shape
+  float sqrt_amp;    // sqrt(A)
+  float ns_half;     // n_s / 2
+  float theta2;      // (T_CMB / 2.7)^2
+  float omh;         // Omega_m h
+  float alpha;       // alpha_Gamma (EH Eq. 31)
+  float s043h;       // 0.43 s h  (EH Eq. 30 written for k in h/Mpc)
+  float lnkmin;      // ln k_min of the growth table
+  float inv_dlnk;    // 1 / (ln k spacing)
+  int nk;
+};
+
+struct Geo {
+  int n;
+  float kf;             // 2 pi / L
+  float box;            // L
+  float cell;           // L / N
+  float inv_cell;       // N / L
+  float inv_n3;         // 1 / N^3 (inverse-transform normalisation)
+  float sqrt_n3_over_v; // sqrt(N^3 / L^3)
+};
+
+enum ZSrc { Z_NOISE = 0, Z_REAL = 1, Z_DENSITY = 2 };
+
+struct ZR2CArgs {      // forward z pass: real rows -> half-spectrum rows
+  Geo g;
+  const float2* tw;
+  int src;             // ZSrc
+  const float* in;     // Z_REAL / Z_DENSITY
+  uint32_t seed_lo, seed_hi;
+  float2* out;         // [N*N][N/2]
+};
+
+struct ZC2RArgs {      // inverse z pass of one field: half-spectrum rows -> real rows
+  Geo g;
+  const float2* tw;
+  const float2* in;
+  float* out;
+};
+
+struct ZSourceArgs {   // inverse z pass of the six phi_ij, source term, forward z pass of S
+  Geo g;
+  const float2* tw;
+  const float2* in[6]; // phi_xx, phi_yy, phi_zz, phi_xy, phi_xz, phi_yz (after the y pass)
+  int ord[6];          // z derivative order still to apply to each
+  float2* out;         // S, z-transformed
+};
+
+struct ZFinalArgs {    // inverse z pass of the displacement potentials, positions, CIC
+  Geo g;
+  const float2* tw;
+  int split;           // 1: separate Psi1 / Psi2 inputs; 0: total only
+  const float2* a[3];  // total (or Psi1) inputs: (order z1 -> Psi_z, z0 -> Psi_y, z0 -> Psi_x)
+  const float2* b[3];  // Psi2 inputs when split
+  float* psi1;         // float[3][N^3] or null
+  float* psi2;
+  float* pos;
+  float* rho;          // CIC mass per cell (accumulated), or null
+};
+
+struct YJob {          // y pass: each output = transform of (i k_y)^ord * input
+  int n_in, n_out;
+  const float2* in[6];
+  float2* out[9];
+  int src[9];
+  int ord[9];
+};
+struct YArgs {
+  Geo g;
+  const float2* tw;
+  int inverse;
+  YJob job;
+};
+
+enum XMode { X_DELTA = 0, X_SOURCE = 1, X_PK = 2, X_FWD = 3, X_INV = 4 };
+struct XArgs {
+  Geo g;
+  const float2* tw;
+  int mode;
+  int split;
+  const float2* in;       // tile source (after the y pass / in k space for X_INV)
+  float2* delta_out;      // X_DELTA: delta(k)
+  const float2* delta_in; // X_SOURCE total mode: delta(k)
+  float2* out[5];         // x-inverse outputs
+  const DevCosmo* cosmo;
+  const float* d1f;       // float growth tables [nk]
+  const float* d2f;
+  double* pk_part;        // X_PK: per-block partials [blocks][3][n_shells]
+  int n_shells;
+};
+
+struct CicArgs {
+  Geo g;
+  const float* pos;      // [3][N^3]
+  float* rho;
+};
+
+// Per grid size launchers (return cudaError_t of the launch).
+#define LPT2_DECLARE_LAUNCHERS(N)                                                  \
+  cudaError_t launch_z_r2c_##N(const ZR2CArgs&, cudaStream_t);                   \
+  cudaError_t launch_z_c2r_##N(const ZC2RArgs&, cudaStream_t);                   \
+  cudaError_t launch_z_source_##N(const ZSourceArgs&, cudaStream_t);             \
+  cudaError_t launch_z_final_##N(const ZFinalArgs&, cudaStream_t);               \
+  cudaError_t launch_y_##N(const YArgs&, cudaStream_t);                          \
+  cudaError_t launch_x_##N(const XArgs&, cudaStream_t);                          \
+  int x_blocks_##N();
+
+LPT2_DECLARE_LAUNCHERS(16)
+LPT2_DECLARE_LAUNCHERS(32)
+LPT2_DECLARE_LAUNCHERS(64)
+LPT2_DECLARE_LAUNCHERS(128)
+LPT2_DECLARE_LAUNCHERS(256)
+LPT2_DECLARE_LAUNCHERS(512)
+LPT2_DECLARE_LAUNCHERS(1024)
+
+// Size-independent kernels (misc.cu / growth.cu).
+cudaError_t launch_cic(const CicArgs&, cudaStream_t);
+cudaError_t launch_fill0(float* p, size_t n, cudaStream_t);
+cudaError_t launch_contrast(const float* rho, float* out, size_t n, cudaStream_t);
+cudaError_t launch_pk_finalize(const double* part, int n_blocks, int n_shells, double* pk,
+                               double* k_mean, int64_t* n_modes, cudaStream_t);
+cudaError_t launch_noise(const Geo& g, uint32_t seed_lo, uint32_t seed_hi, float* out, cudaStream_t);
+cudaError_t launch_philox_words(uint32_t seed_lo, uint32_t seed_hi, uint64_t first, int64_t count,
+                                uint32_t* out, cudaStream_t);
+
+struct GrowthParams {
+  double omega_m, omega_l, omega_b, h, n_s, sigma8, t_cmb, fr0_abs, a_init, a_out;
+  double k_min, k_max;
+  int nk, n_steps;
+};
+int cosmo_partial_blocks();
+cudaError_t launch_cosmo_setup(const GrowthParams&, double* partials, DevCosmo* out, cudaStream_t);
+cudaError_t launch_growth(const GrowthParams&, double* tab /*[4][nk]*/, float* tabf /*[2][nk]*/,
+                          cudaStream_t);
+
+}  // namespace lpt2

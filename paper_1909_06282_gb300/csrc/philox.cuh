@@ -1,0 +1,35 @@
+// Philox4x32-10 (Salmon, Moraes, Dror & Shaw, SC'11) and Box-Muller white noise.
+// Each round multiplies counter words 0 and 2 by the two published multipliers,
+// xors the high halves with words 1 / 3 and the key; the key is bumped by the
+// two Weyl increments between rounds.  Key = (seed lo, seed hi); counter =
+// (cell lo, cell hi, 0, 0) with cell = (ix N + iy) N + iz.
+#pragma once
+#include <stdint.h>
+
+namespace lpt2 {
+
+__host__ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    if (r) { k0 += 0x9E3779B9u; k1 += 0xBB67AE85u; }
+#ifdef __CUDA_ARCH__
+    const uint32_t hi0 = __umulhi(0xD2511F53u, c.x), hi1 = __umulhi(0xCD9E8D57u, c.z);
+#else
+    const uint32_t hi0 = (uint32_t)(((uint64_t)0xD2511F53u * c.x) >> 32);
+    const uint32_t hi1 = (uint32_t)(((uint64_t)0xCD9E8D57u * c.z) >> 32);
+#endif
+    const uint32_t lo0 = 0xD2511F53u * c.x, lo1 = 0xCD9E8D57u * c.z;
+    c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+  }
+  return c;
+}
+
+// u = ((x >> 8) + 1) 2^-24 (exact in FP32, in (0, 1]); g = sqrt(-2 ln u0) cos(2 pi u1).
+__device__ __forceinline__ float philox_gauss(uint64_t cell, uint32_t k0, uint32_t k1) {
+  const uint4 x = philox4x32_10(make_uint4((uint32_t)cell, (uint32_t)(cell >> 32), 0u, 0u), k0, k1);
+  const float u0 = (float)((x.x >> 8) + 1u) * 5.9604644775390625e-8f;
+  const float u1 = (float)((x.y >> 8) + 1u) * 5.9604644775390625e-8f;
+  return sqrtf(-2.0f * logf(u0)) * cospif(2.0f * u1);
+}
+
+}  // namespace lpt2
