@@ -202,13 +202,14 @@ def lpt2_displace(plan: Plan, noise=None, psi1=True, psi2=True, pos=True, dk=Fal
     n = plan.n
     f3 = lambda: torch.empty((3, n, n, n), dtype=torch.float32, device="cuda")
     out = {}
-    if psi1:
+    want = lambda v: torch.is_tensor(v) or bool(v)
+    if want(psi1):
         out["psi1"] = psi1 if torch.is_tensor(psi1) else f3()
-    if psi2:
+    if want(psi2):
         out["psi2"] = psi2 if torch.is_tensor(psi2) else f3()
-    if pos:
+    if want(pos):
         out["pos"] = pos if torch.is_tensor(pos) else f3()
-    if dk:
+    if want(dk):
         out["dk"] = dk if torch.is_tensor(dk) else torch.empty((n, n, n // 2), dtype=torch.complex64,
                                                                device="cuda")
     if noise is not None and (noise.dtype != torch.float32 or noise.numel() != n ** 3):
@@ -226,7 +227,7 @@ def lpt2_cic_pk(plan: Plan, pos=None, density=False, n_shells=32):
     res = dict(pk=torch.empty(n_shells, dtype=torch.float64, device="cuda"),
                k_mean=torch.empty(n_shells, dtype=torch.float64, device="cuda"),
                n_modes=torch.empty(n_shells, dtype=torch.int64, device="cuda"))
-    if density:
+    if torch.is_tensor(density) or density:
         res["density"] = density if torch.is_tensor(density) else torch.empty(
             (n, n, n), dtype=torch.float32, device="cuda")
     if pos is not None and (pos.dtype != torch.float32 or pos.numel() != 3 * n ** 3):

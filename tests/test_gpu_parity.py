@@ -1,7 +1,8 @@
 """GPU parity: every entry point of the C ABI against the FP64 oracle on the same
 seeded inputs.  Tolerances (FP32 CUDA path vs FP64 oracle):
   Philox words             bit-exact
-  white noise (FP32)       <= 4 ulp, >= 99 % of cells exact
+  white noise (FP32)       <= 4 ulp, >= 99 % of cells within 1 ulp (FP32 log / cospi / sqrt
+                           against the FP64 transform rounded once)
   growth tables (FP64)     1e-10 relative (same RK4 step count on both sides)
   Psi1, Psi2, Psi          relative L2 <= 2e-5 and max |delta Psi| <= 1e-4 cell
   P(k)                     <= 1e-4 relative per non-empty shell
@@ -76,9 +77,10 @@ def test_white_noise_against_oracle(n, seed):
     want64 = philox.gaussian_noise(n, seed, as_float64=True)
     want = want64.astype(np.float32)
     ulp = np.abs(got.view(np.int32).astype(np.int64) - want.view(np.int32).astype(np.int64))
-    exact = np.mean(ulp == 0)
+    within1 = np.mean(ulp <= 1)
     assert ulp.max() <= 4, ulp.max()
-    assert exact >= 0.99, exact
+    assert within1 >= 0.99, within1
+    print(f"noise: {np.mean(ulp == 0):.4f} exact, {within1:.6f} within 1 ulp, max {ulp.max()} ulp")
 
 
 @pytest.mark.parametrize("n", [16, 32, 64, 128])
