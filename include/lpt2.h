@@ -166,6 +166,30 @@ typedef struct {
 int lpt2_timing(lpt2_plan_t plan, int enable);
 int lpt2_timing_report(lpt2_plan_t plan, lpt2_kernel_stat* out, int max, int* n_out);
 
+/* lpt2_cic_pk_noalloc: the same CIC density contrast and shell P(k) as
+ * lpt2_cic_pk, for callers that are not allowed to allocate GPU memory - for
+ * example an application whose device memory is handed to its own pool at
+ * start-up, or code running where cudaMalloc is forbidden - and so can create
+ * neither a plan nor a workspace.  The paper has no counterpart: this is a
+ * deployment variant of one step of the path.
+ *   n        grid side, 16, 32, 64 or 128 (larger sizes return LPT2_EUNSUPPORTED)
+ *   box      side of the periodic box, Mpc/h (> 0)
+ *   pos      device float[3][n^3] particle positions (one particle per cell)
+ *   density  device float[n^3] density contrast output, or NULL
+ *   pk, k_mean, n_modes, n_shells: as for lpt2_cic_pk
+ *   cuda_stream  cudaStream_t to launch on
+ * It calls no cudaMalloc/cudaFree and no allocating library routine: all
+ * scratch (about 20 MB: density, spectrum, shell partial sums, twiddles) is one
+ * static __device__ array inside the library, which every GPU that loads the
+ * library keeps until the process exits.  The first call on a device looks up
+ * that array's device address (cudaGetSymbolAddress); make that first call
+ * before any stream capture.  All calls share the one array: calls whose
+ * kernels overlap on the GPU (different streams, or different host threads on
+ * the same device) race and corrupt each other's results - serialise them.
+ * Errors as for lpt2_cic_pk; the message is reported by lpt2_last_error(). */
+int lpt2_cic_pk_noalloc(int n, double box, const float* pos, float* density, double* pk,
+                        double* k_mean, int64_t* n_modes, int n_shells, void* cuda_stream);
+
 /* Message of the last failing call on this thread ("" if none). */
 const char* lpt2_last_error(void);
 

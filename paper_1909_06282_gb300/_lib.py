@@ -84,6 +84,7 @@ def load_library():
         "lpt2_last_error": (C.c_char_p, []),
         "lpt2_launch_count": (i64, [vp]),
         "lpt2_timing": (i, [vp, i]),
+        "lpt2_cic_pk_noalloc": (i, [i, d, vp, vp, vp, vp, vp, i, vp]),
         "lpt2_timing_report": (i, [vp, C.POINTER(_KernelStat), i, C.POINTER(C.c_int)]),
     }
     for name, (res, args) in sig.items():

@@ -206,6 +206,8 @@ int run_growth(lpt2_plan_t p) {
 
 }  // namespace
 
+void lpt2::set_last_error(const char* msg) { g_err = msg; }
+
 extern "C" {
 
 const char* lpt2_last_error(void) { return g_err.c_str(); }

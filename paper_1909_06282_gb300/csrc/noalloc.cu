@@ -1,0 +1,179 @@
+// lpt2_cic_pk_noalloc: CIC density and shell P(k) for callers that cannot
+// allocate device memory.  All scratch lives in one file-scope __device__ array
+// of fixed size (grids up to kNoAllocMaxN per side); the caller passes only
+// inputs and outputs.  The array is part of the library image, so every GPU
+// that loads the library holds it until the process exits.
+#include <math.h>
+
+#include <mutex>
+#include <string>
+
+#include "../../include/lpt2.h"
+#include "passes.h"
+
+using namespace lpt2;
+
+namespace {
+
+constexpr int kNoAllocMaxN = 128;
+constexpr int kMaxShells = 256;
+constexpr size_t kGrid = (size_t)kNoAllocMaxN * kNoAllocMaxN * kNoAllocMaxN;
+// x-pass blocks for the largest grid: (N/2 / 16 kz per block) * N
+constexpr size_t kMaxXBlocks = (kNoAllocMaxN / 2 / 16) * kNoAllocMaxN;
+constexpr size_t kRhoOff = 0;                                        // float[N^3]
+constexpr size_t kSpecOff = kRhoOff + kGrid * sizeof(float);         // float2[N^3/2]
+constexpr size_t kPartOff = kSpecOff + kGrid * sizeof(float);        // double[blocks][3][256]
+constexpr size_t kTwOff = kPartOff + kMaxXBlocks * 3 * kMaxShells * sizeof(double);
+constexpr size_t kCosmoOff = kTwOff + kNoAllocMaxN * sizeof(float2);
+constexpr size_t kScratchBytes = kCosmoOff + 256;
+static_assert(kSpecOff % 256 == 0 && kPartOff % 256 == 0 && kTwOff % 256 == 0 && kCosmoOff % 256 == 0,
+              "scratch sub-arrays must stay 256-byte aligned");
+
+}  // namespace
+
+// The scratch array (about 20 MB).  Host code must not take its address
+// directly: the symbol's device address is fetched with cudaGetSymbolAddress.
+static __device__ __align__(256) unsigned char g_lpt2_noalloc_scratch[kScratchBytes];
+
+namespace {
+
+std::mutex g_mu;
+void* g_dev_ptr[128] = {};   // device address of the scratch, per device ordinal
+
+int fail(int code, const std::string& msg) {
+  set_last_error(msg);   // reported by lpt2_last_error()
+  return code;
+}
+
+// Twiddles exp(-2 pi i m / n) in FP64, rounded once to FP32.
+__global__ void k_noalloc_twiddles(float2* tw, int n) {
+  for (int m = threadIdx.x; m < n; m += blockDim.x) {
+    double s, c;
+    sincospi(2.0 * (double)m / (double)n, &s, &c);
+    tw[m] = make_float2((float)c, (float)(-s));
+  }
+}
+
+cudaError_t z_r2c_n(int n, const ZR2CArgs& a, cudaStream_t s) {
+  switch (n) {
+    case 16: return launch_z_r2c_16(a, s);
+    case 32: return launch_z_r2c_32(a, s);
+    case 64: return launch_z_r2c_64(a, s);
+    default: return launch_z_r2c_128(a, s);
+  }
+}
+cudaError_t y_n(int n, const YArgs& a, cudaStream_t s) {
+  switch (n) {
+    case 16: return launch_y_16(a, s);
+    case 32: return launch_y_32(a, s);
+    case 64: return launch_y_64(a, s);
+    default: return launch_y_128(a, s);
+  }
+}
+cudaError_t x_n(int n, const XArgs& a, cudaStream_t s) {
+  switch (n) {
+    case 16: return launch_x_16(a, s);
+    case 32: return launch_x_32(a, s);
+    case 64: return launch_x_64(a, s);
+    default: return launch_x_128(a, s);
+  }
+}
+int xblocks_n(int n) {
+  switch (n) {
+    case 16: return x_blocks_16();
+    case 32: return x_blocks_32();
+    case 64: return x_blocks_64();
+    default: return x_blocks_128();
+  }
+}
+
+}  // namespace
+
+extern "C" int lpt2_cic_pk_noalloc(int n, double box, const float* pos, float* density, double* pk,
+                                   double* k_mean, int64_t* n_modes, int n_shells, void* cuda_stream) {
+  if (!(n == 16 || n == 32 || n == 64 || n == 128))
+    return fail(LPT2_EUNSUPPORTED, "lpt2_cic_pk_noalloc: grid side must be 16, 32, 64 or 128 "
+                                   "(static scratch holds at most 128^3)");
+  if (!(box > 0) || !isfinite(box)) return fail(LPT2_EINVAL, "lpt2_cic_pk_noalloc: box must be > 0");
+  if (!pos || !pk) return fail(LPT2_EINVAL, "lpt2_cic_pk_noalloc: pos and pk must not be null");
+  if (n_shells < 1 || n_shells > kMaxShells)
+    return fail(LPT2_EINVAL, "lpt2_cic_pk_noalloc: n_shells must be in [1, 256]");
+  if ((uintptr_t)pos % 4 || (density && (uintptr_t)density % 4))
+    return fail(LPT2_EINVAL, "lpt2_cic_pk_noalloc: misaligned pointer");
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+
+  // One-time set-up per device: the scratch symbol's device address.
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return fail(LPT2_ECUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
+  if (dev < 0 || dev >= 128) return fail(LPT2_EUNSUPPORTED, "device ordinal >= 128");
+  char* base = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (!g_dev_ptr[dev]) {
+      void* p = nullptr;
+      e = cudaGetSymbolAddress(&p, g_lpt2_noalloc_scratch);
+      if (e != cudaSuccess)
+        return fail(LPT2_ECUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+      g_dev_ptr[dev] = p;
+    }
+    base = (char*)g_dev_ptr[dev];
+  }
+  float* rho = reinterpret_cast<float*>(base + kRhoOff);
+  float2* spec = reinterpret_cast<float2*>(base + kSpecOff);
+  double* part = reinterpret_cast<double*>(base + kPartOff);
+  float2* tw = reinterpret_cast<float2*>(base + kTwOff);
+  const DevCosmo* cosmo = reinterpret_cast<const DevCosmo*>(base + kCosmoOff);
+
+  Geo g;
+  const double nd = n;
+  g.n = n;
+  g.kf = (float)(2.0 * M_PI / box);
+  g.box = (float)box;
+  g.cell = (float)(box / nd);
+  g.inv_cell = (float)(nd / box);
+  g.inv_n3 = (float)(1.0 / (nd * nd * nd));
+  g.sqrt_n3_over_v = (float)sqrt(nd * nd * nd / (box * box * box));
+  const size_t n3 = (size_t)n * n * n;
+
+#define NA_CHECK(expr)                                                                     \
+  do {                                                                                     \
+    cudaError_t e_ = (expr);                                                               \
+    if (e_ != cudaSuccess) return fail(LPT2_ECUDA, std::string(#expr ": ") + cudaGetErrorString(e_)); \
+  } while (0)
+
+  k_noalloc_twiddles<<<1, 128, 0, s>>>(tw, n);
+  NA_CHECK(cudaGetLastError());
+  NA_CHECK(launch_fill0(rho, n3, s));               // the deposit accumulates: start from zero
+  CicArgs c{g, pos, rho};
+  NA_CHECK(launch_cic(c, s));
+  ZR2CArgs z{};
+  z.g = g;
+  z.tw = tw;
+  z.src = Z_DENSITY;
+  z.in = rho;
+  z.out = spec;
+  NA_CHECK(z_r2c_n(n, z, s));
+  YArgs y{};
+  y.g = g;
+  y.tw = tw;
+  y.inverse = 0;
+  y.job.n_in = 1;
+  y.job.n_out = 1;
+  y.job.in[0] = spec;
+  y.job.out[0] = spec;
+  NA_CHECK(y_n(n, y, s));
+  XArgs x{};
+  x.g = g;
+  x.tw = tw;
+  x.mode = X_PK;
+  x.in = spec;
+  x.cosmo = cosmo;
+  x.pk_part = part;
+  x.n_shells = n_shells;
+  NA_CHECK(x_n(n, x, s));
+  NA_CHECK(launch_pk_finalize(part, xblocks_n(n), n_shells, pk, k_mean, n_modes, s));
+  if (density) NA_CHECK(launch_contrast(rho, density, n3, s));
+#undef NA_CHECK
+  return LPT2_OK;
+}

@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <string>
+
 namespace lpt2 {
 
 // Written by the cosmology set-up kernels (FP64 in, FP32 constants out).
@@ -133,6 +135,10 @@ cudaError_t launch_pk_finalize(const double* part, int n_blocks, int n_shells, d
 cudaError_t launch_noise(const Geo& g, uint32_t seed_lo, uint32_t seed_hi, float* out, cudaStream_t);
 cudaError_t launch_philox_words(uint32_t seed_lo, uint32_t seed_hi, uint64_t first, int64_t count,
                                 uint32_t* out, cudaStream_t);
+
+// Sets the thread-local message returned by lpt2_last_error().
+void set_last_error(const char* msg);
+inline void set_last_error(const std::string& msg) { set_last_error(msg.c_str()); }
 
 struct GrowthParams {
   double omega_m, omega_l, omega_b, h, n_s, sigma8, t_cmb, fr0_abs, a_init, a_out;
