@@ -55,7 +55,8 @@ _lib = None
 
 
 def library_path() -> str:
-    return os.path.join(HERE, "lib", "liblpt2.so")
+    """lib/liblpt2.so next to this file, or the file named by LPT2_LIBRARY."""
+    return os.environ.get("LPT2_LIBRARY") or os.path.join(HERE, "lib", "liblpt2.so")
 
 
 def load_library():

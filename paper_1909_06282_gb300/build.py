@@ -30,9 +30,14 @@ def nvcc() -> str:
     raise RuntimeError("nvcc not found")
 
 
-def _compile(src: str, verbose_ptxas: bool) -> str:
-    obj = os.path.join(BUILDDIR, os.path.splitext(src)[0] + ".o")
-    cmd = [nvcc(), *ARCH, *FLAGS, "-c", os.path.join(CSRC, src), "-o", obj]
+def _extra_flags():
+    """Extra nvcc flags from LPT2_NVCC_EXTRA (e.g. tuning macros -DLPT2_W512=8)."""
+    return os.environ.get("LPT2_NVCC_EXTRA", "").split()
+
+
+def _compile(src: str, verbose_ptxas: bool, builddir: str) -> str:
+    obj = os.path.join(builddir, os.path.splitext(src)[0] + ".o")
+    cmd = [nvcc(), *ARCH, *FLAGS, *_extra_flags(), "-c", os.path.join(CSRC, src), "-o", obj]
     if verbose_ptxas:
         cmd += ["-Xptxas", "-v"]
     r = subprocess.run(cmd, capture_output=True, text=True)
@@ -54,15 +59,18 @@ def _stale(lib: str) -> bool:
     return False
 
 
-def build(force: bool = False, verbose_ptxas: bool = False, jobs: int | None = None) -> str:
-    lib = os.path.join(LIBDIR, LIBNAME)
+def build(force: bool = False, verbose_ptxas: bool = False, jobs: int | None = None,
+          out: str | None = None) -> str:
+    """Builds liblpt2.so (default: lib/liblpt2.so, or the path in LPT2_LIBRARY / `out`)."""
+    lib = out or os.environ.get("LPT2_LIBRARY") or os.path.join(LIBDIR, LIBNAME)
     if not force and not _stale(lib):
         return lib
-    os.makedirs(LIBDIR, exist_ok=True)
-    os.makedirs(BUILDDIR, exist_ok=True)
+    os.makedirs(os.path.dirname(lib), exist_ok=True)
+    builddir = os.path.join(BUILDDIR, os.path.basename(os.path.dirname(lib)) or "default")
+    os.makedirs(builddir, exist_ok=True)
     jobs = jobs or min(len(SOURCES), os.cpu_count() or 4)
     with cf.ThreadPoolExecutor(jobs) as ex:
-        objs = list(ex.map(lambda s: _compile(s, verbose_ptxas), SOURCES))
+        objs = list(ex.map(lambda s: _compile(s, verbose_ptxas, builddir), SOURCES))
     tmp = lib + ".tmp"
     cmd = [nvcc(), *ARCH, "-shared", "-cudart", "shared", "-o", tmp, *objs,
            "-Xlinker", "-rpath,/usr/local/cuda/lib64"]

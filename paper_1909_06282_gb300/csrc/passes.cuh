@@ -15,13 +15,20 @@
 
 namespace lpt2 {
 
+#ifndef LPT2_Z_MINB
+#define LPT2_Z_MINB 2   // minimum resident z-pass CTAs per SM (register cap)
+#endif
+#ifndef LPT2_W512
+#define LPT2_W512 16    // pencils per y/x CTA at N = 512
+#endif
+
 template <int N> struct PassCfg {
   static constexpr int RMAX = Cfg<N>::RMAX;
   static constexpr int TPP = N / RMAX;
   static constexpr int H = N / 2;
   static constexpr int ZP = (256 / TPP) < 1 ? 1 : (256 / TPP);       // pencil pairs per z CTA
   static constexpr int ZT = ZP * TPP;                                 // z CTA threads
-  static constexpr int W = (N <= 16) ? 8 : (N >= 1024 ? 8 : 16);       // pencils per y/x CTA
+  static constexpr int W = (N <= 16) ? 8 : (N >= 1024 ? 8 : (N == 512 ? LPT2_W512 : 16));       // pencils per y/x CTA
   static constexpr int XT = TPP * W;                                  // y/x CTA threads
   static constexpr int ZSMEM = (N + ZP * SmemRow::words(N)) * 8;
   static constexpr int XSMEM = (N + N * W) * 8;
@@ -73,7 +80,7 @@ __device__ __forceinline__ float2 z_assemble(const float2* __restrict__ ra, cons
 }
 
 template <int N>
-__global__ void __launch_bounds__(PassCfg<N>::ZT) k_z_r2c(ZR2CArgs a) {
+__global__ void __launch_bounds__(PassCfg<N>::ZT, LPT2_Z_MINB) k_z_r2c(ZR2CArgs a) {
   using C = PassCfg<N>;
   extern __shared__ float2 smem[];
   float2* s_tw = smem;
@@ -104,7 +111,7 @@ __global__ void __launch_bounds__(PassCfg<N>::ZT) k_z_r2c(ZR2CArgs a) {
 }
 
 template <int N>
-__global__ void __launch_bounds__(PassCfg<N>::ZT) k_z_c2r(ZC2RArgs a) {
+__global__ void __launch_bounds__(PassCfg<N>::ZT, LPT2_Z_MINB) k_z_c2r(ZC2RArgs a) {
   using C = PassCfg<N>;
   extern __shared__ float2 smem[];
   float2* s_tw = smem;
@@ -130,7 +137,7 @@ __global__ void __launch_bounds__(PassCfg<N>::ZT) k_z_c2r(ZC2RArgs a) {
 
 // Six phi_ij -> S = sum_{i<j} (phi_ii phi_jj - phi_ij^2)  (Eq. second-ini) -> forward z.
 template <int N>
-__global__ void __launch_bounds__(PassCfg<N>::ZT) k_z_source(ZSourceArgs a) {
+__global__ void __launch_bounds__(PassCfg<N>::ZT, LPT2_Z_MINB) k_z_source(ZSourceArgs a) {
   using C = PassCfg<N>;
   extern __shared__ float2 smem[];
   float2* s_tw = smem;
@@ -174,6 +181,24 @@ __global__ void __launch_bounds__(PassCfg<N>::ZT) k_z_source(ZSourceArgs a) {
   z_store_pair<N>(v, t, sm, a.out + (size_t)rows[0] * C::H, a.out + (size_t)rows[1] * C::H);
 }
 
+// Adds w0 to rho[b + iz] and w1 to rho[b + jz], jz = (iz + 1) mod N.  When the
+// pair sits inside one aligned group of four floats it is a single 16-byte
+// vector atomic (sm_90+), otherwise two scalar atomics.
+template <int N>
+__device__ __forceinline__ void add_zpair(float* __restrict__ rho, size_t b, int iz, int jz, float w0, float w1) {
+  const int q = iz & 3;
+  if (q != 3) {
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (q == 0) { v.x = w0; v.y = w1; }
+    else if (q == 1) { v.y = w0; v.z = w1; }
+    else { v.z = w0; v.w = w1; }
+    atomicAdd(reinterpret_cast<float4*>(rho + b + (iz - q)), v);
+  } else {
+    atomicAdd(rho + b + iz, w0);
+    atomicAdd(rho + b + jz, w1);
+  }
+}
+
 // Periodic CIC deposit of one unit-mass particle at grid coordinates u (cells).
 template <int N>
 __device__ __forceinline__ void cic_deposit(float* __restrict__ rho, float ux, float uy, float uz) {
@@ -184,14 +209,11 @@ __device__ __forceinline__ void cic_deposit(float* __restrict__ rho, float ux, f
   const float wx0 = 1.f - dx, wy0 = 1.f - dy, wz0 = 1.f - dz;
   const size_t b00 = ((size_t)ix * N + iy) * N, b01 = ((size_t)ix * N + jy) * N;
   const size_t b10 = ((size_t)jx * N + iy) * N, b11 = ((size_t)jx * N + jy) * N;
-  atomicAdd(rho + b00 + iz, wx0 * wy0 * wz0);
-  atomicAdd(rho + b00 + jz, wx0 * wy0 * dz);
-  atomicAdd(rho + b01 + iz, wx0 * dy * wz0);
-  atomicAdd(rho + b01 + jz, wx0 * dy * dz);
-  atomicAdd(rho + b10 + iz, dx * wy0 * wz0);
-  atomicAdd(rho + b10 + jz, dx * wy0 * dz);
-  atomicAdd(rho + b11 + iz, dx * dy * wz0);
-  atomicAdd(rho + b11 + jz, dx * dy * dz);
+  float w;
+  w = wx0 * wy0; add_zpair<N>(rho, b00, iz, jz, w * wz0, w * dz);
+  w = wx0 * dy;  add_zpair<N>(rho, b01, iz, jz, w * wz0, w * dz);
+  w = dx * wy0;  add_zpair<N>(rho, b10, iz, jz, w * wz0, w * dz);
+  w = dx * dy;   add_zpair<N>(rho, b11, iz, jz, w * wz0, w * dz);
 }
 
 // wrap grid coordinate into [0, N)
@@ -202,8 +224,11 @@ __device__ __forceinline__ float wrapN(float u) {
 }
 
 // Psi inputs (z order 1 -> Psi_z, 0 -> Psi_y, 0 -> Psi_x), positions, CIC.
+// The z components of both rows are one packed transform; then each row's
+// (x, y) pair is transformed and that row's particles are finished at once, so
+// only one row's x/y values are live at a time.
 template <int N>
-__global__ void __launch_bounds__(PassCfg<N>::ZT) k_z_final(ZFinalArgs a) {
+__global__ void __launch_bounds__(PassCfg<N>::ZT, LPT2_Z_MINB) k_z_final(ZFinalArgs a) {
   using C = PassCfg<N>;
   extern __shared__ float2 smem[];
   float2* s_tw = smem;
@@ -214,16 +239,35 @@ __global__ void __launch_bounds__(PassCfg<N>::ZT) k_z_final(ZFinalArgs a) {
   const int rows[2] = {2 * pair, 2 * pair + 1};
   const size_t n3 = (size_t)N * N * N;
   const float kf = a.g.kf;
-  float px[2][C::RMAX], py[2][C::RMAX], pz[2][C::RMAX];
-  __syncthreads();
   const int nsets = a.split ? 2 : 1;
+  float pz[2][C::RMAX];
+  __syncthreads();
   for (int set = 0; set < nsets; ++set) {
     const float2* const* in = set == 0 ? a.a : a.b;
     float* outp = a.split ? (set == 0 ? a.psi1 : a.psi2) : nullptr;
-    // (Psi_x, Psi_y) of each row
+    float2 v[C::RMAX];
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const size_t off = (size_t)rows[h] * C::H;
+    for (int r = 0; r < C::RMAX; ++r)
+      v[r] = z_assemble<N>(in[0] + (size_t)rows[0] * C::H, in[0] + (size_t)rows[1] * C::H,
+                           t + r * C::TPP, kf, 1, 1);
+    fft<N, true>(v, t, sm, s_tw);
+#pragma unroll
+    for (int r = 0; r < C::RMAX; ++r) {
+      if (set == 0) { pz[0][r] = v[r].x; pz[1][r] = v[r].y; }
+      else { pz[0][r] += v[r].x; pz[1][r] += v[r].y; }
+      if (outp) {
+        outp[2 * n3 + (size_t)rows[0] * N + t + r * C::TPP] = v[r].x;
+        outp[2 * n3 + (size_t)rows[1] * N + t + r * C::TPP] = v[r].y;
+      }
+    }
+  }
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const size_t off = (size_t)rows[h] * C::H;
+    float px[C::RMAX], py[C::RMAX];
+    for (int set = 0; set < nsets; ++set) {
+      const float2* const* in = set == 0 ? a.a : a.b;
+      float* outp = a.split ? (set == 0 ? a.psi1 : a.psi2) : nullptr;
       float2 v[C::RMAX];
 #pragma unroll
       for (int r = 0; r < C::RMAX; ++r)
@@ -231,8 +275,8 @@ __global__ void __launch_bounds__(PassCfg<N>::ZT) k_z_final(ZFinalArgs a) {
       fft<N, true>(v, t, sm, s_tw);
 #pragma unroll
       for (int r = 0; r < C::RMAX; ++r) {
-        if (set == 0) { px[h][r] = v[r].x; py[h][r] = v[r].y; }
-        else { px[h][r] += v[r].x; py[h][r] += v[r].y; }
+        if (set == 0) { px[r] = v[r].x; py[r] = v[r].y; }
+        else { px[r] += v[r].x; py[r] += v[r].y; }
         if (outp) {
           const size_t e = (size_t)rows[h] * N + t + r * C::TPP;
           outp[e] = v[r].x;
@@ -240,34 +284,13 @@ __global__ void __launch_bounds__(PassCfg<N>::ZT) k_z_final(ZFinalArgs a) {
         }
       }
     }
-    // Psi_z of both rows
-    {
-      float2 v[C::RMAX];
-#pragma unroll
-      for (int r = 0; r < C::RMAX; ++r)
-        v[r] = z_assemble<N>(in[0] + (size_t)rows[0] * C::H, in[0] + (size_t)rows[1] * C::H,
-                             t + r * C::TPP, kf, 1, 1);
-      fft<N, true>(v, t, sm, s_tw);
-#pragma unroll
-      for (int r = 0; r < C::RMAX; ++r) {
-        if (set == 0) { pz[0][r] = v[r].x; pz[1][r] = v[r].y; }
-        else { pz[0][r] += v[r].x; pz[1][r] += v[r].y; }
-        if (outp) {
-          outp[2 * n3 + (size_t)rows[0] * N + t + r * C::TPP] = v[r].x;
-          outp[2 * n3 + (size_t)rows[1] * N + t + r * C::TPP] = v[r].y;
-        }
-      }
-    }
-  }
-  // positions x = q + Psi (Eq. position), wrapped; CIC deposit
-#pragma unroll
-  for (int h = 0; h < 2; ++h) {
+    // positions x = q + Psi (Eq. position), wrapped; CIC deposit
     const int ix = rows[h] / N, iy = rows[h] % N;
 #pragma unroll
     for (int r = 0; r < C::RMAX; ++r) {
       const int iz = t + r * C::TPP;
-      const float ux = wrapN<N>((float)ix + px[h][r] * a.g.inv_cell);
-      const float uy = wrapN<N>((float)iy + py[h][r] * a.g.inv_cell);
+      const float ux = wrapN<N>((float)ix + px[r] * a.g.inv_cell);
+      const float uy = wrapN<N>((float)iy + py[r] * a.g.inv_cell);
       const float uz = wrapN<N>((float)iz + pz[h][r] * a.g.inv_cell);
       if (a.pos) {
         const size_t e = (size_t)rows[h] * N + iz;
@@ -348,7 +371,6 @@ __global__ void __launch_bounds__(PassCfg<N>::XT) k_x(XArgs a) {
   extern __shared__ float2 smem[];
   float2* s_tw = smem;
   load_twiddles(s_tw, a.tw, N);
-  __shared__ double s_pk[3 * 256];
   const int w = threadIdx.x % C::W, t = threadIdx.x / C::W;
   const SmemCol<C::W> sm{smem + N + w};
   const int kz = blockIdx.x * C::W + w;
@@ -358,7 +380,8 @@ __global__ void __launch_bounds__(PassCfg<N>::XT) k_x(XArgs a) {
   const int my = mode_of(ky, N), mz = kz;
   const bool ny_nyq = (ky == C::H);
   if (a.mode == X_PK) {
-    for (int i = threadIdx.x; i < 3 * a.n_shells; i += blockDim.x) s_pk[i] = 0.0;
+    double* s_pkw = reinterpret_cast<double*>(smem + N + N * C::W);
+    for (int i = threadIdx.x; i < (C::XT / 32) * 3 * a.n_shells; i += blockDim.x) s_pkw[i] = 0.0;
   }
   __syncthreads();
 
@@ -379,35 +402,66 @@ __global__ void __launch_bounds__(PassCfg<N>::XT) k_x(XArgs a) {
     return;
   }
 
-  const DevCosmo cz = *a.cosmo;
   const float kf = a.g.kf;
   if (a.mode == X_PK) {
-    // P(k) shells: b = floor(2 ns |n| / N) for 0 < |n| < N/2, exact integer test.
+    // P(k) shells: b = floor(2 ns |n| / N) for 0 < |n| < N/2 (exact integer test).
+    // Lanes of a warp see neighbouring modes, so they fall in few shells: for each
+    // distinct shell in the warp, an FP64 butterfly sums the lanes of that shell
+    // and one lane adds the sums to the block's shared accumulators.
     const float pnorm = a.g.box * a.g.box * a.g.box * a.g.inv_n3 * a.g.inv_n3;
     const int ns = a.n_shells;
+    const int lane = threadIdx.x & 31;
+    double* s_mine = reinterpret_cast<double*>(smem + N + N * C::W) + (threadIdx.x >> 5) * 3 * ns;
 #pragma unroll
     for (int r = 0; r < C::RMAX; ++r) {
       const int kx = t + r * C::TPP;
       const int mx = mode_of(kx, N);
       const long long n2 = (long long)mx * mx + (long long)my * my + (long long)mz * mz;
-      if (n2 == 0 || 4 * n2 >= (long long)N * N) continue;
-      const long long M = 4LL * ns * ns * n2;
-      long long s = (long long)sqrtf((float)M);
-      while ((s + 1) * (s + 1) <= M) ++s;
-      while (s * s > M) --s;
-      const int b = (int)(s / N);
-      const double wgt = (mz == 0) ? 1.0 : 2.0;
-      const float p = (v[r].x * v[r].x + v[r].y * v[r].y) * pnorm;
-      atomicAdd(&s_pk[b], wgt * (double)p);
-      atomicAdd(&s_pk[ns + b], wgt * (double)(kf * sqrtf((float)n2)));
-      atomicAdd(&s_pk[2 * ns + b], wgt);
+      int b = -1;
+      if (n2 != 0 && 4 * n2 < (long long)N * N) {
+        const long long M = 4LL * ns * ns * n2;
+        long long s = (long long)sqrtf((float)M);
+        while ((s + 1) * (s + 1) <= M) ++s;
+        while (s * s > M) --s;
+        b = (int)(s / N);
+      }
+      const int wgt = (b < 0) ? 0 : ((mz == 0) ? 1 : 2);
+      const float pv = (v[r].x * v[r].x + v[r].y * v[r].y) * pnorm * (float)wgt;
+      const float kv = kf * sqrtf((float)n2) * (float)wgt;
+      unsigned todo = __ballot_sync(0xffffffffu, b >= 0);
+      while (todo) {
+        const int leader = __ffs(todo) - 1;
+        const int key = __shfl_sync(0xffffffffu, b, leader);
+        const bool mine = (b == key);
+        // at most 32 terms per warp sum in FP32; the running shell sums are FP64
+        float sp = mine ? pv : 0.f, sk = mine ? kv : 0.f;
+        int sc = mine ? wgt : 0;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+          sp += __shfl_xor_sync(0xffffffffu, sp, off);
+          sk += __shfl_xor_sync(0xffffffffu, sk, off);
+          sc += __shfl_xor_sync(0xffffffffu, sc, off);
+        }
+        if (lane == leader) {   // this warp's own accumulators: no atomics
+          s_mine[key] += (double)sp;
+          s_mine[ns + key] += (double)sk;
+          s_mine[2 * ns + key] += (double)sc;
+        }
+        todo &= ~__ballot_sync(0xffffffffu, mine);
+      }
     }
     __syncthreads();
     const size_t blk = (size_t)blockIdx.y * gridDim.x + blockIdx.x;
-    for (int i = threadIdx.x; i < 3 * ns; i += blockDim.x) a.pk_part[blk * 3 * ns + i] = s_pk[i];
+    const double* s_all = reinterpret_cast<const double*>(smem + N + N * C::W);
+    for (int i = threadIdx.x; i < 3 * ns; i += blockDim.x) {
+      double acc = 0.0;
+      for (int wi = 0; wi < C::XT / 32; ++wi) acc += s_all[wi * 3 * ns + i];   // fixed order
+      a.pk_part[blk * 3 * ns + i] = acc;
+    }
     return;
   }
 
+  const DevCosmo cz = *a.cosmo;
   // k-space multipliers. g = potential to transform back along x.
   float2 g[C::RMAX], hpot[C::RMAX];
 #pragma unroll
@@ -485,8 +539,9 @@ template <int N> cudaError_t launch_y_t(const YArgs& a, cudaStream_t s) {
 }
 template <int N> cudaError_t launch_x_t(const XArgs& a, cudaStream_t s) {
   using C = PassCfg<N>;
-  cudaFuncSetAttribute(k_x<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::XSMEM);
-  k_x<N><<<dim3(C::H / C::W, N), C::XT, C::XSMEM, s>>>(a);
+  const int smem = C::XSMEM + (a.mode == X_PK ? (C::XT / 32) * 3 * a.n_shells * 8 : 0);
+  cudaFuncSetAttribute(k_x<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  k_x<N><<<dim3(C::H / C::W, N), C::XT, smem, s>>>(a);
   return cudaGetLastError();
 }
 template <int N> int x_blocks_t() { return (PassCfg<N>::H / PassCfg<N>::W) * N; }
