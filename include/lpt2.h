@@ -92,7 +92,8 @@ int lpt2_plan(lpt2_plan_t* out, const lpt2_instance* inst, int n_inst, int n_k,
 
 int lpt2_plan_destroy(lpt2_plan_t plan);
 
-/* Bytes of caller-owned device scratch the plan needs (about 14 N^3 floats). */
+/* Bytes of caller-owned device scratch the plan needs (21 N^3 floats plus
+ * small per-block partial sums). */
 int lpt2_workspace_size(lpt2_plan_t plan, size_t* bytes);
 
 /* Attach scratch: dev_ptr must be 256-byte aligned and >= lpt2_workspace_size
@@ -141,6 +142,28 @@ int lpt2_displace(lpt2_plan_t plan, const float* noise, float* psi1, float* psi2
  * 1 <= n_shells <= 256.  Needs the workspace. */
 int lpt2_cic_pk(lpt2_plan_t plan, const float* pos, float* density, double* pk,
                 double* k_mean, int64_t* n_modes, int n_shells);
+
+/* lpt2_set_fr0: change |f_R0| of the plan and recompute its growth tables
+ * (the FP64 RK4 kernel) on the plan's stream.  fr0_abs >= 0 (0 = GR). */
+int lpt2_set_fr0(lpt2_plan_t plan, double fr0_abs);
+
+/* lpt2_displace_vjp: hand-written adjoint (vector-Jacobian product) of the map
+ * (white noise, ln|f_R0|) -> (CIC density contrast, shell P(k)) of
+ * lpt2_displace + lpt2_cic_pk, and of the particle positions (the paper has
+ * no gradients: this is the transpose
+ * of the steps of Sec. 2.1 Eq. second-ini and Sec. 2.4 taken in reverse order).
+ * The forward map is recomputed inside (only delta(k) is kept; the six phi_ij
+ * are recomputed from it for the source-term transpose).
+ *   noise      float[N^3] white noise, or NULL for the plan's Philox noise
+ *   g_pos      float[3][N^3] dL/d(positions), or NULL (zero)
+ *   g_density  float[N^3] dL/d(density contrast), or NULL (zero)
+ *   g_pk       double[n_shells] dL/dP_b, or NULL (zero); shells as lpt2_cic_pk
+ *   g_noise    float[N^3] output dL/dnoise, or NULL
+ *   g_log_fr0  double[1] output dL/dln|f_R0| (FP64 reduction), or NULL
+ * All pointers are device pointers.  Needs the workspace. */
+int lpt2_displace_vjp(lpt2_plan_t plan, const float* noise, const float* g_pos,
+                      const float* g_density, const double* g_pk, int n_shells, float* g_noise,
+                      double* g_log_fr0);
 
 /* lpt2_fft_r2c: forward 3-D transform of a real field (unnormalised,
  * exp(-i k.x)) into the half spectrum; in and out may not alias.

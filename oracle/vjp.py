@@ -14,7 +14,7 @@ dL = sum_k Re[d(field_hat)(k) conj(h(k))].
   1. g_rho = g_density + N^3 IDFT[ w_b delta_rho_hat ],  w_b = 2 V g_pk[b] / (N^6 c_b)
      (dP_b / d delta_rho(x) = 2V/(N^6 c_b) Re sum_{k in b} conj(delta_hat) e^{-ikx})
   2. CIC transpose: dL/dx_p = sum over the 8 cells of g_rho(cell) dW/dx_p
-  3. x = q + Psi  ->  g_Psi_c = dL/dx_c
+  3. x = q + Psi  ->  g_Psi_c = dL/dx_c (plus any cotangent given for the positions)
   4. g_u(k) = sum_c conj(i k_c) DFT[g_Psi_c],  u = (D1 delta - D2 S_hat)/(k^2 N^3)
   5. h_Psi = D1 g_u /(k^2 N^3),  h_S = -D2 g_u /(k^2 N^3)
   6. dL/dtheta = sum_k Re[(dD1 delta - dD2 S_hat) conj(g_u)] /(k^2 N^3)
@@ -77,8 +77,9 @@ def _cic_transpose(n, box, pos, g_rho):
     return out * (n / box)
 
 
-def vjp(n, box, st, tables, g_density, g_pk, n_shells=32):
-    """Returns (g_noise (N,N,N), g_theta) for cotangents of (density, P(k))."""
+def vjp(n, box, st, tables, g_density, g_pk, n_shells=32, g_pos=None):
+    """Returns (g_noise (N,N,N), g_theta) for cotangents of (density, P(k)) and,
+    optionally, of the positions (3, N^3)."""
     kv, k2, zero = lpt2.kvectors(n, box)
     kmag = np.sqrt(k2)
     safe = np.where(zero, 1.0, k2)
@@ -93,7 +94,10 @@ def vjp(n, box, st, tables, g_density, g_pk, n_shells=32):
     dhat = offt.fftn(st["density"])
     g_rho = np.asarray(g_density, dtype=np.float64) + n3 * offt.ifftn(wk * dhat).real
     # 2-3. CIC transpose -> g_Psi
-    g_psi = _cic_transpose(n, box, st["pos"], g_rho).reshape(3, n, n, n)
+    g_psi = _cic_transpose(n, box, st["pos"], g_rho)
+    if g_pos is not None:
+        g_psi = g_psi + np.asarray(g_pos, dtype=np.float64).reshape(3, -1)
+    g_psi = g_psi.reshape(3, n, n, n)
     # 4. g_u
     G = [offt.fftn(g_psi[c]) for c in range(3)]
     g_u = sum(-1j * kv[c] * G[c] for c in range(3))

@@ -86,6 +86,8 @@ def load_library():
         "lpt2_launch_count": (i64, [vp]),
         "lpt2_timing": (i, [vp, i]),
         "lpt2_cic_pk_noalloc": (i, [i, d, vp, vp, vp, vp, vp, i, vp]),
+        "lpt2_set_fr0": (i, [vp, d]),
+        "lpt2_displace_vjp": (i, [vp, vp, vp, vp, vp, i, vp, vp]),
         "lpt2_timing_report": (i, [vp, C.POINTER(_KernelStat), i, C.POINTER(C.c_int)]),
     }
     for name, (res, args) in sig.items():
@@ -266,3 +268,49 @@ def lpt2_timing_report(plan: Plan):
     _check(load_library().lpt2_timing_report(plan.handle, arr, 64, C.byref(n)))
     return {arr[i].name.decode(): dict(launches=int(arr[i].launches), total_ms=float(arr[i].total_ms),
                                        bytes=float(arr[i].bytes)) for i in range(n.value)}
+
+
+def lpt2_set_fr0(plan: Plan, fr0_abs: float):
+    """Changes |f_R0| of the plan and recomputes its growth tables on the plan's stream."""
+    _check(load_library().lpt2_set_fr0(plan.handle, float(fr0_abs)))
+
+
+def lpt2_displace_vjp(plan: Plan, g_density=None, g_pk=None, noise=None, n_shells=32, g_pos=None):
+    """Adjoint of (noise, ln|fR0|) -> (positions, CIC density contrast, P(k)). Returns
+    (g_noise, g_log_fr0) as a float32 (N, N, N) tensor and a float64 0-d tensor."""
+    n = plan.n
+    g_noise = torch.empty((n, n, n), dtype=torch.float32, device="cuda")
+    g_t = torch.empty((), dtype=torch.float64, device="cuda")
+    for tns, dt, cnt in ((g_density, torch.float32, n ** 3), (g_pk, torch.float64, n_shells),
+                         (noise, torch.float32, n ** 3), (g_pos, torch.float32, 3 * n ** 3)):
+        if tns is not None and (tns.dtype != dt or tns.numel() != cnt):
+            raise ValueError("bad cotangent / noise tensor")
+    _check(load_library().lpt2_displace_vjp(plan.handle, _ptr(noise), _ptr(g_pos), _ptr(g_density), _ptr(g_pk),
+                                            int(n_shells), _ptr(g_noise), _ptr(g_t)))
+    return g_noise, g_t
+
+
+class Displace(torch.autograd.Function):
+    """(noise, log|fR0|) -> (CIC density contrast, shell P(k)) with the hand-written
+    adjoint of the library as backward.  The plan's |fR0| follows log_fr0."""
+
+    @staticmethod
+    def forward(ctx, noise, log_fr0, plan, n_shells):
+        fr0 = float(torch.exp(log_fr0.detach().double()).item())
+        if getattr(plan, "_fr0", plan.inst.cosmo.fr0_abs) != fr0:
+            lpt2_set_fr0(plan, fr0)
+        plan._fr0 = fr0
+        nz = noise.detach().contiguous()
+        lpt2_displace(plan, noise=nz, psi1=False, psi2=False, pos=False)
+        r = lpt2_cic_pk(plan, pos=None, density=True, n_shells=n_shells)
+        ctx.save_for_backward(nz)
+        ctx.plan, ctx.n_shells = plan, n_shells
+        return r["density"], r["pk"]
+
+    @staticmethod
+    def backward(ctx, g_density, g_pk):
+        (nz,) = ctx.saved_tensors
+        gd = None if g_density is None else g_density.contiguous().float()
+        gp = None if g_pk is None else g_pk.contiguous().double()
+        g_noise, g_t = lpt2_displace_vjp(ctx.plan, g_density=gd, g_pk=gp, noise=nz, n_shells=ctx.n_shells)
+        return g_noise, g_t.to(torch.float64), None, None

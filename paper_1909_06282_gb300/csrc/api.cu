@@ -32,7 +32,8 @@ bool supported_n(int n) {
 }
 
 // Workspace slots, each N^3 floats (= a half spectrum of N^3/2 complex).
-enum Slot { S_A = 0, S_DELTA = 1, S_X0 = 2, S_Y0 = 7, S_RHO = 16, N_SLOTS = 17 };
+// 0-16 serve the forward map; 17-20 hold what the adjoint keeps of it.
+enum Slot { S_A = 0, S_DELTA = 1, S_X0 = 2, S_Y0 = 7, S_RHO = 16, S_SHAT = 17, S_POS = 18, N_SLOTS = 21 };
 constexpr int kMaxShells = 256;
 constexpr int kMaxRec = 4096;
 
@@ -52,7 +53,7 @@ struct lpt2_plan_s {
   DevCosmo* cosmo_dev;
   double* partials;
   double* tab;    // [4][nk]
-  float* tabf;    // [2][nk]
+  float* tabf;    // [4][nk]: D1, D2, dD1/dln|fR0|, dD2/dln|fR0| in FP32
   char* ws;
   size_t ws_bytes;
   int64_t launches;
@@ -82,12 +83,17 @@ int x_blocks(int n) {
   }
 }
 
-size_t ws_need(const lpt2_plan_s* p) {
-  return N_SLOTS * slot_bytes(p) + (size_t)x_blocks(p->n) * 3 * kMaxShells * sizeof(double);
-}
+// Tail of the workspace after the slots: P(k) block partials [x_blocks][3][256],
+// internal pk / k_mean / n_modes [256] each, shell weights [256], dL/dln|fR0|
+// block partials [x_blocks].
+size_t tail_pk_part(const lpt2_plan_s* p) { return N_SLOTS * slot_bytes(p); }
+size_t tail_pk(const lpt2_plan_s* p) { return tail_pk_part(p) + (size_t)x_blocks(p->n) * 3 * kMaxShells * 8; }
+size_t tail_shw(const lpt2_plan_s* p) { return tail_pk(p) + 3 * kMaxShells * 8; }
+size_t tail_theta(const lpt2_plan_s* p) { return tail_shw(p) + kMaxShells * 4; }
+size_t ws_need(const lpt2_plan_s* p) { return tail_theta(p) + (size_t)x_blocks(p->n) * 8; }
 
 float2* slot(const lpt2_plan_s* p, int i) { return reinterpret_cast<float2*>(p->ws + i * slot_bytes(p)); }
-double* pk_part(const lpt2_plan_s* p) { return reinterpret_cast<double*>(p->ws + N_SLOTS * slot_bytes(p)); }
+double* pk_part(const lpt2_plan_s* p) { return reinterpret_cast<double*>(p->ws + tail_pk_part(p)); }
 
 Geo make_geo(const lpt2_plan_s* p) {
   Geo g;
@@ -138,6 +144,8 @@ cudaError_t z_source(int n, const ZSourceArgs& a, cudaStream_t s) { DISPATCH(lau
 cudaError_t z_final(int n, const ZFinalArgs& a, cudaStream_t s) { DISPATCH(launch_z_final, n, a, s) }
 cudaError_t y_pass(int n, const YArgs& a, cudaStream_t s) { DISPATCH(launch_y, n, a, s) }
 cudaError_t x_pass(int n, const XArgs& a, cudaStream_t s) { DISPATCH(launch_x, n, a, s) }
+cudaError_t z_adj_final(int n, const ZAdjFinalArgs& a, cudaStream_t s) { DISPATCH(launch_z_adj_final, n, a, s) }
+cudaError_t z_adj_source(int n, const ZAdjSourceArgs& a, cudaStream_t s) { DISPATCH(launch_z_adj_source, n, a, s) }
 
 void timing_begin(lpt2_plan_s* p) {
   if (!p->timing_on || p->n_rec >= kMaxRec) return;
@@ -198,6 +206,9 @@ int forward_zy(lpt2_plan_t p, int src, const float* in, float2* out) {
   return LPT2_OK;
 }
 
+int displace_impl(lpt2_plan_t p, const float* noise, float* psi1, float* psi2, float* pos, void* dk,
+                  float2* s_keep);
+
 int run_growth(lpt2_plan_t p) {
   const GrowthParams gp = growth_params(p);
   LAUNCH(p, "growth", 0.0, launch_growth(gp, p->tab, p->tabf, p->stream));
@@ -254,7 +265,7 @@ int lpt2_plan(lpt2_plan_t* out, const lpt2_instance* inst, int n_inst, int n_k, 
   if (e == cudaSuccess) e = cudaMalloc(&p->cosmo_dev, sizeof(DevCosmo));
   if (e == cudaSuccess) e = cudaMalloc(&p->partials, cosmo_partial_blocks() * sizeof(double));
   if (e == cudaSuccess) e = cudaMalloc(&p->tab, 4 * n_k * sizeof(double));
-  if (e == cudaSuccess) e = cudaMalloc(&p->tabf, 2 * n_k * sizeof(float));
+  if (e == cudaSuccess) e = cudaMalloc(&p->tabf, 4 * n_k * sizeof(float));
   if (e != cudaSuccess) {
     lpt2_plan_destroy(p);
     return fail(LPT2_ENOMEM, "plan allocation failed: %s", cudaGetErrorString(e));
@@ -350,6 +361,17 @@ int lpt2_displace(lpt2_plan_t p, const float* noise, float* psi1, float* psi2, f
   int rc = check_plan_ws(p);
   if (rc) return rc;
   if (dk && !aligned(dk, 16)) return fail(LPT2_EINVAL, "dk must be 16-byte aligned");
+  return displace_impl(p, noise, psi1, psi2, pos, dk, nullptr);
+}
+
+}  // extern "C"
+
+namespace {
+
+// The forward map; s_keep (k space, may be null) receives S(k) for the adjoint.
+int displace_impl(lpt2_plan_t p, const float* noise, float* psi1, float* psi2, float* pos, void* dk,
+                  float2* s_keep) {
+  int rc = 0;
   const int n = p->n;
   const Geo g = make_geo(p);
   const bool split = psi1 || psi2;
@@ -375,6 +397,8 @@ int lpt2_displace(lpt2_plan_t p, const float* noise, float* psi1, float* psi2, f
   x.cosmo = p->cosmo_dev;
   x.d1f = p->tabf;
   x.d2f = p->tabf + p->nk;
+  x.t1f = p->tabf + 2 * p->nk;
+  x.t2f = p->tabf + 3 * p->nk;
   LAUNCH(p, "x_delta", (split ? 28.0 : 20.0) * V3(p), x_pass(n, x, p->stream));
 
   // 2. y inverse with y derivatives: the six phi_ij (+ Psi1)
@@ -420,6 +444,7 @@ int lpt2_displace(lpt2_plan_t p, const float* noise, float* psi1, float* psi2, f
   XArgs xs = x;
   xs.mode = X_SOURCE;
   xs.in = A;
+  xs.s_out = s_keep;
   xs.delta_out = nullptr;
   xs.delta_in = D;
   xs.out[0] = X[0];
@@ -466,6 +491,10 @@ int lpt2_displace(lpt2_plan_t p, const float* noise, float* psi1, float* psi2, f
   }
   return LPT2_OK;
 }
+
+}  // namespace
+
+extern "C" {
 
 int lpt2_cic_pk(lpt2_plan_t p, const float* pos, float* density, double* pk, double* k_mean,
                 int64_t* n_modes, int n_shells) {
@@ -537,8 +566,193 @@ int lpt2_fft_c2r(lpt2_plan_t p, const void* in, float* out) {
   y.job.in[0] = A;
   y.job.out[0] = A;
   LAUNCH(p, "y_inv", 8.0 * V3(p), y_pass(p->n, y, p->stream));
-  ZC2RArgs z{g, p->tw, A, out};
+  ZC2RArgs z{g, p->tw, A, out, nullptr};
   LAUNCH(p, "z_c2r", 8.0 * V3(p), z_c2r(p->n, z, p->stream));
+  return LPT2_OK;
+}
+
+int lpt2_set_fr0(lpt2_plan_t p, double fr0_abs) {
+  if (!p) return fail(LPT2_EINVAL, "null plan");
+  if (!(fr0_abs >= 0) || !isfinite(fr0_abs)) return fail(LPT2_EINVAL, "fr0_abs must be >= 0");
+  p->cosmo.fr0_abs = fr0_abs;
+  return run_growth(p);
+}
+
+int lpt2_displace_vjp(lpt2_plan_t p, const float* noise, const float* g_pos, const float* g_density,
+                      const double* g_pk, int n_shells, float* g_noise, double* g_log_fr0) {
+  int rc = check_plan_ws(p);
+  if (rc) return rc;
+  if (n_shells < 1 || n_shells > kMaxShells) return fail(LPT2_EINVAL, "n_shells must be in [1, 256]");
+  const int n = p->n;
+  const Geo g = make_geo(p);
+  float2* S[N_SLOTS];
+  for (int i = 0; i < N_SLOTS; ++i) S[i] = slot(p, i);
+  float* pos = reinterpret_cast<float*>(S[S_POS]);            // 3 consecutive slots
+  float* rho = reinterpret_cast<float*>(S[S_RHO]);
+  double* pk = reinterpret_cast<double*>(p->ws + tail_pk(p));
+  double* kmean = pk + kMaxShells;
+  int64_t* nmodes = reinterpret_cast<int64_t*>(pk + 2 * kMaxShells);
+  float* shw = reinterpret_cast<float*>(p->ws + tail_shw(p));
+  double* thp = reinterpret_cast<double*>(p->ws + tail_theta(p));
+  const double V3d = (double)n * n * n;
+
+  // forward, keeping delta(k) (slot 1), S(k), positions and the CIC density
+  rc = displace_impl(p, noise, nullptr, nullptr, pos, nullptr, S[S_SHAT]);
+  if (rc) return rc;
+  // P(k) of the density: shell counts and the delta_rho spectrum after z, y
+  rc = forward_zy(p, Z_DENSITY, rho, S[S_A]);
+  if (rc) return rc;
+  XArgs xp{};
+  xp.g = g;
+  xp.tw = p->tw;
+  xp.mode = X_PK;
+  xp.in = S[S_A];
+  xp.cosmo = p->cosmo_dev;
+  xp.pk_part = pk_part(p);
+  xp.n_shells = n_shells;
+  LAUNCH(p, "x_pk", 4.0 * V3(p), x_pass(n, xp, p->stream));
+  LAUNCH(p, "pk_finalize", 0.0, launch_pk_finalize(pk_part(p), x_blocks(n), n_shells, pk, kmean, nmodes, p->stream));
+
+  // 1. density cotangent: g_density + IDFT[w_b delta_rho(k)]
+  const double v_over_n6 = p->box * p->box * p->box / (V3d * V3d);
+  LAUNCH(p, "pk_adj_w", 0.0, launch_pk_adj_weights(g_pk, nmodes, n_shells, v_over_n6, shw, p->stream));
+  XArgs xa = xp;
+  xa.mode = X_PKADJ;
+  xa.shell_w = shw;
+  xa.out[0] = S[S_A];
+  LAUNCH(p, "x_pkadj", 8.0 * V3(p), x_pass(n, xa, p->stream));
+  YArgs yi{};
+  yi.g = g;
+  yi.tw = p->tw;
+  yi.inverse = 1;
+  yi.job.n_in = 1;
+  yi.job.n_out = 1;
+  yi.job.in[0] = S[S_A];
+  yi.job.out[0] = S[S_A];
+  LAUNCH(p, "y_inv", 8.0 * V3(p), y_pass(n, yi, p->stream));
+  float* grho = reinterpret_cast<float*>(S[2]);
+  ZC2RArgs zc{g, p->tw, S[S_A], grho, g_density};
+  LAUNCH(p, "z_c2r_grho", (g_density ? 12.0 : 8.0) * V3(p), z_c2r(n, zc, p->stream));
+
+  // 2-3. CIC transpose and forward z of g_Psi: slots 7 (z, order 1), 8 (y), 9 (x)
+  ZAdjFinalArgs zf{g, p->tw, grho, pos, g_pos, S[7], S[8], S[9]};
+  LAUNCH(p, "z_adj_final", 28.0 * V3(p), z_adj_final(n, zf, p->stream));
+  // 4. y transpose: x-order 0 group = Psi_z (y0) + Psi_y (y1); x-order 1 = Psi_x
+  YArgs ys{};
+  ys.g = g;
+  ys.tw = p->tw;
+  ys.job.sum = 1;
+  ys.job.n_in = 3;
+  ys.job.n_out = 2;
+  ys.job.in[0] = S[7];
+  ys.job.in[1] = S[8];
+  ys.job.in[2] = S[9];
+  ys.job.dst[0] = 0; ys.job.ord[0] = 0;
+  ys.job.dst[1] = 0; ys.job.ord[1] = 1;
+  ys.job.dst[2] = 1; ys.job.ord[2] = 0;
+  ys.job.out[0] = S[10];
+  ys.job.out[1] = S[11];
+  LAUNCH(p, "y_adj_psi", 20.0 * V3(p), y_pass(n, ys, p->stream));
+  // 5-6. x transpose of the source step: h_Psi (slot 12), inverse x of h_S (slot 13), theta partials
+  XArgs xs{};
+  xs.g = g;
+  xs.tw = p->tw;
+  xs.mode = X_ADJ_SOURCE;
+  xs.in2[0] = S[10];
+  xs.in2[1] = S[11];
+  xs.delta_in = S[S_DELTA];
+  xs.s_in = S[S_SHAT];
+  xs.hpsi_out = S[12];
+  xs.out[0] = S[13];
+  xs.cosmo = p->cosmo_dev;
+  xs.d1f = p->tabf;
+  xs.d2f = p->tabf + p->nk;
+  xs.t1f = p->tabf + 2 * p->nk;
+  xs.t2f = p->tabf + 3 * p->nk;
+  xs.theta_part = thp;
+  LAUNCH(p, "x_adj_source", 28.0 * V3(p), x_pass(n, xs, p->stream));
+  YArgs yh = yi;
+  yh.job.in[0] = S[13];
+  yh.job.out[0] = S[13];
+  LAUNCH(p, "y_inv", 8.0 * V3(p), y_pass(n, yh, p->stream));
+  // 7. recompute the six phi_ij (checkpointed: from delta(k) in slot 1)
+  XArgs xph{};
+  xph.g = g;
+  xph.tw = p->tw;
+  xph.mode = X_PHI;
+  xph.in = S[S_DELTA];
+  xph.out[0] = S[2];
+  xph.out[1] = S[3];
+  xph.out[2] = S[4];
+  xph.cosmo = p->cosmo_dev;
+  LAUNCH(p, "x_phi", 16.0 * V3(p), x_pass(n, xph, p->stream));
+  YArgs yp{};
+  yp.g = g;
+  yp.tw = p->tw;
+  yp.inverse = 1;
+  yp.job.n_in = 3;
+  yp.job.n_out = 6;
+  const int psrc[6] = {0, 0, 0, 1, 1, 2}, pord[6] = {0, 1, 2, 0, 1, 0};
+  float2* pdst[6] = {S[5], S[6], S[7], S[8], S[9], S[10]};   // (x0y0) (x0y1) (x0y2) (x1y0) (x1y1) (x2y0)
+  for (int i = 0; i < 3; ++i) yp.job.in[i] = S[2 + i];
+  for (int o = 0; o < 6; ++o) {
+    yp.job.out[o] = pdst[o];
+    yp.job.src[o] = psrc[o];
+    yp.job.ord[o] = pord[o];
+  }
+  LAUNCH(p, "y_phi", 36.0 * V3(p), y_pass(n, yp, p->stream));
+  // 8. z transpose of the source term: outputs xx yy zz xy xz yz
+  ZAdjSourceArgs za{};
+  za.g = g;
+  za.tw = p->tw;
+  za.hs = S[13];
+  const float2* phi[6] = {S[10], S[7], S[5], S[9], S[8], S[6]};   // xx yy zz xy xz yz
+  const int zord[6] = {0, 0, 2, 0, 1, 1};
+  float2* gout[6] = {S[0], S[2], S[3], S[4], S[11], S[14]};
+  for (int i = 0; i < 6; ++i) {
+    za.in[i] = phi[i];
+    za.ord[i] = zord[i];
+    za.out[i] = gout[i];
+  }
+  LAUNCH(p, "z_adj_source", 56.0 * V3(p), z_adj_source(n, za, p->stream));
+  // 9. y transpose: x-order 0 <- zz (y0) + yz (y1) + yy (y2); x-order 1 <- xz (y0) + xy (y1); 2 <- xx
+  YArgs y6{};
+  y6.g = g;
+  y6.tw = p->tw;
+  y6.job.sum = 1;
+  y6.job.n_in = 6;
+  y6.job.n_out = 3;
+  const int gdst[6] = {2, 0, 0, 1, 1, 0}, gord[6] = {0, 2, 0, 1, 0, 1};   // xx yy zz xy xz yz
+  for (int i = 0; i < 6; ++i) {
+    y6.job.in[i] = gout[i];
+    y6.job.dst[i] = gdst[i];
+    y6.job.ord[i] = gord[i];
+  }
+  y6.job.out[0] = S[15];
+  y6.job.out[1] = S[16];
+  y6.job.out[2] = S[5];
+  LAUNCH(p, "y_adj_phi", 36.0 * V3(p), y_pass(n, y6, p->stream));
+  // 10. x transpose of the delta step: s(k) (h_Psi + h_phi) -> inverse x (slot 6)
+  XArgs xd{};
+  xd.g = g;
+  xd.tw = p->tw;
+  xd.mode = X_ADJ_DELTA;
+  xd.in2[0] = S[15];
+  xd.in2[1] = S[16];
+  xd.in2[2] = S[5];
+  xd.hpsi_in = S[12];
+  xd.out[0] = S[6];
+  xd.cosmo = p->cosmo_dev;
+  LAUNCH(p, "x_adj_delta", 20.0 * V3(p), x_pass(n, xd, p->stream));
+  YArgs yg = yi;
+  yg.job.in[0] = S[6];
+  yg.job.out[0] = S[6];
+  LAUNCH(p, "y_inv", 8.0 * V3(p), y_pass(n, yg, p->stream));
+  if (g_noise) {
+    ZC2RArgs zn{g, p->tw, S[6], g_noise, nullptr};
+    LAUNCH(p, "z_c2r", 8.0 * V3(p), z_c2r(n, zn, p->stream));
+  }
+  if (g_log_fr0) LAUNCH(p, "theta_sum", 0.0, launch_sum_partials(thp, x_blocks(n), g_log_fr0, p->stream));
   return LPT2_OK;
 }
 

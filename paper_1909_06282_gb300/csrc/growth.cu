@@ -226,6 +226,8 @@ __global__ void k_growth(GrowthParams p, double* tab, float* tabf) {
   tab[3 * nk + t] = TAN ? y[10] / (norm * norm) : 0.0;
   tabf[t] = (float)(y[0] / norm);
   tabf[nk + t] = (float)(y[4] / (norm * norm));
+  tabf[2 * nk + t] = (float)tab[2 * nk + t];
+  tabf[3 * nk + t] = (float)tab[3 * nk + t];
 }
 
 cudaError_t launch_growth(const GrowthParams& p, double* tab, float* tabf, cudaStream_t s) {

@@ -119,4 +119,39 @@ cudaError_t launch_philox_words(uint32_t k0, uint32_t k1, uint64_t first, int64_
   return cudaGetLastError();
 }
 
+// Per-shell weight of the P(k) transpose: dP_b/d delta(k) = 2 V delta(k)/(N^6 c_b),
+// so the density cotangent gains IDFT[w_b delta(k)] with w_b = 2 V g_pk[b] / (N^6 c_b).
+__global__ void k_pk_adj_weights(const double* g_pk, const int64_t* n_modes, int ns, double v_over_n6,
+                                 float* w) {
+  for (int b = threadIdx.x; b < ns; b += blockDim.x) {
+    const double c = (double)n_modes[b];
+    w[b] = (c > 0 && g_pk) ? (float)(2.0 * v_over_n6 * g_pk[b] / c) : 0.f;
+  }
+}
+
+cudaError_t launch_pk_adj_weights(const double* g_pk, const int64_t* n_modes, int n_shells, double v_over_n6,
+                                  float* w, cudaStream_t s) {
+  k_pk_adj_weights<<<1, 256, 0, s>>>(g_pk, n_modes, n_shells, v_over_n6, w);
+  return cudaGetLastError();
+}
+
+// Deterministic sum of n FP64 partials (fixed-order strided sums, then a tree).
+__global__ void k_sum_partials(const double* part, int n, double* out) {
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) acc += part[i];
+  __shared__ double s[256];
+  s[threadIdx.x] = acc;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) s[threadIdx.x] += s[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = s[0];
+}
+
+cudaError_t launch_sum_partials(const double* part, int n, double* out, cudaStream_t s) {
+  k_sum_partials<<<1, 256, 0, s>>>(part, n, out);
+  return cudaGetLastError();
+}
+
 }  // namespace lpt2

@@ -41,6 +41,13 @@ __device__ __forceinline__ float2 deriv(float2 v, float k, int m) {
   return cscale(v, -k * k);
 }
 
+// conj((i k)^m) v for m = 0, 1, 2 (the transpose of deriv)
+__device__ __forceinline__ float2 dconj(float2 v, float k, int m) {
+  if (m == 0) return v;
+  if (m == 1) return cscale(mul_mi(v), k);
+  return cscale(v, -k * k);
+}
+
 // ===================================================================== z pass
 // Thread layout: tid = p * TPP + t (pencil pair p, lane t within the pencil).
 
@@ -61,6 +68,26 @@ __device__ __forceinline__ void z_store_pair(const float2 (&v)[Cfg<N>::RMAX], in
     outb[k] = cscale(mul_mi(csub(zk, zm)), 0.5f);
   }
   (void)H;
+}
+
+// As z_store_pair, each output multiplied by conj((i k_z)^m) (transpose of a z derivative).
+template <int N>
+__device__ __forceinline__ void z_store_pair_d(const float2 (&v)[Cfg<N>::RMAX], int t, const SmemRow& sm,
+                                               float2* __restrict__ outa, float2* __restrict__ outb,
+                                               float kf, int ma, int mb) {
+  constexpr int RMAX = Cfg<N>::RMAX, TPP = N / RMAX;
+#pragma unroll
+  for (int r = 0; r < RMAX; ++r) sm.st(t + r * TPP, v[r]);
+  __syncthreads();
+#pragma unroll
+  for (int r = 0; r < RMAX / 2; ++r) {
+    const int k = t + r * TPP;
+    const float2 zk = sm.ld(k);
+    const float2 zm = cconj(sm.ld((N - k) & (N - 1)));
+    const float kz = kf * (float)k;
+    outa[k] = dconj(cscale(cadd(zk, zm), 0.5f), kz, ma);
+    outb[k] = dconj(cscale(mul_mi(csub(zk, zm)), 0.5f), kz, mb);
+  }
 }
 
 // Z value at element n of the Hermitian extension of two half-spectrum rows,
@@ -130,8 +157,9 @@ __global__ void __launch_bounds__(PassCfg<N>::ZT, LPT2_Z_MINB) k_z_c2r(ZC2RArgs 
 #pragma unroll
   for (int r = 0; r < C::RMAX; ++r) {
     const int n = t + r * C::TPP;
-    a.out[(size_t)rowa * N + n] = v[r].x;
-    a.out[(size_t)rowb * N + n] = v[r].y;
+    const size_t ea = (size_t)rowa * N + n, eb = (size_t)rowb * N + n;
+    a.out[ea] = a.add_in ? v[r].x + __ldg(a.add_in + ea) : v[r].x;
+    a.out[eb] = a.add_in ? v[r].y + __ldg(a.add_in + eb) : v[r].y;
   }
 }
 
@@ -303,6 +331,146 @@ __global__ void __launch_bounds__(PassCfg<N>::ZT, LPT2_Z_MINB) k_z_final(ZFinalA
   }
 }
 
+// Transpose of the CIC deposit + positions + inverse z of k_z_final: gathers
+// dL/drho at the 8 cells of each particle into dL/dx (= dL/dPsi), then forward
+// z transforms with conj z-derivatives: (g_x, g_y) of each row, g_z of both rows.
+template <int N>
+__device__ __forceinline__ void cic_gather_grad(const float* __restrict__ g, const float* __restrict__ pos,
+                                                size_t e, size_t n3, float inv_cell, float& gx, float& gy,
+                                                float& gz) {
+  const float ux = wrapN<N>(__ldg(pos + e) * inv_cell);
+  const float uy = wrapN<N>(__ldg(pos + n3 + e) * inv_cell);
+  const float uz = wrapN<N>(__ldg(pos + 2 * n3 + e) * inv_cell);
+  const float fx = floorf(ux), fy = floorf(uy), fz = floorf(uz);
+  const float dx = ux - fx, dy = uy - fy, dz = uz - fz;
+  const int ix = ((int)fx) & (N - 1), iy = ((int)fy) & (N - 1), iz = ((int)fz) & (N - 1);
+  const int jx = (ix + 1) & (N - 1), jy = (iy + 1) & (N - 1), jz = (iz + 1) & (N - 1);
+  const float wx[2] = {1.f - dx, dx}, wy[2] = {1.f - dy, dy}, wz[2] = {1.f - dz, dz};
+  const int cx[2] = {ix, jx}, cy[2] = {iy, jy}, cz[2] = {iz, jz};
+  float ax = 0.f, ay = 0.f, az = 0.f;
+#pragma unroll
+  for (int ox = 0; ox < 2; ++ox)
+#pragma unroll
+    for (int oy = 0; oy < 2; ++oy)
+#pragma unroll
+      for (int oz = 0; oz < 2; ++oz) {
+        const float gc = __ldg(g + ((size_t)cx[ox] * N + cy[oy]) * N + cz[oz]);
+        const float sx = ox ? 1.f : -1.f, sy = oy ? 1.f : -1.f, sz = oz ? 1.f : -1.f;
+        ax = fmaf(gc * sx, wy[oy] * wz[oz], ax);
+        ay = fmaf(gc * sy, wx[ox] * wz[oz], ay);
+        az = fmaf(gc * sz, wx[ox] * wy[oy], az);
+      }
+  gx = ax * inv_cell;
+  gy = ay * inv_cell;
+  gz = az * inv_cell;
+}
+
+template <int N>
+__global__ void __launch_bounds__(PassCfg<N>::ZT, LPT2_Z_MINB) k_z_adj_final(ZAdjFinalArgs a) {
+  using C = PassCfg<N>;
+  extern __shared__ float2 smem[];
+  float2* s_tw = smem;
+  load_twiddles(s_tw, a.tw, N);
+  const int p = threadIdx.x / C::TPP, t = threadIdx.x % C::TPP;
+  const SmemRow sm{smem + N + p * SmemRow::words(N)};
+  const int pair = blockIdx.x * C::ZP + p;
+  const int rows[2] = {2 * pair, 2 * pair + 1};
+  const size_t n3 = (size_t)N * N * N;
+  const float kf = a.g.kf;
+  float gza[C::RMAX];
+  __syncthreads();
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    float2 v[C::RMAX];
+    float gzb[C::RMAX];
+#pragma unroll
+    for (int r = 0; r < C::RMAX; ++r) {
+      float gx = 0.f, gy = 0.f, gz = 0.f;
+      const size_t e = (size_t)rows[h] * N + t + r * C::TPP;
+      if (a.grho) cic_gather_grad<N>(a.grho, a.pos, e, n3, a.g.inv_cell, gx, gy, gz);
+      if (a.gpos) {
+        gx += __ldg(a.gpos + e);
+        gy += __ldg(a.gpos + n3 + e);
+        gz += __ldg(a.gpos + 2 * n3 + e);
+      }
+      v[r] = make_float2(gx, gy);
+      if (h == 0) gza[r] = gz; else gzb[r] = gz;
+    }
+    fft<N, false>(v, t, sm, s_tw);
+    z_store_pair_d<N>(v, t, sm, a.gx + (size_t)rows[h] * C::H, a.gy + (size_t)rows[h] * C::H, kf, 0, 0);
+    if (h == 1) {
+      __syncthreads();   // partner reads of the store above are done before smem is reused
+#pragma unroll
+      for (int r = 0; r < C::RMAX; ++r) v[r] = make_float2(gza[r], gzb[r]);
+      fft<N, false>(v, t, sm, s_tw);
+      z_store_pair_d<N>(v, t, sm, a.gz + (size_t)rows[0] * C::H, a.gz + (size_t)rows[1] * C::H, kf, 1, 1);
+    } else {
+      __syncthreads();
+    }
+  }
+}
+
+// Transpose of k_z_source: g_S from h_S (inverse z), the six phi_ij recomputed
+// (inverse z), g_phi_ij = g_S dS/dphi_ij, forward z with conj z-derivatives.
+template <int N>
+__global__ void __launch_bounds__(PassCfg<N>::ZT, LPT2_Z_MINB) k_z_adj_source(ZAdjSourceArgs a) {
+  using C = PassCfg<N>;
+  extern __shared__ float2 smem[];
+  float2* s_tw = smem;
+  load_twiddles(s_tw, a.tw, N);
+  const int p = threadIdx.x / C::TPP, t = threadIdx.x % C::TPP;
+  const SmemRow sm{smem + N + p * SmemRow::words(N)};
+  const int pair = blockIdx.x * C::ZP + p;
+  const int rows[2] = {2 * pair, 2 * pair + 1};
+  const float kf = a.g.kf;
+  float gs[2][C::RMAX];
+  __syncthreads();
+  {
+    float2 v[C::RMAX];
+#pragma unroll
+    for (int r = 0; r < C::RMAX; ++r)
+      v[r] = z_assemble<N>(a.hs + (size_t)rows[0] * C::H, a.hs + (size_t)rows[1] * C::H, t + r * C::TPP,
+                           kf, 0, 0);
+    fft<N, true>(v, t, sm, s_tw);
+#pragma unroll
+    for (int r = 0; r < C::RMAX; ++r) { gs[0][r] = v[r].x; gs[1][r] = v[r].y; }
+  }
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const size_t off = (size_t)rows[h] * C::H;
+    float2 A[C::RMAX], B[C::RMAX];
+#pragma unroll
+    for (int r = 0; r < C::RMAX; ++r)
+      A[r] = z_assemble<N>(a.in[0] + off, a.in[1] + off, t + r * C::TPP, kf, a.ord[0], a.ord[1]);
+    fft<N, true>(A, t, sm, s_tw);                       // (phi_xx, phi_yy)
+#pragma unroll
+    for (int r = 0; r < C::RMAX; ++r)
+      B[r] = z_assemble<N>(a.in[2] + off, a.in[3] + off, t + r * C::TPP, kf, a.ord[2], a.ord[3]);
+    fft<N, true>(B, t, sm, s_tw);                       // (phi_zz, phi_xy)
+#pragma unroll
+    for (int r = 0; r < C::RMAX; ++r) {
+      const float xx = A[r].x, yy = A[r].y, zz = B[r].x, xy = B[r].y, g = gs[h][r];
+      A[r] = make_float2(g * (yy + zz), g * (xx + zz));   // dS/dphi_xx, dS/dphi_yy
+      B[r] = make_float2(g * (xx + yy), -2.f * g * xy);   // dS/dphi_zz, dS/dphi_xy
+    }
+    fft<N, false>(A, t, sm, s_tw);
+    z_store_pair_d<N>(A, t, sm, a.out[0] + off, a.out[1] + off, kf, a.ord[0], a.ord[1]);
+    __syncthreads();
+    fft<N, false>(B, t, sm, s_tw);
+    z_store_pair_d<N>(B, t, sm, a.out[2] + off, a.out[3] + off, kf, a.ord[2], a.ord[3]);
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < C::RMAX; ++r)
+      A[r] = z_assemble<N>(a.in[4] + off, a.in[5] + off, t + r * C::TPP, kf, a.ord[4], a.ord[5]);
+    fft<N, true>(A, t, sm, s_tw);                       // (phi_xz, phi_yz)
+#pragma unroll
+    for (int r = 0; r < C::RMAX; ++r) A[r] = make_float2(-2.f * gs[h][r] * A[r].x, -2.f * gs[h][r] * A[r].y);
+    fft<N, false>(A, t, sm, s_tw);
+    z_store_pair_d<N>(A, t, sm, a.out[4] + off, a.out[5] + off, kf, a.ord[4], a.ord[5]);
+    __syncthreads();
+  }
+}
+
 // ===================================================================== y pass
 // CTA = (kz block of W, fixed x). Thread tid = t * W + w.
 template <int N>
@@ -317,6 +485,29 @@ __global__ void __launch_bounds__(PassCfg<N>::XT) k_y(YArgs a) {
   const int x = blockIdx.y;
   const size_t base = (size_t)x * N * C::H + kz;     // element (x, y, kz) = base + y * H
   __syncthreads();
+  if (a.job.sum) {
+    for (int o = 0; o < a.job.n_out; ++o) {
+      float2 acc[C::RMAX];
+#pragma unroll
+      for (int r = 0; r < C::RMAX; ++r) acc[r] = make_float2(0.f, 0.f);
+      for (int i = 0; i < a.job.n_in; ++i) {
+        if (a.job.dst[i] != o) continue;
+        float2 v[C::RMAX];
+#pragma unroll
+        for (int r = 0; r < C::RMAX; ++r) v[r] = a.job.in[i][base + (size_t)(t + r * C::TPP) * C::H];
+        fft<N, false>(v, t, sm, s_tw);
+#pragma unroll
+        for (int r = 0; r < C::RMAX; ++r) {
+          const int n = t + r * C::TPP;
+          acc[r] = cadd(acc[r], dconj(v[r], a.g.kf * (float)mode_of(n, N), a.job.ord[i]));
+        }
+      }
+      float2* dst = a.job.out[o];
+#pragma unroll
+      for (int r = 0; r < C::RMAX; ++r) dst[base + (size_t)(t + r * C::TPP) * C::H] = acc[r];
+    }
+    return;
+  }
   for (int i = 0; i < a.job.n_in; ++i) {
     float2 in[C::RMAX];
 #pragma unroll
@@ -364,6 +555,26 @@ __device__ __forceinline__ float sqrt_pk(const DevCosmo& c, float k) {
   return c.sqrt_amp * expf(c.ns_half * logf(k)) * T;
 }
 
+// Exact integer P(k) shell of mode (mx, my, mz): b = floor(2 ns |n| / N) for
+// 0 < |n| < N/2, else -1.
+template <int N>
+__device__ __forceinline__ int shell_of(int mx, int my, int mz, int ns, long long& n2) {
+  n2 = (long long)mx * mx + (long long)my * my + (long long)mz * mz;
+  if (n2 == 0 || 4 * n2 >= (long long)N * N) return -1;
+  const long long M = 4LL * ns * ns * n2;
+  long long s = (long long)sqrtf((float)M);
+  while ((s + 1) * (s + 1) <= M) ++s;
+  while (s * s > M) --s;
+  return (int)(s / N);
+}
+
+// Sum of a float over the warp (all lanes participate).
+__device__ __forceinline__ float warp_sum(float x) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
+  return x;
+}
+
 // CTA = (kz block of W, fixed ky). Thread tid = t * W + w; kx = t + r TPP.
 template <int N>
 __global__ void __launch_bounds__(PassCfg<N>::XT) k_x(XArgs a) {
@@ -373,58 +584,72 @@ __global__ void __launch_bounds__(PassCfg<N>::XT) k_x(XArgs a) {
   load_twiddles(s_tw, a.tw, N);
   const int w = threadIdx.x % C::W, t = threadIdx.x / C::W;
   const SmemCol<C::W> sm{smem + N + w};
+  double* s_acc = reinterpret_cast<double*>(smem + N + N * C::W);   // per-warp FP64 accumulators
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  constexpr int NWARP = C::XT / 32;
   const int kz = blockIdx.x * C::W + w;
   const int ky = blockIdx.y;
   const size_t base = (size_t)ky * C::H + kz;      // element (kx, ky, kz) = base + kx * N * H
   const size_t stride = (size_t)N * C::H;
   const int my = mode_of(ky, N), mz = kz;
   const bool ny_nyq = (ky == C::H);
+  const float kf = a.g.kf;
+  const size_t blk = (size_t)blockIdx.y * gridDim.x + blockIdx.x;
   if (a.mode == X_PK) {
-    double* s_pkw = reinterpret_cast<double*>(smem + N + N * C::W);
-    for (int i = threadIdx.x; i < (C::XT / 32) * 3 * a.n_shells; i += blockDim.x) s_pkw[i] = 0.0;
+    for (int i = threadIdx.x; i < NWARP * 3 * a.n_shells; i += blockDim.x) s_acc[i] = 0.0;
+  } else if (a.mode == X_ADJ_SOURCE) {
+    for (int i = threadIdx.x; i < NWARP; i += blockDim.x) s_acc[i] = 0.0;
   }
   __syncthreads();
 
   float2 v[C::RMAX];
+  const bool adjoint = (a.mode == X_ADJ_SOURCE || a.mode == X_ADJ_DELTA);
+  if (adjoint) {
+    // forward x transform of each x-order group, summed with conj((i kx)^m)
+    const int ng = (a.mode == X_ADJ_SOURCE) ? 2 : 3;
 #pragma unroll
-  for (int r = 0; r < C::RMAX; ++r) v[r] = a.in[base + (size_t)(t + r * C::TPP) * stride];
-
-  if (a.mode == X_INV) {
-    fft<N, true>(v, t, sm, s_tw);
+    for (int r = 0; r < C::RMAX; ++r) v[r] = make_float2(0.f, 0.f);
+    for (int gi = 0; gi < ng; ++gi) {
+      float2 u[C::RMAX];
 #pragma unroll
-    for (int r = 0; r < C::RMAX; ++r) a.out[0][base + (size_t)(t + r * C::TPP) * stride] = v[r];
-    return;
+      for (int r = 0; r < C::RMAX; ++r) u[r] = a.in2[gi][base + (size_t)(t + r * C::TPP) * stride];
+      fft<N, false>(u, t, sm, s_tw);
+#pragma unroll
+      for (int r = 0; r < C::RMAX; ++r) {
+        const int kx = t + r * C::TPP;
+        v[r] = cadd(v[r], dconj(u[r], kf * (float)mode_of(kx, N), gi));
+      }
+    }
+  } else {
+#pragma unroll
+    for (int r = 0; r < C::RMAX; ++r) v[r] = a.in[base + (size_t)(t + r * C::TPP) * stride];
+    if (a.mode == X_INV) {
+      fft<N, true>(v, t, sm, s_tw);
+#pragma unroll
+      for (int r = 0; r < C::RMAX; ++r) a.out[0][base + (size_t)(t + r * C::TPP) * stride] = v[r];
+      return;
+    }
+    if (a.mode != X_PHI) fft<N, false>(v, t, sm, s_tw);
+    if (a.mode == X_FWD) {
+#pragma unroll
+      for (int r = 0; r < C::RMAX; ++r) a.out[0][base + (size_t)(t + r * C::TPP) * stride] = v[r];
+      return;
+    }
   }
-  fft<N, false>(v, t, sm, s_tw);
-  if (a.mode == X_FWD) {
-#pragma unroll
-    for (int r = 0; r < C::RMAX; ++r) a.out[0][base + (size_t)(t + r * C::TPP) * stride] = v[r];
-    return;
-  }
 
-  const float kf = a.g.kf;
   if (a.mode == X_PK) {
-    // P(k) shells: b = floor(2 ns |n| / N) for 0 < |n| < N/2 (exact integer test).
-    // Lanes of a warp see neighbouring modes, so they fall in few shells: for each
-    // distinct shell in the warp, an FP64 butterfly sums the lanes of that shell
-    // and one lane adds the sums to the block's shared accumulators.
+    // P(k) shells.  Lanes of a warp see neighbouring modes, so they fall in few
+    // shells: for each distinct shell in the warp the lanes of that shell are
+    // summed (at most 32 terms, FP32) and one lane adds the sums to this warp's
+    // own FP64 accumulators.
     const float pnorm = a.g.box * a.g.box * a.g.box * a.g.inv_n3 * a.g.inv_n3;
     const int ns = a.n_shells;
-    const int lane = threadIdx.x & 31;
-    double* s_mine = reinterpret_cast<double*>(smem + N + N * C::W) + (threadIdx.x >> 5) * 3 * ns;
+    double* s_mine = s_acc + warp * 3 * ns;
 #pragma unroll
     for (int r = 0; r < C::RMAX; ++r) {
       const int kx = t + r * C::TPP;
-      const int mx = mode_of(kx, N);
-      const long long n2 = (long long)mx * mx + (long long)my * my + (long long)mz * mz;
-      int b = -1;
-      if (n2 != 0 && 4 * n2 < (long long)N * N) {
-        const long long M = 4LL * ns * ns * n2;
-        long long s = (long long)sqrtf((float)M);
-        while ((s + 1) * (s + 1) <= M) ++s;
-        while (s * s > M) --s;
-        b = (int)(s / N);
-      }
+      long long n2;
+      const int b = shell_of<N>(mode_of(kx, N), my, mz, ns, n2);
       const int wgt = (b < 0) ? 0 : ((mz == 0) ? 1 : 2);
       const float pv = (v[r].x * v[r].x + v[r].y * v[r].y) * pnorm * (float)wgt;
       const float kv = kf * sqrtf((float)n2) * (float)wgt;
@@ -433,7 +658,6 @@ __global__ void __launch_bounds__(PassCfg<N>::XT) k_x(XArgs a) {
         const int leader = __ffs(todo) - 1;
         const int key = __shfl_sync(0xffffffffu, b, leader);
         const bool mine = (b == key);
-        // at most 32 terms per warp sum in FP32; the running shell sums are FP64
         float sp = mine ? pv : 0.f, sk = mine ? kv : 0.f;
         int sc = mine ? wgt : 0;
 #pragma unroll
@@ -442,7 +666,7 @@ __global__ void __launch_bounds__(PassCfg<N>::XT) k_x(XArgs a) {
           sk += __shfl_xor_sync(0xffffffffu, sk, off);
           sc += __shfl_xor_sync(0xffffffffu, sc, off);
         }
-        if (lane == leader) {   // this warp's own accumulators: no atomics
+        if (lane == leader) {
           s_mine[key] += (double)sp;
           s_mine[ns + key] += (double)sk;
           s_mine[2 * ns + key] += (double)sc;
@@ -451,19 +675,38 @@ __global__ void __launch_bounds__(PassCfg<N>::XT) k_x(XArgs a) {
       }
     }
     __syncthreads();
-    const size_t blk = (size_t)blockIdx.y * gridDim.x + blockIdx.x;
-    const double* s_all = reinterpret_cast<const double*>(smem + N + N * C::W);
     for (int i = threadIdx.x; i < 3 * ns; i += blockDim.x) {
       double acc = 0.0;
-      for (int wi = 0; wi < C::XT / 32; ++wi) acc += s_all[wi * 3 * ns + i];   // fixed order
+      for (int wi = 0; wi < NWARP; ++wi) acc += s_acc[wi * 3 * ns + i];   // fixed order
       a.pk_part[blk * 3 * ns + i] = acc;
     }
     return;
   }
 
-  const DevCosmo cz = *a.cosmo;
+  if (a.mode == X_PKADJ) {
+    // d P_b / d delta_rho: multiply delta_rho(k) by the per-shell weight, back along x
+#pragma unroll
+    for (int r = 0; r < C::RMAX; ++r) {
+      const int kx = t + r * C::TPP;
+      long long n2;
+      const int b = shell_of<N>(mode_of(kx, N), my, mz, a.n_shells, n2);
+      v[r] = cscale(v[r], b < 0 ? 0.f : __ldg(a.shell_w + b));
+    }
+    fft<N, true>(v, t, sm, s_tw);
+#pragma unroll
+    for (int r = 0; r < C::RMAX; ++r) a.out[0][base + (size_t)(t + r * C::TPP) * stride] = v[r];
+    return;
+  }
+
+  if (a.mode == X_SOURCE && a.s_out) {
+#pragma unroll
+    for (int r = 0; r < C::RMAX; ++r) a.s_out[base + (size_t)(t + r * C::TPP) * stride] = v[r];
+  }
+
   // k-space multipliers. g = potential to transform back along x.
+  const DevCosmo cz = *a.cosmo;
   float2 g[C::RMAX], hpot[C::RMAX];
+  float theta = 0.f;
 #pragma unroll
   for (int r = 0; r < C::RMAX; ++r) {
     const int kx = t + r * C::TPP;
@@ -472,28 +715,55 @@ __global__ void __launch_bounds__(PassCfg<N>::XT) k_x(XArgs a) {
     const float k2 = kf * kf * (float)(mx * mx + my * my + mz * mz);
     const float k = sqrtf(k2);
     const float inv = zero ? 0.f : a.g.inv_n3 / k2;
+    const size_t e = base + (size_t)kx * stride;
     if (a.mode == X_DELTA) {
       const float sc = zero ? 0.f : sqrt_pk(cz, k) * a.g.sqrt_n3_over_v;
       const float2 d = cscale(v[r], sc);
-      if (a.delta_out) a.delta_out[base + (size_t)kx * stride] = d;
+      if (a.delta_out) a.delta_out[e] = d;
       g[r] = cscale(d, inv);                                // phi1 = delta / k^2 (1/N^3 folded)
       if (a.split) hpot[r] = cscale(g[r], zero ? 0.f : interp_table(a.d1f, cz, k));
-    } else {  // X_SOURCE: v = S(k)
+    } else if (a.mode == X_PHI) {                           // v = delta(k) already
+      g[r] = cscale(v[r], inv);
+    } else if (a.mode == X_SOURCE) {                        // v = S(k)
       const float d2 = zero ? 0.f : interp_table(a.d2f, cz, k);
       float2 u = cscale(v[r], -d2 * inv);                   // phi2 = -S D2 / k^2
       if (!a.split) {
         const float d1 = zero ? 0.f : interp_table(a.d1f, cz, k);
-        const float2 dl = a.delta_in[base + (size_t)kx * stride];
+        const float2 dl = a.delta_in[e];
         u = cadd(u, cscale(dl, d1 * inv));                  // + phi1 D1 (total potential)
       }
       g[r] = u;
+    } else if (a.mode == X_ADJ_SOURCE) {                    // v = g_u(k)
+      const float2 gu = zero ? make_float2(0.f, 0.f) : v[r];
+      const float d1 = zero ? 0.f : interp_table(a.d1f, cz, k);
+      const float d2 = zero ? 0.f : interp_table(a.d2f, cz, k);
+      a.hpsi_out[e] = cscale(gu, d1 * inv);                 // h_Psi = D1 g_u / (k^2 N^3)
+      g[r] = cscale(gu, -d2 * inv);                         // h_S = -D2 g_u / (k^2 N^3)
+      if (!zero) {                                          // dL/dln|fR0| contribution
+        const float t1 = interp_table(a.t1f, cz, k), t2 = interp_table(a.t2f, cz, k);
+        const float2 dl = a.delta_in[e], sk = a.s_in[e];
+        const float cx = t1 * dl.x - t2 * sk.x, cy = t1 * dl.y - t2 * sk.y;
+        theta += (cx * gu.x + cy * gu.y) * inv * (mz == 0 ? 1.f : 2.f);
+      }
+    } else {                                                // X_ADJ_DELTA: v = sum of h_phi groups
+      const float sc = zero ? 0.f : sqrt_pk(cz, k) * a.g.sqrt_n3_over_v;
+      const float2 h = cadd(cscale(v[r], inv), a.hpsi_in[e]);
+      g[r] = cscale(h, sc);                                 // s(k) (h_Psi + h_phi)
     }
   }
+  if (a.mode == X_ADJ_SOURCE) {
+    const float ws = warp_sum(theta);
+    if (lane == 0) s_acc[warp] = (double)ws;
+  }
   // x-inverse transforms with x-derivative orders
-  const int nout = (a.mode == X_DELTA) ? (a.split ? 5 : 3) : 2;
+  int nout;
+  if (a.mode == X_DELTA) nout = a.split ? 5 : 3;
+  else if (a.mode == X_PHI) nout = 3;
+  else if (a.mode == X_SOURCE) nout = 2;
+  else nout = 1;
   for (int o = 0; o < nout; ++o) {
     const bool fromh = (a.mode == X_DELTA) && o >= 3;
-    const int m = (a.mode == X_DELTA) ? (o < 3 ? o : o - 3) : o;
+    const int m = (a.mode == X_DELTA || a.mode == X_PHI) ? (o < 3 ? o : o - 3) : (a.mode == X_SOURCE ? o : 0);
     float2 u[C::RMAX];
 #pragma unroll
     for (int r = 0; r < C::RMAX; ++r) {
@@ -503,6 +773,11 @@ __global__ void __launch_bounds__(PassCfg<N>::XT) k_x(XArgs a) {
     fft<N, true>(u, t, sm, s_tw);
 #pragma unroll
     for (int r = 0; r < C::RMAX; ++r) a.out[o][base + (size_t)(t + r * C::TPP) * stride] = u[r];
+  }
+  if (a.mode == X_ADJ_SOURCE && threadIdx.x == 0) {
+    double acc = 0.0;
+    for (int wi = 0; wi < NWARP; ++wi) acc += s_acc[wi];   // fixed order (barriers inside fft)
+    a.theta_part[blk] = acc;
   }
 }
 
@@ -531,6 +806,18 @@ template <int N> cudaError_t launch_z_final_t(const ZFinalArgs& a, cudaStream_t 
   k_z_final<N><<<N * N / 2 / C::ZP, C::ZT, C::ZSMEM, s>>>(a);
   return cudaGetLastError();
 }
+template <int N> cudaError_t launch_z_adj_final_t(const ZAdjFinalArgs& a, cudaStream_t s) {
+  using C = PassCfg<N>;
+  cudaFuncSetAttribute(k_z_adj_final<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::ZSMEM);
+  k_z_adj_final<N><<<N * N / 2 / C::ZP, C::ZT, C::ZSMEM, s>>>(a);
+  return cudaGetLastError();
+}
+template <int N> cudaError_t launch_z_adj_source_t(const ZAdjSourceArgs& a, cudaStream_t s) {
+  using C = PassCfg<N>;
+  cudaFuncSetAttribute(k_z_adj_source<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::ZSMEM);
+  k_z_adj_source<N><<<N * N / 2 / C::ZP, C::ZT, C::ZSMEM, s>>>(a);
+  return cudaGetLastError();
+}
 template <int N> cudaError_t launch_y_t(const YArgs& a, cudaStream_t s) {
   using C = PassCfg<N>;
   cudaFuncSetAttribute(k_y<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::XSMEM);
@@ -539,7 +826,8 @@ template <int N> cudaError_t launch_y_t(const YArgs& a, cudaStream_t s) {
 }
 template <int N> cudaError_t launch_x_t(const XArgs& a, cudaStream_t s) {
   using C = PassCfg<N>;
-  const int smem = C::XSMEM + (a.mode == X_PK ? (C::XT / 32) * 3 * a.n_shells * 8 : 0);
+  const int smem = C::XSMEM + (a.mode == X_PK ? (C::XT / 32) * 3 * a.n_shells * 8
+                                              : (a.mode == X_ADJ_SOURCE ? (C::XT / 32) * 8 : 0));
   cudaFuncSetAttribute(k_x<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   k_x<N><<<dim3(C::H / C::W, N), C::XT, smem, s>>>(a);
   return cudaGetLastError();
@@ -559,6 +847,12 @@ template <int N> int x_blocks_t() { return (PassCfg<N>::H / PassCfg<N>::W) * N; 
     return launch_z_final_t<N>(a, s);                                                                \
   }                                                                                                  \
   cudaError_t launch_y_##N(const YArgs& a, cudaStream_t s) { return launch_y_t<N>(a, s); }           \
+  cudaError_t launch_z_adj_final_##N(const ZAdjFinalArgs& a, cudaStream_t s) {                       \
+    return launch_z_adj_final_t<N>(a, s);                                                            \
+  }                                                                                                  \
+  cudaError_t launch_z_adj_source_##N(const ZAdjSourceArgs& a, cudaStream_t s) {                     \
+    return launch_z_adj_source_t<N>(a, s);                                                           \
+  }                                                                                                  \
   cudaError_t launch_x_##N(const XArgs& a, cudaStream_t s) { return launch_x_t<N>(a, s); }           \
   int x_blocks_##N() { return x_blocks_t<N>(); }                                                     \
   }

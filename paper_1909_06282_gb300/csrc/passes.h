@@ -49,6 +49,27 @@ struct ZC2RArgs {      // inverse z pass of one field: half-spectrum rows -> rea
   const float2* tw;
   const float2* in;
   float* out;
+  const float* add_in;   // added to the result when not null
+};
+
+struct ZAdjFinalArgs { // transpose of k_z_final: CIC gather of dL/drho, forward z of g_Psi
+  Geo g;
+  const float2* tw;
+  const float* grho;   // dL/d(density contrast) per cell
+  const float* pos;    // [3][N^3] particle positions of the forward
+  const float* gpos;   // [3][N^3] dL/dpositions added to the gathered gradient, or null
+  float2* gz;          // conj(i kz) FFT_z(g_Psi_z)
+  float2* gy;          // FFT_z(g_Psi_y)
+  float2* gx;          // FFT_z(g_Psi_x)
+};
+
+struct ZAdjSourceArgs {  // transpose of k_z_source
+  Geo g;
+  const float2* tw;
+  const float2* hs;      // h_S after the inverse x and y passes
+  const float2* in[6];   // phi_xx, phi_yy, phi_zz, phi_xy, phi_xz, phi_yz (recomputed, after y)
+  int ord[6];            // their z derivative orders
+  float2* out[6];        // conj z-derivative of FFT_z(g_phi_ij), same order
 };
 
 struct ZSourceArgs {   // inverse z pass of the six phi_ij, source term, forward z pass of S
@@ -77,6 +98,9 @@ struct YJob {          // y pass: each output = transform of (i k_y)^ord * input
   float2* out[9];
   int src[9];
   int ord[9];
+  // sum mode (transpose of the above): out[dst[i]] += conj((i k_y)^ord[i]) FFT_y(in[i])
+  int sum;
+  int dst[6];
 };
 struct YArgs {
   Geo g;
@@ -85,21 +109,40 @@ struct YArgs {
   YJob job;
 };
 
-enum XMode { X_DELTA = 0, X_SOURCE = 1, X_PK = 2, X_FWD = 3, X_INV = 4 };
+enum XMode {
+  X_DELTA = 0,      // fwd x of the noise spectrum, sqrt(P), delta(k), inverse x of the phi (+Psi1) potentials
+  X_SOURCE = 1,     // fwd x of S, -D2/k^2 (+D1 delta/k^2), inverse x orders 0, 1
+  X_PK = 2,         // fwd x, shell sums of |delta|^2
+  X_FWD = 3,        // plain forward x
+  X_INV = 4,        // plain inverse x
+  X_PHI = 5,        // phi potential from a stored delta(k) (no transform), inverse x orders 0, 1, 2
+  X_PKADJ = 6,      // fwd x, times per-shell weight, inverse x  (P(k) transpose)
+  X_ADJ_SOURCE = 7, // transpose of X_SOURCE: h_Psi, h_S, dL/dln|fR0| partials
+  X_ADJ_DELTA = 8   // transpose of X_DELTA: s(k) (h_Psi + h_phi), inverse x
+};
 struct XArgs {
   Geo g;
   const float2* tw;
   int mode;
   int split;
-  const float2* in;       // tile source (after the y pass / in k space for X_INV)
+  const float2* in;       // tile source (after the y pass / in k space for X_INV, X_PHI)
+  const float2* in2[3];   // adjoint modes: the x-order 0, 1, 2 groups
   float2* delta_out;      // X_DELTA: delta(k)
-  const float2* delta_in; // X_SOURCE total mode: delta(k)
+  const float2* delta_in; // X_SOURCE total mode, X_ADJ_SOURCE: delta(k)
+  float2* s_out;          // X_SOURCE: S(k), kept for the adjoint (or null)
+  const float2* s_in;     // X_ADJ_SOURCE: S(k)
+  float2* hpsi_out;       // X_ADJ_SOURCE: h_Psi(k)
+  const float2* hpsi_in;  // X_ADJ_DELTA: h_Psi(k)
   float2* out[5];         // x-inverse outputs
   const DevCosmo* cosmo;
   const float* d1f;       // float growth tables [nk]
   const float* d2f;
+  const float* t1f;       // float d/dln|fR0| tables [nk]
+  const float* t2f;
   double* pk_part;        // X_PK: per-block partials [blocks][3][n_shells]
   int n_shells;
+  const float* shell_w;   // X_PKADJ: weight per shell
+  double* theta_part;     // X_ADJ_SOURCE: per-block partial of dL/dln|fR0|
 };
 
 struct CicArgs {
@@ -115,6 +158,8 @@ struct CicArgs {
   cudaError_t launch_z_source_##N(const ZSourceArgs&, cudaStream_t);             \
   cudaError_t launch_z_final_##N(const ZFinalArgs&, cudaStream_t);               \
   cudaError_t launch_y_##N(const YArgs&, cudaStream_t);                          \
+  cudaError_t launch_z_adj_final_##N(const ZAdjFinalArgs&, cudaStream_t);        \
+  cudaError_t launch_z_adj_source_##N(const ZAdjSourceArgs&, cudaStream_t);      \
   cudaError_t launch_x_##N(const XArgs&, cudaStream_t);                          \
   int x_blocks_##N();
 
@@ -147,7 +192,10 @@ struct GrowthParams {
 };
 int cosmo_partial_blocks();
 cudaError_t launch_cosmo_setup(const GrowthParams&, double* partials, DevCosmo* out, cudaStream_t);
-cudaError_t launch_growth(const GrowthParams&, double* tab /*[4][nk]*/, float* tabf /*[2][nk]*/,
+cudaError_t launch_growth(const GrowthParams&, double* tab /*[4][nk]*/, float* tabf /*[4][nk]*/,
                           cudaStream_t);
+cudaError_t launch_pk_adj_weights(const double* g_pk, const int64_t* n_modes, int n_shells, double v_over_n6,
+                                  float* w, cudaStream_t);
+cudaError_t launch_sum_partials(const double* part, int n, double* out, cudaStream_t);
 
 }  // namespace lpt2

@@ -77,3 +77,29 @@ def test_vjp_gr_limit_has_no_fr0_gradient():
                                        np.ones(NS))
     _, g_t = ov.vjp(N, BOX, st, tab, gd, gp, NS)
     assert abs(g_t) < 1e-8
+
+
+def test_vjp_position_cotangent_matches_central_difference():
+    """L = sum_p v_p . Psi_p (a smooth function of the noise): the position cotangent v
+    goes straight into the displacement transpose."""
+    from oracle import lpt2
+    c = W.COSMO.replace(fr0_abs=1e-5)
+    tab = gr.growth_tables(c, 1.0, n_steps=STEPS)
+    noise = philox.gaussian_noise(N, 4, as_float64=True).reshape(N, N, N)
+    v = np.random.default_rng(8).standard_normal((3, N ** 3))
+
+    def L(nz, cc=c):
+        t = gr.growth_tables(cc, 1.0, n_steps=STEPS)
+        st = ov.forward_state(N, BOX, cc, nz, t, NS)
+        return float(np.sum(v * (st["psi1"] + st["psi2"]).reshape(3, -1))), st, t
+
+    _, st, _ = L(noise)
+    g_w, g_t = ov.vjp(N, BOX, st, tab, np.zeros((N, N, N)), np.zeros(NS), NS, g_pos=v)
+    d = np.random.default_rng(9).standard_normal(noise.shape)
+    h = 1e-5
+    fd = (L(noise + h * d)[0] - L(noise - h * d)[0]) / (2 * h)
+    assert abs(fd - np.sum(g_w * d)) < 1e-7 * abs(fd)
+    hf = 1e-4
+    fdt = (L(noise, c.replace(fr0_abs=c.fr0_abs * np.exp(hf)))[0]
+           - L(noise, c.replace(fr0_abs=c.fr0_abs * np.exp(-hf)))[0]) / (2 * hf)
+    assert abs(fdt - g_t) < 1e-5 * abs(fdt), (fdt, g_t)
