@@ -159,6 +159,23 @@ def bench_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def profile_run(args):
+    """A short forward-only run for profilers (`--profile`): plan, args.warmup + args.steps
+    forward steps, no timing output beyond one line."""
+    import torch
+
+    import paper_1909_06282_gb300 as L
+    import workloads as W
+    n = args.grid
+    box = WORKLOAD["box"] * n / WORKLOAD["n"]
+    plan = L.Plan(W.Instance(n, box, 1, W.COSMO.replace(fr0_abs=WORKLOAD["fr0"])), n_steps=1024)
+    for _ in range(args.warmup + args.steps):
+        L.lpt2_displace(plan, psi1=False, psi2=False, pos=True)
+        L.lpt2_cic_pk(plan, pos=None, n_shells=WORKLOAD["n_shells"])
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_run": True, "grid": n, "box": box, "launches": L.lpt2_launch_count(plan)}))
+
+
 def bench_ours(args):
     import numpy as np
     import torch
@@ -214,6 +231,37 @@ def bench_ours(args):
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1) / args.steps
 
+        # forward + adjoint (loss: mean squared density difference to the seed-7 field
+        # plus the squared log P(k) ratio; cotangents formed by torch on the device)
+        tinst = W.Instance(n, box, 7, inst.cosmo)
+        tplan = L.Plan(tinst, n_steps=1024, stream=stream)
+        L.lpt2_displace(tplan, psi1=False, psi2=False, pos=False)
+        tr = L.lpt2_cic_pk(tplan, pos=None, density=True, n_shells=WORKLOAD["n_shells"])
+        tgt_d, tgt_pk = tr["density"].clone(), tr["pk"].clone()
+        del tplan, tr
+
+        def fwd_vjp_step():
+            L.lpt2_displace(plan, psi1=False, psi2=False, pos=False)
+            r = L.lpt2_cic_pk(plan, pos=None, density=True, n_shells=WORKLOAD["n_shells"])
+            d, pkv = r["density"], r["pk"]
+            ok = (pkv > 0) & (tgt_pk > 0)
+            lr = torch.where(ok, torch.log(torch.where(ok, pkv, 1.0) / torch.where(ok, tgt_pk, 1.0)), 0.0)
+            gd = (2.0 / d.numel()) * (d - tgt_d)
+            gp = torch.where(ok, 2.0 * lr / torch.where(ok, pkv, 1.0), 0.0)
+            L.lpt2_displace_vjp(plan, g_density=gd, g_pk=gp, n_shells=WORKLOAD["n_shells"])
+
+        for _ in range(args.warmup):
+            fwd_vjp_step()
+        stream.synchronize()
+        e4, e5 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        vsteps = max(1, args.steps // 2)
+        e4.record(stream)
+        for _ in range(vsteps):
+            fwd_vjp_step()
+        e5.record(stream)
+        stream.synchronize()
+        ms_fv = e4.elapsed_time(e5) / vsteps
+
         # end to end through the public API: pinned host noise in, positions + P(k) out
         noise_h = torch.from_numpy(W.white_noise(n, 1000 + rank)).pin_memory()
         pos_h = torch.empty((3, n, n, n), dtype=torch.float32).pin_memory()
@@ -242,9 +290,9 @@ def bench_ours(args):
         ms_e2e = e2.elapsed_time(e3) / args.steps
 
     if dist:
-        t = torch.tensor([ms, ms_e2e], device="cuda", dtype=torch.float64)
+        t = torch.tensor([ms, ms_e2e, ms_fv], device="cuda", dtype=torch.float64)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms, ms_e2e = float(t[0]), float(t[1])
+        ms, ms_e2e, ms_fv = float(t[0]), float(t[1]), float(t[2])
 
     if rank == 0:
         parts = n ** 3 * world
@@ -275,6 +323,9 @@ def bench_ours(args):
                               "frac": all_bytes / (total_ms / 1e3) / 1e9 / peak},
             "kernels": kernels,
             "growth_ms": growth_ms,
+            "fwd_vjp": {"value": parts / (ms_fv / 1e3), "unit": "particles/s", "ms_per_step": ms_fv,
+                        "vjp_over_fwd": (ms_fv - ms) / ms,
+                        "what": "forward + loss cotangents + lpt2_displace_vjp (noise and ln|fR0| gradients)"},
             "gpu_launches": launches,
             "e2e": {"value": parts / (ms_e2e / 1e3), "unit": "particles/s",
                     "h2d_bytes_per_step": n ** 3 * 4, "d2h_bytes_per_step": 3 * n ** 3 * 4 + 32 * 8},
@@ -301,7 +352,14 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile", action="store_true",
+                    help="forward-only run for ncu (no timing); grid from --grid")
+    ap.add_argument("--grid", type=int, default=WORKLOAD["n"],
+                    help="grid side for --profile (cell size kept at 2 Mpc/h)")
     args = ap.parse_args()
+    if args.profile:
+        profile_run(args)
+        return
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
     if args.impl == "reference":

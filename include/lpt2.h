@@ -19,7 +19,7 @@
  * and are asynchronous with respect to the host; results are ready after the
  * caller synchronises that stream.
  *
- * Layouts.  Grid side N (16, 32, 64, 128, 256, 512 or 1024), box side L in
+ * Layouts.  Grid side N (16, 32, 64, 96, 128, 192, 256, 512 or 1024), box side L in
  * Mpc/h.  A real field is float[N][N][N] (x, y, z; z fastest), cell (ix,iy,iz)
  * at Lagrangian position q = (ix, iy, iz) L / N (cell corner).  Vector fields
  * and particle positions are SoA float[3][N^3].  A spectrum ("half spectrum")

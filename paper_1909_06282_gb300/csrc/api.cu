@@ -28,7 +28,8 @@ int fail(int code, const char* fmt, ...) {
 }
 
 bool supported_n(int n) {
-  return n == 16 || n == 32 || n == 64 || n == 128 || n == 256 || n == 512 || n == 1024;
+  return n == 16 || n == 32 || n == 64 || n == 96 || n == 128 || n == 192 || n == 256 || n == 512 ||
+         n == 1024;
 }
 
 // Workspace slots, each N^3 floats (= a half spectrum of N^3/2 complex).
@@ -76,7 +77,9 @@ int x_blocks(int n) {
     case 16: return x_blocks_16();
     case 32: return x_blocks_32();
     case 64: return x_blocks_64();
+    case 96: return x_blocks_96();
     case 128: return x_blocks_128();
+    case 192: return x_blocks_192();
     case 256: return x_blocks_256();
     case 512: return x_blocks_512();
     default: return x_blocks_1024();
@@ -132,7 +135,9 @@ GrowthParams growth_params(const lpt2_plan_s* p) {
     case 16: return NAME##_16(args, s);     \
     case 32: return NAME##_32(args, s);     \
     case 64: return NAME##_64(args, s);     \
+    case 96: return NAME##_96(args, s);     \
     case 128: return NAME##_128(args, s);   \
+    case 192: return NAME##_192(args, s);   \
     case 256: return NAME##_256(args, s);   \
     case 512: return NAME##_512(args, s);   \
     default: return NAME##_1024(args, s);   \

@@ -1,10 +1,11 @@
 // In-CTA FFT engine for the 2LPT pass kernels (sm_103a).
 //
 // A pencil of N complex points is owned by TPP = N / RMAX threads; thread t of
-// the pencil holds RMAX values in registers.  Both the input of the first stage
-// and the output of the last stage sit at element n = t + r * TPP (r < RMAX),
-// so prologue/epilogue code sees natural-order indices without an extra shared
-// memory round trip.  Stages follow the Stockham autosort formulation (radix-R
+// the pencil holds RMAX values in registers.  The first and the last stage use
+// the same radix R0, so the input of the first stage and the output of the last
+// stage sit at the same element n = elem(t, j) = t + (j / R0) TPP + (j mod R0) N/R0
+// (= t + j TPP when R0 = RMAX): prologue/epilogue code sees natural-order
+// indices without an extra shared memory round trip.  Stages follow the Stockham autosort formulation (radix-R
 // butterflies on inputs b + r N/R, twiddle W_{Ns R}^{r (b mod Ns)}, outputs at
 // (b / Ns) Ns R + b mod Ns + r Ns) with one shared-memory exchange between
 // consecutive stages.  Twiddles come from a table exp(-2 pi i m / N) computed in
@@ -27,9 +28,11 @@ __device__ __forceinline__ float2 mul_i(float2 a) { return make_float2(-a.y, a.x
 __device__ __forceinline__ float2 mul_mi(float2 a) { return make_float2(a.y, -a.x); }   // -i a
 
 // ------------------------------------------------------------ radix schedules
-// Radix sequences with the largest radix first and last (so that stage-0 input
-// and last-stage output share the pattern n = t + r TPP).
+// Radix sequences with the same radix first and last (so that stage-0 input and
+// last-stage output share one element pattern); every radix divides RMAX.
 template <int N> struct Cfg;
+template <> struct Cfg<96>   { static constexpr int NS = 3, RMAX = 12; static __host__ __device__ constexpr int rad(int s) { return s == 1 ? 6 : 4; } };
+template <> struct Cfg<192>  { static constexpr int NS = 3, RMAX = 12; static __host__ __device__ constexpr int rad(int s) { return s == 1 ? 12 : 4; } };
 template <> struct Cfg<16>   { static constexpr int NS = 2, RMAX = 4;  static __host__ __device__ constexpr int rad(int s) { return 4; } };
 template <> struct Cfg<32>   { static constexpr int NS = 3, RMAX = 4;  static __host__ __device__ constexpr int rad(int s) { return s == 1 ? 2 : 4; } };
 template <> struct Cfg<64>   { static constexpr int NS = 2, RMAX = 8;  static __host__ __device__ constexpr int rad(int s) { return 8; } };
@@ -37,6 +40,17 @@ template <> struct Cfg<128>  { static constexpr int NS = 3, RMAX = 8;  static __
 template <> struct Cfg<256>  { static constexpr int NS = 2, RMAX = 16; static __host__ __device__ constexpr int rad(int s) { return 16; } };
 template <> struct Cfg<512>  { static constexpr int NS = 3, RMAX = 16; static __host__ __device__ constexpr int rad(int s) { return s == 1 ? 2 : 16; } };
 template <> struct Cfg<1024> { static constexpr int NS = 3, RMAX = 16; static __host__ __device__ constexpr int rad(int s) { return s == 1 ? 4 : 16; } };
+
+// element index held in register slot j by lane t (first-stage input = last-stage output)
+template <int N> __host__ __device__ __forceinline__ constexpr int elem(int t, int j) {
+  constexpr int R0 = Cfg<N>::rad(0), TPP = N / Cfg<N>::RMAX;
+  return t + (j / R0) * TPP + (j % R0) * (N / R0);
+}
+
+// i mod N for i in [0, 2N) (periodic neighbour index)
+template <int N> __host__ __device__ __forceinline__ constexpr int wrap_idx(int i) {
+  return ((N & (N - 1)) == 0) ? (i & (N - 1)) : (i >= N ? i - N : i);
+}
 
 template <int N> __host__ __device__ constexpr int ns_before(int s) {
   int p = 1;
@@ -46,14 +60,17 @@ template <int N> __host__ __device__ constexpr int ns_before(int s) {
 
 // ------------------------------------------------------- in-register DFTs
 // Forward: X[k] = sum_n x[n] exp(-2 pi i n k / R); INV flips the sign.
-// Roots of unity of order 16: cos / sin of 2 pi j / 16.
-__device__ __forceinline__ float2 root16(int j, bool inv) {
-  // j in [0, 16); value exp(-+ 2 pi i j / 16)
-  const float c[5] = {1.0f, 0.923879532511286756f, 0.707106781186547524f, 0.382683432365089772f, 0.0f};
+// Roots of unity of order 48 (covers R = 2, 3, 4, 6, 8, 12, 16): cos / sin of
+// 2 pi j / 48, from cos(j * 7.5 deg) for j = 0..12.
+__device__ __forceinline__ float2 root48(int j, bool inv) {
+  // j in [0, 48); value exp(-+ 2 pi i j / 48)
+  const float c[13] = {1.0f, 0.99144486137381038f, 0.96592582628906831f, 0.92387953251128674f,
+                       0.86602540378443865f, 0.79335334029123517f, 0.70710678118654752f,
+                       0.60876142900872066f, 0.5f, 0.38268343236508977f, 0.25881904510252074f,
+                       0.13052619222005159f, 0.0f};
   float cs, sn;
-  const int q = j & 3, quad = j >> 2;
-  // cos/sin of (quad * 90 + q * 22.5) degrees
-  const float cq = c[q], sq = c[4 - q];
+  const int q = j % 12, quad = j / 12;
+  const float cq = c[q], sq = c[12 - q];
   switch (quad) {
     case 0: cs = cq; sn = sq; break;
     case 1: cs = -sq; sn = cq; break;
@@ -67,6 +84,18 @@ template <int R, bool INV> struct Dft;
 
 template <bool INV> struct Dft<1, INV> { static __device__ __forceinline__ void run(float2*) {} };
 
+template <bool INV> struct Dft<3, INV> {
+  static __device__ __forceinline__ void run(float2* v) {
+    const float h = 0.86602540378443865f;   // sin(60 deg)
+    const float2 a = v[0], s = cadd(v[1], v[2]), d = csub(v[1], v[2]);
+    const float2 t = make_float2(a.x - 0.5f * s.x, a.y - 0.5f * s.y);
+    const float2 u = INV ? cscale(mul_i(d), h) : cscale(mul_mi(d), h);
+    v[0] = cadd(a, s);
+    v[1] = cadd(t, u);
+    v[2] = csub(t, u);
+  }
+};
+
 template <bool INV> struct Dft<2, INV> {
   static __device__ __forceinline__ void run(float2* v) {
     const float2 a = v[0];
@@ -75,7 +104,8 @@ template <bool INV> struct Dft<2, INV> {
   }
 };
 
-template <int R, bool INV> struct Dft {
+template <int R, bool INV> struct Dft {   // even R: split into even and odd halves
+  static_assert(R % 2 == 0 && 48 % R == 0, "radix must be 2, 4, 6, 8, 12 or 16 here");
   static __device__ __forceinline__ void run(float2* v) {
     float2 e[R / 2], o[R / 2];
 #pragma unroll
@@ -84,11 +114,11 @@ template <int R, bool INV> struct Dft {
     Dft<R / 2, INV>::run(o);
 #pragma unroll
     for (int k = 0; k < R / 2; ++k) {
-      const int j = k * (16 / R);   // exponent in units of 2 pi / 16
+      const int j = k * (48 / R);   // exponent in units of 2 pi / 48
       float2 t;
       if (j == 0) t = o[k];
-      else if (j == 4) t = INV ? mul_i(o[k]) : mul_mi(o[k]);
-      else t = cmul(o[k], root16(j, INV));
+      else if (j == 12) t = INV ? mul_i(o[k]) : mul_mi(o[k]);
+      else t = cmul(o[k], root48(j, INV));
       v[k] = cadd(e[k], t);
       v[k + R / 2] = csub(e[k], t);
     }

@@ -1,37 +1,33 @@
 // Size-independent kernels: CIC deposit from positions, zero fill, P(k) shell
 // finalisation, white noise and raw Philox words.
-#include "passes.h"
-#include "philox.cuh"
+#include "passes.cuh"
 
 namespace lpt2 {
 
 // Periodic cloud-in-cell deposit of unit-mass particles (one thread per particle).
-__global__ void k_cic(CicArgs a) {
-  const int n = a.g.n;
-  const size_t n3 = (size_t)n * n * n;
-  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n3) return;
+template <int N>
+__global__ void __launch_bounds__(256) k_cic(CicArgs a) {
+  const size_t n3 = (size_t)N * N * N;
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;   // grid covers n3 exactly
   float u[3];
-  for (int c = 0; c < 3; ++c) {
-    float x = __ldg(a.pos + c * n3 + i) * a.g.inv_cell;
-    x = x - (float)n * floorf(x / (float)n);
-    u[c] = (x >= (float)n) ? x - (float)n : x;
-  }
-  const float fx = floorf(u[0]), fy = floorf(u[1]), fz = floorf(u[2]);
-  const float dx = u[0] - fx, dy = u[1] - fy, dz = u[2] - fz;
-  const int ix = (int)fx % n, iy = (int)fy % n, iz = (int)fz % n;
-  const int jx = (ix + 1) % n, jy = (iy + 1) % n, jz = (iz + 1) % n;
-  const float wx[2] = {1.f - dx, dx}, wy[2] = {1.f - dy, dy}, wz[2] = {1.f - dz, dz};
-  const int cx[2] = {ix, jx}, cy[2] = {iy, jy}, cz[2] = {iz, jz};
-  for (int ox = 0; ox < 2; ++ox)
-    for (int oy = 0; oy < 2; ++oy)
-      for (int oz = 0; oz < 2; ++oz)
-        atomicAdd(a.rho + ((size_t)cx[ox] * n + cy[oy]) * n + cz[oz], wx[ox] * wy[oy] * wz[oz]);
+  for (int c = 0; c < 3; ++c) u[c] = wrapN<N>(__ldg(a.pos + c * n3 + i) * a.g.inv_cell);
+  cic_deposit_merged<N>(a.rho, u[0], u[1], u[2]);
 }
 
 cudaError_t launch_cic(const CicArgs& a, cudaStream_t s) {
-  const size_t n3 = (size_t)a.g.n * a.g.n * a.g.n;
-  k_cic<<<(unsigned)((n3 + 255) / 256), 256, 0, s>>>(a);
+  const size_t n3 = (size_t)a.g.n * a.g.n * a.g.n;   // every supported N^3 is a multiple of 256
+  const unsigned blocks = (unsigned)(n3 / 256);
+  switch (a.g.n) {
+    case 16: k_cic<16><<<blocks, 256, 0, s>>>(a); break;
+    case 32: k_cic<32><<<blocks, 256, 0, s>>>(a); break;
+    case 64: k_cic<64><<<blocks, 256, 0, s>>>(a); break;
+    case 96: k_cic<96><<<blocks, 256, 0, s>>>(a); break;
+    case 128: k_cic<128><<<blocks, 256, 0, s>>>(a); break;
+    case 192: k_cic<192><<<blocks, 256, 0, s>>>(a); break;
+    case 256: k_cic<256><<<blocks, 256, 0, s>>>(a); break;
+    case 512: k_cic<512><<<blocks, 256, 0, s>>>(a); break;
+    default: k_cic<1024><<<blocks, 256, 0, s>>>(a); break;
+  }
   return cudaGetLastError();
 }
 

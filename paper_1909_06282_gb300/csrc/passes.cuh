@@ -54,16 +54,17 @@ __device__ __forceinline__ float2 dconj(float2 v, float k, int m) {
 template <int N>
 __device__ __forceinline__ void z_store_pair(const float2 (&v)[Cfg<N>::RMAX], int t, const SmemRow& sm,
                                              float2* __restrict__ outa, float2* __restrict__ outb) {
-  // v holds Z = FFT(fa + i fb) at n = t + r TPP. Split into the two real spectra.
+  // v holds Z = FFT(fa + i fb) at n = elem(t, r). Split into the two real spectra;
+  // outputs k = t + r TPP, r < RMAX/2, cover [0, N/2) once.
   constexpr int RMAX = Cfg<N>::RMAX, TPP = N / RMAX, H = N / 2;
 #pragma unroll
-  for (int r = 0; r < RMAX; ++r) sm.st(t + r * TPP, v[r]);
+  for (int r = 0; r < RMAX; ++r) sm.st(elem<N>(t, r), v[r]);
   __syncthreads();
 #pragma unroll
   for (int r = 0; r < RMAX / 2; ++r) {
     const int k = t + r * TPP;                      // < H
     const float2 zk = sm.ld(k);
-    const float2 zm = cconj(sm.ld((N - k) & (N - 1)));
+    const float2 zm = cconj(sm.ld(k == 0 ? 0 : N - k));
     outa[k] = cscale(cadd(zk, zm), 0.5f);
     outb[k] = cscale(mul_mi(csub(zk, zm)), 0.5f);
   }
@@ -77,13 +78,13 @@ __device__ __forceinline__ void z_store_pair_d(const float2 (&v)[Cfg<N>::RMAX], 
                                                float kf, int ma, int mb) {
   constexpr int RMAX = Cfg<N>::RMAX, TPP = N / RMAX;
 #pragma unroll
-  for (int r = 0; r < RMAX; ++r) sm.st(t + r * TPP, v[r]);
+  for (int r = 0; r < RMAX; ++r) sm.st(elem<N>(t, r), v[r]);
   __syncthreads();
 #pragma unroll
   for (int r = 0; r < RMAX / 2; ++r) {
     const int k = t + r * TPP;
     const float2 zk = sm.ld(k);
-    const float2 zm = cconj(sm.ld((N - k) & (N - 1)));
+    const float2 zm = cconj(sm.ld(k == 0 ? 0 : N - k));
     const float kz = kf * (float)k;
     outa[k] = dconj(cscale(cadd(zk, zm), 0.5f), kz, ma);
     outb[k] = dconj(cscale(mul_mi(csub(zk, zm)), 0.5f), kz, mb);
@@ -106,7 +107,7 @@ __device__ __forceinline__ float2 z_assemble(const float2* __restrict__ ra, cons
   return make_float2(A.x - B.y, A.y + B.x);
 }
 
-template <int N>
+template <int N, int SRC>
 __global__ void __launch_bounds__(PassCfg<N>::ZT, LPT2_Z_MINB) k_z_r2c(ZR2CArgs a) {
   using C = PassCfg<N>;
   extern __shared__ float2 smem[];
@@ -119,16 +120,16 @@ __global__ void __launch_bounds__(PassCfg<N>::ZT, LPT2_Z_MINB) k_z_r2c(ZR2CArgs 
   float2 v[C::RMAX];
 #pragma unroll
   for (int r = 0; r < C::RMAX; ++r) {
-    const int n = t + r * C::TPP;
+    const int n = elem<N>(t, r);
     float fa, fb;
-    if (a.src == Z_NOISE) {
+    if (SRC == Z_NOISE) {
       const uint64_t ca = (uint64_t)rowa * N + n, cb = (uint64_t)rowb * N + n;
       fa = philox_gauss(ca, a.seed_lo, a.seed_hi);
       fb = philox_gauss(cb, a.seed_lo, a.seed_hi);
     } else {
       fa = __ldg(a.in + (size_t)rowa * N + n);
       fb = __ldg(a.in + (size_t)rowb * N + n);
-      if (a.src == Z_DENSITY) { fa -= 1.0f; fb -= 1.0f; }
+      if (SRC == Z_DENSITY) { fa -= 1.0f; fb -= 1.0f; }
     }
     v[r] = make_float2(fa, fb);
   }
@@ -151,12 +152,12 @@ __global__ void __launch_bounds__(PassCfg<N>::ZT, LPT2_Z_MINB) k_z_c2r(ZC2RArgs 
   const float2* rb = a.in + (size_t)rowb * C::H;
   float2 v[C::RMAX];
 #pragma unroll
-  for (int r = 0; r < C::RMAX; ++r) v[r] = z_assemble<N>(ra, rb, t + r * C::TPP, 0.f, 0, 0);
+  for (int r = 0; r < C::RMAX; ++r) v[r] = z_assemble<N>(ra, rb, elem<N>(t, r), 0.f, 0, 0);
   __syncthreads();
   fft<N, true>(v, t, sm, s_tw);
 #pragma unroll
   for (int r = 0; r < C::RMAX; ++r) {
-    const int n = t + r * C::TPP;
+    const int n = elem<N>(t, r);
     const size_t ea = (size_t)rowa * N + n, eb = (size_t)rowb * N + n;
     a.out[ea] = a.add_in ? v[r].x + __ldg(a.add_in + ea) : v[r].x;
     a.out[eb] = a.add_in ? v[r].y + __ldg(a.add_in + eb) : v[r].y;
@@ -185,7 +186,7 @@ __global__ void __launch_bounds__(PassCfg<N>::ZT, LPT2_Z_MINB) k_z_source(ZSourc
       float2 v[C::RMAX];
 #pragma unroll
       for (int r = 0; r < C::RMAX; ++r)
-        v[r] = z_assemble<N>(a.in[2 * pr] + off, a.in[2 * pr + 1] + off, t + r * C::TPP, a.g.kf,
+        v[r] = z_assemble<N>(a.in[2 * pr] + off, a.in[2 * pr + 1] + off, elem<N>(t, r), a.g.kf,
                              a.ord[2 * pr], a.ord[2 * pr + 1]);
       fft<N, true>(v, t, sm, s_tw);
 #pragma unroll
@@ -209,39 +210,35 @@ __global__ void __launch_bounds__(PassCfg<N>::ZT, LPT2_Z_MINB) k_z_source(ZSourc
   z_store_pair<N>(v, t, sm, a.out + (size_t)rows[0] * C::H, a.out + (size_t)rows[1] * C::H);
 }
 
-// Adds w0 to rho[b + iz] and w1 to rho[b + jz], jz = (iz + 1) mod N.  When the
-// pair sits inside one aligned group of four floats it is a single 16-byte
-// vector atomic (sm_90+), otherwise two scalar atomics.
+// Periodic CIC deposit of one unit-mass particle per lane at grid coordinates u
+// (cells), with all 32 lanes of the warp active.  When neighbouring lanes carry
+// particles that are neighbours along z (the z pass gives each warp 32
+// consecutive particles of one row), the upper z weight of lane i and the lower
+// z weight of lane i+1 usually land in the same cell: they are summed with one
+// shuffle and deposited by a single atomic, so about 5 instead of 8 float
+// atomics are issued per particle.
 template <int N>
-__device__ __forceinline__ void add_zpair(float* __restrict__ rho, size_t b, int iz, int jz, float w0, float w1) {
-  const int q = iz & 3;
-  if (q != 3) {
-    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (q == 0) { v.x = w0; v.y = w1; }
-    else if (q == 1) { v.y = w0; v.z = w1; }
-    else { v.z = w0; v.w = w1; }
-    atomicAdd(reinterpret_cast<float4*>(rho + b + (iz - q)), v);
-  } else {
-    atomicAdd(rho + b + iz, w0);
-    atomicAdd(rho + b + jz, w1);
-  }
-}
-
-// Periodic CIC deposit of one unit-mass particle at grid coordinates u (cells).
-template <int N>
-__device__ __forceinline__ void cic_deposit(float* __restrict__ rho, float ux, float uy, float uz) {
+__device__ __forceinline__ void cic_deposit_merged(float* __restrict__ rho, float ux, float uy, float uz) {
+  const int lane = threadIdx.x & 31;
   const float fx = floorf(ux), fy = floorf(uy), fz = floorf(uz);
   const float dx = ux - fx, dy = uy - fy, dz = uz - fz;
-  const int ix = ((int)fx) & (N - 1), iy = ((int)fy) & (N - 1), iz = ((int)fz) & (N - 1);
-  const int jx = (ix + 1) & (N - 1), jy = (iy + 1) & (N - 1), jz = (iz + 1) & (N - 1);
-  const float wx0 = 1.f - dx, wy0 = 1.f - dy, wz0 = 1.f - dz;
-  const size_t b00 = ((size_t)ix * N + iy) * N, b01 = ((size_t)ix * N + jy) * N;
-  const size_t b10 = ((size_t)jx * N + iy) * N, b11 = ((size_t)jx * N + jy) * N;
-  float w;
-  w = wx0 * wy0; add_zpair<N>(rho, b00, iz, jz, w * wz0, w * dz);
-  w = wx0 * dy;  add_zpair<N>(rho, b01, iz, jz, w * wz0, w * dz);
-  w = dx * wy0;  add_zpair<N>(rho, b10, iz, jz, w * wz0, w * dz);
-  w = dx * dy;   add_zpair<N>(rho, b11, iz, jz, w * wz0, w * dz);
+  const int ix = wrap_idx<N>((int)fx), iy = wrap_idx<N>((int)fy), cz = wrap_idx<N>((int)fz);
+#pragma unroll
+  for (int corner = 0; corner < 4; ++corner) {
+    const int ox = corner >> 1, oy = corner & 1;
+    const int key = wrap_idx<N>(ix + ox) * N + wrap_idx<N>(iy + oy);
+    const float wxy = (ox ? dx : 1.f - dx) * (oy ? dy : 1.f - dy);
+    float w0 = wxy * (1.f - dz);
+    const float w1 = wxy * dz;
+    const int pkey = __shfl_up_sync(0xffffffffu, key, 1), pcz = __shfl_up_sync(0xffffffffu, cz, 1);
+    const float pw1 = __shfl_up_sync(0xffffffffu, w1, 1);
+    const int nkey = __shfl_down_sync(0xffffffffu, key, 1), ncz = __shfl_down_sync(0xffffffffu, cz, 1);
+    if (lane > 0 && pkey == key && pcz + 1 == cz) w0 += pw1;             // take the left neighbour's
+    const bool give = lane < 31 && nkey == key && cz + 1 == ncz;          // right neighbour takes mine
+    float* row = rho + (size_t)key * N;
+    atomicAdd(row + cz, w0);
+    if (!give) atomicAdd(row + wrap_idx<N>(cz + 1), w1);
+  }
 }
 
 // wrap grid coordinate into [0, N)
@@ -277,15 +274,15 @@ __global__ void __launch_bounds__(PassCfg<N>::ZT, LPT2_Z_MINB) k_z_final(ZFinalA
 #pragma unroll
     for (int r = 0; r < C::RMAX; ++r)
       v[r] = z_assemble<N>(in[0] + (size_t)rows[0] * C::H, in[0] + (size_t)rows[1] * C::H,
-                           t + r * C::TPP, kf, 1, 1);
+                           elem<N>(t, r), kf, 1, 1);
     fft<N, true>(v, t, sm, s_tw);
 #pragma unroll
     for (int r = 0; r < C::RMAX; ++r) {
       if (set == 0) { pz[0][r] = v[r].x; pz[1][r] = v[r].y; }
       else { pz[0][r] += v[r].x; pz[1][r] += v[r].y; }
       if (outp) {
-        outp[2 * n3 + (size_t)rows[0] * N + t + r * C::TPP] = v[r].x;
-        outp[2 * n3 + (size_t)rows[1] * N + t + r * C::TPP] = v[r].y;
+        outp[2 * n3 + (size_t)rows[0] * N + elem<N>(t, r)] = v[r].x;
+        outp[2 * n3 + (size_t)rows[1] * N + elem<N>(t, r)] = v[r].y;
       }
     }
   }
@@ -299,14 +296,14 @@ __global__ void __launch_bounds__(PassCfg<N>::ZT, LPT2_Z_MINB) k_z_final(ZFinalA
       float2 v[C::RMAX];
 #pragma unroll
       for (int r = 0; r < C::RMAX; ++r)
-        v[r] = z_assemble<N>(in[2] + off, in[1] + off, t + r * C::TPP, kf, 0, 0);
+        v[r] = z_assemble<N>(in[2] + off, in[1] + off, elem<N>(t, r), kf, 0, 0);
       fft<N, true>(v, t, sm, s_tw);
 #pragma unroll
       for (int r = 0; r < C::RMAX; ++r) {
         if (set == 0) { px[r] = v[r].x; py[r] = v[r].y; }
         else { px[r] += v[r].x; py[r] += v[r].y; }
         if (outp) {
-          const size_t e = (size_t)rows[h] * N + t + r * C::TPP;
+          const size_t e = (size_t)rows[h] * N + elem<N>(t, r);
           outp[e] = v[r].x;
           outp[n3 + e] = v[r].y;
         }
@@ -316,7 +313,7 @@ __global__ void __launch_bounds__(PassCfg<N>::ZT, LPT2_Z_MINB) k_z_final(ZFinalA
     const int ix = rows[h] / N, iy = rows[h] % N;
 #pragma unroll
     for (int r = 0; r < C::RMAX; ++r) {
-      const int iz = t + r * C::TPP;
+      const int iz = elem<N>(t, r);
       const float ux = wrapN<N>((float)ix + px[r] * a.g.inv_cell);
       const float uy = wrapN<N>((float)iy + py[r] * a.g.inv_cell);
       const float uz = wrapN<N>((float)iz + pz[h][r] * a.g.inv_cell);
@@ -326,7 +323,7 @@ __global__ void __launch_bounds__(PassCfg<N>::ZT, LPT2_Z_MINB) k_z_final(ZFinalA
         a.pos[n3 + e] = uy * a.g.cell;
         a.pos[2 * n3 + e] = uz * a.g.cell;
       }
-      if (a.rho) cic_deposit<N>(a.rho, ux, uy, uz);
+      if (a.rho) cic_deposit_merged<N>(a.rho, ux, uy, uz);
     }
   }
 }
@@ -343,8 +340,8 @@ __device__ __forceinline__ void cic_gather_grad(const float* __restrict__ g, con
   const float uz = wrapN<N>(__ldg(pos + 2 * n3 + e) * inv_cell);
   const float fx = floorf(ux), fy = floorf(uy), fz = floorf(uz);
   const float dx = ux - fx, dy = uy - fy, dz = uz - fz;
-  const int ix = ((int)fx) & (N - 1), iy = ((int)fy) & (N - 1), iz = ((int)fz) & (N - 1);
-  const int jx = (ix + 1) & (N - 1), jy = (iy + 1) & (N - 1), jz = (iz + 1) & (N - 1);
+  const int ix = wrap_idx<N>((int)fx), iy = wrap_idx<N>((int)fy), iz = wrap_idx<N>((int)fz);
+  const int jx = wrap_idx<N>(ix + 1), jy = wrap_idx<N>(iy + 1), jz = wrap_idx<N>(iz + 1);
   const float wx[2] = {1.f - dx, dx}, wy[2] = {1.f - dy, dy}, wz[2] = {1.f - dz, dz};
   const int cx[2] = {ix, jx}, cy[2] = {iy, jy}, cz[2] = {iz, jz};
   float ax = 0.f, ay = 0.f, az = 0.f;
@@ -386,7 +383,7 @@ __global__ void __launch_bounds__(PassCfg<N>::ZT, LPT2_Z_MINB) k_z_adj_final(ZAd
 #pragma unroll
     for (int r = 0; r < C::RMAX; ++r) {
       float gx = 0.f, gy = 0.f, gz = 0.f;
-      const size_t e = (size_t)rows[h] * N + t + r * C::TPP;
+      const size_t e = (size_t)rows[h] * N + elem<N>(t, r);
       if (a.grho) cic_gather_grad<N>(a.grho, a.pos, e, n3, a.g.inv_cell, gx, gy, gz);
       if (a.gpos) {
         gx += __ldg(a.gpos + e);
@@ -429,7 +426,7 @@ __global__ void __launch_bounds__(PassCfg<N>::ZT, LPT2_Z_MINB) k_z_adj_source(ZA
     float2 v[C::RMAX];
 #pragma unroll
     for (int r = 0; r < C::RMAX; ++r)
-      v[r] = z_assemble<N>(a.hs + (size_t)rows[0] * C::H, a.hs + (size_t)rows[1] * C::H, t + r * C::TPP,
+      v[r] = z_assemble<N>(a.hs + (size_t)rows[0] * C::H, a.hs + (size_t)rows[1] * C::H, elem<N>(t, r),
                            kf, 0, 0);
     fft<N, true>(v, t, sm, s_tw);
 #pragma unroll
@@ -441,11 +438,11 @@ __global__ void __launch_bounds__(PassCfg<N>::ZT, LPT2_Z_MINB) k_z_adj_source(ZA
     float2 A[C::RMAX], B[C::RMAX];
 #pragma unroll
     for (int r = 0; r < C::RMAX; ++r)
-      A[r] = z_assemble<N>(a.in[0] + off, a.in[1] + off, t + r * C::TPP, kf, a.ord[0], a.ord[1]);
+      A[r] = z_assemble<N>(a.in[0] + off, a.in[1] + off, elem<N>(t, r), kf, a.ord[0], a.ord[1]);
     fft<N, true>(A, t, sm, s_tw);                       // (phi_xx, phi_yy)
 #pragma unroll
     for (int r = 0; r < C::RMAX; ++r)
-      B[r] = z_assemble<N>(a.in[2] + off, a.in[3] + off, t + r * C::TPP, kf, a.ord[2], a.ord[3]);
+      B[r] = z_assemble<N>(a.in[2] + off, a.in[3] + off, elem<N>(t, r), kf, a.ord[2], a.ord[3]);
     fft<N, true>(B, t, sm, s_tw);                       // (phi_zz, phi_xy)
 #pragma unroll
     for (int r = 0; r < C::RMAX; ++r) {
@@ -461,7 +458,7 @@ __global__ void __launch_bounds__(PassCfg<N>::ZT, LPT2_Z_MINB) k_z_adj_source(ZA
     __syncthreads();
 #pragma unroll
     for (int r = 0; r < C::RMAX; ++r)
-      A[r] = z_assemble<N>(a.in[4] + off, a.in[5] + off, t + r * C::TPP, kf, a.ord[4], a.ord[5]);
+      A[r] = z_assemble<N>(a.in[4] + off, a.in[5] + off, elem<N>(t, r), kf, a.ord[4], a.ord[5]);
     fft<N, true>(A, t, sm, s_tw);                       // (phi_xz, phi_yz)
 #pragma unroll
     for (int r = 0; r < C::RMAX; ++r) A[r] = make_float2(-2.f * gs[h][r] * A[r].x, -2.f * gs[h][r] * A[r].y);
@@ -494,31 +491,31 @@ __global__ void __launch_bounds__(PassCfg<N>::XT) k_y(YArgs a) {
         if (a.job.dst[i] != o) continue;
         float2 v[C::RMAX];
 #pragma unroll
-        for (int r = 0; r < C::RMAX; ++r) v[r] = a.job.in[i][base + (size_t)(t + r * C::TPP) * C::H];
+        for (int r = 0; r < C::RMAX; ++r) v[r] = a.job.in[i][base + (size_t)(elem<N>(t, r)) * C::H];
         fft<N, false>(v, t, sm, s_tw);
 #pragma unroll
         for (int r = 0; r < C::RMAX; ++r) {
-          const int n = t + r * C::TPP;
+          const int n = elem<N>(t, r);
           acc[r] = cadd(acc[r], dconj(v[r], a.g.kf * (float)mode_of(n, N), a.job.ord[i]));
         }
       }
       float2* dst = a.job.out[o];
 #pragma unroll
-      for (int r = 0; r < C::RMAX; ++r) dst[base + (size_t)(t + r * C::TPP) * C::H] = acc[r];
+      for (int r = 0; r < C::RMAX; ++r) dst[base + (size_t)(elem<N>(t, r)) * C::H] = acc[r];
     }
     return;
   }
   for (int i = 0; i < a.job.n_in; ++i) {
     float2 in[C::RMAX];
 #pragma unroll
-    for (int r = 0; r < C::RMAX; ++r) in[r] = a.job.in[i][base + (size_t)(t + r * C::TPP) * C::H];
+    for (int r = 0; r < C::RMAX; ++r) in[r] = a.job.in[i][base + (size_t)(elem<N>(t, r)) * C::H];
     for (int o = 0; o < a.job.n_out; ++o) {
       if (a.job.src[o] != i) continue;
       const int m = a.job.ord[o];
       float2 v[C::RMAX];
 #pragma unroll
       for (int r = 0; r < C::RMAX; ++r) {
-        const int n = t + r * C::TPP;
+        const int n = elem<N>(t, r);
         const int my = mode_of(n, N);
         v[r] = (m != 0 && n == C::H) ? make_float2(0.f, 0.f) : deriv(in[r], a.g.kf * (float)my, m);
       }
@@ -526,7 +523,7 @@ __global__ void __launch_bounds__(PassCfg<N>::XT) k_y(YArgs a) {
       else fft<N, false>(v, t, sm, s_tw);
       float2* dst = a.job.out[o];
 #pragma unroll
-      for (int r = 0; r < C::RMAX; ++r) dst[base + (size_t)(t + r * C::TPP) * C::H] = v[r];
+      for (int r = 0; r < C::RMAX; ++r) dst[base + (size_t)(elem<N>(t, r)) * C::H] = v[r];
     }
   }
 }
@@ -556,16 +553,17 @@ __device__ __forceinline__ float sqrt_pk(const DevCosmo& c, float k) {
 }
 
 // Exact integer P(k) shell of mode (mx, my, mz): b = floor(2 ns |n| / N) for
-// 0 < |n| < N/2, else -1.
+// 0 < |n| < N/2, else -1.  A float estimate is corrected by exact 64-bit integer
+// comparisons (b N)^2 <= 4 ns^2 |n|^2 < ((b+1) N)^2; no 64-bit int/float conversion.
 template <int N>
-__device__ __forceinline__ int shell_of(int mx, int my, int mz, int ns, long long& n2) {
-  n2 = (long long)mx * mx + (long long)my * my + (long long)mz * mz;
-  if (n2 == 0 || 4 * n2 >= (long long)N * N) return -1;
-  const long long M = 4LL * ns * ns * n2;
-  long long s = (long long)sqrtf((float)M);
-  while ((s + 1) * (s + 1) <= M) ++s;
-  while (s * s > M) --s;
-  return (int)(s / N);
+__device__ __forceinline__ int shell_of(int mx, int my, int mz, int ns, int& n2) {
+  n2 = mx * mx + my * my + mz * mz;                 // < 3 (N/2)^2: exact in int32 and in float
+  if (n2 == 0 || 4 * n2 >= N * N) return -1;
+  const long long M = 4LL * ns * ns * (long long)n2;
+  int b = (int)(sqrtf((float)n2) * (2.0f * (float)ns / (float)N));
+  while (b > 0 && (long long)(b * N) * (long long)(b * N) > M) --b;
+  while ((long long)((b + 1) * N) * (long long)((b + 1) * N) <= M) ++b;
+  return b;
 }
 
 // Sum of a float over the warp (all lanes participate).
@@ -575,8 +573,8 @@ __device__ __forceinline__ float warp_sum(float x) {
   return x;
 }
 
-// CTA = (kz block of W, fixed ky). Thread tid = t * W + w; kx = t + r TPP.
-template <int N>
+// CTA = (kz block of W, fixed ky). Thread tid = t * W + w; kx = elem(t, r).
+template <int N, int MODE>
 __global__ void __launch_bounds__(PassCfg<N>::XT) k_x(XArgs a) {
   using C = PassCfg<N>;
   extern __shared__ float2 smem[];
@@ -595,49 +593,49 @@ __global__ void __launch_bounds__(PassCfg<N>::XT) k_x(XArgs a) {
   const bool ny_nyq = (ky == C::H);
   const float kf = a.g.kf;
   const size_t blk = (size_t)blockIdx.y * gridDim.x + blockIdx.x;
-  if (a.mode == X_PK) {
+  if (MODE == X_PK) {
     for (int i = threadIdx.x; i < NWARP * 3 * a.n_shells; i += blockDim.x) s_acc[i] = 0.0;
-  } else if (a.mode == X_ADJ_SOURCE) {
+  } else if (MODE == X_ADJ_SOURCE) {
     for (int i = threadIdx.x; i < NWARP; i += blockDim.x) s_acc[i] = 0.0;
   }
   __syncthreads();
 
   float2 v[C::RMAX];
-  const bool adjoint = (a.mode == X_ADJ_SOURCE || a.mode == X_ADJ_DELTA);
+  const bool adjoint = (MODE == X_ADJ_SOURCE || MODE == X_ADJ_DELTA);
   if (adjoint) {
     // forward x transform of each x-order group, summed with conj((i kx)^m)
-    const int ng = (a.mode == X_ADJ_SOURCE) ? 2 : 3;
+    const int ng = (MODE == X_ADJ_SOURCE) ? 2 : 3;
 #pragma unroll
     for (int r = 0; r < C::RMAX; ++r) v[r] = make_float2(0.f, 0.f);
     for (int gi = 0; gi < ng; ++gi) {
       float2 u[C::RMAX];
 #pragma unroll
-      for (int r = 0; r < C::RMAX; ++r) u[r] = a.in2[gi][base + (size_t)(t + r * C::TPP) * stride];
+      for (int r = 0; r < C::RMAX; ++r) u[r] = a.in2[gi][base + (size_t)(elem<N>(t, r)) * stride];
       fft<N, false>(u, t, sm, s_tw);
 #pragma unroll
       for (int r = 0; r < C::RMAX; ++r) {
-        const int kx = t + r * C::TPP;
+        const int kx = elem<N>(t, r);
         v[r] = cadd(v[r], dconj(u[r], kf * (float)mode_of(kx, N), gi));
       }
     }
   } else {
 #pragma unroll
-    for (int r = 0; r < C::RMAX; ++r) v[r] = a.in[base + (size_t)(t + r * C::TPP) * stride];
-    if (a.mode == X_INV) {
+    for (int r = 0; r < C::RMAX; ++r) v[r] = a.in[base + (size_t)(elem<N>(t, r)) * stride];
+    if (MODE == X_INV) {
       fft<N, true>(v, t, sm, s_tw);
 #pragma unroll
-      for (int r = 0; r < C::RMAX; ++r) a.out[0][base + (size_t)(t + r * C::TPP) * stride] = v[r];
+      for (int r = 0; r < C::RMAX; ++r) a.out[0][base + (size_t)(elem<N>(t, r)) * stride] = v[r];
       return;
     }
-    if (a.mode != X_PHI) fft<N, false>(v, t, sm, s_tw);
-    if (a.mode == X_FWD) {
+    if (MODE != X_PHI) fft<N, false>(v, t, sm, s_tw);
+    if (MODE == X_FWD) {
 #pragma unroll
-      for (int r = 0; r < C::RMAX; ++r) a.out[0][base + (size_t)(t + r * C::TPP) * stride] = v[r];
+      for (int r = 0; r < C::RMAX; ++r) a.out[0][base + (size_t)(elem<N>(t, r)) * stride] = v[r];
       return;
     }
   }
 
-  if (a.mode == X_PK) {
+  if (MODE == X_PK) {
     // P(k) shells.  Lanes of a warp see neighbouring modes, so they fall in few
     // shells: for each distinct shell in the warp the lanes of that shell are
     // summed (at most 32 terms, FP32) and one lane adds the sums to this warp's
@@ -647,8 +645,8 @@ __global__ void __launch_bounds__(PassCfg<N>::XT) k_x(XArgs a) {
     double* s_mine = s_acc + warp * 3 * ns;
 #pragma unroll
     for (int r = 0; r < C::RMAX; ++r) {
-      const int kx = t + r * C::TPP;
-      long long n2;
+      const int kx = elem<N>(t, r);
+      int n2;
       const int b = shell_of<N>(mode_of(kx, N), my, mz, ns, n2);
       const int wgt = (b < 0) ? 0 : ((mz == 0) ? 1 : 2);
       const float pv = (v[r].x * v[r].x + v[r].y * v[r].y) * pnorm * (float)wgt;
@@ -683,24 +681,24 @@ __global__ void __launch_bounds__(PassCfg<N>::XT) k_x(XArgs a) {
     return;
   }
 
-  if (a.mode == X_PKADJ) {
+  if (MODE == X_PKADJ) {
     // d P_b / d delta_rho: multiply delta_rho(k) by the per-shell weight, back along x
 #pragma unroll
     for (int r = 0; r < C::RMAX; ++r) {
-      const int kx = t + r * C::TPP;
-      long long n2;
+      const int kx = elem<N>(t, r);
+      int n2;
       const int b = shell_of<N>(mode_of(kx, N), my, mz, a.n_shells, n2);
       v[r] = cscale(v[r], b < 0 ? 0.f : __ldg(a.shell_w + b));
     }
     fft<N, true>(v, t, sm, s_tw);
 #pragma unroll
-    for (int r = 0; r < C::RMAX; ++r) a.out[0][base + (size_t)(t + r * C::TPP) * stride] = v[r];
+    for (int r = 0; r < C::RMAX; ++r) a.out[0][base + (size_t)(elem<N>(t, r)) * stride] = v[r];
     return;
   }
 
-  if (a.mode == X_SOURCE && a.s_out) {
+  if (MODE == X_SOURCE && a.s_out) {
 #pragma unroll
-    for (int r = 0; r < C::RMAX; ++r) a.s_out[base + (size_t)(t + r * C::TPP) * stride] = v[r];
+    for (int r = 0; r < C::RMAX; ++r) a.s_out[base + (size_t)(elem<N>(t, r)) * stride] = v[r];
   }
 
   // k-space multipliers. g = potential to transform back along x.
@@ -709,22 +707,22 @@ __global__ void __launch_bounds__(PassCfg<N>::XT) k_x(XArgs a) {
   float theta = 0.f;
 #pragma unroll
   for (int r = 0; r < C::RMAX; ++r) {
-    const int kx = t + r * C::TPP;
+    const int kx = elem<N>(t, r);
     const int mx = mode_of(kx, N);
     const bool zero = ny_nyq || kx == C::H || (mx == 0 && my == 0 && mz == 0);
     const float k2 = kf * kf * (float)(mx * mx + my * my + mz * mz);
     const float k = sqrtf(k2);
     const float inv = zero ? 0.f : a.g.inv_n3 / k2;
     const size_t e = base + (size_t)kx * stride;
-    if (a.mode == X_DELTA) {
+    if (MODE == X_DELTA) {
       const float sc = zero ? 0.f : sqrt_pk(cz, k) * a.g.sqrt_n3_over_v;
       const float2 d = cscale(v[r], sc);
       if (a.delta_out) a.delta_out[e] = d;
       g[r] = cscale(d, inv);                                // phi1 = delta / k^2 (1/N^3 folded)
       if (a.split) hpot[r] = cscale(g[r], zero ? 0.f : interp_table(a.d1f, cz, k));
-    } else if (a.mode == X_PHI) {                           // v = delta(k) already
+    } else if (MODE == X_PHI) {                           // v = delta(k) already
       g[r] = cscale(v[r], inv);
-    } else if (a.mode == X_SOURCE) {                        // v = S(k)
+    } else if (MODE == X_SOURCE) {                        // v = S(k)
       const float d2 = zero ? 0.f : interp_table(a.d2f, cz, k);
       float2 u = cscale(v[r], -d2 * inv);                   // phi2 = -S D2 / k^2
       if (!a.split) {
@@ -733,7 +731,7 @@ __global__ void __launch_bounds__(PassCfg<N>::XT) k_x(XArgs a) {
         u = cadd(u, cscale(dl, d1 * inv));                  // + phi1 D1 (total potential)
       }
       g[r] = u;
-    } else if (a.mode == X_ADJ_SOURCE) {                    // v = g_u(k)
+    } else if (MODE == X_ADJ_SOURCE) {                    // v = g_u(k)
       const float2 gu = zero ? make_float2(0.f, 0.f) : v[r];
       const float d1 = zero ? 0.f : interp_table(a.d1f, cz, k);
       const float d2 = zero ? 0.f : interp_table(a.d2f, cz, k);
@@ -751,30 +749,30 @@ __global__ void __launch_bounds__(PassCfg<N>::XT) k_x(XArgs a) {
       g[r] = cscale(h, sc);                                 // s(k) (h_Psi + h_phi)
     }
   }
-  if (a.mode == X_ADJ_SOURCE) {
+  if (MODE == X_ADJ_SOURCE) {
     const float ws = warp_sum(theta);
     if (lane == 0) s_acc[warp] = (double)ws;
   }
   // x-inverse transforms with x-derivative orders
   int nout;
-  if (a.mode == X_DELTA) nout = a.split ? 5 : 3;
-  else if (a.mode == X_PHI) nout = 3;
-  else if (a.mode == X_SOURCE) nout = 2;
+  if (MODE == X_DELTA) nout = a.split ? 5 : 3;
+  else if (MODE == X_PHI) nout = 3;
+  else if (MODE == X_SOURCE) nout = 2;
   else nout = 1;
   for (int o = 0; o < nout; ++o) {
-    const bool fromh = (a.mode == X_DELTA) && o >= 3;
-    const int m = (a.mode == X_DELTA || a.mode == X_PHI) ? (o < 3 ? o : o - 3) : (a.mode == X_SOURCE ? o : 0);
+    const bool fromh = (MODE == X_DELTA) && o >= 3;
+    const int m = (MODE == X_DELTA || MODE == X_PHI) ? (o < 3 ? o : o - 3) : (MODE == X_SOURCE ? o : 0);
     float2 u[C::RMAX];
 #pragma unroll
     for (int r = 0; r < C::RMAX; ++r) {
-      const int kx = t + r * C::TPP;
+      const int kx = elem<N>(t, r);
       u[r] = deriv(fromh ? hpot[r] : g[r], kf * (float)mode_of(kx, N), m);
     }
     fft<N, true>(u, t, sm, s_tw);
 #pragma unroll
-    for (int r = 0; r < C::RMAX; ++r) a.out[o][base + (size_t)(t + r * C::TPP) * stride] = u[r];
+    for (int r = 0; r < C::RMAX; ++r) a.out[o][base + (size_t)(elem<N>(t, r)) * stride] = u[r];
   }
-  if (a.mode == X_ADJ_SOURCE && threadIdx.x == 0) {
+  if (MODE == X_ADJ_SOURCE && threadIdx.x == 0) {
     double acc = 0.0;
     for (int wi = 0; wi < NWARP; ++wi) acc += s_acc[wi];   // fixed order (barriers inside fft)
     a.theta_part[blk] = acc;
@@ -782,11 +780,19 @@ __global__ void __launch_bounds__(PassCfg<N>::XT) k_x(XArgs a) {
 }
 
 // ================================================================ launchers
-template <int N> cudaError_t launch_z_r2c_t(const ZR2CArgs& a, cudaStream_t s) {
+template <int N, int SRC> cudaError_t launch_z_r2c_m(const ZR2CArgs& a, cudaStream_t s) {
   using C = PassCfg<N>;
-  cudaFuncSetAttribute(k_z_r2c<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::ZSMEM);
-  k_z_r2c<N><<<N * N / 2 / C::ZP, C::ZT, C::ZSMEM, s>>>(a);
+  cudaFuncSetAttribute(k_z_r2c<N, SRC>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::ZSMEM);
+  k_z_r2c<N, SRC><<<N * N / 2 / C::ZP, C::ZT, C::ZSMEM, s>>>(a);
   return cudaGetLastError();
+}
+template <int N> cudaError_t launch_z_r2c_t(const ZR2CArgs& a, cudaStream_t s) {
+  switch (a.src) {
+    case Z_NOISE: return launch_z_r2c_m<N, Z_NOISE>(a, s);
+    case Z_REAL: return launch_z_r2c_m<N, Z_REAL>(a, s);
+    case Z_DENSITY: return launch_z_r2c_m<N, Z_DENSITY>(a, s);
+    default: return cudaErrorInvalidValue;
+  }
 }
 template <int N> cudaError_t launch_z_c2r_t(const ZC2RArgs& a, cudaStream_t s) {
   using C = PassCfg<N>;
@@ -824,13 +830,27 @@ template <int N> cudaError_t launch_y_t(const YArgs& a, cudaStream_t s) {
   k_y<N><<<dim3(C::H / C::W, N), C::XT, C::XSMEM, s>>>(a);
   return cudaGetLastError();
 }
-template <int N> cudaError_t launch_x_t(const XArgs& a, cudaStream_t s) {
+template <int N, int MODE> cudaError_t launch_x_m(const XArgs& a, cudaStream_t s) {
   using C = PassCfg<N>;
-  const int smem = C::XSMEM + (a.mode == X_PK ? (C::XT / 32) * 3 * a.n_shells * 8
-                                              : (a.mode == X_ADJ_SOURCE ? (C::XT / 32) * 8 : 0));
-  cudaFuncSetAttribute(k_x<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  k_x<N><<<dim3(C::H / C::W, N), C::XT, smem, s>>>(a);
+  const int smem = C::XSMEM + (MODE == X_PK ? (C::XT / 32) * 3 * a.n_shells * 8
+                                            : (MODE == X_ADJ_SOURCE ? (C::XT / 32) * 8 : 0));
+  cudaFuncSetAttribute(k_x<N, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  k_x<N, MODE><<<dim3(C::H / C::W, N), C::XT, smem, s>>>(a);
   return cudaGetLastError();
+}
+template <int N> cudaError_t launch_x_t(const XArgs& a, cudaStream_t s) {
+  switch (a.mode) {
+    case X_DELTA: return launch_x_m<N, X_DELTA>(a, s);
+    case X_SOURCE: return launch_x_m<N, X_SOURCE>(a, s);
+    case X_PK: return launch_x_m<N, X_PK>(a, s);
+    case X_FWD: return launch_x_m<N, X_FWD>(a, s);
+    case X_INV: return launch_x_m<N, X_INV>(a, s);
+    case X_PHI: return launch_x_m<N, X_PHI>(a, s);
+    case X_PKADJ: return launch_x_m<N, X_PKADJ>(a, s);
+    case X_ADJ_SOURCE: return launch_x_m<N, X_ADJ_SOURCE>(a, s);
+    case X_ADJ_DELTA: return launch_x_m<N, X_ADJ_DELTA>(a, s);
+    default: return cudaErrorInvalidValue;
+  }
 }
 template <int N> int x_blocks_t() { return (PassCfg<N>::H / PassCfg<N>::W) * N; }
 

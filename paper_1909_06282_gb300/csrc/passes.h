@@ -166,7 +166,9 @@ struct CicArgs {
 LPT2_DECLARE_LAUNCHERS(16)
 LPT2_DECLARE_LAUNCHERS(32)
 LPT2_DECLARE_LAUNCHERS(64)
+LPT2_DECLARE_LAUNCHERS(96)
 LPT2_DECLARE_LAUNCHERS(128)
+LPT2_DECLARE_LAUNCHERS(192)
 LPT2_DECLARE_LAUNCHERS(256)
 LPT2_DECLARE_LAUNCHERS(512)
 LPT2_DECLARE_LAUNCHERS(1024)

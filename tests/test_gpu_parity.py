@@ -83,7 +83,7 @@ def test_white_noise_against_oracle(n, seed):
     print(f"noise: {np.mean(ulp == 0):.4f} exact, {within1:.6f} within 1 ulp, max {ulp.max()} ulp")
 
 
-@pytest.mark.parametrize("n", [16, 32, 64, 128])
+@pytest.mark.parametrize("n", [16, 32, 64, 96, 128, 192])
 def test_fft_r2c_c2r_against_oracle(n):
     from oracle import fft as of
     plan = lp().Plan(W.Instance(n, 100.0, 1, W.COSMO), n_steps=16)
@@ -116,7 +116,7 @@ def test_growth_tables_against_oracle(fr0, a_out):
 
 
 @pytest.mark.parametrize("n,box,fr0", [(64, 256.0, 1e-5), (32, 200.0, 1e-4), (16, 64.0, 0.0),
-                                       (128, 512.0, 1e-6)])
+                                       (128, 512.0, 1e-6), (96, 384.0, 3e-5)])
 def test_displace_split_against_oracle(n, box, fr0):
     inst = W.Instance(n, box, 1, W.COSMO.replace(fr0_abs=fr0))
     plan = lp().Plan(inst, n_steps=STEPS)

