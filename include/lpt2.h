@@ -49,6 +49,13 @@ enum {
   LPT2_ENOWORKSPACE = -6  /* workspace missing or smaller than required          */
 };
 
+/* Plan flags. */
+enum {
+  LPT2_GRAPH = 1  /* capture lpt2_displace / lpt2_cic_pk into CUDA graphs on first use and
+                     replay them while the argument pointers stay the same (needs a stream
+                     other than the legacy default stream) */
+};
+
 /* D2 variants (the triangle configuration of the second-order growth, Sec. 3). */
 enum { LPT2_D2_T1 = 0 /* k1 = k2 = k/sqrt2, theta = 90 deg: the paper's choice */ };
 
@@ -76,24 +83,32 @@ typedef struct {
 
 typedef struct lpt2_plan_s* lpt2_plan_t;
 
-/* lpt2_plan: create a plan for n_inst instances (n_inst must be 1 in this
- * version) with growth tables on n_k log-spaced wavenumbers in [k_min, k_max]
- * h/Mpc (Sec. 2.4: D1(k,a) is solved per k and interpolated), integrated with
- * n_steps classical RK4 steps in ln a.  cuda_stream is a cudaStream_t (NULL =
- * legacy default stream).  flags: reserved, pass 0.  Allocates the plan's small
- * device tables and computes the P(k) normalisation (sigma_8) and the growth
- * tables on the stream.  Errors: LPT2_EINVAL (null pointers, n_k < 2,
- * k_min <= 0, k_max <= k_min, box <= 0, a range, non-flat cosmology,
- * fr0_abs < 0, n_steps < 1), LPT2_EUNSUPPORTED (n not in the list above,
- * hs_n != 1, d2_variant != T1, n_inst != 1), LPT2_ENOMEM, LPT2_ECUDA. */
+/* lpt2_plan: create a plan for n_inst instances (1 <= n_inst <= 65535) with
+ * growth tables on n_k log-spaced wavenumbers in [k_min, k_max] h/Mpc (Sec. 2.4:
+ * D1(k,a) is solved per k and interpolated), integrated with n_steps classical
+ * RK4 steps in ln a.  Instances share the background cosmology and a_out; seed
+ * and fr0_abs may differ (one growth table per instance).  Instances of equal
+ * grid size must be contiguous in `inst` and share the box; each such group runs
+ * as one batch (every pass kernel covers all its instances).  Per-instance
+ * arrays of the other calls are the instances' arrays concatenated in plan
+ * order.  cuda_stream is a cudaStream_t (NULL = legacy default stream).  flags:
+ * 0 or LPT2_GRAPH.  Allocates the plan's small device tables and computes the
+ * P(k) normalisation (sigma_8) and the growth tables on the stream.  Errors:
+ * LPT2_EINVAL (null pointers, n_k < 2, k_min <= 0, k_max <= k_min, box <= 0,
+ * a range, non-flat cosmology, fr0_abs < 0, n_steps < 1, instance ordering or
+ * differing backgrounds, unknown flags), LPT2_EUNSUPPORTED (n not in the list
+ * above, hs_n != 1, d2_variant != T1, differing boxes within a grid size),
+ * LPT2_ENOMEM, LPT2_ECUDA.  lpt2_white_noise, lpt2_fft_*, lpt2_set_fr0 and
+ * lpt2_displace_vjp need a single-instance plan. */
 int lpt2_plan(lpt2_plan_t* out, const lpt2_instance* inst, int n_inst, int n_k,
               double k_min, double k_max, int n_steps, void* cuda_stream,
               unsigned flags);
 
 int lpt2_plan_destroy(lpt2_plan_t plan);
 
-/* Bytes of caller-owned device scratch the plan needs (21 N^3 floats plus
- * small per-block partial sums). */
+/* Bytes of caller-owned device scratch the plan needs: 21 slots of the largest
+ * group (count N^3 floats each), the CIC density of every instance and small
+ * per-block partial sums. */
 int lpt2_workspace_size(lpt2_plan_t plan, size_t* bytes);
 
 /* Attach scratch: dev_ptr must be 256-byte aligned and >= lpt2_workspace_size
@@ -103,8 +118,9 @@ int lpt2_set_workspace(lpt2_plan_t plan, void* dev_ptr, size_t bytes);
 /* lpt2_growth_tables: D1(k,a_out), D2(k,a_out) of the T1 configuration and
  * their derivatives with respect to ln|f_R0| (Eq. d1, Eq. full-d2 at k1 = k2 =
  * k/sqrt2, theta = 90 deg; D2 sign such that GR gives -3/7 D1^2), recomputed
- * on the plan's stream by the batched FP64 RK4 kernel and copied into the
- * caller's device arrays double[n_k] (each pointer may be NULL). */
+ * on the plan's stream by the batched FP64 RK4 kernel (one thread per
+ * (instance, k)) and copied into the caller's device arrays double[n_inst][n_k]
+ * (each pointer may be NULL). */
 int lpt2_growth_tables(lpt2_plan_t plan, double* d1, double* d2,
                        double* dd1_dlogf, double* dd2_dlogf);
 
@@ -139,7 +155,8 @@ int lpt2_displace(lpt2_plan_t plan, const float* noise, float* psi1, float* psi2
  *   density : float[N^3] density contrast output, or NULL
  *   pk, k_mean : double[n_shells] shell mean of P and of |k| (0 if empty)
  *   n_modes : int64[n_shells] number of modes per shell (full spectrum count)
- * 1 <= n_shells <= 256.  Needs the workspace. */
+ * 1 <= n_shells <= 256; per-instance outputs are [n_inst][n_shells].  Needs the
+ * workspace. */
 int lpt2_cic_pk(lpt2_plan_t plan, const float* pos, float* density, double* pk,
                 double* k_mean, int64_t* n_modes, int n_shells);
 

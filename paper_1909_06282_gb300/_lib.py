@@ -121,24 +121,35 @@ def _stream(stream=None):
 
 
 class Plan:
-    """Owns an lpt2 plan handle and its workspace (a torch uint8 CUDA tensor)."""
+    """Owns an lpt2 plan handle and its workspace (a torch uint8 CUDA tensor).
+
+    `inst` is one instance or a list of instances (equal grid sizes contiguous);
+    `graph=True` sets LPT2_GRAPH (needs a non-default stream)."""
 
     def __init__(self, inst, n_k=512, k_min=1e-4, k_max=10.0, n_steps=1024, stream=None,
-                 workspace=True):
+                 workspace=True, graph=False):
         lib = load_library()
-        c = inst.cosmo
-        cs = _Cosmo(c.omega_m, c.omega_l, c.omega_b, c.h, c.n_s, c.sigma8, c.t_cmb, c.fr0_abs,
-                    int(c.hs_n), c.a_init, 0)
-        self.inst = inst
-        self.n = int(inst.n)
+        insts = list(inst) if isinstance(inst, (list, tuple)) else [inst]
+        self.insts = insts
+        self.inst = insts[0]
+        self.n_inst = len(insts)
+        self.ns = [int(i.n) for i in insts]
+        self.n = self.ns[0]
+        self.cells = sum(n ** 3 for n in self.ns)
         self.n_k = int(n_k)
         self.n_steps = int(n_steps)
-        self._cinst = _Instance(int(inst.n), float(inst.box), int(inst.seed) & (2 ** 64 - 1),
-                                float(getattr(inst, "a_out", 1.0)), cs)
+        arr = (_Instance * self.n_inst)()
+        for j, it in enumerate(insts):
+            c = it.cosmo
+            arr[j] = _Instance(int(it.n), float(it.box), int(it.seed) & (2 ** 64 - 1),
+                               float(getattr(it, "a_out", 1.0)),
+                               _Cosmo(c.omega_m, c.omega_l, c.omega_b, c.h, c.n_s, c.sigma8, c.t_cmb,
+                                      c.fr0_abs, int(c.hs_n), c.a_init, 0))
+        self._cinst = arr
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         h = C.c_void_p()
-        _check(lib.lpt2_plan(C.byref(h), C.byref(self._cinst), 1, self.n_k, float(k_min),
-                             float(k_max), self.n_steps, _stream(self.stream), 0))
+        _check(lib.lpt2_plan(C.byref(h), arr, self.n_inst, self.n_k, float(k_min), float(k_max),
+                             self.n_steps, _stream(self.stream), 1 if graph else 0))
         self.handle = h
         self.workspace = None
         if workspace:
@@ -146,6 +157,15 @@ class Plan:
             _check(lib.lpt2_workspace_size(h, C.byref(nb)))
             self.workspace = torch.empty(nb.value, dtype=torch.uint8, device="cuda")
             _check(lib.lpt2_set_workspace(h, _ptr(self.workspace), nb.value))
+
+    def split(self, flat, per_cell=1):
+        """Views of a flat per-instance-concatenated tensor, one per instance."""
+        out, off = [], 0
+        for n in self.ns:
+            m = per_cell * n ** 3
+            out.append(flat[off:off + m])
+            off += m
+        return out
 
     def close(self):
         if getattr(self, "handle", None) is not None and self.handle.value:
@@ -178,8 +198,10 @@ def lpt2_launch_count(plan: Plan) -> int:
 
 
 def lpt2_growth_tables(plan: Plan):
-    """Returns (D1, D2, dD1/dln|fR0|, dD2/dln|fR0|), float64 CUDA tensors [n_k]."""
-    out = [torch.empty(plan.n_k, dtype=torch.float64, device="cuda") for _ in range(4)]
+    """Returns (D1, D2, dD1/dln|fR0|, dD2/dln|fR0|), float64 CUDA tensors [n_k] (single
+    instance) or [n_inst, n_k]."""
+    shape = (plan.n_k,) if plan.n_inst == 1 else (plan.n_inst, plan.n_k)
+    out = [torch.empty(shape, dtype=torch.float64, device="cuda") for _ in range(4)]
     _check(load_library().lpt2_growth_tables(plan.handle, *[_ptr(t) for t in out]))
     return tuple(out)
 
@@ -202,9 +224,15 @@ def lpt2_philox_words(seed: int, first: int, count: int, stream=None):
 
 def lpt2_displace(plan: Plan, noise=None, psi1=True, psi2=True, pos=True, dk=False):
     """Forward 2LPT map. Returns dict with the requested outputs ('psi1', 'psi2' and 'pos'
-    as float32 (3, N, N, N) tensors, 'dk' as complex64 (N, N, N/2) tensor)."""
+    as float32 (3, N, N, N) tensors, 'dk' as complex64 (N, N, N/2) tensor; for a multi-instance
+    plan flat tensors of the instances' arrays concatenated, see Plan.split)."""
     n = plan.n
-    f3 = lambda: torch.empty((3, n, n, n), dtype=torch.float32, device="cuda")
+    if plan.n_inst == 1:
+        f3 = lambda: torch.empty((3, n, n, n), dtype=torch.float32, device="cuda")
+        dshape = (n, n, n // 2)
+    else:
+        f3 = lambda: torch.empty(3 * plan.cells, dtype=torch.float32, device="cuda")
+        dshape = (plan.cells // 2,)
     out = {}
     want = lambda v: torch.is_tensor(v) or bool(v)
     if want(psi1):
@@ -214,10 +242,9 @@ def lpt2_displace(plan: Plan, noise=None, psi1=True, psi2=True, pos=True, dk=Fal
     if want(pos):
         out["pos"] = pos if torch.is_tensor(pos) else f3()
     if want(dk):
-        out["dk"] = dk if torch.is_tensor(dk) else torch.empty((n, n, n // 2), dtype=torch.complex64,
-                                                               device="cuda")
-    if noise is not None and (noise.dtype != torch.float32 or noise.numel() != n ** 3):
-        raise ValueError("noise must be float32 with N^3 elements")
+        out["dk"] = dk if torch.is_tensor(dk) else torch.empty(dshape, dtype=torch.complex64, device="cuda")
+    if noise is not None and (noise.dtype != torch.float32 or noise.numel() != plan.cells):
+        raise ValueError("noise must be float32 with N^3 elements per instance")
     _check(load_library().lpt2_displace(plan.handle, _ptr(noise), _ptr(out.get("psi1")),
                                         _ptr(out.get("psi2")), _ptr(out.get("pos")),
                                         _ptr(out.get("dk"))))
@@ -228,14 +255,16 @@ def lpt2_cic_pk(plan: Plan, pos=None, density=False, n_shells=32):
     """CIC density contrast and shell P(k). pos None uses the density deposited by the
     last lpt2_displace on this plan."""
     n = plan.n
-    res = dict(pk=torch.empty(n_shells, dtype=torch.float64, device="cuda"),
-               k_mean=torch.empty(n_shells, dtype=torch.float64, device="cuda"),
-               n_modes=torch.empty(n_shells, dtype=torch.int64, device="cuda"))
+    sh = (n_shells,) if plan.n_inst == 1 else (plan.n_inst, n_shells)
+    res = dict(pk=torch.empty(sh, dtype=torch.float64, device="cuda"),
+               k_mean=torch.empty(sh, dtype=torch.float64, device="cuda"),
+               n_modes=torch.empty(sh, dtype=torch.int64, device="cuda"))
     if torch.is_tensor(density) or density:
+        dsh = (n, n, n) if plan.n_inst == 1 else (plan.cells,)
         res["density"] = density if torch.is_tensor(density) else torch.empty(
-            (n, n, n), dtype=torch.float32, device="cuda")
-    if pos is not None and (pos.dtype != torch.float32 or pos.numel() != 3 * n ** 3):
-        raise ValueError("pos must be float32 with 3 N^3 elements")
+            dsh, dtype=torch.float32, device="cuda")
+    if pos is not None and (pos.dtype != torch.float32 or pos.numel() != 3 * plan.cells):
+        raise ValueError("pos must be float32 with 3 N^3 elements per instance")
     _check(load_library().lpt2_cic_pk(plan.handle, _ptr(pos), _ptr(res.get("density")),
                                       _ptr(res["pk"]), _ptr(res["k_mean"]), _ptr(res["n_modes"]),
                                       int(n_shells)))

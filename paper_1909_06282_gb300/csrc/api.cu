@@ -40,9 +40,38 @@ constexpr int kMaxRec = 4096;
 
 }  // namespace
 
-struct lpt2_plan_s {
+// Instances of one grid size run together: every pass kernel covers the whole
+// group (grid z = instance).
+struct Group {
   int n;
   double box;
+  int count;
+  int inst0;       // index of the group's first instance in the plan
+  float2* tw;      // twiddles exp(-2 pi i m / n)
+  size_t off;      // floats before the group's first instance in per-instance real fields
+};
+
+struct GraphCache {  // one captured launch sequence per entry point (LPT2_GRAPH)
+  const void* key[8];
+  cudaGraphExec_t exec;
+  int64_t launches;
+};
+
+struct lpt2_plan_s {
+  // current group (set by set_group): grid side, box, twiddles, batch
+  int n;
+  double box;
+  float2* tw;
+  int cur_batch, cur_inst0;
+  std::vector<Group> groups;
+  int n_inst;
+  uint64_t* seeds_dev;        // [n_inst]
+  double* fr0_dev;            // [n_inst]
+  size_t slot_sz;             // bytes per workspace slot: max over groups of count n^3 4
+  int xb_max;                 // max over groups of count * x-pass blocks
+  size_t total_cells;         // sum over instances of n^3
+  bool use_graph;
+  GraphCache graphs[2] = {};  // lpt2_displace, lpt2_cic_pk
   uint64_t seed;
   double a_out;
   lpt2_cosmo cosmo;
@@ -50,11 +79,10 @@ struct lpt2_plan_s {
   double k_min, k_max;
   int n_steps;
   cudaStream_t stream;
-  float2* tw;
   DevCosmo* cosmo_dev;
   double* partials;
-  double* tab;    // [4][nk]
-  float* tabf;    // [4][nk]: D1, D2, dD1/dln|fR0|, dD2/dln|fR0| in FP32
+  double* tab;    // [n_inst][4][nk]
+  float* tabf;    // [n_inst][4][nk]: D1, D2, dD1/dln|fR0|, dD2/dln|fR0| in FP32
   char* ws;
   size_t ws_bytes;
   int64_t launches;
@@ -68,9 +96,19 @@ struct lpt2_plan_s {
 
 namespace {
 
-double V3(const lpt2_plan_s* p) { return (double)p->n * p->n * p->n; }
+// algorithmic-byte unit of the current group: N^3 times the instances in the launch
+double V3(const lpt2_plan_s* p) { return (double)p->n * p->n * p->n * p->cur_batch; }
 
-size_t slot_bytes(const lpt2_plan_s* p) { return (size_t)p->n * p->n * p->n * sizeof(float); }
+size_t slot_bytes(const lpt2_plan_s* p) { return p->slot_sz; }
+
+void set_group(lpt2_plan_s* p, int gi) {
+  const Group& g = p->groups[gi];
+  p->n = g.n;
+  p->box = g.box;
+  p->tw = g.tw;
+  p->cur_batch = g.count;
+  p->cur_inst0 = g.inst0;
+}
 
 int x_blocks(int n) {
   switch (n) {
@@ -89,11 +127,21 @@ int x_blocks(int n) {
 // Tail of the workspace after the slots: P(k) block partials [x_blocks][3][256],
 // internal pk / k_mean / n_modes [256] each, shell weights [256], dL/dln|fR0|
 // block partials [x_blocks].
-size_t tail_pk_part(const lpt2_plan_s* p) { return N_SLOTS * slot_bytes(p); }
-size_t tail_pk(const lpt2_plan_s* p) { return tail_pk_part(p) + (size_t)x_blocks(p->n) * 3 * kMaxShells * 8; }
+// CIC density of every instance (sum of n^3 floats) after the slots, then the tail.
+size_t rho_all_off(const lpt2_plan_s* p) { return N_SLOTS * slot_bytes(p); }
+float* rho_group(const lpt2_plan_s* p) {
+  const Group* g = nullptr;
+  for (const Group& x : p->groups)
+    if (x.inst0 == p->cur_inst0) g = &x;
+  return reinterpret_cast<float*>(p->ws + rho_all_off(p)) + (g ? g->off : 0);
+}
+size_t tail_pk_part(const lpt2_plan_s* p) {
+  return (rho_all_off(p) + p->total_cells * sizeof(float) + 255) / 256 * 256;
+}
+size_t tail_pk(const lpt2_plan_s* p) { return tail_pk_part(p) + (size_t)p->xb_max * 3 * kMaxShells * 8; }
 size_t tail_shw(const lpt2_plan_s* p) { return tail_pk(p) + 3 * kMaxShells * 8; }
 size_t tail_theta(const lpt2_plan_s* p) { return tail_shw(p) + kMaxShells * 4; }
-size_t ws_need(const lpt2_plan_s* p) { return tail_theta(p) + (size_t)x_blocks(p->n) * 8; }
+size_t ws_need(const lpt2_plan_s* p) { return tail_theta(p) + (size_t)p->xb_max * 8; }
 
 float2* slot(const lpt2_plan_s* p, int i) { return reinterpret_cast<float2*>(p->ws + i * slot_bytes(p)); }
 double* pk_part(const lpt2_plan_s* p) { return reinterpret_cast<double*>(p->ws + tail_pk_part(p)); }
@@ -108,6 +156,9 @@ Geo make_geo(const lpt2_plan_s* p) {
   g.inv_cell = (float)(n / p->box);
   g.inv_n3 = (float)(1.0 / (n * n * n));
   g.sqrt_n3_over_v = (float)sqrt(n * n * n / (p->box * p->box * p->box));
+  g.batch = p->cur_batch;
+  g.inst0 = p->cur_inst0;
+  g.tab_stride = 4 * p->nk;
   return g;
 }
 
@@ -127,6 +178,8 @@ GrowthParams growth_params(const lpt2_plan_s* p) {
   g.k_max = p->k_max;
   g.nk = p->nk;
   g.n_steps = p->n_steps;
+  g.n_inst = p->n_inst;
+  g.fr0s = p->fr0_dev;
   return g;
 }
 
@@ -194,6 +247,7 @@ int forward_zy(lpt2_plan_t p, int src, const float* in, float2* out) {
   z.in = in;
   z.seed_lo = (uint32_t)p->seed;
   z.seed_hi = (uint32_t)(p->seed >> 32);
+  z.seeds = p->seeds_dev;
   z.out = out;
   LAUNCH(p, src == Z_NOISE ? "z_r2c_noise" : (src == Z_DENSITY ? "z_r2c_density" : "z_r2c"),
          (src == Z_NOISE ? 4.0 : 8.0) * V3(p), z_r2c(p->n, z, p->stream));
@@ -214,6 +268,78 @@ int forward_zy(lpt2_plan_t p, int src, const float* in, float2* out) {
 int displace_impl(lpt2_plan_t p, const float* noise, float* psi1, float* psi2, float* pos, void* dk,
                   float2* s_keep);
 
+// CIC (when positions are given) and P(k) of the current group.
+int cic_pk_group(lpt2_plan_t p, const float* pos, float* density, double* pk, double* k_mean,
+                 int64_t* n_modes, int n_shells) {
+  const int n = p->n;
+  const Geo g = make_geo(p);
+  const size_t cells = (size_t)n * n * n * p->cur_batch;
+  float* rho = rho_group(p);
+  float2* A = slot(p, S_A);
+  if (pos) {
+    LAUNCH(p, "fill0", 4.0 * V3(p), launch_fill0(rho, cells, p->stream));
+    CicArgs c{g, pos, rho};
+    LAUNCH(p, "cic", 20.0 * V3(p), launch_cic(c, p->stream));
+  }
+  int rc = forward_zy(p, Z_DENSITY, rho, A);   // rho - 1 is formed in the z pass; rho is kept
+  if (rc) return rc;
+  if (density) LAUNCH(p, "contrast", 8.0 * V3(p), launch_contrast(rho, density, cells, p->stream));
+  XArgs x{};
+  x.g = g;
+  x.tw = p->tw;
+  x.mode = X_PK;
+  x.in = A;
+  x.cosmo = p->cosmo_dev;
+  x.pk_part = pk_part(p);
+  x.n_shells = n_shells;
+  LAUNCH(p, "x_pk", 4.0 * V3(p), x_pass(n, x, p->stream));
+  LAUNCH(p, "pk_finalize", 0.0,
+         launch_pk_finalize(pk_part(p), x_blocks(n), n_shells, pk, k_mean, n_modes, p->stream, p->cur_batch));
+  return LPT2_OK;
+}
+
+// Runs `body` through a CUDA graph captured on the plan's stream; the graph is
+// re-captured when any pointer in `key` changes.
+template <class F>
+int run_graph(lpt2_plan_t p, int slot_i, const void* const key[8], F body) {
+  GraphCache& gc = p->graphs[slot_i];
+  bool same = gc.exec != nullptr;
+  for (int i = 0; i < 8 && same; ++i) same = (gc.key[i] == key[i]);
+  if (!same) {
+    const bool timing = p->timing_on;
+    p->timing_on = false;
+    cudaError_t e = cudaStreamBeginCapture(p->stream, cudaStreamCaptureModeRelaxed);
+    if (e != cudaSuccess) {
+      p->timing_on = timing;
+      return fail(LPT2_ECUDA, "stream capture: %s", cudaGetErrorString(e));
+    }
+    const int64_t l0 = p->launches;
+    const int rc = body();
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamEndCapture(p->stream, &graph);
+    p->timing_on = timing;
+    const int64_t captured = p->launches - l0;
+    p->launches = l0;
+    if (rc) {
+      if (graph) cudaGraphDestroy(graph);
+      return rc;
+    }
+    if (e != cudaSuccess) return fail(LPT2_ECUDA, "end capture: %s", cudaGetErrorString(e));
+    cudaGraphExec_t exec = nullptr;
+    e = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return fail(LPT2_ECUDA, "graph instantiate: %s", cudaGetErrorString(e));
+    if (gc.exec) cudaGraphExecDestroy(gc.exec);
+    gc.exec = exec;
+    gc.launches = captured;
+    for (int i = 0; i < 8; ++i) gc.key[i] = key[i];
+  }
+  cudaError_t e = cudaGraphLaunch(gc.exec, p->stream);
+  if (e != cudaSuccess) return fail(LPT2_ECUDA, "graph launch: %s", cudaGetErrorString(e));
+  p->launches += gc.launches;
+  return LPT2_OK;
+}
+
 int run_growth(lpt2_plan_t p) {
   const GrowthParams gp = growth_params(p);
   LAUNCH(p, "growth", 0.0, launch_growth(gp, p->tab, p->tabf, p->stream));
@@ -230,19 +356,10 @@ const char* lpt2_last_error(void) { return g_err.c_str(); }
 
 int64_t lpt2_launch_count(lpt2_plan_t plan) { return plan ? plan->launches : -1; }
 
-int lpt2_plan(lpt2_plan_t* out, const lpt2_instance* inst, int n_inst, int n_k, double k_min,
-              double k_max, int n_steps, void* cuda_stream, unsigned flags) {
-  g_err.clear();
-  if (!out || !inst) return fail(LPT2_EINVAL, "null out/inst pointer");
-  *out = nullptr;
-  if (n_inst != 1) return fail(LPT2_EUNSUPPORTED, "n_inst must be 1 (got %d)", n_inst);
-  if (flags != 0) return fail(LPT2_EINVAL, "flags must be 0");
+static int check_cosmo(const lpt2_instance* inst) {
   const lpt2_cosmo& c = inst->cosmo;
   if (!supported_n(inst->n)) return fail(LPT2_EUNSUPPORTED, "grid size %d not supported", inst->n);
   if (!(inst->box > 0) || !isfinite(inst->box)) return fail(LPT2_EINVAL, "box must be > 0");
-  if (n_k < 2 || n_k > 4096) return fail(LPT2_EINVAL, "n_k must be in [2, 4096]");
-  if (!(k_min > 0) || !(k_max > k_min)) return fail(LPT2_EINVAL, "need 0 < k_min < k_max");
-  if (n_steps < 1 || n_steps > 2800) return fail(LPT2_EINVAL, "n_steps must be in [1, 2800]");
   if (!(c.a_init > 0) || !(inst->a_out > c.a_init) || !(inst->a_out <= 1.0))
     return fail(LPT2_EINVAL, "need 0 < a_init < a_out <= 1");
   if (!(c.omega_m > 0) || !(c.omega_l >= 0) || fabs(c.omega_m + c.omega_l - 1.0) > 1e-6)
@@ -252,40 +369,107 @@ int lpt2_plan(lpt2_plan_t* out, const lpt2_instance* inst, int n_inst, int n_k, 
   if (!(c.fr0_abs >= 0) || !isfinite(c.fr0_abs)) return fail(LPT2_EINVAL, "fr0_abs must be >= 0");
   if (c.hs_n != 1) return fail(LPT2_EUNSUPPORTED, "only Hu-Sawicki n = 1 is supported");
   if (c.d2_variant != LPT2_D2_T1) return fail(LPT2_EUNSUPPORTED, "only the T1 D2 variant is supported");
+  return LPT2_OK;
+}
+
+static bool same_background(const lpt2_instance& a, const lpt2_instance& b) {
+  const lpt2_cosmo &x = a.cosmo, &y = b.cosmo;
+  return x.omega_m == y.omega_m && x.omega_l == y.omega_l && x.omega_b == y.omega_b && x.h == y.h &&
+         x.n_s == y.n_s && x.sigma8 == y.sigma8 && x.t_cmb == y.t_cmb && x.a_init == y.a_init &&
+         x.hs_n == y.hs_n && x.d2_variant == y.d2_variant && a.a_out == b.a_out;
+}
+
+int lpt2_plan(lpt2_plan_t* out, const lpt2_instance* inst, int n_inst, int n_k, double k_min,
+              double k_max, int n_steps, void* cuda_stream, unsigned flags) {
+  g_err.clear();
+  if (!out || !inst) return fail(LPT2_EINVAL, "null out/inst pointer");
+  *out = nullptr;
+  if (n_inst < 1 || n_inst > 65535) return fail(LPT2_EINVAL, "n_inst must be in [1, 65535] (got %d)", n_inst);
+  if (flags & ~(unsigned)LPT2_GRAPH) return fail(LPT2_EINVAL, "unknown flags");
+  if ((flags & LPT2_GRAPH) && cuda_stream == nullptr)
+    return fail(LPT2_EINVAL, "LPT2_GRAPH needs a stream other than the legacy default stream");
+  if (n_k < 2 || n_k > 4096) return fail(LPT2_EINVAL, "n_k must be in [2, 4096]");
+  if (!(k_min > 0) || !(k_max > k_min)) return fail(LPT2_EINVAL, "need 0 < k_min < k_max");
+  if (n_steps < 1 || n_steps > 2800) return fail(LPT2_EINVAL, "n_steps must be in [1, 2800]");
+  std::vector<Group> groups;
+  for (int i = 0; i < n_inst; ++i) {
+    const int rc = check_cosmo(&inst[i]);
+    if (rc) return rc;
+    if (!same_background(inst[i], inst[0]))
+      return fail(LPT2_EINVAL, "instance %d: all instances must share the background cosmology and a_out "
+                               "(only fr0_abs and seed may differ)", i);
+    if (groups.empty() || groups.back().n != inst[i].n) {
+      for (const Group& g : groups)
+        if (g.n == inst[i].n)
+          return fail(LPT2_EINVAL, "instances of equal grid size must be contiguous (instance %d)", i);
+      groups.push_back(Group{inst[i].n, inst[i].box, 0, i, nullptr});
+    }
+    if (inst[i].box != groups.back().box)
+      return fail(LPT2_EUNSUPPORTED, "instances of one grid size must share the box (instance %d)", i);
+    groups.back().count++;
+  }
 
   lpt2_plan_s* p = new lpt2_plan_s();
-  p->n = inst->n;
-  p->box = inst->box;
-  p->seed = inst->seed;
-  p->a_out = inst->a_out;
-  p->cosmo = c;
+  p->groups = groups;
+  p->n_inst = n_inst;
+  p->seed = inst[0].seed;
+  p->a_out = inst[0].a_out;
+  p->cosmo = inst[0].cosmo;
   p->nk = n_k;
   p->k_min = k_min;
   p->k_max = k_max;
   p->n_steps = n_steps;
   p->stream = (cudaStream_t)cuda_stream;
-  const int n = p->n;
+  p->use_graph = (flags & LPT2_GRAPH) != 0;
+  p->slot_sz = 0;
+  p->xb_max = 0;
+  p->total_cells = 0;
+  for (Group& g : p->groups) {
+    g.off = p->total_cells;
+    p->total_cells += (size_t)g.count * g.n * g.n * g.n;
+  }
+  for (const Group& g : groups) {
+    const size_t sz = (size_t)g.count * g.n * g.n * g.n * sizeof(float);
+    if (sz > p->slot_sz) p->slot_sz = sz;
+    if (g.count * x_blocks(g.n) > p->xb_max) p->xb_max = g.count * x_blocks(g.n);
+  }
   cudaError_t e = cudaSuccess;
-  e = cudaMalloc(&p->tw, n * sizeof(float2));
+  for (Group& g : p->groups) {
+    if (e == cudaSuccess) e = cudaMalloc(&g.tw, g.n * sizeof(float2));
+  }
   if (e == cudaSuccess) e = cudaMalloc(&p->cosmo_dev, sizeof(DevCosmo));
   if (e == cudaSuccess) e = cudaMalloc(&p->partials, cosmo_partial_blocks() * sizeof(double));
-  if (e == cudaSuccess) e = cudaMalloc(&p->tab, 4 * n_k * sizeof(double));
-  if (e == cudaSuccess) e = cudaMalloc(&p->tabf, 4 * n_k * sizeof(float));
+  if (e == cudaSuccess) e = cudaMalloc(&p->tab, (size_t)n_inst * 4 * n_k * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&p->tabf, (size_t)n_inst * 4 * n_k * sizeof(float));
+  if (e == cudaSuccess) e = cudaMalloc(&p->seeds_dev, (size_t)n_inst * sizeof(uint64_t));
+  if (e == cudaSuccess) e = cudaMalloc(&p->fr0_dev, (size_t)n_inst * sizeof(double));
   if (e != cudaSuccess) {
     lpt2_plan_destroy(p);
     return fail(LPT2_ENOMEM, "plan allocation failed: %s", cudaGetErrorString(e));
   }
   // twiddles exp(-2 pi i m / N), FP64 then rounded once
-  std::vector<float2> tw(n);
-  for (int m = 0; m < n; ++m) {
-    const double ang = 2.0 * M_PI * (double)m / (double)n;
-    tw[m] = make_float2((float)cos(ang), (float)(-sin(ang)));
+  for (Group& g : p->groups) {
+    std::vector<float2> tw(g.n);
+    for (int m = 0; m < g.n; ++m) {
+      const double ang = 2.0 * M_PI * (double)m / (double)g.n;
+      tw[m] = make_float2((float)cos(ang), (float)(-sin(ang)));
+    }
+    e = cudaMemcpy(g.tw, tw.data(), g.n * sizeof(float2), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) break;
   }
-  e = cudaMemcpy(p->tw, tw.data(), n * sizeof(float2), cudaMemcpyHostToDevice);
+  std::vector<uint64_t> seeds(n_inst);
+  std::vector<double> fr0s(n_inst);
+  for (int i = 0; i < n_inst; ++i) {
+    seeds[i] = inst[i].seed;
+    fr0s[i] = inst[i].cosmo.fr0_abs;
+  }
+  if (e == cudaSuccess) e = cudaMemcpy(p->seeds_dev, seeds.data(), n_inst * sizeof(uint64_t), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(p->fr0_dev, fr0s.data(), n_inst * sizeof(double), cudaMemcpyHostToDevice);
   if (e != cudaSuccess) {
     lpt2_plan_destroy(p);
-    return fail(LPT2_ECUDA, "twiddle upload: %s", cudaGetErrorString(e));
+    return fail(LPT2_ECUDA, "plan upload: %s", cudaGetErrorString(e));
   }
+  set_group(p, 0);
   const GrowthParams gp = growth_params(p);
   e = launch_cosmo_setup(gp, p->partials, p->cosmo_dev, p->stream);
   p->launches += 2;   // partial sums + final
@@ -303,11 +487,15 @@ int lpt2_plan(lpt2_plan_t* out, const lpt2_instance* inst, int n_inst, int n_k, 
 
 int lpt2_plan_destroy(lpt2_plan_t p) {
   if (!p) return LPT2_OK;
-  cudaFree(p->tw);
+  for (Group& g : p->groups) cudaFree(g.tw);
   cudaFree(p->cosmo_dev);
   cudaFree(p->partials);
   cudaFree(p->tab);
   cudaFree(p->tabf);
+  cudaFree(p->seeds_dev);
+  cudaFree(p->fr0_dev);
+  for (auto& gc : p->graphs)
+    if (gc.exec) cudaGraphExecDestroy(gc.exec);
   if (p->ev) {
     for (int i = 0; i < 2 * kMaxRec; ++i) cudaEventDestroy(p->ev[i]);
     delete[] p->ev;
@@ -336,10 +524,11 @@ int lpt2_growth_tables(lpt2_plan_t p, double* d1, double* d2, double* dd1, doubl
   int rc = run_growth(p);
   if (rc) return rc;
   double* dst[4] = {d1, d2, dd1, dd2};
-  for (int i = 0; i < 4; ++i) {
+  for (int i = 0; i < 4; ++i) {   // plan tables are [n_inst][4][nk]; outputs [n_inst][nk]
     if (!dst[i]) continue;
-    cudaError_t e = cudaMemcpyAsync(dst[i], p->tab + (size_t)i * p->nk, p->nk * sizeof(double),
-                                    cudaMemcpyDeviceToDevice, p->stream);
+    cudaError_t e = cudaMemcpy2DAsync(dst[i], p->nk * sizeof(double), p->tab + (size_t)i * p->nk,
+                                      4 * p->nk * sizeof(double), p->nk * sizeof(double), p->n_inst,
+                                      cudaMemcpyDeviceToDevice, p->stream);
     if (e != cudaSuccess) return fail(LPT2_ECUDA, "table copy: %s", cudaGetErrorString(e));
   }
   return LPT2_OK;
@@ -347,6 +536,7 @@ int lpt2_growth_tables(lpt2_plan_t p, double* d1, double* d2, double* dd1, doubl
 
 int lpt2_white_noise(lpt2_plan_t p, float* noise) {
   if (!p || !noise) return fail(LPT2_EINVAL, "null argument");
+  if (p->n_inst != 1) return fail(LPT2_EUNSUPPORTED, "lpt2_white_noise needs a single-instance plan");
   if (!aligned(noise, 4)) return fail(LPT2_EINVAL, "misaligned output");
   LAUNCH(p, "noise", 4.0 * V3(p), launch_noise(make_geo(p), (uint32_t)p->seed, (uint32_t)(p->seed >> 32), noise, p->stream));
   return LPT2_OK;
@@ -366,7 +556,20 @@ int lpt2_displace(lpt2_plan_t p, const float* noise, float* psi1, float* psi2, f
   int rc = check_plan_ws(p);
   if (rc) return rc;
   if (dk && !aligned(dk, 16)) return fail(LPT2_EINVAL, "dk must be 16-byte aligned");
-  return displace_impl(p, noise, psi1, psi2, pos, dk, nullptr);
+  auto body = [&]() -> int {
+    for (int gi = 0; gi < (int)p->groups.size(); ++gi) {
+      set_group(p, gi);
+      const size_t off = p->groups[gi].off;   // real elements before the group
+      const int r = displace_impl(p, noise ? noise + off : nullptr, psi1 ? psi1 + 3 * off : nullptr,
+                                  psi2 ? psi2 + 3 * off : nullptr, pos ? pos + 3 * off : nullptr,
+                                  dk ? (char*)dk + off * sizeof(float) : nullptr, nullptr);
+      if (r) return r;
+    }
+    return LPT2_OK;
+  };
+  if (!p->use_graph) return body();
+  const void* key[8] = {noise, psi1, psi2, pos, dk, p->ws, nullptr, nullptr};
+  return run_graph(p, 0, key, body);
 }
 
 }  // extern "C"
@@ -386,7 +589,8 @@ int displace_impl(lpt2_plan_t p, const float* noise, float* psi1, float* psi2, f
   float2* Y[9];
   for (int i = 0; i < 5; ++i) X[i] = slot(p, S_X0 + i);
   for (int i = 0; i < 9; ++i) Y[i] = slot(p, S_Y0 + i);
-  float* rho = reinterpret_cast<float*>(slot(p, S_RHO));
+  float* rho = rho_group(p);
+  const size_t cells = (size_t)n * n * n * p->cur_batch;   // real elements of the group
 
   // 1. delta(k): noise -> z, y passes; x pass with sqrt(P) and the phi / Psi1 potentials
   rc = forward_zy(p, noise ? Z_REAL : Z_NOISE, noise, A);
@@ -474,7 +678,7 @@ int displace_impl(lpt2_plan_t p, const float* noise, float* psi1, float* psi2, f
   LAUNCH(p, "y_psi", 20.0 * V3(p), y_pass(n, y2, p->stream));
 
   // 6. z inverse, positions, CIC
-  LAUNCH(p, "fill0", 4.0 * V3(p), launch_fill0(rho, (size_t)n * n * n, p->stream));
+  LAUNCH(p, "fill0", 4.0 * V3(p), launch_fill0(rho, cells, p->stream));
   ZFinalArgs zf{};
   zf.g = g;
   zf.tw = p->tw;
@@ -491,7 +695,7 @@ int displace_impl(lpt2_plan_t p, const float* noise, float* psi1, float* psi2, f
          ((split ? 24.0 : 12.0) + (pos ? 12.0 : 0.0) + (psi1 ? 12.0 : 0.0) + (psi2 ? 12.0 : 0.0) + 8.0) * V3(p),
          z_final(n, zf, p->stream));
   if (dk) {
-    cudaError_t e = cudaMemcpyAsync(dk, D, slot_bytes(p), cudaMemcpyDeviceToDevice, p->stream);
+    cudaError_t e = cudaMemcpyAsync(dk, D, cells * sizeof(float), cudaMemcpyDeviceToDevice, p->stream);
     if (e != cudaSuccess) return fail(LPT2_ECUDA, "dk copy: %s", cudaGetErrorString(e));
   }
   return LPT2_OK;
@@ -507,34 +711,27 @@ int lpt2_cic_pk(lpt2_plan_t p, const float* pos, float* density, double* pk, dou
   if (rc) return rc;
   if (!pk) return fail(LPT2_EINVAL, "pk must not be null");
   if (n_shells < 1 || n_shells > kMaxShells) return fail(LPT2_EINVAL, "n_shells must be in [1, 256]");
-  const int n = p->n;
-  const Geo g = make_geo(p);
-  float* rho = reinterpret_cast<float*>(slot(p, S_RHO));
-  float2* A = slot(p, S_A);
-  if (pos) {
-    LAUNCH(p, "fill0", 4.0 * V3(p), launch_fill0(rho, (size_t)n * n * n, p->stream));
-    CicArgs c{g, pos, rho};
-    LAUNCH(p, "cic", 20.0 * V3(p), launch_cic(c, p->stream));
-  }
-  rc = forward_zy(p, Z_DENSITY, rho, A);   // rho - 1 is formed in the z pass; rho is kept
-  if (rc) return rc;
-  if (density) LAUNCH(p, "contrast", 8.0 * V3(p), launch_contrast(rho, density, (size_t)n * n * n, p->stream));
-  XArgs x{};
-  x.g = g;
-  x.tw = p->tw;
-  x.mode = X_PK;
-  x.in = A;
-  x.cosmo = p->cosmo_dev;
-  x.pk_part = pk_part(p);
-  x.n_shells = n_shells;
-  LAUNCH(p, "x_pk", 4.0 * V3(p), x_pass(n, x, p->stream));
-  LAUNCH(p, "pk_finalize", 0.0, launch_pk_finalize(pk_part(p), x_blocks(n), n_shells, pk, k_mean, n_modes, p->stream));
-  return LPT2_OK;
+  auto body = [&]() -> int {
+    for (int gi = 0; gi < (int)p->groups.size(); ++gi) {
+      set_group(p, gi);
+      const Group& gr = p->groups[gi];
+      const int r = cic_pk_group(p, pos ? pos + 3 * gr.off : nullptr, density ? density + gr.off : nullptr,
+                                 pk + (size_t)gr.inst0 * n_shells, k_mean ? k_mean + (size_t)gr.inst0 * n_shells : nullptr,
+                                 n_modes ? n_modes + (size_t)gr.inst0 * n_shells : nullptr, n_shells);
+      if (r) return r;
+    }
+    return LPT2_OK;
+  };
+  if (!p->use_graph) return body();
+  const void* key[8] = {pos, density, pk, k_mean, n_modes, p->ws, (const void*)(intptr_t)n_shells, nullptr};
+  return run_graph(p, 1, key, body);
 }
 
 int lpt2_fft_r2c(lpt2_plan_t p, const float* in, void* out) {
   int rc = check_plan_ws(p);
   if (rc) return rc;
+  if (p->n_inst != 1) return fail(LPT2_EUNSUPPORTED, "lpt2_fft_r2c needs a single-instance plan");
+  set_group(p, 0);
   if (!in || !out || !aligned(out, 16)) return fail(LPT2_EINVAL, "bad in/out");
   float2* o = reinterpret_cast<float2*>(out);
   rc = forward_zy(p, Z_REAL, in, o);
@@ -552,6 +749,8 @@ int lpt2_fft_r2c(lpt2_plan_t p, const float* in, void* out) {
 int lpt2_fft_c2r(lpt2_plan_t p, const void* in, float* out) {
   int rc = check_plan_ws(p);
   if (rc) return rc;
+  if (p->n_inst != 1) return fail(LPT2_EUNSUPPORTED, "lpt2_fft_c2r needs a single-instance plan");
+  set_group(p, 0);
   if (!in || !out || !aligned(in, 16)) return fail(LPT2_EINVAL, "bad in/out");
   const Geo g = make_geo(p);
   float2* A = slot(p, S_A);
@@ -578,8 +777,13 @@ int lpt2_fft_c2r(lpt2_plan_t p, const void* in, float* out) {
 
 int lpt2_set_fr0(lpt2_plan_t p, double fr0_abs) {
   if (!p) return fail(LPT2_EINVAL, "null plan");
+  if (p->n_inst != 1) return fail(LPT2_EUNSUPPORTED, "lpt2_set_fr0 needs a single-instance plan");
   if (!(fr0_abs >= 0) || !isfinite(fr0_abs)) return fail(LPT2_EINVAL, "fr0_abs must be >= 0");
   p->cosmo.fr0_abs = fr0_abs;
+  cudaError_t e = cudaMemcpyAsync(p->fr0_dev, &p->cosmo.fr0_abs, sizeof(double), cudaMemcpyHostToDevice, p->stream);
+  if (e != cudaSuccess) return fail(LPT2_ECUDA, "fr0 upload: %s", cudaGetErrorString(e));
+  e = cudaStreamSynchronize(p->stream);   // the host value must outlive the copy
+  if (e != cudaSuccess) return fail(LPT2_ECUDA, "fr0 upload: %s", cudaGetErrorString(e));
   return run_growth(p);
 }
 
@@ -587,13 +791,15 @@ int lpt2_displace_vjp(lpt2_plan_t p, const float* noise, const float* g_pos, con
                       const double* g_pk, int n_shells, float* g_noise, double* g_log_fr0) {
   int rc = check_plan_ws(p);
   if (rc) return rc;
+  if (p->n_inst != 1) return fail(LPT2_EUNSUPPORTED, "lpt2_displace_vjp needs a single-instance plan");
+  set_group(p, 0);
   if (n_shells < 1 || n_shells > kMaxShells) return fail(LPT2_EINVAL, "n_shells must be in [1, 256]");
   const int n = p->n;
   const Geo g = make_geo(p);
   float2* S[N_SLOTS];
   for (int i = 0; i < N_SLOTS; ++i) S[i] = slot(p, i);
   float* pos = reinterpret_cast<float*>(S[S_POS]);            // 3 consecutive slots
-  float* rho = reinterpret_cast<float*>(S[S_RHO]);
+  float* rho = rho_group(p);
   double* pk = reinterpret_cast<double*>(p->ws + tail_pk(p));
   double* kmean = pk + kMaxShells;
   int64_t* nmodes = reinterpret_cast<int64_t*>(pk + 2 * kMaxShells);

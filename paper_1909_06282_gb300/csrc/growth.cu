@@ -195,6 +195,9 @@ __device__ void fill_bg(Bg* tab, const GrowthParams& p, double s0, double h, int
 template <bool TAN>
 __global__ void k_growth(GrowthParams p, double* tab, float* tabf) {
   extern __shared__ Bg s_bg[];
+  if (p.fr0s) p.fr0_abs = p.fr0s[blockIdx.y];     // instance blockIdx.y
+  tab += (size_t)blockIdx.y * 4 * p.nk;
+  tabf += (size_t)blockIdx.y * 4 * p.nk;
   const bool gr = (p.fr0_abs == 0.0);
   const double s0 = log(p.a_init);
   // GR normalisation D1_GR(a = 1)
@@ -235,7 +238,7 @@ cudaError_t launch_growth(const GrowthParams& p, double* tab, float* tabf, cudaS
   const int blocks = (p.nk + threads - 1) / threads;
   const size_t smem = (size_t)(2 * p.n_steps + 1) * sizeof(Bg);
   cudaFuncSetAttribute(k_growth<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  k_growth<true><<<blocks, threads, smem, s>>>(p, tab, tabf);
+  k_growth<true><<<dim3(blocks, p.n_inst > 0 ? p.n_inst : 1), threads, smem, s>>>(p, tab, tabf);
   return cudaGetLastError();
 }
 

@@ -9,6 +9,8 @@ template <int N>
 __global__ void __launch_bounds__(256) k_cic(CicArgs a) {
   const size_t n3 = (size_t)N * N * N;
   const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;   // grid covers n3 exactly
+  a.pos += (size_t)blockIdx.y * 3 * n3;                               // instance blockIdx.y
+  a.rho += (size_t)blockIdx.y * n3;
   float u[3];
   for (int c = 0; c < 3; ++c) u[c] = wrapN<N>(__ldg(a.pos + c * n3 + i) * a.g.inv_cell);
   cic_deposit_merged<N>(a.rho, u[0], u[1], u[2]);
@@ -16,7 +18,8 @@ __global__ void __launch_bounds__(256) k_cic(CicArgs a) {
 
 cudaError_t launch_cic(const CicArgs& a, cudaStream_t s) {
   const size_t n3 = (size_t)a.g.n * a.g.n * a.g.n;   // every supported N^3 is a multiple of 256
-  const unsigned blocks = (unsigned)(n3 / 256);
+  if (a.g.batch < 1 || a.g.batch > 65535) return cudaErrorInvalidValue;
+  const dim3 blocks((unsigned)(n3 / 256), a.g.batch);
   switch (a.g.n) {
     case 16: k_cic<16><<<blocks, 256, 0, s>>>(a); break;
     case 32: k_cic<32><<<blocks, 256, 0, s>>>(a); break;
@@ -57,6 +60,10 @@ cudaError_t launch_contrast(const float* rho, float* out, size_t n, cudaStream_t
 __global__ void k_pk_finalize(const double* part, int n_blocks, int ns, double* pk, double* kmean,
                               int64_t* nmodes) {
   const int b = blockIdx.x;
+  part += (size_t)blockIdx.y * n_blocks * 3 * ns;       // instance blockIdx.y
+  pk += (size_t)blockIdx.y * ns;
+  if (kmean) kmean += (size_t)blockIdx.y * ns;
+  if (nmodes) nmodes += (size_t)blockIdx.y * ns;
   double sp = 0.0, sk = 0.0, sc = 0.0;
   for (int i = threadIdx.x; i < n_blocks; i += blockDim.x) {
     const double* q = part + (size_t)i * 3 * ns;
@@ -86,8 +93,8 @@ __global__ void k_pk_finalize(const double* part, int n_blocks, int ns, double* 
 }
 
 cudaError_t launch_pk_finalize(const double* part, int n_blocks, int n_shells, double* pk, double* k_mean,
-                               int64_t* n_modes, cudaStream_t s) {
-  k_pk_finalize<<<n_shells, 256, 0, s>>>(part, n_blocks, n_shells, pk, k_mean, n_modes);
+                               int64_t* n_modes, cudaStream_t s, int batch) {
+  k_pk_finalize<<<dim3(n_shells, batch), 256, 0, s>>>(part, n_blocks, n_shells, pk, k_mean, n_modes);
   return cudaGetLastError();
 }
 

@@ -125,7 +125,7 @@ extern "C" int lpt2_cic_pk_noalloc(int n, double box, const float* pos, float* d
   float2* tw = reinterpret_cast<float2*>(base + kTwOff);
   const DevCosmo* cosmo = reinterpret_cast<const DevCosmo*>(base + kCosmoOff);
 
-  Geo g;
+  Geo g{};
   const double nd = n;
   g.n = n;
   g.kf = (float)(2.0 * M_PI / box);
@@ -134,6 +134,9 @@ extern "C" int lpt2_cic_pk_noalloc(int n, double box, const float* pos, float* d
   g.inv_cell = (float)(nd / box);
   g.inv_n3 = (float)(1.0 / (nd * nd * nd));
   g.sqrt_n3_over_v = (float)sqrt(nd * nd * nd / (box * box * box));
+  g.batch = 1;        // one grid per call
+  g.inst0 = 0;
+  g.tab_stride = 0;
   const size_t n3 = (size_t)n * n * n;
 
 #define NA_CHECK(expr)                                                                     \

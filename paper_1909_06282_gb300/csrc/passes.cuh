@@ -117,6 +117,14 @@ __global__ void __launch_bounds__(PassCfg<N>::ZT, LPT2_Z_MINB) k_z_r2c(ZR2CArgs 
   const SmemRow sm{smem + N + p * SmemRow::words(N)};
   const int pair = blockIdx.x * C::ZP + p;
   const int rowa = 2 * pair, rowb = rowa + 1;
+  const size_t n3 = (size_t)N * N * N;                 // instance blockIdx.z of the batch
+  if (SRC != Z_NOISE) a.in += blockIdx.z * n3;
+  a.out += blockIdx.z * (n3 / 2);
+  if (SRC == Z_NOISE && a.seeds) {
+    const uint64_t sd = a.seeds[a.g.inst0 + blockIdx.z];
+    a.seed_lo = (uint32_t)sd;
+    a.seed_hi = (uint32_t)(sd >> 32);
+  }
   float2 v[C::RMAX];
 #pragma unroll
   for (int r = 0; r < C::RMAX; ++r) {
@@ -148,6 +156,10 @@ __global__ void __launch_bounds__(PassCfg<N>::ZT, LPT2_Z_MINB) k_z_c2r(ZC2RArgs 
   const SmemRow sm{smem + N + p * SmemRow::words(N)};
   const int pair = blockIdx.x * C::ZP + p;
   const int rowa = 2 * pair, rowb = rowa + 1;
+  const size_t n3 = (size_t)N * N * N;                 // instance blockIdx.z of the batch
+  a.in += blockIdx.z * (n3 / 2);
+  a.out += blockIdx.z * n3;
+  if (a.add_in) a.add_in += blockIdx.z * n3;
   const float2* ra = a.in + (size_t)rowa * C::H;
   const float2* rb = a.in + (size_t)rowb * C::H;
   float2 v[C::RMAX];
@@ -175,6 +187,10 @@ __global__ void __launch_bounds__(PassCfg<N>::ZT, LPT2_Z_MINB) k_z_source(ZSourc
   const SmemRow sm{smem + N + p * SmemRow::words(N)};
   const int pair = blockIdx.x * C::ZP + p;
   const int rows[2] = {2 * pair, 2 * pair + 1};
+  const size_t zoff = blockIdx.z * ((size_t)N * N * N / 2);   // instance blockIdx.z
+#pragma unroll
+  for (int i = 0; i < 6; ++i) a.in[i] += zoff;
+  a.out += zoff;
   float S[2][C::RMAX];
   __syncthreads();
 #pragma unroll
@@ -265,6 +281,15 @@ __global__ void __launch_bounds__(PassCfg<N>::ZT, LPT2_Z_MINB) k_z_final(ZFinalA
   const size_t n3 = (size_t)N * N * N;
   const float kf = a.g.kf;
   const int nsets = a.split ? 2 : 1;
+  {                                                   // instance blockIdx.z of the batch
+    const size_t zs = blockIdx.z * (n3 / 2), zr = blockIdx.z * n3;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) { a.a[i] += zs; if (a.b[i]) a.b[i] += zs; }
+    if (a.psi1) a.psi1 += 3 * zr;
+    if (a.psi2) a.psi2 += 3 * zr;
+    if (a.pos) a.pos += 3 * zr;
+    if (a.rho) a.rho += zr;
+  }
   float pz[2][C::RMAX];
   __syncthreads();
   for (int set = 0; set < nsets; ++set) {
@@ -480,7 +505,7 @@ __global__ void __launch_bounds__(PassCfg<N>::XT) k_y(YArgs a) {
   const SmemCol<C::W> sm{smem + N + w};
   const int kz = blockIdx.x * C::W + w;
   const int x = blockIdx.y;
-  const size_t base = (size_t)x * N * C::H + kz;     // element (x, y, kz) = base + y * H
+  const size_t base = blockIdx.z * ((size_t)N * N * C::H) + (size_t)x * N * C::H + kz;   // + y * H
   __syncthreads();
   if (a.job.sum) {
     for (int o = 0; o < a.job.n_out; ++o) {
@@ -587,12 +612,19 @@ __global__ void __launch_bounds__(PassCfg<N>::XT) k_x(XArgs a) {
   constexpr int NWARP = C::XT / 32;
   const int kz = blockIdx.x * C::W + w;
   const int ky = blockIdx.y;
-  const size_t base = (size_t)ky * C::H + kz;      // element (kx, ky, kz) = base + kx * N * H
+  const size_t base = blockIdx.z * ((size_t)N * N * C::H) + (size_t)ky * C::H + kz;   // + kx * N * H
   const size_t stride = (size_t)N * C::H;
   const int my = mode_of(ky, N), mz = kz;
   const bool ny_nyq = (ky == C::H);
   const float kf = a.g.kf;
-  const size_t blk = (size_t)blockIdx.y * gridDim.x + blockIdx.x;
+  const size_t blk = ((size_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+  {                                                   // growth tables of instance inst0 + z
+    const size_t toff = (size_t)(a.g.inst0 + blockIdx.z) * a.g.tab_stride;
+    a.d1f += toff;
+    a.d2f += toff;
+    a.t1f += toff;
+    a.t2f += toff;
+  }
   if (MODE == X_PK) {
     for (int i = threadIdx.x; i < NWARP * 3 * a.n_shells; i += blockDim.x) s_acc[i] = 0.0;
   } else if (MODE == X_ADJ_SOURCE) {
@@ -780,10 +812,15 @@ __global__ void __launch_bounds__(PassCfg<N>::XT) k_x(XArgs a) {
 }
 
 // ================================================================ launchers
+// every launcher refuses a batch outside [1, 65535] (grid z) before launching
+#define LPT2_CHECK_BATCH(a) \
+  if ((a).g.batch < 1 || (a).g.batch > 65535) return cudaErrorInvalidValue
+
 template <int N, int SRC> cudaError_t launch_z_r2c_m(const ZR2CArgs& a, cudaStream_t s) {
   using C = PassCfg<N>;
+  LPT2_CHECK_BATCH(a);
   cudaFuncSetAttribute(k_z_r2c<N, SRC>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::ZSMEM);
-  k_z_r2c<N, SRC><<<N * N / 2 / C::ZP, C::ZT, C::ZSMEM, s>>>(a);
+  k_z_r2c<N, SRC><<<dim3(N * N / 2 / C::ZP, 1, a.g.batch), C::ZT, C::ZSMEM, s>>>(a);
   return cudaGetLastError();
 }
 template <int N> cudaError_t launch_z_r2c_t(const ZR2CArgs& a, cudaStream_t s) {
@@ -796,20 +833,23 @@ template <int N> cudaError_t launch_z_r2c_t(const ZR2CArgs& a, cudaStream_t s) {
 }
 template <int N> cudaError_t launch_z_c2r_t(const ZC2RArgs& a, cudaStream_t s) {
   using C = PassCfg<N>;
+  LPT2_CHECK_BATCH(a);
   cudaFuncSetAttribute(k_z_c2r<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::ZSMEM);
-  k_z_c2r<N><<<N * N / 2 / C::ZP, C::ZT, C::ZSMEM, s>>>(a);
+  k_z_c2r<N><<<dim3(N * N / 2 / C::ZP, 1, a.g.batch), C::ZT, C::ZSMEM, s>>>(a);
   return cudaGetLastError();
 }
 template <int N> cudaError_t launch_z_source_t(const ZSourceArgs& a, cudaStream_t s) {
   using C = PassCfg<N>;
+  LPT2_CHECK_BATCH(a);
   cudaFuncSetAttribute(k_z_source<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::ZSMEM);
-  k_z_source<N><<<N * N / 2 / C::ZP, C::ZT, C::ZSMEM, s>>>(a);
+  k_z_source<N><<<dim3(N * N / 2 / C::ZP, 1, a.g.batch), C::ZT, C::ZSMEM, s>>>(a);
   return cudaGetLastError();
 }
 template <int N> cudaError_t launch_z_final_t(const ZFinalArgs& a, cudaStream_t s) {
   using C = PassCfg<N>;
+  LPT2_CHECK_BATCH(a);
   cudaFuncSetAttribute(k_z_final<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::ZSMEM);
-  k_z_final<N><<<N * N / 2 / C::ZP, C::ZT, C::ZSMEM, s>>>(a);
+  k_z_final<N><<<dim3(N * N / 2 / C::ZP, 1, a.g.batch), C::ZT, C::ZSMEM, s>>>(a);
   return cudaGetLastError();
 }
 template <int N> cudaError_t launch_z_adj_final_t(const ZAdjFinalArgs& a, cudaStream_t s) {
@@ -826,16 +866,18 @@ template <int N> cudaError_t launch_z_adj_source_t(const ZAdjSourceArgs& a, cuda
 }
 template <int N> cudaError_t launch_y_t(const YArgs& a, cudaStream_t s) {
   using C = PassCfg<N>;
+  LPT2_CHECK_BATCH(a);
   cudaFuncSetAttribute(k_y<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::XSMEM);
-  k_y<N><<<dim3(C::H / C::W, N), C::XT, C::XSMEM, s>>>(a);
+  k_y<N><<<dim3(C::H / C::W, N, a.g.batch), C::XT, C::XSMEM, s>>>(a);
   return cudaGetLastError();
 }
 template <int N, int MODE> cudaError_t launch_x_m(const XArgs& a, cudaStream_t s) {
   using C = PassCfg<N>;
+  LPT2_CHECK_BATCH(a);
   const int smem = C::XSMEM + (MODE == X_PK ? (C::XT / 32) * 3 * a.n_shells * 8
                                             : (MODE == X_ADJ_SOURCE ? (C::XT / 32) * 8 : 0));
   cudaFuncSetAttribute(k_x<N, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  k_x<N, MODE><<<dim3(C::H / C::W, N), C::XT, smem, s>>>(a);
+  k_x<N, MODE><<<dim3(C::H / C::W, N, a.g.batch), C::XT, smem, s>>>(a);
   return cudaGetLastError();
 }
 template <int N> cudaError_t launch_x_t(const XArgs& a, cudaStream_t s) {

@@ -31,6 +31,11 @@ struct Geo {
   float inv_cell;       // N / L
   float inv_n3;         // 1 / N^3 (inverse-transform normalisation)
   float sqrt_n3_over_v; // sqrt(N^3 / L^3)
+  // batching: grid z runs over `batch` instances of this grid size; instance z of
+  // the launch is global instance inst0 + z (growth tables, seeds, outputs)
+  int batch;
+  int inst0;
+  int tab_stride;       // floats per instance in the float growth tables
 };
 
 enum ZSrc { Z_NOISE = 0, Z_REAL = 1, Z_DENSITY = 2 };
@@ -41,6 +46,7 @@ struct ZR2CArgs {      // forward z pass: real rows -> half-spectrum rows
   int src;             // ZSrc
   const float* in;     // Z_REAL / Z_DENSITY
   uint32_t seed_lo, seed_hi;
+  const uint64_t* seeds;  // per global instance (Z_NOISE), or null to use seed_lo/hi
   float2* out;         // [N*N][N/2]
 };
 
@@ -174,11 +180,11 @@ LPT2_DECLARE_LAUNCHERS(512)
 LPT2_DECLARE_LAUNCHERS(1024)
 
 // Size-independent kernels (misc.cu / growth.cu).
-cudaError_t launch_cic(const CicArgs&, cudaStream_t);
+cudaError_t launch_cic(const CicArgs&, cudaStream_t);   // grid y = a.g.batch
 cudaError_t launch_fill0(float* p, size_t n, cudaStream_t);
 cudaError_t launch_contrast(const float* rho, float* out, size_t n, cudaStream_t);
 cudaError_t launch_pk_finalize(const double* part, int n_blocks, int n_shells, double* pk,
-                               double* k_mean, int64_t* n_modes, cudaStream_t);
+                               double* k_mean, int64_t* n_modes, cudaStream_t, int batch = 1);
 cudaError_t launch_noise(const Geo& g, uint32_t seed_lo, uint32_t seed_hi, float* out, cudaStream_t);
 cudaError_t launch_philox_words(uint32_t seed_lo, uint32_t seed_hi, uint64_t first, int64_t count,
                                 uint32_t* out, cudaStream_t);
@@ -191,6 +197,8 @@ struct GrowthParams {
   double omega_m, omega_l, omega_b, h, n_s, sigma8, t_cmb, fr0_abs, a_init, a_out;
   double k_min, k_max;
   int nk, n_steps;
+  int n_inst;            // tables for n_inst instances (grid y)
+  const double* fr0s;    // device |fR0| per instance, or null for fr0_abs
 };
 int cosmo_partial_blocks();
 cudaError_t launch_cosmo_setup(const GrowthParams&, double* partials, DevCosmo* out, cudaStream_t);

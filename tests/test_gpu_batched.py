@@ -1,0 +1,90 @@
+"""Batched plans: several instances of mixed grid sizes, seeds and |f_R0| in one
+plan (each grid size one batch), with and without CUDA-graph replay.  Every
+instance must reproduce its single-instance plan exactly (the kernels are the
+same; only the batch offsets differ) and the FP64 oracle within the parity
+tolerances."""
+import numpy as np
+import pytest
+
+import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+STEPS = 256
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1909_06282_gb300 import build as B
+    B.build()
+
+
+def lp():
+    import paper_1909_06282_gb300 as L
+    return L
+
+
+def instances():
+    out = []
+    fr0s = [1e-6, 3e-5, 1e-4, 2e-5, 5e-6, 7e-5, 1e-5]
+    sizes = [(32, 128.0)] * 2 + [(64, 256.0)] * 3 + [(96, 384.0)] * 2
+    for i, ((n, box), f) in enumerate(zip(sizes, fr0s)):
+        out.append(W.Instance(n, box, 11 + i, W.COSMO.replace(fr0_abs=f)))
+    return out
+
+
+@pytest.mark.parametrize("graph", [False, True])
+def test_batched_matches_single_instance_plans(graph):
+    L = lp()
+    insts = instances()
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        plan = L.Plan(insts, n_steps=STEPS, stream=stream, graph=graph)
+        for rep in range(2):   # second call replays the captured graph
+            out = L.lpt2_displace(plan, psi1=True, psi2=True, pos=True)
+            pk = L.lpt2_cic_pk(plan, pos=None, n_shells=16)
+        stream.synchronize()
+        d1, d2, _, _ = L.lpt2_growth_tables(plan)
+        for j, it in enumerate(insts):
+            single = L.Plan(it, n_steps=STEPS, stream=stream)
+            ref = L.lpt2_displace(single, psi1=True, psi2=True, pos=True)
+            rpk = L.lpt2_cic_pk(single, pos=None, n_shells=16)
+            sd1, sd2, _, _ = L.lpt2_growth_tables(single)
+            stream.synchronize()
+            for key in ("psi1", "psi2", "pos"):
+                got = plan.split(out[key], 3)[j].reshape(ref[key].shape)
+                assert torch.equal(got, ref[key]), (j, key)
+            torch.testing.assert_close(pk["pk"][j], rpk["pk"], rtol=1e-6, atol=0)
+            assert torch.equal(pk["n_modes"][j], rpk["n_modes"])
+            assert torch.equal(d1[j], sd1) and torch.equal(d2[j], sd2)
+
+
+def test_batched_instance_against_oracle():
+    from oracle import lpt2
+    L = lp()
+    insts = instances()
+    plan = L.Plan(insts, n_steps=STEPS)
+    out = L.lpt2_displace(plan, psi1=True, psi2=True, pos=False)
+    j = 3   # second 64^3 instance
+    it = insts[j]
+    ref = lpt2.run(it.n, it.box, it.cosmo, seed=it.seed, n_steps=STEPS)
+    for key in ("psi1", "psi2"):
+        got = plan.split(out[key], 3)[j].reshape(3, it.n, it.n, it.n).cpu().numpy()
+        rel = np.linalg.norm(got - ref[key]) / np.linalg.norm(ref[key])
+        assert rel <= 2e-5, (key, rel)
+
+
+def test_batched_rejects_bad_orderings():
+    L = lp()
+    a, b = W.Instance(32, 128.0, 1, W.COSMO), W.Instance(64, 256.0, 2, W.COSMO)
+    with pytest.raises(L.LPT2Error):
+        L.Plan([a, b, a])                                   # grid sizes not contiguous
+    with pytest.raises(L.LPT2Error):
+        L.Plan([a, W.Instance(32, 100.0, 3, W.COSMO)])      # same size, different box
+    with pytest.raises(L.LPT2Error):
+        L.Plan([a, W.Instance(32, 128.0, 3, W.COSMO.replace(sigma8=0.9))])
+    p = L.Plan([a, b])
+    with pytest.raises(L.LPT2Error):
+        L.lpt2_displace_vjp(p)
