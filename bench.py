@@ -176,6 +176,140 @@ def profile_run(args):
     print(json.dumps({"profile_run": True, "grid": n, "box": box, "launches": L.lpt2_launch_count(plan)}))
 
 
+def bench_batched(args, L, W, torch, stream):
+    """96 instances (32 each of 96^3/384, 128^3/512, 192^3/768 Mpc/h; seeds 1..96; |fR0|
+    log-uniform in [1e-6, 1e-4]): one graph-captured batched plan vs the same instances
+    through single-instance plans one after the other.  Step = positions + CIC + P(k)."""
+    insts = W.batched_96()
+    parts = sum(i.n ** 3 for i in insts)
+    with torch.cuda.stream(stream):
+        plan = L.Plan(insts, n_steps=1024, stream=stream, graph=True)
+        pos = torch.empty(3 * plan.cells, dtype=torch.float32, device="cuda")
+
+        def bstep():
+            L.lpt2_displace(plan, psi1=False, psi2=False, pos=pos)
+            L.lpt2_cic_pk(plan, pos=None, n_shells=WORKLOAD["n_shells"])
+
+        singles = [L.Plan(i, n_steps=1024, stream=stream) for i in insts]
+        spos = [torch.empty((3, i.n, i.n, i.n), dtype=torch.float32, device="cuda") for i in insts]
+
+        def sstep():
+            for pl, ps in zip(singles, spos):
+                L.lpt2_displace(pl, psi1=False, psi2=False, pos=ps)
+                L.lpt2_cic_pk(pl, pos=None, n_shells=WORKLOAD["n_shells"])
+
+        res = {}
+        for name, fn in (("batched", bstep), ("one_by_one", sstep)):
+            for _ in range(args.warmup):
+                fn()
+            stream.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            k = max(1, args.steps // 2)
+            e0.record(stream)
+            for _ in range(k):
+                fn()
+            e1.record(stream)
+            stream.synchronize()
+            res[name] = e0.elapsed_time(e1) / k
+        del singles, spos, plan, pos
+    return {"instances": len(insts), "particles_per_step": parts,
+            "value": parts / (res["batched"] / 1e3), "unit": "particles/s",
+            "instances_per_s": len(insts) / (res["batched"] / 1e3),
+            "ms_per_step": res["batched"],
+            "one_by_one": {"value": parts / (res["one_by_one"] / 1e3), "ms_per_step": res["one_by_one"]},
+            "speedup_vs_one_by_one": res["one_by_one"] / res["batched"],
+            "what": "96 instances (32 x 96^3/384, 128^3/512, 192^3/768 Mpc/h), positions + CIC + P(k), "
+                    "one CUDA graph vs single-instance plans one by one"}
+
+
+def cufft_pipeline(plan, L, torch, n, box, n_shells):
+    """The same forward path with cuFFT (torch.fft) for every transform and unfused torch
+    element-wise kernels for the k-space multipliers, source term, CIC (scatter-add) and
+    P(k) (bincount); only the white noise and the growth tables come from the library.
+    A timed comparison, not a product path."""
+    import numpy as np
+    f32 = torch.float32
+    dev = "cuda"
+    d1t, d2t, _, _ = L.lpt2_growth_tables(plan)
+    kt = torch.logspace(-4, 1, plan.n_k, dtype=torch.float64, device=dev)
+    c = plan.inst.cosmo
+    kf = 2 * np.pi / box
+    m = torch.fft.fftfreq(n, d=1.0 / n, device=dev).to(f32)
+    mz = torch.arange(n // 2 + 1, device=dev, dtype=f32)
+    kx, ky, kz = (kf * m)[:, None, None], (kf * m)[None, :, None], (kf * mz)[None, None, :]
+    k2 = kx * kx + ky * ky + kz * kz
+    zero = (k2 == 0) | (m.abs() == n // 2)[:, None, None] | (m.abs() == n // 2)[None, :, None] \
+        | (mz == n // 2)[None, None, :]
+    kk = torch.sqrt(k2).clamp_min(1e-30)
+    lk = torch.log(kk.double())
+    lt = torch.log(kt)
+    idx = torch.clamp(torch.searchsorted(lt, lk) - 1, 0, plan.n_k - 2)
+    fr = ((lk - lt[idx]) / (lt[idx + 1] - lt[idx])).clamp(0, 1)
+    D1 = (d1t[idx] + fr * (d1t[idx + 1] - d1t[idx])).to(f32)
+    D2 = (d2t[idx] + fr * (d2t[idx + 1] - d2t[idx])).to(f32)
+    # sqrt(P(k) N^3 / V): Eisenstein-Hu no-wiggle fit, amplitude from sigma_8 (Simpson in ln k)
+    h, wm, wb = c.h, c.omega_m * c.h ** 2, c.omega_b * c.h ** 2
+    fb, th = c.omega_b / c.omega_m, c.t_cmb / 2.7
+    ssnd = 44.5 * np.log(9.83 / wm) / np.sqrt(1 + 10 * wb ** 0.75)
+    alpha = 1 - 0.328 * np.log(431 * wm) * fb + 0.38 * np.log(22.3 * wm) * fb * fb
+
+    def transfer(kx_):
+        gam = c.omega_m * h * (alpha + (1 - alpha) / (1 + (0.43 * kx_ * h * ssnd) ** 4))
+        q = kx_ * th * th / gam
+        l0 = np.log(2 * np.e + 1.8 * q) if isinstance(q, np.ndarray) else torch.log(2 * np.e + 1.8 * q)
+        return l0 / (l0 + (14.2 + 731 / (1 + 62.5 * q)) * q * q)
+
+    lk_ = np.linspace(np.log(1e-5), np.log(1e3), 20001)
+    k_ = np.exp(lk_)
+    x_ = 8 * k_
+    f_ = k_ ** (3 + c.n_s) * transfer(k_) ** 2 * (3 * (np.sin(x_) - x_ * np.cos(x_)) / x_ ** 3) ** 2 / (2 * np.pi ** 2)
+    wts = np.ones_like(f_)
+    wts[1:-1:2], wts[2:-1:2] = 4, 2
+    amp = c.sigma8 ** 2 / ((lk_[1] - lk_[0]) / 3 * np.dot(wts, f_))
+    T = transfer(kk)
+    sk = torch.where(zero, 0.0, np.sqrt(amp) * kk ** (c.n_s / 2) * T * np.sqrt(n ** 3 / box ** 3))
+    inv = torch.where(zero, 0.0, 1.0 / k2)
+    kv = (kx, ky, kz)
+    qg = [torch.arange(n, device=dev, dtype=f32).view(s_) * (box / n)
+          for s_ in ((n, 1, 1), (1, n, 1), (1, 1, n))]
+    noise = L.lpt2_white_noise(plan)
+
+    def run():
+        dk = torch.fft.rfftn(noise) * sk
+        pot = dk * inv
+        names = ((0, 0), (1, 1), (2, 2), (0, 1), (0, 2), (1, 2))
+        ph = {nm: torch.fft.irfftn(-kv[nm[0]] * kv[nm[1]] * pot, s=(n, n, n)) for nm in names}
+        S = (ph[(0, 0)] * ph[(1, 1)] + ph[(0, 0)] * ph[(2, 2)] + ph[(1, 1)] * ph[(2, 2)]
+             - ph[(0, 1)] ** 2 - ph[(0, 2)] ** 2 - ph[(1, 2)] ** 2)
+        del ph
+        u = (D1 * dk - D2 * torch.fft.rfftn(S) * torch.where(zero, 0.0, 1.0)) * inv
+        rho = torch.zeros(n ** 3, dtype=f32, device=dev)
+        uc = [torch.remainder(qg[c_] + torch.fft.irfftn(1j * kv[c_] * u, s=(n, n, n)), box) * (n / box)
+              for c_ in range(3)]
+        fl = [torch.floor(x) for x in uc]
+        d = [x - f for x, f in zip(uc, fl)]
+        i0 = [f.long() % n for f in fl]
+        for ox in (0, 1):
+            for oy in (0, 1):
+                for oz in (0, 1):
+                    w = (d[0] if ox else 1 - d[0]) * (d[1] if oy else 1 - d[1]) * (d[2] if oz else 1 - d[2])
+                    cell = (((i0[0] + ox) % n) * n + (i0[1] + oy) % n) * n + (i0[2] + oz) % n
+                    rho.index_add_(0, cell.reshape(-1), w.reshape(-1))
+        dr = torch.fft.rfftn((rho - 1).view(n, n, n))
+        pw = (dr.real ** 2 + dr.imag ** 2) * (box ** 3 / float(n) ** 6)
+        nn = (k2 / (kf * kf)).round().long()
+        ok = (nn > 0) & (4 * nn < n * n) & (mz < n // 2)[None, None, :]
+        b = torch.floor(torch.sqrt(nn.double()) * (2 * n_shells / n)).long().clamp(0, n_shells - 1)
+        wgt = torch.where(mz == 0, 1.0, 2.0)[None, None, :].expand_as(pw)
+        sel = ok.reshape(-1)
+        bb = b.reshape(-1)[sel]
+        cnt = torch.bincount(bb, weights=wgt.reshape(-1)[sel].double(), minlength=n_shells)
+        ps = torch.bincount(bb, weights=(pw * wgt).reshape(-1)[sel].double(), minlength=n_shells)
+        return ps / cnt.clamp_min(1)
+
+    return run
+
+
 def bench_ours(args):
     import numpy as np
     import torch
@@ -262,6 +396,33 @@ def bench_ours(args):
         stream.synchronize()
         ms_fv = e4.elapsed_time(e5) / vsteps
 
+        batched = bench_batched(args, L, W, torch, stream) if not args.no_batched else None
+
+        # the same path with cuFFT transforms and unfused element-wise kernels
+        cuf = None
+        if not args.no_cufft:
+            run = cufft_pipeline(plan, L, torch, n, box, WORKLOAD["n_shells"])
+            for _ in range(2):
+                pk_c = run()
+            stream.synchronize()
+            e6, e7 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            kc = max(1, args.steps // 4)
+            e6.record(stream)
+            for _ in range(kc):
+                pk_c = run()
+            e7.record(stream)
+            stream.synchronize()
+            ms_c = e6.elapsed_time(e7) / kc
+            L.lpt2_displace(plan, psi1=False, psi2=False, pos=pos)
+            pk_o = L.lpt2_cic_pk(plan, pos=None, n_shells=WORKLOAD["n_shells"])["pk"]
+            okm = pk_o > 0
+            cuf = {"value": n ** 3 / (ms_c / 1e3), "unit": "particles/s", "ms_per_step": ms_c,
+                   "ours_over_cufft": ms_c / ms,
+                   "pk_max_rel_diff": float(((pk_c - pk_o).abs() / pk_o.clamp_min(1e-300))[okm].max()),
+                   "what": "same forward path, torch.fft (cuFFT) transforms + unfused torch element-wise "
+                           "kernels, scatter-add CIC, bincount P(k)"}
+            del run
+
         # end to end through the public API: pinned host noise in, positions + P(k) out
         noise_h = torch.from_numpy(W.white_noise(n, 1000 + rank)).pin_memory()
         pos_h = torch.empty((3, n, n, n), dtype=torch.float32).pin_memory()
@@ -323,6 +484,8 @@ def bench_ours(args):
                               "frac": all_bytes / (total_ms / 1e3) / 1e9 / peak},
             "kernels": kernels,
             "growth_ms": growth_ms,
+            "batched": batched,
+            "cufft_pipeline": cuf,
             "fwd_vjp": {"value": parts / (ms_fv / 1e3), "unit": "particles/s", "ms_per_step": ms_fv,
                         "vjp_over_fwd": (ms_fv - ms) / ms,
                         "what": "forward + loss cotangents + lpt2_displace_vjp (noise and ln|fR0| gradients)"},
@@ -352,6 +515,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batched", action="store_true", help="skip the 96-instance batched measurement")
+    ap.add_argument("--no-cufft", action="store_true", help="skip the cuFFT comparison pipeline")
     ap.add_argument("--profile", action="store_true",
                     help="forward-only run for ncu (no timing); grid from --grid")
     ap.add_argument("--grid", type=int, default=WORKLOAD["n"],
