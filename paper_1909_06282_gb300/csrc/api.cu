@@ -49,6 +49,8 @@ struct Group {
   int inst0;       // index of the group's first instance in the plan
   float2* tw;      // twiddles exp(-2 pi i m / n)
   size_t off;      // floats before the group's first instance in per-instance real fields
+  float4* mt0;     // per-|n|^2 multiplier tables [count][mode_table_len(n)]
+  float2* mt1;
 };
 
 struct GraphCache {  // one captured launch sequence per entry point (LPT2_GRAPH)
@@ -62,6 +64,8 @@ struct lpt2_plan_s {
   int n;
   double box;
   float2* tw;
+  const float4* mt0;
+  const float2* mt1;
   int cur_batch, cur_inst0;
   std::vector<Group> groups;
   int n_inst;
@@ -106,6 +110,8 @@ void set_group(lpt2_plan_s* p, int gi) {
   p->n = g.n;
   p->box = g.box;
   p->tw = g.tw;
+  p->mt0 = g.mt0;
+  p->mt1 = g.mt1;
   p->cur_batch = g.count;
   p->cur_inst0 = g.inst0;
 }
@@ -343,6 +349,9 @@ int run_graph(lpt2_plan_t p, int slot_i, const void* const key[8], F body) {
 int run_growth(lpt2_plan_t p) {
   const GrowthParams gp = growth_params(p);
   LAUNCH(p, "growth", 0.0, launch_growth(gp, p->tab, p->tabf, p->stream));
+  for (const Group& g : p->groups)
+    LAUNCH(p, "mode_tables", 0.0,
+           launch_mode_tables(gp, p->cosmo_dev, p->tab, g.inst0, g.count, g.n, g.box, g.mt0, g.mt1, p->stream));
   return LPT2_OK;
 }
 
@@ -436,6 +445,8 @@ int lpt2_plan(lpt2_plan_t* out, const lpt2_instance* inst, int n_inst, int n_k, 
   cudaError_t e = cudaSuccess;
   for (Group& g : p->groups) {
     if (e == cudaSuccess) e = cudaMalloc(&g.tw, g.n * sizeof(float2));
+    if (e == cudaSuccess) e = cudaMalloc(&g.mt0, (size_t)g.count * mode_table_len(g.n) * sizeof(float4));
+    if (e == cudaSuccess) e = cudaMalloc(&g.mt1, (size_t)g.count * mode_table_len(g.n) * sizeof(float2));
   }
   if (e == cudaSuccess) e = cudaMalloc(&p->cosmo_dev, sizeof(DevCosmo));
   if (e == cudaSuccess) e = cudaMalloc(&p->partials, cosmo_partial_blocks() * sizeof(double));
@@ -473,13 +484,14 @@ int lpt2_plan(lpt2_plan_t* out, const lpt2_instance* inst, int n_inst, int n_k, 
   const GrowthParams gp = growth_params(p);
   e = launch_cosmo_setup(gp, p->partials, p->cosmo_dev, p->stream);
   p->launches += 2;   // partial sums + final
-  if (e == cudaSuccess) {
-    e = launch_growth(gp, p->tab, p->tabf, p->stream);
-    p->launches += 1;
-  }
   if (e != cudaSuccess) {
     lpt2_plan_destroy(p);
     return fail(LPT2_ECUDA, "set-up kernels: %s", cudaGetErrorString(e));
+  }
+  const int rc = run_growth(p);   // growth tables, then the per-|n|^2 multiplier tables
+  if (rc) {
+    lpt2_plan_destroy(p);
+    return rc;
   }
   *out = p;
   return LPT2_OK;
@@ -487,7 +499,11 @@ int lpt2_plan(lpt2_plan_t* out, const lpt2_instance* inst, int n_inst, int n_k, 
 
 int lpt2_plan_destroy(lpt2_plan_t p) {
   if (!p) return LPT2_OK;
-  for (Group& g : p->groups) cudaFree(g.tw);
+  for (Group& g : p->groups) {
+    cudaFree(g.tw);
+    cudaFree(g.mt0);
+    cudaFree(g.mt1);
+  }
   cudaFree(p->cosmo_dev);
   cudaFree(p->partials);
   cudaFree(p->tab);
@@ -604,6 +620,8 @@ int displace_impl(lpt2_plan_t p, const float* noise, float* psi1, float* psi2, f
   x.delta_out = D;
   for (int i = 0; i < 5; ++i) x.out[i] = X[i];
   x.cosmo = p->cosmo_dev;
+  x.mt0 = p->mt0;
+  x.mt1 = p->mt1;
   x.d1f = p->tabf;
   x.d2f = p->tabf + p->nk;
   x.t1f = p->tabf + 2 * p->nk;
@@ -876,6 +894,8 @@ int lpt2_displace_vjp(lpt2_plan_t p, const float* noise, const float* g_pos, con
   xs.hpsi_out = S[12];
   xs.out[0] = S[13];
   xs.cosmo = p->cosmo_dev;
+  xs.mt0 = p->mt0;
+  xs.mt1 = p->mt1;
   xs.d1f = p->tabf;
   xs.d2f = p->tabf + p->nk;
   xs.t1f = p->tabf + 2 * p->nk;
@@ -896,6 +916,8 @@ int lpt2_displace_vjp(lpt2_plan_t p, const float* noise, const float* g_pos, con
   xph.out[1] = S[3];
   xph.out[2] = S[4];
   xph.cosmo = p->cosmo_dev;
+  xph.mt0 = p->mt0;
+  xph.mt1 = p->mt1;
   LAUNCH(p, "x_phi", 16.0 * V3(p), x_pass(n, xph, p->stream));
   YArgs yp{};
   yp.g = g;
@@ -954,6 +976,8 @@ int lpt2_displace_vjp(lpt2_plan_t p, const float* noise, const float* g_pos, con
   xd.hpsi_in = S[12];
   xd.out[0] = S[6];
   xd.cosmo = p->cosmo_dev;
+  xd.mt0 = p->mt0;
+  xd.mt1 = p->mt1;
   LAUNCH(p, "x_adj_delta", 20.0 * V3(p), x_pass(n, xd, p->stream));
   YArgs yg = yi;
   yg.job.in[0] = S[6];

@@ -242,4 +242,56 @@ cudaError_t launch_growth(const GrowthParams& p, double* tab, float* tabf, cudaS
   return cudaGetLastError();
 }
 
+// ------------------------------------------------------------- mode tables
+// For every integer |n|^2 of an n^3 grid: k = (2 pi / L) sqrt(|n|^2),
+//   x = sqrt(P_lin(k) N^3 / V)  (EH no-wiggle, sigma_8 amplitude),
+//   y = 1 / (k^2 N^3),
+//   z, w = D1(k), D2(k) and (mt1) dD1, dD2 / dln|fR0|, linear in ln k between the
+// growth-table nodes and clamped at the ends - all in FP64, rounded once.
+__device__ double interp_lnk64(const double* t, int nk, double lnkmin, double dlnk, double lnk) {
+  double x = (lnk - lnkmin) / dlnk;
+  if (x <= 0.0) return t[0];
+  if (x >= (double)(nk - 1)) return t[nk - 1];
+  int i = (int)x;
+  if (i > nk - 2) i = nk - 2;
+  const double f = x - (double)i;
+  return t[i] + f * (t[i + 1] - t[i]);
+}
+
+__global__ void k_mode_tables(GrowthParams p, const DevCosmo* cosmo, const double* tab, int inst0, int n, double box,
+                              float4* mt0, float2* mt1) {
+  const int len = mode_table_len(n);
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= len) return;
+  const int inst = inst0 + blockIdx.y;
+  const double* tb = tab + (size_t)inst * 4 * p.nk;
+  float4* o0 = mt0 + (size_t)blockIdx.y * len;
+  float2* o1 = mt1 + (size_t)blockIdx.y * len;
+  if (idx == 0) {
+    o0[0] = make_float4(0.f, 0.f, 0.f, 0.f);
+    o1[0] = make_float2(0.f, 0.f);
+    return;
+  }
+  const double nd = n, kf = 2.0 * M_PI / box;
+  const double k = kf * sqrt((double)idx);
+  const EhConst c = eh_constants(p);
+  const double T = eh_T64(c, k, p.h);
+  const double sp = sqrt(cosmo->amp) * pow(k, 0.5 * p.n_s) * T * sqrt(nd * nd * nd / (box * box * box));
+  const double inv = 1.0 / (k * k * nd * nd * nd);
+  const double lnkmin = log(p.k_min), dlnk = (log(p.k_max) - log(p.k_min)) / (p.nk - 1), lk = log(k);
+  const double d1 = interp_lnk64(tb, p.nk, lnkmin, dlnk, lk);
+  const double d2 = interp_lnk64(tb + p.nk, p.nk, lnkmin, dlnk, lk);
+  const double t1 = interp_lnk64(tb + 2 * p.nk, p.nk, lnkmin, dlnk, lk);
+  const double t2 = interp_lnk64(tb + 3 * p.nk, p.nk, lnkmin, dlnk, lk);
+  o0[idx] = make_float4((float)sp, (float)inv, (float)d1, (float)d2);
+  o1[idx] = make_float2((float)t1, (float)t2);
+}
+
+cudaError_t launch_mode_tables(const GrowthParams& p, const DevCosmo* cosmo, const double* tab, int inst0, int count,
+                               int n, double box, float4* mt0, float2* mt1, cudaStream_t s) {
+  const int len = mode_table_len(n);
+  k_mode_tables<<<dim3((len + 127) / 128, count), 128, 0, s>>>(p, cosmo, tab, inst0, n, box, mt0, mt1);
+  return cudaGetLastError();
+}
+
 }  // namespace lpt2

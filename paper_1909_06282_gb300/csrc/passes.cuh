@@ -257,6 +257,42 @@ __device__ __forceinline__ void cic_deposit_merged(float* __restrict__ rho, floa
   }
 }
 
+// Periodic CIC deposit of one particle with 16-byte vector atomics where the two
+// z cells of a corner row fall in one aligned group of four floats (sm_90+),
+// two scalar atomics otherwise: 4 to 8 atomic instructions per particle.
+template <int N>
+__device__ __forceinline__ void add_zpair(float* __restrict__ rho, size_t b, int iz, int jz, float w0, float w1) {
+  const int q = iz & 3;
+  if (q != 3 && iz + 1 < N) {
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (q == 0) { v.x = w0; v.y = w1; }
+    else if (q == 1) { v.y = w0; v.z = w1; }
+    else { v.z = w0; v.w = w1; }
+    atomicAdd(reinterpret_cast<float4*>(rho + b + (iz - q)), v);
+  } else {
+    atomicAdd(rho + b + iz, w0);
+    atomicAdd(rho + b + jz, w1);
+  }
+}
+
+template <int N>
+__device__ __forceinline__ void cic_deposit_vec(float* __restrict__ rho, float ux, float uy, float uz) {
+  const float fx = floorf(ux), fy = floorf(uy), fz = floorf(uz);
+  const float dx = ux - fx, dy = uy - fy, dz = uz - fz;
+  const int ix = wrap_idx<N>((int)fx), iy = wrap_idx<N>((int)fy), iz = wrap_idx<N>((int)fz);
+  const int jx = wrap_idx<N>(ix + 1), jy = wrap_idx<N>(iy + 1), jz = wrap_idx<N>(iz + 1);
+  const float wx0 = 1.f - dx, wy0 = 1.f - dy, wz0 = 1.f - dz;
+  float w;
+  w = wx0 * wy0; add_zpair<N>(rho, ((size_t)ix * N + iy) * N, iz, jz, w * wz0, w * dz);
+  w = wx0 * dy;  add_zpair<N>(rho, ((size_t)ix * N + jy) * N, iz, jz, w * wz0, w * dz);
+  w = dx * wy0;  add_zpair<N>(rho, ((size_t)jx * N + iy) * N, iz, jz, w * wz0, w * dz);
+  w = dx * dy;   add_zpair<N>(rho, ((size_t)jx * N + jy) * N, iz, jz, w * wz0, w * dz);
+}
+
+#ifndef LPT2_CIC_FUSED
+#define LPT2_CIC_FUSED 0   // deposit used inside k_z_final: 0 scalar-merged, 1 vector
+#endif
+
 // wrap grid coordinate into [0, N)
 template <int N>
 __device__ __forceinline__ float wrapN(float u) {
@@ -348,7 +384,10 @@ __global__ void __launch_bounds__(PassCfg<N>::ZT, LPT2_Z_MINB) k_z_final(ZFinalA
         a.pos[n3 + e] = uy * a.g.cell;
         a.pos[2 * n3 + e] = uz * a.g.cell;
       }
-      if (a.rho) cic_deposit_merged<N>(a.rho, ux, uy, uz);
+      if (a.rho) {
+        if (LPT2_CIC_FUSED == 1) cic_deposit_vec<N>(a.rho, ux, uy, uz);
+        else cic_deposit_merged<N>(a.rho, ux, uy, uz);
+      }
     }
   }
 }
@@ -495,7 +534,14 @@ __global__ void __launch_bounds__(PassCfg<N>::ZT, LPT2_Z_MINB) k_z_adj_source(ZA
 
 // ===================================================================== y pass
 // CTA = (kz block of W, fixed x). Thread tid = t * W + w.
-template <int N>
+// KIND: Y_MULTI  each output = transform of (i k_y)^ord times its input; the input
+//                tile is re-read (an L2 hit after the first) for every output so no
+//                input copy stays in registers;
+//       Y_SUM    out[dst[i]] += conj((i k_y)^ord[i]) forward-transform(in[i]);
+//       Y_ONE    one input, one output, no derivative (forward or inverse).
+enum YKind { Y_MULTI = 0, Y_SUM = 1, Y_ONE = 2 };
+
+template <int N, int KIND>
 __global__ void __launch_bounds__(PassCfg<N>::XT) k_y(YArgs a) {
   using C = PassCfg<N>;
   extern __shared__ float2 smem[];
@@ -507,7 +553,7 @@ __global__ void __launch_bounds__(PassCfg<N>::XT) k_y(YArgs a) {
   const int x = blockIdx.y;
   const size_t base = blockIdx.z * ((size_t)N * N * C::H) + (size_t)x * N * C::H + kz;   // + y * H
   __syncthreads();
-  if (a.job.sum) {
+  if (KIND == Y_SUM) {
     for (int o = 0; o < a.job.n_out; ++o) {
       float2 acc[C::RMAX];
 #pragma unroll
@@ -530,53 +576,35 @@ __global__ void __launch_bounds__(PassCfg<N>::XT) k_y(YArgs a) {
     }
     return;
   }
-  for (int i = 0; i < a.job.n_in; ++i) {
-    float2 in[C::RMAX];
+  if (KIND == Y_ONE) {
+    float2 v[C::RMAX];
 #pragma unroll
-    for (int r = 0; r < C::RMAX; ++r) in[r] = a.job.in[i][base + (size_t)(elem<N>(t, r)) * C::H];
-    for (int o = 0; o < a.job.n_out; ++o) {
-      if (a.job.src[o] != i) continue;
-      const int m = a.job.ord[o];
-      float2 v[C::RMAX];
+    for (int r = 0; r < C::RMAX; ++r) v[r] = a.job.in[0][base + (size_t)(elem<N>(t, r)) * C::H];
+    if (a.inverse) fft<N, true>(v, t, sm, s_tw);
+    else fft<N, false>(v, t, sm, s_tw);
 #pragma unroll
-      for (int r = 0; r < C::RMAX; ++r) {
-        const int n = elem<N>(t, r);
-        const int my = mode_of(n, N);
-        v[r] = (m != 0 && n == C::H) ? make_float2(0.f, 0.f) : deriv(in[r], a.g.kf * (float)my, m);
-      }
-      if (a.inverse) fft<N, true>(v, t, sm, s_tw);
-      else fft<N, false>(v, t, sm, s_tw);
-      float2* dst = a.job.out[o];
+    for (int r = 0; r < C::RMAX; ++r) a.job.out[0][base + (size_t)(elem<N>(t, r)) * C::H] = v[r];
+    return;
+  }
+  for (int o = 0; o < a.job.n_out; ++o) {
+    const float2* src = a.job.in[a.job.src[o]];
+    const int m = a.job.ord[o];
+    float2 v[C::RMAX];
 #pragma unroll
-      for (int r = 0; r < C::RMAX; ++r) dst[base + (size_t)(elem<N>(t, r)) * C::H] = v[r];
+    for (int r = 0; r < C::RMAX; ++r) {
+      const int n = elem<N>(t, r);
+      const float2 u = src[base + (size_t)n * C::H];
+      v[r] = (m != 0 && n == C::H) ? make_float2(0.f, 0.f) : deriv(u, a.g.kf * (float)mode_of(n, N), m);
     }
+    if (a.inverse) fft<N, true>(v, t, sm, s_tw);
+    else fft<N, false>(v, t, sm, s_tw);
+    float2* dst = a.job.out[o];
+#pragma unroll
+    for (int r = 0; r < C::RMAX; ++r) dst[base + (size_t)(elem<N>(t, r)) * C::H] = v[r];
   }
 }
 
 // ===================================================================== x pass
-__device__ __forceinline__ float interp_table(const float* __restrict__ tab, const DevCosmo& c, float k) {
-  float x = (logf(k) - c.lnkmin) * c.inv_dlnk;
-  x = fminf(fmaxf(x, 0.f), (float)(c.nk - 1));
-  int i = (int)x;
-  i = i > c.nk - 2 ? c.nk - 2 : i;
-  const float f = x - (float)i;
-  const float d0 = __ldg(tab + i), d1 = __ldg(tab + i + 1);
-  return fmaf(f, d1 - d0, d0);
-}
-
-// sqrt(P_lin(k)) with the Eisenstein-Hu no-wiggle transfer function (their
-// Eqs. 28-30) in FP32; constants from the set-up kernel.
-__device__ __forceinline__ float sqrt_pk(const DevCosmo& c, float k) {
-  const float sk = c.s043h * k;
-  const float sk2 = sk * sk;
-  const float gamma = c.omh * (c.alpha + (1.f - c.alpha) / (1.f + sk2 * sk2));
-  const float q = k * c.theta2 / gamma;
-  const float L0 = logf(2.f * 2.718281828459045f + 1.8f * q);
-  const float C0 = 14.2f + 731.f / (1.f + 62.5f * q);
-  const float T = L0 / fmaf(C0 * q, q, L0);
-  return c.sqrt_amp * expf(c.ns_half * logf(k)) * T;
-}
-
 // Exact integer P(k) shell of mode (mx, my, mz): b = floor(2 ns |n| / N) for
 // 0 < |n| < N/2, else -1.  A float estimate is corrected by exact 64-bit integer
 // comparisons (b N)^2 <= 4 ns^2 |n|^2 < ((b+1) N)^2; no 64-bit int/float conversion.
@@ -618,13 +646,6 @@ __global__ void __launch_bounds__(PassCfg<N>::XT) k_x(XArgs a) {
   const bool ny_nyq = (ky == C::H);
   const float kf = a.g.kf;
   const size_t blk = ((size_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
-  {                                                   // growth tables of instance inst0 + z
-    const size_t toff = (size_t)(a.g.inst0 + blockIdx.z) * a.g.tab_stride;
-    a.d1f += toff;
-    a.d2f += toff;
-    a.t1f += toff;
-    a.t2f += toff;
-  }
   if (MODE == X_PK) {
     for (int i = threadIdx.x; i < NWARP * 3 * a.n_shells; i += blockDim.x) s_acc[i] = 0.0;
   } else if (MODE == X_ADJ_SOURCE) {
@@ -733,8 +754,8 @@ __global__ void __launch_bounds__(PassCfg<N>::XT) k_x(XArgs a) {
     for (int r = 0; r < C::RMAX; ++r) a.s_out[base + (size_t)(elem<N>(t, r)) * stride] = v[r];
   }
 
-  // k-space multipliers. g = potential to transform back along x.
-  const DevCosmo cz = *a.cosmo;
+  // k-space multipliers from the per-|n|^2 tables.  g = potential to transform back along x.
+  const size_t toff = (size_t)blockIdx.z * mode_table_len(N);
   float2 g[C::RMAX], hpot[C::RMAX];
   float theta = 0.f;
 #pragma unroll
@@ -742,41 +763,35 @@ __global__ void __launch_bounds__(PassCfg<N>::XT) k_x(XArgs a) {
     const int kx = elem<N>(t, r);
     const int mx = mode_of(kx, N);
     const bool zero = ny_nyq || kx == C::H || (mx == 0 && my == 0 && mz == 0);
-    const float k2 = kf * kf * (float)(mx * mx + my * my + mz * mz);
-    const float k = sqrtf(k2);
-    const float inv = zero ? 0.f : a.g.inv_n3 / k2;
+    const int n2 = mx * mx + my * my + mz * mz;
+    const float4 mt = zero ? make_float4(0.f, 0.f, 0.f, 0.f) : __ldg(a.mt0 + toff + n2);
+    const float sc = mt.x, inv = mt.y, d1 = mt.z, d2 = mt.w;   // sqrt(P N^3/V), 1/(k^2 N^3), D1, D2
     const size_t e = base + (size_t)kx * stride;
     if (MODE == X_DELTA) {
-      const float sc = zero ? 0.f : sqrt_pk(cz, k) * a.g.sqrt_n3_over_v;
       const float2 d = cscale(v[r], sc);
       if (a.delta_out) a.delta_out[e] = d;
       g[r] = cscale(d, inv);                                // phi1 = delta / k^2 (1/N^3 folded)
-      if (a.split) hpot[r] = cscale(g[r], zero ? 0.f : interp_table(a.d1f, cz, k));
+      if (a.split) hpot[r] = cscale(g[r], d1);
     } else if (MODE == X_PHI) {                           // v = delta(k) already
       g[r] = cscale(v[r], inv);
     } else if (MODE == X_SOURCE) {                        // v = S(k)
-      const float d2 = zero ? 0.f : interp_table(a.d2f, cz, k);
       float2 u = cscale(v[r], -d2 * inv);                   // phi2 = -S D2 / k^2
       if (!a.split) {
-        const float d1 = zero ? 0.f : interp_table(a.d1f, cz, k);
         const float2 dl = a.delta_in[e];
         u = cadd(u, cscale(dl, d1 * inv));                  // + phi1 D1 (total potential)
       }
       g[r] = u;
     } else if (MODE == X_ADJ_SOURCE) {                    // v = g_u(k)
       const float2 gu = zero ? make_float2(0.f, 0.f) : v[r];
-      const float d1 = zero ? 0.f : interp_table(a.d1f, cz, k);
-      const float d2 = zero ? 0.f : interp_table(a.d2f, cz, k);
       a.hpsi_out[e] = cscale(gu, d1 * inv);                 // h_Psi = D1 g_u / (k^2 N^3)
       g[r] = cscale(gu, -d2 * inv);                         // h_S = -D2 g_u / (k^2 N^3)
       if (!zero) {                                          // dL/dln|fR0| contribution
-        const float t1 = interp_table(a.t1f, cz, k), t2 = interp_table(a.t2f, cz, k);
+        const float2 tt = __ldg(a.mt1 + toff + n2);
         const float2 dl = a.delta_in[e], sk = a.s_in[e];
-        const float cx = t1 * dl.x - t2 * sk.x, cy = t1 * dl.y - t2 * sk.y;
+        const float cx = tt.x * dl.x - tt.y * sk.x, cy = tt.x * dl.y - tt.y * sk.y;
         theta += (cx * gu.x + cy * gu.y) * inv * (mz == 0 ? 1.f : 2.f);
       }
     } else {                                                // X_ADJ_DELTA: v = sum of h_phi groups
-      const float sc = zero ? 0.f : sqrt_pk(cz, k) * a.g.sqrt_n3_over_v;
       const float2 h = cadd(cscale(v[r], inv), a.hpsi_in[e]);
       g[r] = cscale(h, sc);                                 // s(k) (h_Psi + h_phi)
     }
@@ -864,12 +879,18 @@ template <int N> cudaError_t launch_z_adj_source_t(const ZAdjSourceArgs& a, cuda
   k_z_adj_source<N><<<N * N / 2 / C::ZP, C::ZT, C::ZSMEM, s>>>(a);
   return cudaGetLastError();
 }
-template <int N> cudaError_t launch_y_t(const YArgs& a, cudaStream_t s) {
+template <int N, int KIND> cudaError_t launch_y_k(const YArgs& a, cudaStream_t s) {
   using C = PassCfg<N>;
   LPT2_CHECK_BATCH(a);
-  cudaFuncSetAttribute(k_y<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::XSMEM);
-  k_y<N><<<dim3(C::H / C::W, N, a.g.batch), C::XT, C::XSMEM, s>>>(a);
+  cudaFuncSetAttribute(k_y<N, KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::XSMEM);
+  k_y<N, KIND><<<dim3(C::H / C::W, N, a.g.batch), C::XT, C::XSMEM, s>>>(a);
   return cudaGetLastError();
+}
+template <int N> cudaError_t launch_y_t(const YArgs& a, cudaStream_t s) {
+  if (a.job.sum) return launch_y_k<N, Y_SUM>(a, s);
+  if (a.job.n_in == 1 && a.job.n_out == 1 && a.job.ord[0] == 0 && a.job.src[0] == 0)
+    return launch_y_k<N, Y_ONE>(a, s);
+  return launch_y_k<N, Y_MULTI>(a, s);
 }
 template <int N, int MODE> cudaError_t launch_x_m(const XArgs& a, cudaStream_t s) {
   using C = PassCfg<N>;

@@ -148,6 +148,10 @@ struct XArgs {
   double* pk_part;        // X_PK: per-block partials [blocks][3][n_shells]
   int n_shells;
   const float* shell_w;   // X_PKADJ: weight per shell
+  // per-|n|^2 multiplier tables of the group (index = global instance - inst0 of the
+  // group, then |n|^2): {sqrt(P N^3/V), 1/(k^2 N^3), D1, D2} and {dD1, dD2}/dln|fR0|
+  const float4* mt0;
+  const float2* mt1;
   double* theta_part;     // X_ADJ_SOURCE: per-block partial of dL/dln|fR0|
 };
 
@@ -204,6 +208,11 @@ int cosmo_partial_blocks();
 cudaError_t launch_cosmo_setup(const GrowthParams&, double* partials, DevCosmo* out, cudaStream_t);
 cudaError_t launch_growth(const GrowthParams&, double* tab /*[4][nk]*/, float* tabf /*[4][nk]*/,
                           cudaStream_t);
+// Multiplier tables of one group of `count` instances of grid n, box L: entries
+// |n|^2 = 0 .. 3 (n/2)^2 per instance (FP64 evaluation, rounded once).
+__host__ __device__ inline int mode_table_len(int n) { return 3 * (n / 2) * (n / 2) + 1; }
+cudaError_t launch_mode_tables(const GrowthParams&, const DevCosmo* cosmo, const double* tab, int inst0, int count,
+                               int n, double box, float4* mt0, float2* mt1, cudaStream_t);
 cudaError_t launch_pk_adj_weights(const double* g_pk, const int64_t* n_modes, int n_shells, double v_over_n6,
                                   float* w, cudaStream_t);
 cudaError_t launch_sum_partials(const double* part, int n, double* out, cudaStream_t);
