@@ -10,9 +10,11 @@ rounds.
 
 Stream layout (a reading; the paper has no RNG):
   key     = (seed mod 2^32, seed div 2^32)
-  counter = (c mod 2^32, c div 2^32, 0, 0), c = (ix*N + iy)*N + iz (z fastest)
+  counter = (c mod 2^32, c div 2^32, 0, 0) with c = (ix*N + iy)*N + iz (z fastest) of the
+            cell with even iy; the cells (ix, iy, iz) and (ix, iy+1, iz) share that draw
   u_j     = ((x_j >> 8) + 1) * 2^-24 for output words x_0, x_1  (exact in FP32, in (0, 1])
-  g       = sqrt(-2 ln u_0) * cos(2 pi u_1), evaluated in float64, stored as float32.
+  g       = sqrt(-2 ln u_0) * (cos, sin)(2 pi u_1) for (even iy, odd iy): both outputs of
+            one Box-Muller transform, evaluated in float64, stored as float32.
 """
 from __future__ import annotations
 
@@ -61,9 +63,18 @@ def uniforms(x: np.ndarray) -> np.ndarray:
 
 def gaussian_noise(n: int, seed: int, first: int = 0, count: int | None = None,
                    as_float64: bool = False) -> np.ndarray:
-    """Unit-variance Gaussian per cell via Box-Muller on Philox words 0 and 1.
-    Returns the flat cells [first, first+count) (all N^3 cells by default)."""
-    x0, x1, _, _ = _words(n, seed, first, count)
+    """Unit-variance Gaussian per cell via Box-Muller on Philox words 0 and 1 of the
+    draw of its even-iy cell.  Returns the flat cells [first, first+count) (all N^3
+    cells by default)."""
+    total = n ** 3
+    count = total - first if count is None else count
+    cell = np.arange(first, first + count, dtype=np.int64)
+    iy = (cell // n) % n
+    base = np.where(iy % 2 == 0, cell, cell - n).astype(np.uint64)      # counter of the pair
+    ctr = (base & _M32, base >> np.uint64(32), np.zeros_like(base), np.zeros_like(base))
+    key = (seed & 0xFFFFFFFF, (seed >> 32) & 0xFFFFFFFF)
+    x0, x1, _, _ = philox4x32_10(ctr, key)
     u0, u1 = uniforms(x0), uniforms(x1)
-    g = np.sqrt(-2.0 * np.log(u0)) * np.cos(2.0 * np.pi * u1)
+    r = np.sqrt(-2.0 * np.log(u0))
+    g = np.where(iy % 2 == 0, r * np.cos(2.0 * np.pi * u1), r * np.sin(2.0 * np.pi * u1))
     return g if as_float64 else g.astype(np.float32)

@@ -707,11 +707,16 @@ int displace_impl(lpt2_plan_t p, const float* noise, float* psi1, float* psi2, f
   }
   zf.psi1 = psi1;
   zf.psi2 = psi2;
-  zf.pos = pos;
-  zf.rho = rho;
-  LAUNCH(p, "z_final",
-         ((split ? 24.0 : 12.0) + (pos ? 12.0 : 0.0) + (psi1 ? 12.0 : 0.0) + (psi2 ? 12.0 : 0.0) + 8.0) * V3(p),
+  // The CIC deposit runs as its own kernel at full occupancy (atomic throughput
+  // needs many warps in flight): z_final writes the positions (to the caller's
+  // array, or to dead workspace slots 2-4) and k_cic reads them back.
+  float* posw = pos ? pos : reinterpret_cast<float*>(X[0]);
+  zf.pos = posw;
+  zf.rho = nullptr;
+  LAUNCH(p, "z_final", ((split ? 24.0 : 12.0) + 12.0 + (psi1 ? 12.0 : 0.0) + (psi2 ? 12.0 : 0.0)) * V3(p),
          z_final(n, zf, p->stream));
+  CicArgs ca{g, posw, rho};
+  LAUNCH(p, "cic", 20.0 * V3(p), launch_cic(ca, p->stream));
   if (dk) {
     cudaError_t e = cudaMemcpyAsync(dk, D, cells * sizeof(float), cudaMemcpyDeviceToDevice, p->stream);
     if (e != cudaSuccess) return fail(LPT2_ECUDA, "dk copy: %s", cudaGetErrorString(e));

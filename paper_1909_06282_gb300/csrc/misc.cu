@@ -13,7 +13,7 @@ __global__ void __launch_bounds__(256) k_cic(CicArgs a) {
   a.rho += (size_t)blockIdx.y * n3;
   float u[3];
   for (int c = 0; c < 3; ++c) u[c] = wrapN<N>(__ldg(a.pos + c * n3 + i) * a.g.inv_cell);
-  cic_deposit_merged<N>(a.rho, u[0], u[1], u[2]);
+  cic_deposit_vec<N>(a.rho, u[0], u[1], u[2]);   // fastest of scalar / neighbour-merged / vector on real positions
 }
 
 cudaError_t launch_cic(const CicArgs& a, cudaStream_t s) {
@@ -100,8 +100,11 @@ cudaError_t launch_pk_finalize(const double* part, int n_blocks, int n_shells, d
 
 __global__ void k_noise(int n, uint32_t k0, uint32_t k1, float* out) {
   const size_t n3 = (size_t)n * n * n;
-  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n3; i += (size_t)gridDim.x * blockDim.x)
-    out[i] = philox_gauss(i, k0, k1);
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n3; i += (size_t)gridDim.x * blockDim.x) {
+    const bool odd = ((i / n) % n) & 1;   // iy odd: sine output of the draw at iy - 1
+    const float2 g2 = philox_gauss2(odd ? i - n : i, k0, k1);
+    out[i] = odd ? g2.y : g2.x;
+  }
 }
 
 cudaError_t launch_noise(const Geo& g, uint32_t k0, uint32_t k1, float* out, cudaStream_t s) {

@@ -130,10 +130,10 @@ __global__ void __launch_bounds__(PassCfg<N>::ZT, LPT2_Z_MINB) k_z_r2c(ZR2CArgs 
   for (int r = 0; r < C::RMAX; ++r) {
     const int n = elem<N>(t, r);
     float fa, fb;
-    if (SRC == Z_NOISE) {
-      const uint64_t ca = (uint64_t)rowa * N + n, cb = (uint64_t)rowb * N + n;
-      fa = philox_gauss(ca, a.seed_lo, a.seed_hi);
-      fb = philox_gauss(cb, a.seed_lo, a.seed_hi);
+    if (SRC == Z_NOISE) {   // rows (x, y) and (x, y+1), y even: one Box-Muller pair per z
+      const float2 g2 = philox_gauss2((uint64_t)rowa * N + n, a.seed_lo, a.seed_hi);
+      fa = g2.x;
+      fb = g2.y;
     } else {
       fa = __ldg(a.in + (size_t)rowa * N + n);
       fb = __ldg(a.in + (size_t)rowb * N + n);
@@ -647,7 +647,8 @@ __global__ void __launch_bounds__(PassCfg<N>::XT) k_x(XArgs a) {
   const float kf = a.g.kf;
   const size_t blk = ((size_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
   if (MODE == X_PK) {
-    for (int i = threadIdx.x; i < NWARP * 3 * a.n_shells; i += blockDim.x) s_acc[i] = 0.0;
+    float* s_accf = reinterpret_cast<float*>(s_acc);
+    for (int i = threadIdx.x; i < NWARP * 5 * a.n_shells; i += blockDim.x) s_accf[i] = 0.f;
   } else if (MODE == X_ADJ_SOURCE) {
     for (int i = threadIdx.x; i < NWARP; i += blockDim.x) s_acc[i] = 0.0;
   }
@@ -691,11 +692,13 @@ __global__ void __launch_bounds__(PassCfg<N>::XT) k_x(XArgs a) {
   if (MODE == X_PK) {
     // P(k) shells.  Lanes of a warp see neighbouring modes, so they fall in few
     // shells: for each distinct shell in the warp the lanes of that shell are
-    // summed (at most 32 terms, FP32) and one lane adds the sums to this warp's
-    // own FP64 accumulators.
+    // summed and one lane adds the sum to this warp's own accumulator, a
+    // Kahan-compensated FP32 pair (FP64-class accuracy without FP64 adds, which
+    // are slow on this part); the sums over warps and blocks are FP64.
     const float pnorm = a.g.box * a.g.box * a.g.box * a.g.inv_n3 * a.g.inv_n3;
     const int ns = a.n_shells;
-    double* s_mine = s_acc + warp * 3 * ns;
+    // per warp: sum P [ns], its compensation [ns], sum |k| [ns], compensation [ns], count [ns]
+    float* s_mine = reinterpret_cast<float*>(s_acc) + warp * 5 * ns;
 #pragma unroll
     for (int r = 0; r < C::RMAX; ++r) {
       const int kx = elem<N>(t, r);
@@ -717,18 +720,31 @@ __global__ void __launch_bounds__(PassCfg<N>::XT) k_x(XArgs a) {
           sk += __shfl_xor_sync(0xffffffffu, sk, off);
           sc += __shfl_xor_sync(0xffffffffu, sc, off);
         }
-        if (lane == leader) {
-          s_mine[key] += (double)sp;
-          s_mine[ns + key] += (double)sk;
-          s_mine[2 * ns + key] += (double)sc;
+        if (lane == leader) {   // this warp's own accumulators: no atomics
+          {
+            const float y = sp - s_mine[ns + key], t2 = s_mine[key] + y;
+            s_mine[ns + key] = (t2 - s_mine[key]) - y;
+            s_mine[key] = t2;
+          }
+          {
+            const float y = sk - s_mine[3 * ns + key], t2 = s_mine[2 * ns + key] + y;
+            s_mine[3 * ns + key] = (t2 - s_mine[2 * ns + key]) - y;
+            s_mine[2 * ns + key] = t2;
+          }
+          s_mine[4 * ns + key] += (float)sc;   // integer counts <= 2 * 32 * RMAX: exact
         }
         todo &= ~__ballot_sync(0xffffffffu, mine);
       }
     }
     __syncthreads();
+    const float* s_all = reinterpret_cast<const float*>(s_acc);
     for (int i = threadIdx.x; i < 3 * ns; i += blockDim.x) {
+      const int q = i / ns, b = i % ns;   // quantity (P, |k|, count), shell
       double acc = 0.0;
-      for (int wi = 0; wi < NWARP; ++wi) acc += s_acc[wi * 3 * ns + i];   // fixed order
+      for (int wi = 0; wi < NWARP; ++wi) {   // fixed order
+        const float* wv = s_all + wi * 5 * ns;
+        acc += (q < 2) ? (double)wv[2 * q * ns + b] - (double)wv[(2 * q + 1) * ns + b] : (double)wv[4 * ns + b];
+      }
       a.pk_part[blk * 3 * ns + i] = acc;
     }
     return;
@@ -895,7 +911,7 @@ template <int N> cudaError_t launch_y_t(const YArgs& a, cudaStream_t s) {
 template <int N, int MODE> cudaError_t launch_x_m(const XArgs& a, cudaStream_t s) {
   using C = PassCfg<N>;
   LPT2_CHECK_BATCH(a);
-  const int smem = C::XSMEM + (MODE == X_PK ? (C::XT / 32) * 3 * a.n_shells * 8
+  const int smem = C::XSMEM + (MODE == X_PK ? (C::XT / 32) * 5 * a.n_shells * 4
                                             : (MODE == X_ADJ_SOURCE ? (C::XT / 32) * 8 : 0));
   cudaFuncSetAttribute(k_x<N, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   k_x<N, MODE><<<dim3(C::H / C::W, N, a.g.batch), C::XT, smem, s>>>(a);

@@ -123,3 +123,19 @@ def test_noise_is_counter_addressed():
     b = philox.gaussian_noise(32, 9, first=1000, count=77)
     np.testing.assert_array_equal(a[1000:1077], b)
     assert not np.array_equal(a, philox.gaussian_noise(32, 10))
+
+
+def test_noise_pairs_are_one_box_muller_draw():
+    """Cells (x, 2j, z) and (x, 2j+1, z) are the cosine and sine outputs of the draw at
+    the even cell: their squares sum to -2 ln u0 and their angle is 2 pi u1."""
+    n, seed = 8, 4
+    g = philox.gaussian_noise(n, seed, as_float64=True).reshape(n, n, n)
+    x0, x1, _, _ = philox._words(n, seed)
+    u0 = philox.uniforms(x0).reshape(n, n, n)[:, 0::2, :]
+    u1 = philox.uniforms(x1).reshape(n, n, n)[:, 0::2, :]
+    ge, go = g[:, 0::2, :], g[:, 1::2, :]
+    np.testing.assert_allclose(ge ** 2 + go ** 2, -2 * np.log(u0), rtol=1e-12, atol=1e-15)
+    ang = np.mod(np.arctan2(go, ge), 2 * np.pi)
+    np.testing.assert_allclose(np.cos(ang - 2 * np.pi * u1), 1.0, atol=1e-9)
+    big = philox.gaussian_noise(64, 5, as_float64=True).reshape(64, 64, 64)
+    assert abs(np.corrcoef(big[:, 0::2, :].ravel(), big[:, 1::2, :].ravel())[0, 1]) < 0.01
