@@ -43,6 +43,27 @@ def dist_env():
     return world, rank, local
 
 
+def rank_seed(rank):
+    """Seed of the realisation a rank runs: one independent realisation per rank."""
+    return WORKLOAD["seed"] + rank
+
+
+def max_over_ranks(dist, values, device):
+    """Element-wise maximum over ranks of per-rank timings (ms); identity without a
+    process group.  The slowest rank sets the whole job's time."""
+    if dist is None:
+        return [float(v) for v in values]
+    import torch
+    t = torch.tensor([float(v) for v in values], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(x) for x in t]
+
+
+def whole_job_rate(per_rank, world, ms):
+    """Units all ranks processed per second, from the max-over-ranks step time."""
+    return per_rank * world / (ms / 1e3)
+
+
 class ClockSampler:
     """nvidia-smi clock / throttle sampling during the timed region."""
 
@@ -325,7 +346,7 @@ def bench_ours(args):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
     n, box = WORKLOAD["n"], WORKLOAD["box"]
-    inst = W.Instance(n, box, WORKLOAD["seed"] + rank, W.COSMO.replace(fr0_abs=WORKLOAD["fr0"]))
+    inst = W.Instance(n, box, rank_seed(rank), W.COSMO.replace(fr0_abs=WORKLOAD["fr0"]))
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
         t0 = time.perf_counter()
@@ -450,14 +471,11 @@ def bench_ours(args):
         stream.synchronize()
         ms_e2e = e2.elapsed_time(e3) / args.steps
 
-    if dist:
-        t = torch.tensor([ms, ms_e2e, ms_fv], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms, ms_e2e, ms_fv = float(t[0]), float(t[1]), float(t[2])
+    ms, ms_e2e, ms_fv = max_over_ranks(dist, [ms, ms_e2e, ms_fv], "cuda")
 
     if rank == 0:
         parts = n ** 3 * world
-        value = parts / (ms / 1e3)
+        value = whole_job_rate(n ** 3, world, ms)
         peak, peak_kind = measured_peak_gbs()
         total_ms = sum(v["total_ms"] for v in kstats.values())
         dom = max(kstats.items(), key=lambda kv: kv[1]["total_ms"])

@@ -237,6 +237,14 @@ const char* lpt2_last_error(void);
  * the host; used to report launch counts). */
 int64_t lpt2_launch_count(lpt2_plan_t plan);
 
+/* Waits for the plan's stream and reads the plan's device error word.  Kernels that
+ * stage data with bulk asynchronous copies wait on them with a bounded wait (about
+ * one second); a wait that runs out makes its CTA return early and sets the word.
+ * Returns LPT2_OK, or LPT2_ETIMEOUT (the word is then cleared and the outputs of
+ * every launch since the previous check are invalid), or LPT2_ECUDA.  Not part of
+ * the paper's method: a run-time health check of the asynchronous launches. */
+int lpt2_device_status(lpt2_plan_t plan);
+
 #ifdef __cplusplus
 }
 #endif

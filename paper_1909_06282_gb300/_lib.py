@@ -84,6 +84,7 @@ def load_library():
         "lpt2_fft_c2r": (i, [vp, vp, vp]),
         "lpt2_last_error": (C.c_char_p, []),
         "lpt2_launch_count": (i64, [vp]),
+        "lpt2_device_status": (i, [vp]),
         "lpt2_timing": (i, [vp, i]),
         "lpt2_cic_pk_noalloc": (i, [i, d, vp, vp, vp, vp, vp, i, vp]),
         "lpt2_set_fr0": (i, [vp, d]),
@@ -195,6 +196,12 @@ def lpt2_workspace_size(plan: Plan) -> int:
 
 def lpt2_launch_count(plan: Plan) -> int:
     return int(load_library().lpt2_launch_count(plan.handle))
+
+
+def lpt2_device_status(plan: Plan) -> None:
+    """Synchronises the plan's stream; raises LPT2Error if a bounded device-side wait
+    gave up since the previous check."""
+    _check(load_library().lpt2_device_status(plan.handle))
 
 
 def lpt2_growth_tables(plan: Plan):

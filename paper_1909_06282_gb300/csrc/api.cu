@@ -71,6 +71,7 @@ struct lpt2_plan_s {
   int n_inst;
   uint64_t* seeds_dev;        // [n_inst]
   double* fr0_dev;            // [n_inst]
+  int* dev_err;               // device error word written by bounded waits (0 = ok)
   size_t slot_sz;             // bytes per workspace slot: max over groups of count n^3 4
   int xb_max;                 // max over groups of count * x-pass blocks
   size_t total_cells;         // sum over instances of n^3
@@ -153,7 +154,7 @@ float2* slot(const lpt2_plan_s* p, int i) { return reinterpret_cast<float2*>(p->
 double* pk_part(const lpt2_plan_s* p) { return reinterpret_cast<double*>(p->ws + tail_pk_part(p)); }
 
 Geo make_geo(const lpt2_plan_s* p) {
-  Geo g;
+  Geo g{};
   const double n = p->n;
   g.n = p->n;
   g.kf = (float)(2.0 * M_PI / p->box);
@@ -165,6 +166,7 @@ Geo make_geo(const lpt2_plan_s* p) {
   g.batch = p->cur_batch;
   g.inst0 = p->cur_inst0;
   g.tab_stride = 4 * p->nk;
+  g.err = p->dev_err;
   return g;
 }
 
@@ -365,6 +367,21 @@ const char* lpt2_last_error(void) { return g_err.c_str(); }
 
 int64_t lpt2_launch_count(lpt2_plan_t plan) { return plan ? plan->launches : -1; }
 
+int lpt2_device_status(lpt2_plan_t p) {
+  if (!p) return fail(LPT2_EINVAL, "null plan");
+  cudaError_t e = cudaStreamSynchronize(p->stream);
+  if (e != cudaSuccess) return fail(LPT2_ECUDA, "stream: %s", cudaGetErrorString(e));
+  int code = 0;
+  e = cudaMemcpy(&code, p->dev_err, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return fail(LPT2_ECUDA, "error word: %s", cudaGetErrorString(e));
+  if (code) {
+    cudaMemset(p->dev_err, 0, sizeof(int));
+    return fail(LPT2_ETIMEOUT, "a bounded device-side wait gave up (kernel code %d); outputs of the "
+                "launches since the last check are invalid", code);
+  }
+  return LPT2_OK;
+}
+
 static int check_cosmo(const lpt2_instance* inst) {
   const lpt2_cosmo& c = inst->cosmo;
   if (!supported_n(inst->n)) return fail(LPT2_EUNSUPPORTED, "grid size %d not supported", inst->n);
@@ -454,6 +471,8 @@ int lpt2_plan(lpt2_plan_t* out, const lpt2_instance* inst, int n_inst, int n_k, 
   if (e == cudaSuccess) e = cudaMalloc(&p->tabf, (size_t)n_inst * 4 * n_k * sizeof(float));
   if (e == cudaSuccess) e = cudaMalloc(&p->seeds_dev, (size_t)n_inst * sizeof(uint64_t));
   if (e == cudaSuccess) e = cudaMalloc(&p->fr0_dev, (size_t)n_inst * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&p->dev_err, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(p->dev_err, 0, sizeof(int));
   if (e != cudaSuccess) {
     lpt2_plan_destroy(p);
     return fail(LPT2_ENOMEM, "plan allocation failed: %s", cudaGetErrorString(e));
@@ -510,6 +529,7 @@ int lpt2_plan_destroy(lpt2_plan_t p) {
   cudaFree(p->tabf);
   cudaFree(p->seeds_dev);
   cudaFree(p->fr0_dev);
+  cudaFree(p->dev_err);
   for (auto& gc : p->graphs)
     if (gc.exec) cudaGraphExecDestroy(gc.exec);
   if (p->ev) {
@@ -712,7 +732,6 @@ int displace_impl(lpt2_plan_t p, const float* noise, float* psi1, float* psi2, f
   // array, or to dead workspace slots 2-4) and k_cic reads them back.
   float* posw = pos ? pos : reinterpret_cast<float*>(X[0]);
   zf.pos = posw;
-  zf.rho = nullptr;
   LAUNCH(p, "z_final", ((split ? 24.0 : 12.0) + 12.0 + (psi1 ? 12.0 : 0.0) + (psi2 ? 12.0 : 0.0)) * V3(p),
          z_final(n, zf, p->stream));
   CicArgs ca{g, posw, rho};

@@ -12,6 +12,7 @@
 #include "fft_core.cuh"
 #include "passes.h"
 #include "philox.cuh"
+#include "tma.cuh"
 
 namespace lpt2 {
 
@@ -177,84 +178,121 @@ __global__ void __launch_bounds__(PassCfg<N>::ZT, LPT2_Z_MINB) k_z_c2r(ZC2RArgs 
 }
 
 // Six phi_ij -> S = sum_{i<j} (phi_ii phi_jj - phi_ij^2)  (Eq. second-ini) -> forward z.
+//
+// A CTA owns ROWS = 2 ZP consecutive real rows (x, y) of every field.  The rows of
+// one field are contiguous in the half-spectrum layout, so each field's tile is one
+// bulk copy into a ring of STAGES shared-memory buffers: the copy of field f +
+// STAGES is in flight while field f is transformed.  Rows 2p and 2p + 1 of a field
+// are packed as one complex pencil (Z = A + i B), so its inverse transform gives the
+// field on both rows; the source term accumulates per row in registers:
+//   S = phi_xx phi_yy + (phi_xx + phi_yy) phi_zz - phi_xy^2 - phi_xz^2 - phi_yz^2.
+#ifndef LPT2_ZS_STAGES
+#define LPT2_ZS_STAGES 2
+#endif
+
+template <int N> struct ZSrcCfg {
+  using C = PassCfg<N>;
+  static constexpr int STAGES = LPT2_ZS_STAGES;
+  static constexpr int ROWS = 2 * C::ZP;                     // real rows per CTA
+  static constexpr int STAGE_F2 = ROWS * C::H;               // one field's tile (float2)
+  static constexpr unsigned STAGE_BYTES = STAGE_F2 * 8u;
+  static constexpr int BAR_OFF = STAGES * STAGE_BYTES;       // mbarriers after the ring
+  static constexpr int SMEM = BAR_OFF + 64 + C::ZSMEM;       // + twiddles and exchange rows
+  static_assert(STAGES >= 1 && STAGES <= 6 && STAGES * 8 <= 64, "stage count");
+  static_assert(STAGE_BYTES % 16 == 0 && (C::H * 8) % 16 == 0, "bulk copies need 16-byte multiples");
+};
+
+// Z value at element n of the Hermitian extension of half rows ra, rb (shared
+// memory), both multiplied by (i k_z)^m first: Z = A + i B.
+template <int N>
+__device__ __forceinline__ float2 z_assemble_smem(const float2* ra, const float2* rb, int n, float kf, int m) {
+  constexpr int H = N / 2;
+  if (n == H) return make_float2(0.f, 0.f);
+  const bool lo = n < H;
+  const int j = lo ? n : N - n;
+  const float kz = kf * (float)j;
+  float2 A = deriv(ra[j], kz, m);
+  float2 B = deriv(rb[j], kz, m);
+  if (!lo) { A = cconj(A); B = cconj(B); }
+  return make_float2(A.x - B.y, A.y + B.x);
+}
+
 template <int N>
 __global__ void __launch_bounds__(PassCfg<N>::ZT, LPT2_Z_MINB) k_z_source(ZSourceArgs a) {
   using C = PassCfg<N>;
-  extern __shared__ float2 smem[];
-  float2* s_tw = smem;
-  load_twiddles(s_tw, a.tw, N);
+  using Q = ZSrcCfg<N>;
+  extern __shared__ __align__(128) unsigned char zs_raw[];
+  float2* ring = reinterpret_cast<float2*>(zs_raw);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(zs_raw + Q::BAR_OFF);
+  float2* s_tw = reinterpret_cast<float2*>(zs_raw + Q::BAR_OFF + 64);
+  __shared__ int s_fail;
   const int p = threadIdx.x / C::TPP, t = threadIdx.x % C::TPP;
-  const SmemRow sm{smem + N + p * SmemRow::words(N)};
-  const int pair = blockIdx.x * C::ZP + p;
-  const int rows[2] = {2 * pair, 2 * pair + 1};
+  const SmemRow sm{s_tw + N + p * SmemRow::words(N)};
   const size_t zoff = blockIdx.z * ((size_t)N * N * N / 2);   // instance blockIdx.z
-#pragma unroll
-  for (int i = 0; i < 6; ++i) a.in[i] += zoff;
-  a.out += zoff;
-  float S[2][C::RMAX];
+  const size_t tile = (size_t)blockIdx.x * Q::STAGE_F2;        // first float2 of the tile in a field
+  if (threadIdx.x == 0) {
+    s_fail = 0;
+    for (int s = 0; s < Q::STAGES; ++s) mbar_init(&bar[s], 1);
+    mbar_init_fence();
+  }
   __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int f = 0; f < Q::STAGES; ++f) {
+      mbar_expect_tx(&bar[f], Q::STAGE_BYTES);
+      bulk_load(ring + f * Q::STAGE_F2, a.in[f] + zoff + tile, Q::STAGE_BYTES, &bar[f]);
+    }
+  }
+  load_twiddles(s_tw, a.tw, N);
+  float S0[C::RMAX], S1[C::RMAX], T0[C::RMAX], T1[C::RMAX];
 #pragma unroll
-  for (int h = 0; h < 2; ++h) {
-    const size_t off = (size_t)rows[h] * C::H;
-    float T[C::RMAX];
+  for (int f = 0; f < 6; ++f) {
+    const int s = f % Q::STAGES;
+    const bool ok = mbar_wait(&bar[s], (f / Q::STAGES) & 1);
+    if (!ok) s_fail = 1;
+    float2 v[C::RMAX];
+    const float2* ra = ring + s * Q::STAGE_F2 + (2 * p) * C::H;
 #pragma unroll
-    for (int pr = 0; pr < 3; ++pr) {
-      float2 v[C::RMAX];
+    for (int r = 0; r < C::RMAX; ++r)
+      v[r] = ok ? z_assemble_smem<N>(ra, ra + C::H, elem<N>(t, r), a.g.kf, a.ord[f]) : make_float2(0.f, 0.f);
+    __syncthreads();   // stage s consumed by every thread (and, at f = 0, twiddles visible)
+    if (s_fail) {      // a copy never landed: wait (bounded) for the copies in flight, report
+      if (threadIdx.x == 0) {
+        for (int g = f; g < 6 && g < f + Q::STAGES; ++g) mbar_wait(&bar[g % Q::STAGES], (g / Q::STAGES) & 1);
+        report_device_error(a.g.err, LPT2_DEV_ETIMEOUT_ZSOURCE);
+      }
+      return;
+    }
+    if (threadIdx.x == 0 && f + Q::STAGES < 6) {
+      mbar_expect_tx(&bar[s], Q::STAGE_BYTES);
+      bulk_load(ring + s * Q::STAGE_F2, a.in[f + Q::STAGES] + zoff + tile, Q::STAGE_BYTES, &bar[s]);
+    }
+    fft<N, true>(v, t, sm, s_tw);
 #pragma unroll
-      for (int r = 0; r < C::RMAX; ++r)
-        v[r] = z_assemble<N>(a.in[2 * pr] + off, a.in[2 * pr + 1] + off, elem<N>(t, r), a.g.kf,
-                             a.ord[2 * pr], a.ord[2 * pr + 1]);
-      fft<N, true>(v, t, sm, s_tw);
-#pragma unroll
-      for (int r = 0; r < C::RMAX; ++r) {
-        const float e = v[r].x, f = v[r].y;
-        if (pr == 0) {          // phi_xx, phi_yy
-          S[h][r] = e * f;
-          T[r] = e + f;
-        } else if (pr == 1) {   // phi_zz, phi_xy
-          S[h][r] = fmaf(T[r], e, fmaf(-f, f, S[h][r]));
-        } else {                // phi_xz, phi_yz
-          S[h][r] = fmaf(-e, e, fmaf(-f, f, S[h][r]));
-        }
+    for (int r = 0; r < C::RMAX; ++r) {
+      const float e = v[r].x, g = v[r].y;   // rows 2p and 2p + 1
+      if (f == 0) {            // phi_xx
+        S0[r] = e;
+        S1[r] = g;
+      } else if (f == 1) {     // phi_yy
+        T0[r] = S0[r] + e;
+        T1[r] = S1[r] + g;
+        S0[r] *= e;
+        S1[r] *= g;
+      } else if (f == 2) {     // phi_zz
+        S0[r] = fmaf(T0[r], e, S0[r]);
+        S1[r] = fmaf(T1[r], g, S1[r]);
+      } else {                 // phi_xy, phi_xz, phi_yz
+        S0[r] = fmaf(-e, e, S0[r]);
+        S1[r] = fmaf(-g, g, S1[r]);
       }
     }
   }
   float2 v[C::RMAX];
 #pragma unroll
-  for (int r = 0; r < C::RMAX; ++r) v[r] = make_float2(S[0][r], S[1][r]);
+  for (int r = 0; r < C::RMAX; ++r) v[r] = make_float2(S0[r], S1[r]);
   fft<N, false>(v, t, sm, s_tw);
-  z_store_pair<N>(v, t, sm, a.out + (size_t)rows[0] * C::H, a.out + (size_t)rows[1] * C::H);
-}
-
-// Periodic CIC deposit of one unit-mass particle per lane at grid coordinates u
-// (cells), with all 32 lanes of the warp active.  When neighbouring lanes carry
-// particles that are neighbours along z (the z pass gives each warp 32
-// consecutive particles of one row), the upper z weight of lane i and the lower
-// z weight of lane i+1 usually land in the same cell: they are summed with one
-// shuffle and deposited by a single atomic, so about 5 instead of 8 float
-// atomics are issued per particle.
-template <int N>
-__device__ __forceinline__ void cic_deposit_merged(float* __restrict__ rho, float ux, float uy, float uz) {
-  const int lane = threadIdx.x & 31;
-  const float fx = floorf(ux), fy = floorf(uy), fz = floorf(uz);
-  const float dx = ux - fx, dy = uy - fy, dz = uz - fz;
-  const int ix = wrap_idx<N>((int)fx), iy = wrap_idx<N>((int)fy), cz = wrap_idx<N>((int)fz);
-#pragma unroll
-  for (int corner = 0; corner < 4; ++corner) {
-    const int ox = corner >> 1, oy = corner & 1;
-    const int key = wrap_idx<N>(ix + ox) * N + wrap_idx<N>(iy + oy);
-    const float wxy = (ox ? dx : 1.f - dx) * (oy ? dy : 1.f - dy);
-    float w0 = wxy * (1.f - dz);
-    const float w1 = wxy * dz;
-    const int pkey = __shfl_up_sync(0xffffffffu, key, 1), pcz = __shfl_up_sync(0xffffffffu, cz, 1);
-    const float pw1 = __shfl_up_sync(0xffffffffu, w1, 1);
-    const int nkey = __shfl_down_sync(0xffffffffu, key, 1), ncz = __shfl_down_sync(0xffffffffu, cz, 1);
-    if (lane > 0 && pkey == key && pcz + 1 == cz) w0 += pw1;             // take the left neighbour's
-    const bool give = lane < 31 && nkey == key && cz + 1 == ncz;          // right neighbour takes mine
-    float* row = rho + (size_t)key * N;
-    atomicAdd(row + cz, w0);
-    if (!give) atomicAdd(row + wrap_idx<N>(cz + 1), w1);
-  }
+  float2* out = a.out + zoff + tile + (size_t)(2 * p) * C::H;
+  z_store_pair<N>(v, t, sm, out, out + C::H);
 }
 
 // Periodic CIC deposit of one particle with 16-byte vector atomics where the two
@@ -289,10 +327,6 @@ __device__ __forceinline__ void cic_deposit_vec(float* __restrict__ rho, float u
   w = dx * dy;   add_zpair<N>(rho, ((size_t)jx * N + jy) * N, iz, jz, w * wz0, w * dz);
 }
 
-#ifndef LPT2_CIC_FUSED
-#define LPT2_CIC_FUSED 0   // deposit used inside k_z_final: 0 scalar-merged, 1 vector
-#endif
-
 // wrap grid coordinate into [0, N)
 template <int N>
 __device__ __forceinline__ float wrapN(float u) {
@@ -300,93 +334,103 @@ __device__ __forceinline__ float wrapN(float u) {
   return (u >= (float)N) ? u - (float)N : u;
 }
 
-// Psi inputs (z order 1 -> Psi_z, 0 -> Psi_y, 0 -> Psi_x), positions, CIC.
-// The z components of both rows are one packed transform; then each row's
-// (x, y) pair is transformed and that row's particles are finished at once, so
-// only one row's x/y values are live at a time.
-template <int N>
+// Psi inputs (z order 1 -> Psi_z, 0 -> Psi_y, 0 -> Psi_x) -> particle positions
+// x = q + Psi (Eq. position), periodic.  The tile and copy ring are those of
+// k_z_source: a CTA owns ROWS consecutive rows of every input, one bulk copy per
+// input tile, rows 2p and 2p + 1 of a field packed as one complex pencil.  The
+// three components are independent, so nothing is carried from one input to the
+// next except, when SPLIT (separate Psi1 / Psi2 inputs), the Psi1 part of the
+// current component.
+template <int N, bool SPLIT>
 __global__ void __launch_bounds__(PassCfg<N>::ZT, LPT2_Z_MINB) k_z_final(ZFinalArgs a) {
   using C = PassCfg<N>;
-  extern __shared__ float2 smem[];
-  float2* s_tw = smem;
-  load_twiddles(s_tw, a.tw, N);
+  using Q = ZSrcCfg<N>;
+  constexpr int NQ = SPLIT ? 6 : 3;   // input tiles: (Psi1, Psi2) per component, or the totals
+  extern __shared__ __align__(128) unsigned char zs_raw[];
+  float2* ring = reinterpret_cast<float2*>(zs_raw);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(zs_raw + Q::BAR_OFF);
+  float2* s_tw = reinterpret_cast<float2*>(zs_raw + Q::BAR_OFF + 64);
+  __shared__ int s_fail;
   const int p = threadIdx.x / C::TPP, t = threadIdx.x % C::TPP;
-  const SmemRow sm{smem + N + p * SmemRow::words(N)};
-  const int pair = blockIdx.x * C::ZP + p;
-  const int rows[2] = {2 * pair, 2 * pair + 1};
+  const SmemRow sm{s_tw + N + p * SmemRow::words(N)};
   const size_t n3 = (size_t)N * N * N;
-  const float kf = a.g.kf;
-  const int nsets = a.split ? 2 : 1;
-  {                                                   // instance blockIdx.z of the batch
-    const size_t zs = blockIdx.z * (n3 / 2), zr = blockIdx.z * n3;
-#pragma unroll
-    for (int i = 0; i < 3; ++i) { a.a[i] += zs; if (a.b[i]) a.b[i] += zs; }
-    if (a.psi1) a.psi1 += 3 * zr;
-    if (a.psi2) a.psi2 += 3 * zr;
-    if (a.pos) a.pos += 3 * zr;
-    if (a.rho) a.rho += zr;
+  const size_t zs = blockIdx.z * (n3 / 2), zr = blockIdx.z * n3;   // instance blockIdx.z
+  const size_t tile = (size_t)blockIdx.x * Q::STAGE_F2;
+  const int row = blockIdx.x * Q::ROWS + 2 * p;                    // rows `row`, `row` + 1
+  auto input = [&](int q) -> const float2* {
+    return (SPLIT ? ((q & 1) ? a.b[q >> 1] : a.a[q >> 1]) : a.a[q]) + zs + tile;
+  };
+  if (threadIdx.x == 0) {
+    s_fail = 0;
+    for (int st = 0; st < Q::STAGES; ++st) mbar_init(&bar[st], 1);
+    mbar_init_fence();
   }
-  float pz[2][C::RMAX];
   __syncthreads();
-  for (int set = 0; set < nsets; ++set) {
-    const float2* const* in = set == 0 ? a.a : a.b;
-    float* outp = a.split ? (set == 0 ? a.psi1 : a.psi2) : nullptr;
+  if (threadIdx.x == 0) {
+    for (int q = 0; q < Q::STAGES && q < NQ; ++q) {
+      mbar_expect_tx(&bar[q], Q::STAGE_BYTES);
+      bulk_load(ring + q * Q::STAGE_F2, input(q), Q::STAGE_BYTES, &bar[q]);
+    }
+  }
+  load_twiddles(s_tw, a.tw, N);
+  float2 keep[C::RMAX];
+#pragma unroll 1
+  for (int q = 0; q < NQ; ++q) {
+    const int st = q % Q::STAGES;
+    const int c = SPLIT ? (q >> 1) : q;   // 0: Psi_z, 1: Psi_y, 2: Psi_x
+    const bool ok = mbar_wait(&bar[st], (q / Q::STAGES) & 1);
+    if (!ok) s_fail = 1;
     float2 v[C::RMAX];
+    const float2* ra = ring + st * Q::STAGE_F2 + (2 * p) * C::H;
 #pragma unroll
     for (int r = 0; r < C::RMAX; ++r)
-      v[r] = z_assemble<N>(in[0] + (size_t)rows[0] * C::H, in[0] + (size_t)rows[1] * C::H,
-                           elem<N>(t, r), kf, 1, 1);
-    fft<N, true>(v, t, sm, s_tw);
-#pragma unroll
-    for (int r = 0; r < C::RMAX; ++r) {
-      if (set == 0) { pz[0][r] = v[r].x; pz[1][r] = v[r].y; }
-      else { pz[0][r] += v[r].x; pz[1][r] += v[r].y; }
-      if (outp) {
-        outp[2 * n3 + (size_t)rows[0] * N + elem<N>(t, r)] = v[r].x;
-        outp[2 * n3 + (size_t)rows[1] * N + elem<N>(t, r)] = v[r].y;
+      v[r] = ok ? z_assemble_smem<N>(ra, ra + C::H, elem<N>(t, r), a.g.kf, c == 0 ? 1 : 0) : make_float2(0.f, 0.f);
+    __syncthreads();   // stage consumed by every thread (and, at q = 0, twiddles visible)
+    if (s_fail) {
+      if (threadIdx.x == 0) {
+        for (int g = q; g < NQ && g < q + Q::STAGES; ++g) mbar_wait(&bar[g % Q::STAGES], (g / Q::STAGES) & 1);
+        report_device_error(a.g.err, LPT2_DEV_ETIMEOUT_ZFINAL);
       }
+      return;
     }
-  }
+    if (threadIdx.x == 0 && q + Q::STAGES < NQ) {
+      mbar_expect_tx(&bar[st], Q::STAGE_BYTES);
+      bulk_load(ring + st * Q::STAGE_F2, input(q + Q::STAGES), Q::STAGE_BYTES, &bar[st]);
+    }
+    fft<N, true>(v, t, sm, s_tw);
+    const int d = 2 - c;                  // output component: x 0, y 1, z 2
+    if (SPLIT) {
+      float* outp = (q & 1) ? a.psi2 : a.psi1;
+      if (outp) {
+        outp += 3 * zr + d * n3;
 #pragma unroll
-  for (int h = 0; h < 2; ++h) {
-    const size_t off = (size_t)rows[h] * C::H;
-    float px[C::RMAX], py[C::RMAX];
-    for (int set = 0; set < nsets; ++set) {
-      const float2* const* in = set == 0 ? a.a : a.b;
-      float* outp = a.split ? (set == 0 ? a.psi1 : a.psi2) : nullptr;
-      float2 v[C::RMAX];
-#pragma unroll
-      for (int r = 0; r < C::RMAX; ++r)
-        v[r] = z_assemble<N>(in[2] + off, in[1] + off, elem<N>(t, r), kf, 0, 0);
-      fft<N, true>(v, t, sm, s_tw);
-#pragma unroll
-      for (int r = 0; r < C::RMAX; ++r) {
-        if (set == 0) { px[r] = v[r].x; py[r] = v[r].y; }
-        else { px[r] += v[r].x; py[r] += v[r].y; }
-        if (outp) {
-          const size_t e = (size_t)rows[h] * N + elem<N>(t, r);
-          outp[e] = v[r].x;
-          outp[n3 + e] = v[r].y;
+        for (int r = 0; r < C::RMAX; ++r) {
+          const int iz = elem<N>(t, r);
+          outp[(size_t)row * N + iz] = v[r].x;
+          outp[(size_t)(row + 1) * N + iz] = v[r].y;
         }
       }
-    }
-    // positions x = q + Psi (Eq. position), wrapped; CIC deposit
-    const int ix = rows[h] / N, iy = rows[h] % N;
+      if (!(q & 1)) {
 #pragma unroll
-    for (int r = 0; r < C::RMAX; ++r) {
-      const int iz = elem<N>(t, r);
-      const float ux = wrapN<N>((float)ix + px[r] * a.g.inv_cell);
-      const float uy = wrapN<N>((float)iy + py[r] * a.g.inv_cell);
-      const float uz = wrapN<N>((float)iz + pz[h][r] * a.g.inv_cell);
-      if (a.pos) {
-        const size_t e = (size_t)rows[h] * N + iz;
-        a.pos[e] = ux * a.g.cell;
-        a.pos[n3 + e] = uy * a.g.cell;
-        a.pos[2 * n3 + e] = uz * a.g.cell;
+        for (int r = 0; r < C::RMAX; ++r) keep[r] = v[r];
+        continue;
       }
-      if (a.rho) {
-        if (LPT2_CIC_FUSED == 1) cic_deposit_vec<N>(a.rho, ux, uy, uz);
-        else cic_deposit_merged<N>(a.rho, ux, uy, uz);
+#pragma unroll
+      for (int r = 0; r < C::RMAX; ++r) v[r] = cadd(v[r], keep[r]);
+    }
+    if (a.pos) {
+      float* pos = a.pos + 3 * zr + d * n3;
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int R = row + h;
+        const float q0 = (d == 0) ? (float)(R / N) : (float)(R % N);   // Lagrangian x or y
+#pragma unroll
+        for (int r = 0; r < C::RMAX; ++r) {
+          const int iz = elem<N>(t, r);
+          const float psi = h ? v[r].y : v[r].x;
+          const float u = wrapN<N>((d == 2 ? (float)iz : q0) + psi * a.g.inv_cell);
+          pos[(size_t)R * N + iz] = u * a.g.cell;
+        }
       }
     }
   }
@@ -872,15 +916,18 @@ template <int N> cudaError_t launch_z_c2r_t(const ZC2RArgs& a, cudaStream_t s) {
 template <int N> cudaError_t launch_z_source_t(const ZSourceArgs& a, cudaStream_t s) {
   using C = PassCfg<N>;
   LPT2_CHECK_BATCH(a);
-  cudaFuncSetAttribute(k_z_source<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::ZSMEM);
-  k_z_source<N><<<dim3(N * N / 2 / C::ZP, 1, a.g.batch), C::ZT, C::ZSMEM, s>>>(a);
+  using Q = ZSrcCfg<N>;
+  cudaFuncSetAttribute(k_z_source<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, Q::SMEM);
+  k_z_source<N><<<dim3(N * N / Q::ROWS, 1, a.g.batch), C::ZT, Q::SMEM, s>>>(a);
   return cudaGetLastError();
 }
 template <int N> cudaError_t launch_z_final_t(const ZFinalArgs& a, cudaStream_t s) {
   using C = PassCfg<N>;
   LPT2_CHECK_BATCH(a);
-  cudaFuncSetAttribute(k_z_final<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::ZSMEM);
-  k_z_final<N><<<dim3(N * N / 2 / C::ZP, 1, a.g.batch), C::ZT, C::ZSMEM, s>>>(a);
+  using Q = ZSrcCfg<N>;
+  auto k = a.split ? k_z_final<N, true> : k_z_final<N, false>;
+  cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, Q::SMEM);
+  k<<<dim3(N * N / Q::ROWS, 1, a.g.batch), C::ZT, Q::SMEM, s>>>(a);
   return cudaGetLastError();
 }
 template <int N> cudaError_t launch_z_adj_final_t(const ZAdjFinalArgs& a, cudaStream_t s) {

@@ -36,7 +36,11 @@ struct Geo {
   int batch;
   int inst0;
   int tab_stride;       // floats per instance in the float growth tables
+  int* err;             // device error word (0 = ok), may be null
 };
+
+// Codes a kernel writes into Geo::err when a bounded wait gives up.
+enum { LPT2_DEV_ETIMEOUT_ZSOURCE = 1, LPT2_DEV_ETIMEOUT_ZFINAL = 2 };
 
 enum ZSrc { Z_NOISE = 0, Z_REAL = 1, Z_DENSITY = 2 };
 
@@ -86,7 +90,7 @@ struct ZSourceArgs {   // inverse z pass of the six phi_ij, source term, forward
   float2* out;         // S, z-transformed
 };
 
-struct ZFinalArgs {    // inverse z pass of the displacement potentials, positions, CIC
+struct ZFinalArgs {    // inverse z pass of the displacement potentials, positions
   Geo g;
   const float2* tw;
   int split;           // 1: separate Psi1 / Psi2 inputs; 0: total only
@@ -95,7 +99,6 @@ struct ZFinalArgs {    // inverse z pass of the displacement potentials, positio
   float* psi1;         // float[3][N^3] or null
   float* psi2;
   float* pos;
-  float* rho;          // CIC mass per cell (accumulated), or null
 };
 
 struct YJob {          // y pass: each output = transform of (i k_y)^ord * input

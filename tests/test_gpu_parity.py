@@ -206,6 +206,7 @@ def test_repeat_calls_are_deterministic_and_launch_counted():
     assert lp().lpt2_launch_count(plan) > c0
     for k in a:
         assert torch.equal(a[k], b[k])
+    lp().lpt2_device_status(plan)   # no bounded device-side wait ran out
 
 
 def test_256_full_against_oracle():
