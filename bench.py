@@ -118,6 +118,17 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the kernels
+# that can dominate the 512^3 step, from one ncu capture each of the 256^3 case of the same
+# kernel scaled by the cell count (x 8; the traffic of these passes is proportional to
+# N^3).  Sources: profiles/z_source_256.md, profiles/cic_256.md.  A kernel changed since
+# its capture must be removed here (its traffic is then reported as null).
+TRAFFIC_512 = {
+    "z_source": (402.791936 + 51.977472) * 1e6 * 8,
+    "cic": (270.235136 + 45.912832) * 1e6 * 8,
+}
+
+
 def measured_peak_gbs():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -496,7 +507,8 @@ def bench_ours(args):
                        "parallelism": f"{world} independent realisation(s), one per GPU"},
             "roofline": {"bound": "hbm", "kernel": dname, "achieved": achieved, "peak": peak,
                          "peak_kind": f"hbm_gbs of {peak_kind}", "unit": "GB/s", "frac": achieved / peak,
-                         "traffic": None},
+                         "traffic": TRAFFIC_512.get(dname) if n == 512 else None,
+                         "algorithmic_bytes": dv["bytes"] / dv["launches"]},
             "path_roofline": {"algorithmic_gb_per_step": all_bytes / args.steps / 1e9,
                               "achieved_gbs": all_bytes / (total_ms / 1e3) / 1e9,
                               "frac": all_bytes / (total_ms / 1e3) / 1e9 / peak},

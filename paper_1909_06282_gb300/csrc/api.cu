@@ -51,6 +51,9 @@ struct Group {
   size_t off;      // floats before the group's first instance in per-instance real fields
   float4* mt0;     // per-|n|^2 multiplier tables [count][mode_table_len(n)]
   float2* mt1;
+  double* geo_k;             // P(k) shell geometry for geo_ns shells: sum of |k| per shell
+  unsigned long long* geo_n; // and mode count per shell [kMaxShells]
+  int geo_ns;                // 0: not computed yet
 };
 
 struct GraphCache {  // one captured launch sequence per entry point (LPT2_GRAPH)
@@ -276,8 +279,21 @@ int forward_zy(lpt2_plan_t p, int src, const float* in, float2* out) {
 int displace_impl(lpt2_plan_t p, const float* noise, float* psi1, float* psi2, float* pos, void* dk,
                   float2* s_keep);
 
-// CIC (when positions are given) and P(k) of the current group.
-int cic_pk_group(lpt2_plan_t p, const float* pos, float* density, double* pk, double* k_mean,
+// Shell geometry (mode counts, sum of |k|) of group gi for n_shells shells; made
+// once per shell count, outside any graph capture, and reused by every P(k).
+int ensure_geometry(lpt2_plan_t p, int gi, int n_shells) {
+  Group& gr = p->groups[gi];
+  if (gr.geo_ns == n_shells) return LPT2_OK;
+  cudaError_t e = cudaMemsetAsync(gr.geo_k, 0, kMaxShells * sizeof(double), p->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(gr.geo_n, 0, kMaxShells * sizeof(unsigned long long), p->stream);
+  if (e != cudaSuccess) return fail(LPT2_ECUDA, "shell geometry: %s", cudaGetErrorString(e));
+  LAUNCH(p, "shell_geometry", 0.0, launch_shell_geometry(gr.n, gr.box, n_shells, gr.geo_k, gr.geo_n, p->stream));
+  gr.geo_ns = n_shells;
+  return LPT2_OK;
+}
+
+// CIC (when positions are given) and P(k) of the current group (geometry made).
+int cic_pk_group(lpt2_plan_t p, int gi, const float* pos, float* density, double* pk, double* k_mean,
                  int64_t* n_modes, int n_shells) {
   const int n = p->n;
   const Geo g = make_geo(p);
@@ -295,14 +311,16 @@ int cic_pk_group(lpt2_plan_t p, const float* pos, float* density, double* pk, do
   XArgs x{};
   x.g = g;
   x.tw = p->tw;
-  x.mode = X_PK;
+  x.mode = X_PKP;
   x.in = A;
   x.cosmo = p->cosmo_dev;
   x.pk_part = pk_part(p);
   x.n_shells = n_shells;
   LAUNCH(p, "x_pk", 4.0 * V3(p), x_pass(n, x, p->stream));
+  const Group& gr = p->groups[gi];
   LAUNCH(p, "pk_finalize", 0.0,
-         launch_pk_finalize(pk_part(p), x_blocks(n), n_shells, pk, k_mean, n_modes, p->stream, p->cur_batch));
+         launch_pk_finalize_p(pk_part(p), x_blocks(n), n_shells, gr.geo_k, gr.geo_n, pk, k_mean, n_modes,
+                              p->stream, p->cur_batch));
   return LPT2_OK;
 }
 
@@ -464,6 +482,9 @@ int lpt2_plan(lpt2_plan_t* out, const lpt2_instance* inst, int n_inst, int n_k, 
     if (e == cudaSuccess) e = cudaMalloc(&g.tw, g.n * sizeof(float2));
     if (e == cudaSuccess) e = cudaMalloc(&g.mt0, (size_t)g.count * mode_table_len(g.n) * sizeof(float4));
     if (e == cudaSuccess) e = cudaMalloc(&g.mt1, (size_t)g.count * mode_table_len(g.n) * sizeof(float2));
+    if (e == cudaSuccess) e = cudaMalloc(&g.geo_k, kMaxShells * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&g.geo_n, kMaxShells * sizeof(unsigned long long));
+    g.geo_ns = 0;
   }
   if (e == cudaSuccess) e = cudaMalloc(&p->cosmo_dev, sizeof(DevCosmo));
   if (e == cudaSuccess) e = cudaMalloc(&p->partials, cosmo_partial_blocks() * sizeof(double));
@@ -522,6 +543,8 @@ int lpt2_plan_destroy(lpt2_plan_t p) {
     cudaFree(g.tw);
     cudaFree(g.mt0);
     cudaFree(g.mt1);
+    cudaFree(g.geo_k);
+    cudaFree(g.geo_n);
   }
   cudaFree(p->cosmo_dev);
   cudaFree(p->partials);
@@ -757,13 +780,17 @@ int lpt2_cic_pk(lpt2_plan_t p, const float* pos, float* density, double* pk, dou
     for (int gi = 0; gi < (int)p->groups.size(); ++gi) {
       set_group(p, gi);
       const Group& gr = p->groups[gi];
-      const int r = cic_pk_group(p, pos ? pos + 3 * gr.off : nullptr, density ? density + gr.off : nullptr,
+      const int r = cic_pk_group(p, gi, pos ? pos + 3 * gr.off : nullptr, density ? density + gr.off : nullptr,
                                  pk + (size_t)gr.inst0 * n_shells, k_mean ? k_mean + (size_t)gr.inst0 * n_shells : nullptr,
                                  n_modes ? n_modes + (size_t)gr.inst0 * n_shells : nullptr, n_shells);
       if (r) return r;
     }
     return LPT2_OK;
   };
+  for (int gi = 0; gi < (int)p->groups.size(); ++gi) {
+    rc = ensure_geometry(p, gi, n_shells);
+    if (rc) return rc;
+  }
   if (!p->use_graph) return body();
   const void* key[8] = {pos, density, pk, k_mean, n_modes, p->ws, (const void*)(intptr_t)n_shells, nullptr};
   return run_graph(p, 1, key, body);
@@ -858,13 +885,17 @@ int lpt2_displace_vjp(lpt2_plan_t p, const float* noise, const float* g_pos, con
   XArgs xp{};
   xp.g = g;
   xp.tw = p->tw;
-  xp.mode = X_PK;
+  xp.mode = X_PKP;
   xp.in = S[S_A];
   xp.cosmo = p->cosmo_dev;
   xp.pk_part = pk_part(p);
   xp.n_shells = n_shells;
   LAUNCH(p, "x_pk", 4.0 * V3(p), x_pass(n, xp, p->stream));
-  LAUNCH(p, "pk_finalize", 0.0, launch_pk_finalize(pk_part(p), x_blocks(n), n_shells, pk, kmean, nmodes, p->stream));
+  rc = ensure_geometry(p, 0, n_shells);
+  if (rc) return rc;
+  LAUNCH(p, "pk_finalize", 0.0,
+         launch_pk_finalize_p(pk_part(p), x_blocks(n), n_shells, p->groups[0].geo_k, p->groups[0].geo_n, pk, kmean,
+                              nmodes, p->stream, 1));
 
   // 1. density cotangent: g_density + IDFT[w_b delta_rho(k)]
   const double v_over_n6 = p->box * p->box * p->box / (V3d * V3d);

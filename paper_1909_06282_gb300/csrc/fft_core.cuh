@@ -38,7 +38,11 @@ template <> struct Cfg<32>   { static constexpr int NS = 3, RMAX = 4;  static __
 template <> struct Cfg<64>   { static constexpr int NS = 2, RMAX = 8;  static __host__ __device__ constexpr int rad(int s) { return 8; } };
 template <> struct Cfg<128>  { static constexpr int NS = 3, RMAX = 8;  static __host__ __device__ constexpr int rad(int s) { return s == 1 ? 2 : 8; } };
 template <> struct Cfg<256>  { static constexpr int NS = 2, RMAX = 16; static __host__ __device__ constexpr int rad(int s) { return 16; } };
-template <> struct Cfg<512>  { static constexpr int NS = 3, RMAX = 16; static __host__ __device__ constexpr int rad(int s) { return s == 1 ? 2 : 16; } };
+#ifndef LPT2_R512
+#define LPT2_R512 16   // N = 512: radix 16-2-16 (16 values per thread) or 8-8-8 (8 values)
+#endif
+template <> struct Cfg<512>  { static constexpr int NS = 3, RMAX = LPT2_R512;
+  static __host__ __device__ constexpr int rad(int s) { return LPT2_R512 == 8 ? 8 : (s == 1 ? 2 : 16); } };
 template <> struct Cfg<1024> { static constexpr int NS = 3, RMAX = 16; static __host__ __device__ constexpr int rad(int s) { return s == 1 ? 4 : 16; } };
 
 // element index held in register slot j by lane t (first-stage input = last-stage output)

@@ -1,5 +1,7 @@
 // Size-independent kernels: CIC deposit from positions, zero fill, P(k) shell
 // finalisation, white noise and raw Philox words.
+#include <math.h>
+
 #include "passes.cuh"
 
 namespace lpt2 {
@@ -188,6 +190,96 @@ __global__ void k_pk_finalize(const double* part, int n_blocks, int ns, double* 
 cudaError_t launch_pk_finalize(const double* part, int n_blocks, int n_shells, double* pk, double* k_mean,
                                int64_t* n_modes, cudaStream_t s, int batch) {
   k_pk_finalize<<<dim3(n_shells, batch), 256, 0, s>>>(part, n_blocks, n_shells, pk, k_mean, n_modes);
+  return cudaGetLastError();
+}
+
+// Shell geometry of the P(k) estimator: for every mode of the stored half spectrum
+// (kz < N/2; kz > 0 stands for itself and its conjugate, so it counts twice) with
+// 0 < |n| < N/2, shell b = floor(2 n_shells |n| / N) by exact integer comparison,
+// the weighted mode count and sum of |k|.  One thread per (kx, ky) walks kz, where
+// |n| grows monotonically, and flushes its running sums when the shell changes.
+__device__ __forceinline__ int shell_index_int(long long n2, int n, int ns) {
+  // largest b with (b n)^2 <= 4 ns^2 n2
+  const long long M = 4LL * ns * ns * n2;
+  int b = (int)(sqrtf((float)n2) * (2.0f * (float)ns / (float)n));
+  while (b > 0 && (long long)b * n * (long long)b * n > M) --b;
+  while ((long long)(b + 1) * n * (long long)(b + 1) * n <= M) ++b;
+  return b;
+}
+
+__global__ void k_shell_geometry(int n, float kf, int ns, double* ksum, unsigned long long* count) {
+  extern __shared__ double s_geo[];   // [ns] |k| sums, then [ns] counts
+  unsigned long long* s_cnt = reinterpret_cast<unsigned long long*>(s_geo + ns);
+  for (int i = threadIdx.x; i < ns; i += blockDim.x) { s_geo[i] = 0.0; s_cnt[i] = 0ull; }
+  __syncthreads();
+  const int h = n / 2;
+  const int ky = blockIdx.x;
+  const int my = ky < h ? ky : ky - n;
+  for (int kx = threadIdx.x; kx < n; kx += blockDim.x) {
+    const int mx = kx < h ? kx : kx - n;
+    int cur = -1;
+    double ks = 0.0;
+    unsigned long long c = 0;
+    for (int kz = 0; kz < h; ++kz) {
+      const long long n2 = (long long)mx * mx + (long long)my * my + (long long)kz * kz;
+      if (n2 == 0 || 4 * n2 >= (long long)n * n) continue;
+      const int b = shell_index_int(n2, n, ns);
+      if (b != cur) {
+        if (cur >= 0) { atomicAdd(&s_geo[cur], ks); atomicAdd(&s_cnt[cur], c); }
+        cur = b;
+        ks = 0.0;
+        c = 0;
+      }
+      const unsigned w = kz == 0 ? 1u : 2u;
+      ks += (double)w * (double)(kf * sqrtf((float)n2));   // n2 < 2^24: exact in FP32
+      c += w;
+    }
+    if (cur >= 0) { atomicAdd(&s_geo[cur], ks); atomicAdd(&s_cnt[cur], c); }
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < ns; i += blockDim.x) {
+    if (s_cnt[i]) {
+      atomicAdd(&ksum[i], s_geo[i]);
+      atomicAdd(&count[i], s_cnt[i]);
+    }
+  }
+}
+
+cudaError_t launch_shell_geometry(int n, double box, int n_shells, double* ksum, unsigned long long* nmodes,
+                                  cudaStream_t s) {
+  const float kf = (float)(2.0 * M_PI / box);
+  k_shell_geometry<<<n, 128, n_shells * 16, s>>>(n, kf, n_shells, ksum, nmodes);
+  return cudaGetLastError();
+}
+
+__global__ void k_pk_finalize_p(const double* part, int n_blocks, int ns, const double* ksum,
+                                const unsigned long long* count, double* pk, double* kmean, int64_t* nmodes) {
+  const int b = blockIdx.x;
+  part += (size_t)blockIdx.y * n_blocks * ns;   // instance blockIdx.y
+  pk += (size_t)blockIdx.y * ns;
+  if (kmean) kmean += (size_t)blockIdx.y * ns;
+  if (nmodes) nmodes += (size_t)blockIdx.y * ns;
+  double sp = 0.0;
+  for (int i = threadIdx.x; i < n_blocks; i += blockDim.x) sp += part[(size_t)i * ns + b];
+  __shared__ double sh[256];
+  sh[threadIdx.x] = sp;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const double c = (double)count[b];
+    pk[b] = c > 0 ? sh[0] / c : 0.0;
+    if (kmean) kmean[b] = c > 0 ? ksum[b] / c : 0.0;
+    if (nmodes) nmodes[b] = (int64_t)count[b];
+  }
+}
+
+cudaError_t launch_pk_finalize_p(const double* part, int n_blocks, int n_shells, const double* ksum,
+                                 const unsigned long long* count, double* pk, double* k_mean, int64_t* n_modes,
+                                 cudaStream_t s, int batch) {
+  k_pk_finalize_p<<<dim3(n_shells, batch), 256, 0, s>>>(part, n_blocks, n_shells, ksum, count, pk, k_mean, n_modes);
   return cudaGetLastError();
 }
 

@@ -690,9 +690,9 @@ __global__ void __launch_bounds__(PassCfg<N>::XT) k_x(XArgs a) {
   const bool ny_nyq = (ky == C::H);
   const float kf = a.g.kf;
   const size_t blk = ((size_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
-  if (MODE == X_PK) {
+  if (MODE == X_PK || MODE == X_PKP) {
     float* s_accf = reinterpret_cast<float*>(s_acc);
-    for (int i = threadIdx.x; i < NWARP * 5 * a.n_shells; i += blockDim.x) s_accf[i] = 0.f;
+    for (int i = threadIdx.x; i < NWARP * (MODE == X_PK ? 5 : 2) * a.n_shells; i += blockDim.x) s_accf[i] = 0.f;
   } else if (MODE == X_ADJ_SOURCE) {
     for (int i = threadIdx.x; i < NWARP; i += blockDim.x) s_acc[i] = 0.0;
   }
@@ -733,16 +733,18 @@ __global__ void __launch_bounds__(PassCfg<N>::XT) k_x(XArgs a) {
     }
   }
 
-  if (MODE == X_PK) {
+  if (MODE == X_PK || MODE == X_PKP) {
     // P(k) shells.  Lanes of a warp see neighbouring modes, so they fall in few
     // shells: for each distinct shell in the warp the lanes of that shell are
     // summed and one lane adds the sum to this warp's own accumulator, a
     // Kahan-compensated FP32 pair (FP64-class accuracy without FP64 adds, which
-    // are slow on this part); the sums over warps and blocks are FP64.
+    // are slow on this part); the sums over warps and blocks are FP64.  X_PK also
+    // sums |k| and the mode counts; X_PKP leaves them to the cached shell geometry.
+    constexpr bool GEO = (MODE == X_PK);
+    constexpr int NQ = GEO ? 5 : 2;   // per warp: P, its compensation (, |k|, compensation, count)
     const float pnorm = a.g.box * a.g.box * a.g.box * a.g.inv_n3 * a.g.inv_n3;
     const int ns = a.n_shells;
-    // per warp: sum P [ns], its compensation [ns], sum |k| [ns], compensation [ns], count [ns]
-    float* s_mine = reinterpret_cast<float*>(s_acc) + warp * 5 * ns;
+    float* s_mine = reinterpret_cast<float*>(s_acc) + warp * NQ * ns;
 #pragma unroll
     for (int r = 0; r < C::RMAX; ++r) {
       const int kx = elem<N>(t, r);
@@ -750,7 +752,7 @@ __global__ void __launch_bounds__(PassCfg<N>::XT) k_x(XArgs a) {
       const int b = shell_of<N>(mode_of(kx, N), my, mz, ns, n2);
       const int wgt = (b < 0) ? 0 : ((mz == 0) ? 1 : 2);
       const float pv = (v[r].x * v[r].x + v[r].y * v[r].y) * pnorm * (float)wgt;
-      const float kv = kf * sqrtf((float)n2) * (float)wgt;
+      const float kv = GEO ? kf * sqrtf((float)n2) * (float)wgt : 0.f;
       unsigned todo = __ballot_sync(0xffffffffu, b >= 0);
       while (todo) {
         const int leader = __ffs(todo) - 1;
@@ -761,8 +763,10 @@ __global__ void __launch_bounds__(PassCfg<N>::XT) k_x(XArgs a) {
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) {
           sp += __shfl_xor_sync(0xffffffffu, sp, off);
-          sk += __shfl_xor_sync(0xffffffffu, sk, off);
-          sc += __shfl_xor_sync(0xffffffffu, sc, off);
+          if (GEO) {
+            sk += __shfl_xor_sync(0xffffffffu, sk, off);
+            sc += __shfl_xor_sync(0xffffffffu, sc, off);
+          }
         }
         if (lane == leader) {   // this warp's own accumulators: no atomics
           {
@@ -770,26 +774,27 @@ __global__ void __launch_bounds__(PassCfg<N>::XT) k_x(XArgs a) {
             s_mine[ns + key] = (t2 - s_mine[key]) - y;
             s_mine[key] = t2;
           }
-          {
+          if (GEO) {
             const float y = sk - s_mine[3 * ns + key], t2 = s_mine[2 * ns + key] + y;
             s_mine[3 * ns + key] = (t2 - s_mine[2 * ns + key]) - y;
             s_mine[2 * ns + key] = t2;
+            s_mine[4 * ns + key] += (float)sc;   // integer counts <= 2 * 32 * RMAX: exact
           }
-          s_mine[4 * ns + key] += (float)sc;   // integer counts <= 2 * 32 * RMAX: exact
         }
         todo &= ~__ballot_sync(0xffffffffu, mine);
       }
     }
     __syncthreads();
     const float* s_all = reinterpret_cast<const float*>(s_acc);
-    for (int i = threadIdx.x; i < 3 * ns; i += blockDim.x) {
+    constexpr int NOUT = GEO ? 3 : 1;
+    for (int i = threadIdx.x; i < NOUT * ns; i += blockDim.x) {
       const int q = i / ns, b = i % ns;   // quantity (P, |k|, count), shell
       double acc = 0.0;
       for (int wi = 0; wi < NWARP; ++wi) {   // fixed order
-        const float* wv = s_all + wi * 5 * ns;
+        const float* wv = s_all + wi * NQ * ns;
         acc += (q < 2) ? (double)wv[2 * q * ns + b] - (double)wv[(2 * q + 1) * ns + b] : (double)wv[4 * ns + b];
       }
-      a.pk_part[blk * 3 * ns + i] = acc;
+      a.pk_part[blk * NOUT * ns + i] = acc;
     }
     return;
   }
@@ -959,6 +964,7 @@ template <int N, int MODE> cudaError_t launch_x_m(const XArgs& a, cudaStream_t s
   using C = PassCfg<N>;
   LPT2_CHECK_BATCH(a);
   const int smem = C::XSMEM + (MODE == X_PK ? (C::XT / 32) * 5 * a.n_shells * 4
+                            : MODE == X_PKP ? (C::XT / 32) * 2 * a.n_shells * 4
                                             : (MODE == X_ADJ_SOURCE ? (C::XT / 32) * 8 : 0));
   cudaFuncSetAttribute(k_x<N, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   k_x<N, MODE><<<dim3(C::H / C::W, N, a.g.batch), C::XT, smem, s>>>(a);
@@ -969,6 +975,7 @@ template <int N> cudaError_t launch_x_t(const XArgs& a, cudaStream_t s) {
     case X_DELTA: return launch_x_m<N, X_DELTA>(a, s);
     case X_SOURCE: return launch_x_m<N, X_SOURCE>(a, s);
     case X_PK: return launch_x_m<N, X_PK>(a, s);
+    case X_PKP: return launch_x_m<N, X_PKP>(a, s);
     case X_FWD: return launch_x_m<N, X_FWD>(a, s);
     case X_INV: return launch_x_m<N, X_INV>(a, s);
     case X_PHI: return launch_x_m<N, X_PHI>(a, s);

@@ -127,7 +127,8 @@ enum XMode {
   X_PHI = 5,        // phi potential from a stored delta(k) (no transform), inverse x orders 0, 1, 2
   X_PKADJ = 6,      // fwd x, times per-shell weight, inverse x  (P(k) transpose)
   X_ADJ_SOURCE = 7, // transpose of X_SOURCE: h_Psi, h_S, dL/dln|fR0| partials
-  X_ADJ_DELTA = 8   // transpose of X_DELTA: s(k) (h_Psi + h_phi), inverse x
+  X_ADJ_DELTA = 8,  // transpose of X_DELTA: s(k) (h_Psi + h_phi), inverse x
+  X_PKP = 9,        // fwd x, shell sums of |delta|^2 only (mode counts and mean |k| cached)
 };
 struct XArgs {
   Geo g;
@@ -192,6 +193,15 @@ cudaError_t launch_fill0(float* p, size_t n, cudaStream_t);
 cudaError_t launch_contrast(const float* rho, float* out, size_t n, cudaStream_t);
 cudaError_t launch_pk_finalize(const double* part, int n_blocks, int n_shells, double* pk,
                                double* k_mean, int64_t* n_modes, cudaStream_t, int batch = 1);
+// Mode count and sum of |k| per shell (0 < |n| < N/2, half spectrum kz < N/2, kz > 0
+// counted twice) for n_shells shells of width k_Ny / n_shells: the data-independent
+// part of the P(k) estimator.  kmean and nmodes must be zeroed before the launch.
+cudaError_t launch_shell_geometry(int n, double box, int n_shells, double* ksum, unsigned long long* nmodes,
+                                  cudaStream_t s);
+// P(k) from per-block |delta|^2 shell sums [n_blocks][n_shells] and the cached geometry.
+cudaError_t launch_pk_finalize_p(const double* part, int n_blocks, int n_shells, const double* ksum,
+                                 const unsigned long long* count, double* pk, double* k_mean, int64_t* n_modes,
+                                 cudaStream_t s, int batch);
 cudaError_t launch_noise(const Geo& g, uint32_t seed_lo, uint32_t seed_hi, float* out, cudaStream_t);
 cudaError_t launch_philox_words(uint32_t seed_lo, uint32_t seed_hi, uint64_t first, int64_t count,
                                 uint32_t* out, cudaStream_t);
