@@ -233,8 +233,11 @@ __global__ void k_growth(GrowthParams p, double* tab, float* tabf) {
   tabf[3 * nk + t] = (float)tab[3 * nk + t];
 }
 
+#ifndef LPT2_GROWTH_THREADS
+#define LPT2_GROWTH_THREADS 32   // k nodes per block: the RK4 chains are FP64-bound, so spread them over SMs
+#endif
 cudaError_t launch_growth(const GrowthParams& p, double* tab, float* tabf, cudaStream_t s) {
-  const int threads = 32;
+  const int threads = LPT2_GROWTH_THREADS;
   const int blocks = (p.nk + threads - 1) / threads;
   const size_t smem = (size_t)(2 * p.n_steps + 1) * sizeof(Bg);
   cudaFuncSetAttribute(k_growth<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

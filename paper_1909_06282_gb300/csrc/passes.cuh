@@ -517,6 +517,9 @@ __global__ void __launch_bounds__(PassCfg<N>::ZT, LPT2_Z_MINB) k_z_adj_final(ZAd
 
 // Transpose of k_z_source: g_S from h_S (inverse z), the six phi_ij recomputed
 // (inverse z), g_phi_ij = g_S dS/dphi_ij, forward z with conj z-derivatives.
+// g_S of both rows and the (g_zz, g_xy) products are parked in shared memory while
+// other transforms run (each thread reads back only its own elements), so that no
+// more than one 16-value transform is live in registers.
 template <int N>
 __global__ void __launch_bounds__(PassCfg<N>::ZT, LPT2_Z_MINB) k_z_adj_source(ZAdjSourceArgs a) {
   using C = PassCfg<N>;
@@ -528,7 +531,8 @@ __global__ void __launch_bounds__(PassCfg<N>::ZT, LPT2_Z_MINB) k_z_adj_source(ZA
   const int pair = blockIdx.x * C::ZP + p;
   const int rows[2] = {2 * pair, 2 * pair + 1};
   const float kf = a.g.kf;
-  float gs[2][C::RMAX];
+  float* s_gs = reinterpret_cast<float*>(smem + N + C::ZP * SmemRow::words(N)) + p * 2 * N;   // [2][N]
+  float2* s_park = smem + N + C::ZP * SmemRow::words(N) + C::ZP * N + threadIdx.x;   // [RMAX][ZT]
   __syncthreads();
   {
     float2 v[C::RMAX];
@@ -538,7 +542,10 @@ __global__ void __launch_bounds__(PassCfg<N>::ZT, LPT2_Z_MINB) k_z_adj_source(ZA
                            kf, 0, 0);
     fft<N, true>(v, t, sm, s_tw);
 #pragma unroll
-    for (int r = 0; r < C::RMAX; ++r) { gs[0][r] = v[r].x; gs[1][r] = v[r].y; }
+    for (int r = 0; r < C::RMAX; ++r) {
+      s_gs[elem<N>(t, r)] = v[r].x;
+      s_gs[N + elem<N>(t, r)] = v[r].y;
+    }
   }
 #pragma unroll
   for (int h = 0; h < 2; ++h) {
@@ -549,18 +556,23 @@ __global__ void __launch_bounds__(PassCfg<N>::ZT, LPT2_Z_MINB) k_z_adj_source(ZA
       A[r] = z_assemble<N>(a.in[0] + off, a.in[1] + off, elem<N>(t, r), kf, a.ord[0], a.ord[1]);
     fft<N, true>(A, t, sm, s_tw);                       // (phi_xx, phi_yy)
 #pragma unroll
+    for (int r = 0; r < C::RMAX; ++r) s_park[r * C::ZT] = A[r];
+#pragma unroll
     for (int r = 0; r < C::RMAX; ++r)
       B[r] = z_assemble<N>(a.in[2] + off, a.in[3] + off, elem<N>(t, r), kf, a.ord[2], a.ord[3]);
     fft<N, true>(B, t, sm, s_tw);                       // (phi_zz, phi_xy)
 #pragma unroll
     for (int r = 0; r < C::RMAX; ++r) {
-      const float xx = A[r].x, yy = A[r].y, zz = B[r].x, xy = B[r].y, g = gs[h][r];
-      A[r] = make_float2(g * (yy + zz), g * (xx + zz));   // dS/dphi_xx, dS/dphi_yy
-      B[r] = make_float2(g * (xx + yy), -2.f * g * xy);   // dS/dphi_zz, dS/dphi_xy
+      A[r] = s_park[r * C::ZT];
+      const float xx = A[r].x, yy = A[r].y, zz = B[r].x, xy = B[r].y, g = s_gs[h * N + elem<N>(t, r)];
+      A[r] = make_float2(g * (yy + zz), g * (xx + zz));            // dS/dphi_xx, dS/dphi_yy
+      s_park[r * C::ZT] = make_float2(g * (xx + yy), -2.f * g * xy); // dS/dphi_zz, dS/dphi_xy
     }
     fft<N, false>(A, t, sm, s_tw);
     z_store_pair_d<N>(A, t, sm, a.out[0] + off, a.out[1] + off, kf, a.ord[0], a.ord[1]);
     __syncthreads();
+#pragma unroll
+    for (int r = 0; r < C::RMAX; ++r) B[r] = s_park[r * C::ZT];
     fft<N, false>(B, t, sm, s_tw);
     z_store_pair_d<N>(B, t, sm, a.out[2] + off, a.out[3] + off, kf, a.ord[2], a.ord[3]);
     __syncthreads();
@@ -569,7 +581,10 @@ __global__ void __launch_bounds__(PassCfg<N>::ZT, LPT2_Z_MINB) k_z_adj_source(ZA
       A[r] = z_assemble<N>(a.in[4] + off, a.in[5] + off, elem<N>(t, r), kf, a.ord[4], a.ord[5]);
     fft<N, true>(A, t, sm, s_tw);                       // (phi_xz, phi_yz)
 #pragma unroll
-    for (int r = 0; r < C::RMAX; ++r) A[r] = make_float2(-2.f * gs[h][r] * A[r].x, -2.f * gs[h][r] * A[r].y);
+    for (int r = 0; r < C::RMAX; ++r) {
+      const float g = s_gs[h * N + elem<N>(t, r)];
+      A[r] = make_float2(-2.f * g * A[r].x, -2.f * g * A[r].y);
+    }
     fft<N, false>(A, t, sm, s_tw);
     z_store_pair_d<N>(A, t, sm, a.out[4] + off, a.out[5] + off, kf, a.ord[4], a.ord[5]);
     __syncthreads();
@@ -943,8 +958,10 @@ template <int N> cudaError_t launch_z_adj_final_t(const ZAdjFinalArgs& a, cudaSt
 }
 template <int N> cudaError_t launch_z_adj_source_t(const ZAdjSourceArgs& a, cudaStream_t s) {
   using C = PassCfg<N>;
-  cudaFuncSetAttribute(k_z_adj_source<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::ZSMEM);
-  k_z_adj_source<N><<<N * N / 2 / C::ZP, C::ZT, C::ZSMEM, s>>>(a);
+  // + g_S of both rows per pencil pair + one parked 16-value transform per thread
+  const int smem = C::ZSMEM + C::ZP * 2 * N * (int)sizeof(float) + C::ZT * C::RMAX * (int)sizeof(float2);
+  cudaFuncSetAttribute(k_z_adj_source<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  k_z_adj_source<N><<<N * N / 2 / C::ZP, C::ZT, smem, s>>>(a);
   return cudaGetLastError();
 }
 template <int N, int KIND> cudaError_t launch_y_k(const YArgs& a, cudaStream_t s) {
