@@ -428,6 +428,31 @@ def bench_ours(args):
         stream.synchronize()
         ms_fv = e4.elapsed_time(e5) / vsteps
 
+        # full second-order source term / GR diagnostic (Sec. 3), same plan and noise
+        src = None
+        if not args.no_source:
+            L.lpt2_source_ratio(plan, n_bins=WORKLOAD["n_shells"])
+            stream.synchronize()
+            L.lpt2_timing(plan, True)
+            e8, e9 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e8.record(stream)
+            for _ in range(2):
+                sr = L.lpt2_source_ratio(plan, n_bins=WORKLOAD["n_shells"])
+            e9.record(stream)
+            stream.synchronize()
+            srep = L.lpt2_timing_report(plan)
+            L.lpt2_timing(plan, False)
+            ms_src = e8.elapsed_time(e9) / 2
+            sbytes = sum(v["bytes"] for v in srep.values()) / 2
+            sms = sum(v["total_ms"] for v in srep.values()) / 2
+            src = {"ms_per_call": ms_src, "algorithmic_gb_per_call": sbytes / 1e9,
+                   "achieved_gbs": sbytes / (sms / 1e3) / 1e9,
+                   "launches_per_call": sum(v["launches"] for v in srep.values()) // 2,
+                   "ratio_last_shells": [round(x, 4) for x in sr["mean"].cpu().tolist()[-4:]],
+                   "t1_last_shells": [round(x, 4) for x in sr["t1"].cpu().tolist()[-4:]],
+                   "what": "lpt2_source_ratio: full S1+S2+S3+S4 and S_GR (31 inverse + 5 forward 3-D "
+                           "transforms), per-mode ratio binned in 32 shells, T1 curve"}
+
         batched = bench_batched(args, L, W, torch, stream) if not args.no_batched else None
 
         # the same path with cuFFT transforms and unfused element-wise kernels
@@ -550,6 +575,7 @@ def bench_ours(args):
             "growth_ms": growth_ms,
             "batched": batched,
             "cufft_pipeline": cuf,
+            "source_diagnostic": src,
             "fwd_vjp": {"value": parts / (ms_fv / 1e3), "unit": "particles/s", "ms_per_step": ms_fv,
                         "vjp_over_fwd": (ms_fv - ms) / ms,
                         "what": "forward + loss cotangents + lpt2_displace_vjp (noise and ln|fR0| gradients)"},
@@ -581,6 +607,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the 96-instance batched measurement")
     ap.add_argument("--no-cufft", action="store_true", help="skip the cuFFT comparison pipeline")
+    ap.add_argument("--no-source", action="store_true", help="skip the full-source diagnostic timing")
     ap.add_argument("--profile", action="store_true",
                     help="forward-only run for ncu (no timing); grid from --grid")
     ap.add_argument("--grid", type=int, default=WORKLOAD["n"],

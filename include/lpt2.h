@@ -182,6 +182,32 @@ int lpt2_displace_vjp(lpt2_plan_t plan, const float* noise, const float* g_pos,
                       const float* g_density, const double* g_pk, int n_shells, float* g_noise,
                       double* g_log_fr0);
 
+/* Full second-order source term and its ratio to GR (Sec. 3, Eqs. full, s1-s4; the
+ * diagnostic behind the paper's source-term figure, from which the T1 triangle was chosen).
+ * With delta1(k) = D1(k,a) delta0(k) (a = the plan's a_out), phi = delta1/k^2 and
+ * psi = delta1/Pi(k,a):
+ *   S1 = 4piGrho DFT[phi_,ij IDFT[mu(k) DFT[phi_,ij]]],
+ *   S2 = -2piGrho mu(k) DFT[phi_,ii phi_,jj + phi_,ij phi_,ij]   (the printed "-" between the two
+ *        products is read as "+": with it S1 + S2 is the GR source at mu = 1 and the sum of the
+ *        four terms reproduces Eq. full-d2 for any pair of modes),
+ *   S3 = (8piGrho/3)^2 M2/12 (k^2/a^2)/Pi(k) DFT[psi^2],
+ *   S4 = -(8piGrho/3) m^2/(2a^2)/Pi(k) DFT[2 phi_,ij psi_,ij + phi_,iij psi_,j],
+ * and the GR source S_GR (same delta0, fields evolved with D1_GR(a)).  The per-mode ratio
+ * Re(S_MG / S_GR) (modes with |S_GR| below 1e-8 of its rms skipped) is binned in n_bins
+ * linear shells of width k_Ny / n_bins, as the P(k) of lpt2_cic_pk.
+ *   noise    float[N^3] white noise, or NULL for the plan's Philox noise
+ *   mean, sigma  double[n_bins] mean and scatter of the ratio per shell (output)
+ *   count    int64[n_bins] modes per shell, conjugate pairs counted twice (output)
+ *   t1       double[n_bins] the T1 analytic ratio (D1(k/sqrt2)/D1_GR)^2 [mu(k) - (2/27) 4piGrho
+ *            (k^2/a^2) M2 / (Pi(k) Pi(k/sqrt2)^2)] at the shell's mean |k|, or NULL
+ *   k_mean   double[n_bins] mean |k| per shell (h/Mpc), or NULL (required when t1 is given)
+ *   s_mg, s_gr  complex64 [N][N][N/2] half spectra of S_MG and S_GR (output), or both NULL
+ * Device pointers; single-instance plans; needs the workspace (uses most slots); returns
+ * LPT2_EINVAL for bad arguments, LPT2_EUNSUPPORTED for multi-instance plans.  Not on the
+ * displacement path: about 36 three-pass transforms per call. */
+int lpt2_source_ratio(lpt2_plan_t plan, const float* noise, int n_bins, double* mean, double* sigma,
+                      int64_t* count, double* t1, double* k_mean, void* s_mg, void* s_gr);
+
 /* lpt2_fft_r2c: forward 3-D transform of a real field (unnormalised,
  * exp(-i k.x)) into the half spectrum; in and out may not alias.
  * lpt2_fft_c2r: inverse (exp(+i k.x), unnormalised: the result is N^3 times the

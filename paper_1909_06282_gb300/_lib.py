@@ -85,6 +85,7 @@ def load_library():
         "lpt2_last_error": (C.c_char_p, []),
         "lpt2_launch_count": (i64, [vp]),
         "lpt2_device_status": (i, [vp]),
+        "lpt2_source_ratio": (i, [vp, vp, i, vp, vp, vp, vp, vp, vp, vp]),
         "lpt2_timing": (i, [vp, i]),
         "lpt2_cic_pk_noalloc": (i, [i, d, vp, vp, vp, vp, vp, i, vp]),
         "lpt2_set_fr0": (i, [vp, d]),
@@ -196,6 +197,24 @@ def lpt2_workspace_size(plan: Plan) -> int:
 
 def lpt2_launch_count(plan: Plan) -> int:
     return int(load_library().lpt2_launch_count(plan.handle))
+
+
+def lpt2_source_ratio(plan: Plan, noise=None, n_bins=32, spectra=False):
+    """Full second-order source term / GR, binned (mean, sigma, count, t1, k_mean); with
+    spectra=True also the per-mode S_MG and S_GR half spectra (complex64 (N, N, N/2))."""
+    n = plan.n
+    f64 = lambda: torch.empty(n_bins, dtype=torch.float64, device="cuda")
+    res = dict(mean=f64(), sigma=f64(), count=torch.empty(n_bins, dtype=torch.int64, device="cuda"),
+               t1=f64(), k_mean=f64())
+    if spectra:
+        res["s_mg"] = torch.empty((n, n, n // 2), dtype=torch.complex64, device="cuda")
+        res["s_gr"] = torch.empty((n, n, n // 2), dtype=torch.complex64, device="cuda")
+    if noise is not None and (noise.dtype != torch.float32 or noise.numel() != plan.cells):
+        raise ValueError("noise must be float32 with N^3 elements")
+    _check(load_library().lpt2_source_ratio(plan.handle, _ptr(noise), n_bins, _ptr(res["mean"]),
+                                            _ptr(res["sigma"]), _ptr(res["count"]), _ptr(res["t1"]),
+                                            _ptr(res["k_mean"]), _ptr(res.get("s_mg")), _ptr(res.get("s_gr"))))
+    return res
 
 
 def lpt2_device_status(plan: Plan) -> None:

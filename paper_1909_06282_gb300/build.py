@@ -17,7 +17,7 @@ LIBDIR = os.path.join(HERE, "lib")
 BUILDDIR = os.path.join(HERE, "_build")
 LIBNAME = "liblpt2.so"
 
-SOURCES = ["api.cu", "misc.cu", "growth.cu", "noalloc.cu"] + [f"inst_{n}.cu" for n in (16, 32, 64, 96, 128, 192, 256, 512, 1024)]
+SOURCES = ["api.cu", "misc.cu", "growth.cu", "noalloc.cu", "source.cu"] + [f"inst_{n}.cu" for n in (16, 32, 64, 96, 128, 192, 256, 512, 1024)]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-I", os.path.join(os.path.dirname(HERE), "include")]

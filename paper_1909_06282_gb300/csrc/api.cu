@@ -75,6 +75,8 @@ struct lpt2_plan_s {
   uint64_t* seeds_dev;        // [n_inst]
   double* fr0_dev;            // [n_inst]
   int* dev_err;               // device error word written by bounded waits (0 = ok)
+  double* gr_tab;             // [4][2] GR growth (D1_GR(a) / D1_GR(1)) for the source diagnostic
+  float* gr_tabf;
   size_t slot_sz;             // bytes per workspace slot: max over groups of count n^3 4
   int xb_max;                 // max over groups of count * x-pass blocks
   size_t total_cells;         // sum over instances of n^3
@@ -493,6 +495,8 @@ int lpt2_plan(lpt2_plan_t* out, const lpt2_instance* inst, int n_inst, int n_k, 
   if (e == cudaSuccess) e = cudaMalloc(&p->seeds_dev, (size_t)n_inst * sizeof(uint64_t));
   if (e == cudaSuccess) e = cudaMalloc(&p->fr0_dev, (size_t)n_inst * sizeof(double));
   if (e == cudaSuccess) e = cudaMalloc(&p->dev_err, sizeof(int));
+  if (e == cudaSuccess) e = cudaMalloc(&p->gr_tab, 8 * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&p->gr_tabf, 8 * sizeof(float));
   if (e == cudaSuccess) e = cudaMemset(p->dev_err, 0, sizeof(int));
   if (e != cudaSuccess) {
     lpt2_plan_destroy(p);
@@ -553,6 +557,8 @@ int lpt2_plan_destroy(lpt2_plan_t p) {
   cudaFree(p->seeds_dev);
   cudaFree(p->fr0_dev);
   cudaFree(p->dev_err);
+  cudaFree(p->gr_tab);
+  cudaFree(p->gr_tabf);
   for (auto& gc : p->graphs)
     if (gc.exec) cudaGraphExecDestroy(gc.exec);
   if (p->ev) {
@@ -794,6 +800,178 @@ int lpt2_cic_pk(lpt2_plan_t p, const float* pos, float* density, double* pk, dou
   if (!p->use_graph) return body();
   const void* key[8] = {pos, density, pk, k_mean, n_modes, p->ws, (const void*)(intptr_t)n_shells, nullptr};
   return run_graph(p, 1, key, body);
+}
+
+// ------------------------------------------------------------ full-source diagnostic
+int lpt2_source_ratio(lpt2_plan_t p, const float* noise, int n_bins, double* mean, double* sigma, int64_t* count,
+                      double* t1, double* k_mean, void* s_mg, void* s_gr) {
+  int rc = check_plan_ws(p);
+  if (rc) return rc;
+  if (p->n_inst != 1) return fail(LPT2_EUNSUPPORTED, "lpt2_source_ratio needs a single-instance plan");
+  if (n_bins < 1 || n_bins > kMaxShells) return fail(LPT2_EINVAL, "n_bins must be in [1, 256]");
+  if (!mean || !sigma || !count) return fail(LPT2_EINVAL, "mean, sigma and count must not be null");
+  if ((s_mg == nullptr) != (s_gr == nullptr)) return fail(LPT2_EINVAL, "give both s_mg and s_gr or neither");
+  if ((s_mg && !aligned(s_mg, 16)) || (s_gr && !aligned(s_gr, 16))) return fail(LPT2_EINVAL, "misaligned spectra");
+  set_group(p, 0);
+  const int n = p->n;
+  const Geo g = make_geo(p);
+  const size_t cells = (size_t)n * n * n;
+  rc = ensure_geometry(p, 0, n_bins);
+  if (rc) return rc;
+
+  // background at a (FP64 on the host): 4 pi G rho, m^2, M2 (Sec. 2.4, n = 1)
+  const double a = p->a_out, H0c = 1.0 / 2997.92458;
+  const double om = p->cosmo.omega_m, ol = p->cosmo.omega_l, fr0 = p->cosmo.fr0_abs;
+  const double fpg = 1.5 * om / (a * a * a) * H0c * H0c;
+  const double xa = om / (a * a * a) + 4.0 * ol, x0 = om + 4.0 * ol;
+  const double m2a = fr0 > 0 ? 0.5 * H0c * H0c * xa * xa * xa / (fr0 * x0 * x0) : 0.0;
+  const double M2a = fr0 > 0 ? 2.25 * H0c * H0c * pow(xa, 5) / (fr0 * fr0 * pow(x0, 4)) : 0.0;
+
+  // D1_GR(a) / D1_GR(1): the growth integration with |fR0| = 0 on two dummy k nodes
+  GrowthParams gp = growth_params(p);
+  gp.fr0_abs = 0.0;
+  gp.fr0s = nullptr;
+  gp.n_inst = 1;
+  gp.nk = 2;
+  gp.k_min = 1e-3;
+  gp.k_max = 2e-3;
+  LAUNCH(p, "growth_gr", 0.0, launch_growth(gp, p->gr_tab, p->gr_tabf, p->stream));
+  double d1gr_h = 0.0;
+  cudaError_t ce = cudaMemcpyAsync(&d1gr_h, p->gr_tab, sizeof(double), cudaMemcpyDeviceToHost, p->stream);
+  if (ce == cudaSuccess) ce = cudaStreamSynchronize(p->stream);
+  if (ce != cudaSuccess) return fail(LPT2_ECUDA, "GR growth: %s", cudaGetErrorString(ce));
+
+  // slots: 0 temporary spectrum, 1 delta0(k), 2-5 real temporaries, 6-11 accumulators,
+  // 12 psi / s3, 13-17 spectra of s1, s2, s3, s4, s_GR
+  float2* T = slot(p, S_A);
+  float2* D = slot(p, S_DELTA);
+  auto real = [&](int i) { return reinterpret_cast<float*>(slot(p, i)); };
+  float *P = real(2), *Q = real(3), *R = real(4), *P0 = real(5);
+  SrcAccum acc{real(6), real(7), real(8), real(9), real(10), real(11)};
+  float* PS = real(12);
+  float2* F[5] = {slot(p, 13), slot(p, 14), slot(p, 15), slot(p, 16), slot(p, 17)};
+  for (int i = 6; i <= 11; ++i) {
+    ce = cudaMemsetAsync(real(i), 0, cells * sizeof(float), p->stream);
+    if (ce != cudaSuccess) return fail(LPT2_ECUDA, "clear: %s", cudaGetErrorString(ce));
+  }
+
+  // delta0(k) (the x pass of the forward path writes it; its potential outputs are scratch)
+  rc = forward_zy(p, noise ? Z_REAL : Z_NOISE, noise, T);
+  if (rc) return rc;
+  {
+    XArgs x{};
+    x.g = g;
+    x.tw = p->tw;
+    x.mode = X_DELTA;
+    x.in = T;
+    x.delta_out = D;
+    for (int i = 0; i < 3; ++i) x.out[i] = F[i];
+    x.cosmo = p->cosmo_dev;
+    x.mt0 = p->mt0;
+    x.mt1 = p->mt1;
+    x.d1f = p->tabf;
+    x.d2f = p->tabf + p->nk;
+    x.t1f = p->tabf + 2 * p->nk;
+    x.t2f = p->tabf + 3 * p->nk;
+    LAUNCH(p, "x_delta", 20.0 * V3(p), x_pass(n, x, p->stream));
+  }
+  // one real field: IDFT[(i k)^ord g(|k|) delta0(k)]
+  auto field = [&](int gk, int ox, int oy, int oz, float* out) -> int {
+    XArgs x{};
+    x.g = g;
+    x.tw = p->tw;
+    x.mode = X_MUL;
+    x.in = D;
+    x.out[0] = T;
+    x.mt0 = p->mt0;
+    x.mul_g = gk;
+    x.mul_ord[0] = ox;
+    x.mul_ord[1] = oy;
+    x.mul_ord[2] = oz;
+    x.mul_m2a = (float)m2a;
+    x.mul_inv_a2 = (float)(1.0 / (a * a));
+    x.mul_d1gr = (float)d1gr_h;
+    LAUNCH(p, "x_mul", 8.0 * V3(p), x_pass(n, x, p->stream));
+    YArgs y{};
+    y.g = g;
+    y.tw = p->tw;
+    y.inverse = 1;
+    y.job.n_in = 1;
+    y.job.n_out = 1;
+    y.job.in[0] = T;
+    y.job.out[0] = T;
+    LAUNCH(p, "y_inv", 8.0 * V3(p), y_pass(n, y, p->stream));
+    ZC2RArgs z{g, p->tw, T, out, nullptr};
+    LAUNCH(p, "z_c2r", 8.0 * V3(p), z_c2r(n, z, p->stream));
+    return LPT2_OK;
+  };
+  static const int pairs[6][2] = {{0, 0}, {1, 1}, {2, 2}, {0, 1}, {0, 2}, {1, 2}};
+  for (const auto& ij : pairs) {
+    int o[3] = {0, 0, 0};
+    ++o[ij[0]];
+    ++o[ij[1]];
+    if ((rc = field(G_POT, o[0], o[1], o[2], P)) || (rc = field(G_MUPOT, o[0], o[1], o[2], Q)) ||
+        (rc = field(G_PSI, o[0], o[1], o[2], R)) || (rc = field(G_POT0, o[0], o[1], o[2], P0)))
+      return rc;
+    const bool diag = ij[0] == ij[1];
+    LAUNCH(p, "src_pair", 40.0 * V3(p),
+           launch_src_pair(cells, P, Q, R, P0, diag ? 1.f : 2.f, diag ? 1 : 0, acc, p->stream));
+  }
+  for (int j = 0; j < 3; ++j) {
+    int o[3] = {0, 0, 0};
+    o[j] = 1;
+    if ((rc = field(G_D1, o[0], o[1], o[2], P)) || (rc = field(G_PSI, o[0], o[1], o[2], Q))) return rc;
+    LAUNCH(p, "src_grad", 16.0 * V3(p), launch_src_grad(cells, P, Q, acc.s4, p->stream));
+  }
+  if ((rc = field(G_PSI, 0, 0, 0, PS))) return rc;
+  LAUNCH(p, "src_final", 28.0 * V3(p), launch_src_final(cells, acc, PS, p->stream));
+
+  // forward transforms of s1, s2, s3, s4, s_GR
+  const float* src[5] = {acc.s1, acc.s2, PS, acc.s4, acc.sg};
+  for (int i = 0; i < 5; ++i) {
+    if ((rc = forward_zy(p, Z_REAL, src[i], F[i]))) return rc;
+    XArgs x{};
+    x.g = g;
+    x.tw = p->tw;
+    x.mode = X_FWD;
+    x.in = F[i];
+    x.out[0] = F[i];
+    LAUNCH(p, "x_fwd", 8.0 * V3(p), x_pass(n, x, p->stream));
+  }
+  // per-mode ratio, shell mean and scatter
+  SrcRatioArgs ra{};
+  ra.n = n;
+  ra.n_bins = n_bins;
+  ra.kf = g.kf;
+  ra.fpg = (float)fpg;
+  ra.e3 = (float)(2.0 / 3.0 * fpg);
+  ra.m2a = (float)m2a;
+  ra.inv_a2 = (float)(1.0 / (a * a));
+  ra.M2a = (float)M2a;
+  ra.fr0 = (float)fr0;
+  ra.f1 = F[0];
+  ra.f2 = F[1];
+  ra.f3 = F[2];
+  ra.f4 = F[3];
+  ra.fg = F[4];
+  ra.smg = reinterpret_cast<float2*>(s_mg);
+  ra.sgr = reinterpret_cast<float2*>(s_gr);
+  const int nblk = src_ratio_blocks(n);
+  double* part0 = pk_part(p);                          // [nblk][2]
+  double* part1 = part0 + (size_t)2 * nblk;            // [nblk][3][n_bins]
+  ra.part = part0;
+  LAUNCH(p, "src_ratio0", 20.0 * V3(p), launch_src_ratio(ra, 0, nullptr, p->stream));
+  ra.part = part1;
+  LAUNCH(p, "src_ratio1", 20.0 * V3(p), launch_src_ratio(ra, 1, part0, p->stream));
+  LAUNCH(p, "src_finalize", 0.0, launch_src_finalize(part1, nblk, n_bins, mean, sigma, count, p->stream));
+  if (t1 && !k_mean) return fail(LPT2_EINVAL, "t1 needs k_mean");
+  if (k_mean) {
+    const Group& gr = p->groups[0];
+    LAUNCH(p, "src_t1", 0.0,
+           launch_src_t1(n_bins, gr.geo_k, gr.geo_n, k_mean, p->tab, p->nk, p->k_min, p->k_max, p->gr_tab, a, m2a,
+                         M2a, fpg, fr0 > 0 ? 0 : 1, t1, p->stream));
+  }
+  return LPT2_OK;
 }
 
 int lpt2_fft_r2c(lpt2_plan_t p, const float* in, void* out) {

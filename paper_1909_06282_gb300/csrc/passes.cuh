@@ -734,6 +734,34 @@ __global__ void __launch_bounds__(PassCfg<N>::XT) k_x(XArgs a) {
   } else {
 #pragma unroll
     for (int r = 0; r < C::RMAX; ++r) v[r] = a.in[base + (size_t)(elem<N>(t, r)) * stride];
+    if (MODE == X_MUL) {   // full-source diagnostic: multiplier, then inverse x
+      const size_t toff = (size_t)blockIdx.z * mode_table_len(N);
+#pragma unroll
+      for (int r = 0; r < C::RMAX; ++r) {
+        const int kx = elem<N>(t, r);
+        const int mx = mode_of(kx, N);
+        const int n2 = mx * mx + my * my + mz * mz;
+        const bool zero = ny_nyq || kx == C::H || n2 == 0;
+        const float4 mt = zero ? make_float4(0.f, 0.f, 0.f, 0.f) : __ldg(a.mt0 + toff + n2);
+        const float q = kf * kf * (float)n2 * a.mul_inv_a2;   // k^2 / a^2
+        float gk;
+        switch (a.mul_g) {
+          case G_POT: gk = mt.z * mt.y; break;                                          // D1 / (k^2 N^3)
+          case G_MUPOT: gk = mt.z * mt.y * (1.f + q / (3.f * (q + a.mul_m2a))); break;
+          case G_PSI: gk = mt.z * a.g.inv_n3 / (q + a.mul_m2a); break;
+          case G_POT0: gk = a.mul_d1gr * mt.y; break;
+          default: gk = mt.z * a.g.inv_n3; break;                                       // G_D1
+        }
+        float2 u = zero ? make_float2(0.f, 0.f) : cscale(v[r], gk);
+        u = deriv(u, kf * (float)mx, a.mul_ord[0]);
+        u = deriv(u, kf * (float)my, a.mul_ord[1]);
+        v[r] = deriv(u, kf * (float)mz, a.mul_ord[2]);
+      }
+      fft<N, true>(v, t, sm, s_tw);
+#pragma unroll
+      for (int r = 0; r < C::RMAX; ++r) a.out[0][base + (size_t)(elem<N>(t, r)) * stride] = v[r];
+      return;
+    }
     if (MODE == X_INV) {
       fft<N, true>(v, t, sm, s_tw);
 #pragma unroll
@@ -993,6 +1021,7 @@ template <int N> cudaError_t launch_x_t(const XArgs& a, cudaStream_t s) {
     case X_SOURCE: return launch_x_m<N, X_SOURCE>(a, s);
     case X_PK: return launch_x_m<N, X_PK>(a, s);
     case X_PKP: return launch_x_m<N, X_PKP>(a, s);
+    case X_MUL: return launch_x_m<N, X_MUL>(a, s);
     case X_FWD: return launch_x_m<N, X_FWD>(a, s);
     case X_INV: return launch_x_m<N, X_INV>(a, s);
     case X_PHI: return launch_x_m<N, X_PHI>(a, s);

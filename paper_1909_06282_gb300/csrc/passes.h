@@ -129,6 +129,7 @@ enum XMode {
   X_ADJ_SOURCE = 7, // transpose of X_SOURCE: h_Psi, h_S, dL/dln|fR0| partials
   X_ADJ_DELTA = 8,  // transpose of X_DELTA: s(k) (h_Psi + h_phi), inverse x
   X_PKP = 9,        // fwd x, shell sums of |delta|^2 only (mode counts and mean |k| cached)
+  X_MUL = 10,       // k-space multiplier (i k)^ord g(|k|) of the full-source diagnostic, inverse x
 };
 struct XArgs {
   Geo g;
@@ -157,6 +158,20 @@ struct XArgs {
   const float4* mt0;
   const float2* mt1;
   double* theta_part;     // X_ADJ_SOURCE: per-block partial of dL/dln|fR0|
+  // X_MUL: multiplier (i kx)^ord[0] (i ky)^ord[1] (i kz)^ord[2] g(|k|) / N^3, g one of MulG,
+  // with m^2(a), 1/a^2 and D1_GR(a) for mu(k) and Pi(k)
+  int mul_g;
+  int mul_ord[3];
+  float mul_m2a, mul_inv_a2, mul_d1gr;
+};
+
+// Radial factors of the full-source diagnostic (Sec. 3, Eqs. s1-s4):
+enum MulG {
+  G_POT = 0,    // D1(k) / k^2               phi
+  G_MUPOT = 1,  // D1(k) mu(k) / k^2         mu * phi
+  G_PSI = 2,    // D1(k) / Pi(k)             psi
+  G_POT0 = 3,   // D1_GR / k^2               phi of the GR realisation
+  G_D1 = 4      // D1(k)                     delta1
 };
 
 struct CicArgs {
@@ -198,6 +213,30 @@ cudaError_t launch_pk_finalize(const double* part, int n_blocks, int n_shells, d
 // part of the P(k) estimator.  kmean and nmodes must be zeroed before the launch.
 cudaError_t launch_shell_geometry(int n, double box, int n_shells, double* ksum, unsigned long long* nmodes,
                                   cudaStream_t s);
+// Full-source diagnostic (source.cu): real-space accumulations over the pairs (i, j),
+// the per-mode ratio of the MG to the GR source, its shell mean / scatter, the T1 curve.
+struct SrcAccum {
+  float *s1, *s2, *s4, *sg, *tr, *tr0;   // accumulators [N^3]
+};
+cudaError_t launch_src_pair(size_t cells, const float* phi, const float* muphi, const float* psi_ij,
+                            const float* phi0, float w, int diag, SrcAccum acc, cudaStream_t s);
+cudaError_t launch_src_grad(size_t cells, const float* del_j, const float* psi_j, float* s4, cudaStream_t s);
+cudaError_t launch_src_final(size_t cells, SrcAccum acc, float* psi_to_s3, cudaStream_t s);
+struct SrcRatioArgs {
+  int n, n_bins;
+  float kf, fpg, e3, m2a, inv_a2, M2a, fr0;   // 4 pi G rho, 8 pi G rho / 3, m^2(a), 1/a^2, M2(a)
+  const float2 *f1, *f2, *f3, *f4, *fg;       // DFT of s1, s2, s3, s4, s_GR (half spectra)
+  float2 *smg, *sgr;                          // optional per-mode sources out
+  double* part;                               // [blocks][2] for pass 0, [blocks][3][n_bins] for pass 1
+};
+int src_ratio_blocks(int n);
+cudaError_t launch_src_ratio(const SrcRatioArgs& a, int pass, const double* rms_part, cudaStream_t s);
+cudaError_t launch_src_finalize(const double* part, int n_blocks, int n_bins, double* mean, double* sigma,
+                                int64_t* count, cudaStream_t s);
+cudaError_t launch_src_t1(int n_bins, const double* ksum, const unsigned long long* count, double* kmean,
+                          const double* tab_d1, int nk, double k_min, double k_max, const double* d1gr, double a,
+                          double m2a, double M2a, double fpg, int gr, double* t1, cudaStream_t s);
+
 // P(k) from per-block |delta|^2 shell sums [n_blocks][n_shells] and the cached geometry.
 cudaError_t launch_pk_finalize_p(const double* part, int n_blocks, int n_shells, const double* ksum,
                                  const unsigned long long* count, double* pk, double* k_mean, int64_t* n_modes,
