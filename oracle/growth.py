@@ -25,6 +25,17 @@ D1 normalisation.
 Tangents: d/dtheta of every state, theta = ln|f_R0|, by forward sensitivity
 (dm^2/dtheta = -m^2, dM2/dtheta = -2 M2), integrated by the same RK4.
 
+Other triangle configurations (Sec. 3, the comparison of the full source term with
+triangles): k1 = r k2 at angle theta between the vectors k1 and k2, k = |k1 + k2|, so
+k2 = k / sqrt(r^2 + 1 + 2 r cos theta).  The D2 source is D1(k1) D1(k2) times the braces
+of Eq. full-d2 for that triangle divided by sin^2 theta (the GR braces), so that every
+configuration keeps the GR limit -3/7 D1^2 (a reading: the factorisation Psi2 = D2 grad phi2
+takes the geometric sin^2 theta of each mode pair from the GR source S).  Variants:
+  0 T1 (r = 1, 90 deg)   1 T2 (r = 1, 80 deg)   2 isosceles 70 deg
+  3 r = 2, 80 deg        4 r = 2, 70 deg
+  5 Winther: the T1 braces with D1(k)^2 in place of D1(k1) D1(k2)
+  6 GR: the D2 equation with mu = 1 and the GR braces (scale-independent D2).
+
 The k table is k_t = k_min (k_max/k_min)^(t/(n_k-1)); lookups interpolate
 linearly in ln k between nodes and clamp outside the table (a reading: the
 paper only says the solution is interpolated in k, Sec. 2.4).
@@ -35,7 +46,8 @@ import numpy as np
 
 from . import cosmology as cm
 
-__all__ = ["k_table", "growth_tables", "interp_lnk", "d1_gr", "DEFAULT_STEPS"]
+__all__ = ["k_table", "growth_tables", "interp_lnk", "d1_gr", "DEFAULT_STEPS", "VARIANTS",
+           "triangle", "d2_braces"]
 
 DEFAULT_STEPS = 2048
 
@@ -52,57 +64,111 @@ def _background(c, s):
     return a, om, damp
 
 
-def _rhs(c, k, s, y):
-    """y: (12, n_k) = [D1, D1_s, D1h, D1h_s, D2, D2_s] and their theta-tangents."""
+# (r = k1 / k2, angle between k1 and k2 in degrees); 5 Winther and 6 GR use the T1 geometry
+VARIANTS = {0: (1.0, 90.0), 1: (1.0, 80.0), 2: (1.0, 70.0), 3: (2.0, 80.0), 4: (2.0, 70.0),
+            5: (1.0, 90.0), 6: (1.0, 90.0)}
+WINTHER, GR_D2 = 5, 6
+
+
+def triangle(k, variant):
+    """(k1, k2, cos theta) of the variant's triangle with |k1 + k2| = k."""
+    r, th = VARIANTS[variant]
+    ct = np.cos(np.deg2rad(th)) if th != 90.0 else 0.0
+    k2 = k / np.sqrt(r * r + 1.0 + 2.0 * r * ct)
+    return r * k2, k2, ct
+
+
+def d2_braces(c, k, a, variant, tangent=False):
+    """Braces of Eq. full-d2 for the variant's triangle at |k1 + k2| = k, divided by
+    sin^2 theta (and, with tangent, their d/dln|fR0|)."""
+    k1, k2, ct = triangle(k, variant)
+    r = VARIANTS[variant][0]
+    c2 = ct * ct
+    s2 = 1.0 - c2
+    if c.fr0_abs == 0.0 or variant == GR_D2:
+        one = np.ones_like(np.asarray(k, dtype=np.float64))
+        return (one, 0.0 * one) if tangent else one
+    q, q1, q2 = (k / a) ** 2, (k1 / a) ** 2, (k2 / a) ** 2
+    msq = cm.m2(c, a)
+    P, P1, P2 = q + msq, q1 + msq, q2 + msq
+    mu, mu1, mu2 = 1.0 + q / (3.0 * P), 1.0 + q1 / (3.0 * P1), 1.0 + q2 / (3.0 * P2)
+    G = msq / P
+    lin = 2.0 * c2 * (mu1 + mu2 - 2.0) + (ct / r) * (mu1 - 1.0) + r * ct * (mu2 - 1.0)
+    B = (2.0 / 27.0) * cm.four_pi_g_rho(c, a) * q * cm.M2(c, a) / (P * P1 * P2)
+    br = mu - c2 * (mu1 + mu2 - mu) + G * lin - B
+    if not tangent:
+        return br / s2
+    mut, mu1t, mu2t = q * msq / (3 * P * P), q1 * msq / (3 * P1 * P1), q2 * msq / (3 * P2 * P2)
+    Gt = -G * q / P
+    lint = 2.0 * c2 * (mu1t + mu2t) + (ct / r) * mu1t + r * ct * mu2t
+    Bt = B * (-2.0 + msq / P + msq / P1 + msq / P2)
+    brt = mut - c2 * (mu1t + mu2t - mut) + Gt * lin + G * lint - Bt
+    return br / s2, brt / s2
+
+
+def _rhs(c, k, s, y, variant=0):
+    """y: (16, n_k) = [D1, D1_s, Da, Da_s, Db, Db_s, D2, D2_s] (Da = D1(k1), Db = D1(k2))
+    and their theta-tangents, theta = ln|f_R0|."""
     a, om, damp = _background(c, s)
-    kh = k / np.sqrt(2.0)
-    D1, D1s, D1h, D1hs, D2, D2s, Z1, Z1s, Z1h, Z1hs, Z2, Z2s = y
+    k1, k2, _ = triangle(k, variant)
+    D1, D1s, Da, Das, Db, Dbs, D2, D2s, Z1, Z1s, Za, Zas, Zb, Zbs, Z2, Z2s = y
     cc = 1.5 * om
     if c.fr0_abs == 0.0:
-        mu_k = np.ones_like(k)
-        mu_h = np.ones_like(k)
-        mu_kt = mu_ht = B = Bt = np.zeros_like(k)
+        mu_k = mu_a = mu_b = np.ones_like(k)
+        mu_kt = mu_at = mu_bt = np.zeros_like(k)
     else:
-        q, qh = (k / a) ** 2, (kh / a) ** 2
         msq = cm.m2(c, a)
-        Pk, Ph = q + msq, qh + msq
-        mu_k = 1.0 + q / (3.0 * Pk)
-        mu_h = 1.0 + qh / (3.0 * Ph)
-        mu_kt = q * msq / (3.0 * Pk * Pk)
-        mu_ht = qh * msq / (3.0 * Ph * Ph)
-        B = (2.0 / 27.0) * cm.four_pi_g_rho(c, a) * q * cm.M2(c, a) / (Pk * Ph * Ph)
-        Bt = B * (-2.0 + msq / Pk + 2.0 * msq / Ph)
-    src = mu_k - B
+        def mus(kk):
+            qq = (kk / a) ** 2
+            pp = qq + msq
+            return 1.0 + qq / (3.0 * pp), qq * msq / (3.0 * pp * pp)
+        mu_k, mu_kt = mus(k)
+        mu_a, mu_at = mus(k1)
+        mu_b, mu_bt = mus(k2)
+    if variant == GR_D2:       # D2 of GR: GR chains a, b and mu = 1 in its equation
+        mu_a = mu_b = mu_2 = np.ones_like(k)
+        mu_at = mu_bt = mu_2t = np.zeros_like(k)
+    else:
+        mu_2, mu_2t = mu_k, mu_kt
+    src, srct = d2_braces(c, k, a, variant, tangent=True)
+    if variant == WINTHER:     # D1(k)^2 in place of D1(k1) D1(k2)
+        Pa, Pb, Pat, Pbt = D1, D1, Z1, Z1
+    else:
+        Pa, Pb, Pat, Pbt = Da, Db, Za, Zb
     dy = np.empty_like(y)
     dy[0] = D1s
     dy[1] = -damp * D1s + cc * mu_k * D1
-    dy[2] = D1hs
-    dy[3] = -damp * D1hs + cc * mu_h * D1h
-    dy[4] = D2s
-    dy[5] = -damp * D2s + cc * mu_k * D2 - cc * D1h * D1h * src
-    dy[6] = Z1s
-    dy[7] = -damp * Z1s + cc * (mu_k * Z1 + mu_kt * D1)
-    dy[8] = Z1hs
-    dy[9] = -damp * Z1hs + cc * (mu_h * Z1h + mu_ht * D1h)
-    dy[10] = Z2s
-    dy[11] = (-damp * Z2s + cc * (mu_k * Z2 + mu_kt * D2)
-              - cc * (2.0 * D1h * Z1h * src + D1h * D1h * (mu_kt - Bt)))
+    dy[2] = Das
+    dy[3] = -damp * Das + cc * mu_a * Da
+    dy[4] = Dbs
+    dy[5] = -damp * Dbs + cc * mu_b * Db
+    dy[6] = D2s
+    dy[7] = -damp * D2s + cc * mu_2 * D2 - cc * Pa * Pb * src
+    dy[8] = Z1s
+    dy[9] = -damp * Z1s + cc * (mu_k * Z1 + mu_kt * D1)
+    dy[10] = Zas
+    dy[11] = -damp * Zas + cc * (mu_a * Za + mu_at * Da)
+    dy[12] = Zbs
+    dy[13] = -damp * Zbs + cc * (mu_b * Zb + mu_bt * Db)
+    dy[14] = Z2s
+    dy[15] = (-damp * Z2s + cc * (mu_2 * Z2 + mu_2t * D2)
+              - cc * ((Pat * Pb + Pa * Pbt) * src + Pa * Pb * srct))
     return dy
 
 
-def _rk4(c, k, a_in, a_out, n_steps):
+def _rk4(c, k, a_in, a_out, n_steps, variant=0):
     s0, s1 = np.log(a_in), np.log(a_out)
     h = (s1 - s0) / n_steps
-    y = np.zeros((12, k.size))
-    y[0] = y[1] = y[2] = y[3] = a_in
-    y[4] = -3.0 / 7.0 * a_in ** 2
-    y[5] = -6.0 / 7.0 * a_in ** 2
+    y = np.zeros((16, k.size))
+    y[0:6] = a_in
+    y[6] = -3.0 / 7.0 * a_in ** 2
+    y[7] = -6.0 / 7.0 * a_in ** 2
     for i in range(n_steps):
         s = s0 + i * h
-        k1 = _rhs(c, k, s, y)
-        k2 = _rhs(c, k, s + 0.5 * h, y + 0.5 * h * k1)
-        k3 = _rhs(c, k, s + 0.5 * h, y + 0.5 * h * k2)
-        k4 = _rhs(c, k, s + h, y + h * k3)
+        k1 = _rhs(c, k, s, y, variant)
+        k2 = _rhs(c, k, s + 0.5 * h, y + 0.5 * h * k1, variant)
+        k3 = _rhs(c, k, s + 0.5 * h, y + 0.5 * h * k2, variant)
+        k4 = _rhs(c, k, s + h, y + h * k3, variant)
         y = y + (h / 6.0) * (k1 + 2.0 * k2 + 2.0 * k3 + k4)
     return y
 
@@ -113,13 +179,16 @@ def d1_gr(c, a_out=1.0, n_steps=DEFAULT_STEPS):
     return float(y[0, 0])
 
 
-def growth_tables(c, a_out=1.0, k=None, n_steps=DEFAULT_STEPS):
-    """Returns dict with k, D1, D2 and dD1/dln|fR0|, dD2/dln|fR0| (all (n_k,))."""
+def growth_tables(c, a_out=1.0, k=None, n_steps=DEFAULT_STEPS, variant=None):
+    """Returns dict with k, D1, D2 and dD1/dln|fR0|, dD2/dln|fR0| (all (n_k,)); D2 for
+    the triangle variant (default: the cosmology's d2_variant, else T1)."""
     k = k_table() if k is None else np.asarray(k, dtype=np.float64)
-    y = _rk4(c, k, c.a_init, a_out, n_steps)
+    if variant is None:
+        variant = int(getattr(c, "d2_variant", 0))
+    y = _rk4(c, k, c.a_init, a_out, n_steps, variant)
     n1 = d1_gr(c, 1.0, n_steps)
-    return dict(k=k, D1=y[0] / n1, D2=y[4] / n1 ** 2,
-                dD1=y[6] / n1, dD2=y[10] / n1 ** 2, norm=n1)
+    return dict(k=k, D1=y[0] / n1, D2=y[6] / n1 ** 2,
+                dD1=y[8] / n1, dD2=y[14] / n1 ** 2, norm=n1)
 
 
 def interp_lnk(table_k, table_v, kq):

@@ -146,7 +146,8 @@ class Plan:
             arr[j] = _Instance(int(it.n), float(it.box), int(it.seed) & (2 ** 64 - 1),
                                float(getattr(it, "a_out", 1.0)),
                                _Cosmo(c.omega_m, c.omega_l, c.omega_b, c.h, c.n_s, c.sigma8, c.t_cmb,
-                                      c.fr0_abs, int(c.hs_n), c.a_init, 0))
+                                      c.fr0_abs, int(c.hs_n), c.a_init,
+                                      int(getattr(c, "d2_variant", 0))))
         self._cinst = arr
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         h = C.c_void_p()

@@ -97,26 +97,26 @@ def test_lcdm_gr_heath_integral_and_bouchet_fit():
         assert abs(ratio / om ** (-1 / 143) - 1) < 1.5e-3
 
 
-def test_rk4_against_scipy_dop853():
+@pytest.mark.parametrize("variant", [0, 3, 5])
+def test_rk4_against_scipy_dop853(variant):
     """Pins the RK4 stepping: the same right-hand side integrated by an adaptive
-    8th-order method agrees to 1e-10."""
+    8th-order method agrees to 1e-10 (T1, a k1 = 2 k2 triangle, Winther)."""
     c = W.COSMO
     k = np.array([1e-3, 0.05, 0.3, 3.0])
-    t = gr.growth_tables(c, 1.0, k=k)
-    y0 = np.zeros(12 * k.size)
-    y0 = np.zeros((12, k.size))
-    y0[0:4] = c.a_init
-    y0[4] = -3 / 7 * c.a_init ** 2
-    y0[5] = -6 / 7 * c.a_init ** 2
-    f = lambda s, y: gr._rhs(c, k, s, y.reshape(12, -1)).ravel()
+    t = gr.growth_tables(c, 1.0, k=k, variant=variant)
+    y0 = np.zeros((16, k.size))
+    y0[0:6] = c.a_init
+    y0[6] = -3 / 7 * c.a_init ** 2
+    y0[7] = -6 / 7 * c.a_init ** 2
+    f = lambda s, y: gr._rhs(c, k, s, y.reshape(16, -1), variant).ravel()
     sol = integrate.solve_ivp(f, (np.log(c.a_init), 0.0), y0.ravel(), method="DOP853",
                               rtol=1e-13, atol=1e-16)
-    y = sol.y[:, -1].reshape(12, -1)
+    y = sol.y[:, -1].reshape(16, -1)
     n1 = gr.d1_gr(c)
     np.testing.assert_allclose(t["D1"], y[0] / n1, rtol=1e-10)
-    np.testing.assert_allclose(t["D2"], y[4] / n1 ** 2, rtol=1e-10)
-    np.testing.assert_allclose(t["dD1"], y[6] / n1, rtol=1e-8, atol=1e-14)
-    np.testing.assert_allclose(t["dD2"], y[10] / n1 ** 2, rtol=1e-8, atol=1e-14)
+    np.testing.assert_allclose(t["D2"], y[6] / n1 ** 2, rtol=1e-10)
+    np.testing.assert_allclose(t["dD1"], y[8] / n1, rtol=1e-8, atol=1e-14)
+    np.testing.assert_allclose(t["dD2"], y[14] / n1 ** 2, rtol=1e-8, atol=1e-14)
 
 
 def test_mg_limits_of_tables():

@@ -33,6 +33,7 @@ class Cosmology:
     fr0_abs: float = 1e-5     # |f_R0|; 0 means GR (mu = 1)
     hs_n: int = 1             # Hu-Sawicki n; only n = 1 is defined (Sec. 2.3)
     a_init: float = 1e-3      # start of the growth integration
+    d2_variant: int = 0       # triangle configuration of D2: 0 = T1 (the paper's choice)
 
     def replace(self, **kw) -> "Cosmology":
         return dataclasses.replace(self, **kw)
