@@ -56,8 +56,20 @@ enum {
                      other than the legacy default stream) */
 };
 
-/* D2 variants (the triangle configuration of the second-order growth, Sec. 3). */
-enum { LPT2_D2_T1 = 0 /* k1 = k2 = k/sqrt2, theta = 90 deg: the paper's choice */ };
+/* D2 variants: the triangle configuration (k1, k2, angle theta between the vectors k1 and
+ * k2, |k1 + k2| = k) at which the second-order growth of Eq. full-d2 is solved (Sec. 3,
+ * the comparison of the full source term with triangles).  The source is D1(k1) D1(k2)
+ * times the braces of Eq. full-d2 divided by sin^2 theta, so that every configuration keeps
+ * the GR limit -3/7 D1^2. */
+enum {
+  LPT2_D2_T1 = 0,       /* k1 = k2 = k/sqrt2, theta = 90 deg: the paper's choice (T1)       */
+  LPT2_D2_T2 = 1,       /* k1 = k2, theta = 80 deg (T2)                                      */
+  LPT2_D2_ISO70 = 2,    /* k1 = k2, theta = 70 deg                                           */
+  LPT2_D2_R2_80 = 3,    /* k1 = 2 k2, theta = 80 deg                                         */
+  LPT2_D2_R2_70 = 4,    /* k1 = 2 k2, theta = 70 deg                                         */
+  LPT2_D2_WINTHER = 5,  /* T1 braces with D1(k)^2 in place of D1(k1) D1(k2) (Winther et al.) */
+  LPT2_D2_GR = 6        /* the D2 equation of GR (mu = 1): scale-independent                 */
+};
 
 /* Background cosmology and f(R) parameters. fr0_abs = |f_R0|; 0 selects GR
  * (mu = 1).  Flat: omega_m + omega_l must equal 1 to 1e-6.  hs_n must be 1
@@ -97,7 +109,7 @@ typedef struct lpt2_plan_s* lpt2_plan_t;
  * LPT2_EINVAL (null pointers, n_k < 2, k_min <= 0, k_max <= k_min, box <= 0,
  * a range, non-flat cosmology, fr0_abs < 0, n_steps < 1, instance ordering or
  * differing backgrounds, unknown flags), LPT2_EUNSUPPORTED (n not in the list
- * above, hs_n != 1, d2_variant != T1, differing boxes within a grid size),
+ * above, hs_n != 1, d2_variant outside LPT2_D2_T1 .. LPT2_D2_GR, differing boxes within a grid size),
  * LPT2_ENOMEM, LPT2_ECUDA.  lpt2_white_noise, lpt2_fft_*, lpt2_set_fr0 and
  * lpt2_displace_vjp need a single-instance plan. */
 int lpt2_plan(lpt2_plan_t* out, const lpt2_instance* inst, int n_inst, int n_k,

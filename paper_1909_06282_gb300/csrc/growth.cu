@@ -1,6 +1,7 @@
 // FP64 set-up kernels: Eisenstein-Hu constants and sigma_8 normalisation of
 // P(k), and the batched RK4 integration of the growth tables D1(k,a), D2(k,a)
-// (T1 triangle) with their ln|f_R0| tangents.
+// (T1 triangle by default, or another triangle of the Sec. 3 comparison) with
+// their ln|f_R0| tangents.
 //
 // Equations (units h/Mpc, s = ln a, flat E^2 = Om a^-3 + OL):
 //   D1_ss + (2 - 1.5 Om(a)) D1_s = 1.5 Om(a) mu(k,a) D1                    (Eq. d1)
@@ -11,6 +12,12 @@
 // with D2 taken with the sign that gives -3/7 D1^2 in GR, the EdS growing mode at
 // a_init and D1 normalised to the GR solution at a = 1.  Tangents use
 // dm^2/dln|fR0| = -m^2 and dM2/dln|fR0| = -2 M2.
+// Other triangles (k1 = r k2 at angle theta between k1 and k2, |k1 + k2| = k): the
+// source is -1.5 Om D1(k1) D1(k2) times the Eq. full-d2 braces
+//   mu - c^2 (mu1 + mu2 - mu) + m^2/Pi [2 c^2 (mu1 + mu2 - 2) + (c/r)(mu1 - 1) + r c (mu2 - 1)]
+//   - (2/27) 4piGrho (k^2/a^2) M2 / (Pi Pi1 Pi2),   c = cos theta,
+// divided by sin^2 theta so that every triangle keeps the GR limit; Winther's variant
+// takes D1(k)^2 with the T1 braces; the GR variant solves the D2 equation with mu = 1.
 #include <math.h>
 
 #include "passes.h"
@@ -123,62 +130,126 @@ __device__ Bg background(const GrowthParams& p, double s, bool gr) {
   return b;
 }
 
-template <bool TAN>
-struct State {
-  double v[TAN ? 12 : 6];
+// Triangle of a D2 variant: fa, fb = (k1/k)^2, (k2/k)^2, c = cos theta, r = k1/k2.
+struct D2Geo {
+  double fa, fb, c, c2, inv_s2, r;
+  int winther, gr2;
 };
 
-// right-hand side: y = [D1, D1s, D1h, D1hs, D2, D2s (, tangents of each)]
-template <bool TAN>
-__device__ __forceinline__ void rhs(const Bg& b, double k2, bool gr, const double* y, double* dy) {
-  const double q = k2 * b.inv_a2, qh = 0.5 * q;
-  double mu_k = 1.0, mu_h = 1.0, mu_kt = 0.0, mu_ht = 0.0, B = 0.0, Bt = 0.0;
+__host__ __device__ inline D2Geo d2_geo(int variant) {
+  // (r, theta in degrees) of the Sec. 3 comparison; Winther and GR use the T1 geometry
+  double r = 1.0, th = 90.0;
+  switch (variant) {
+    case 1: th = 80.0; break;
+    case 2: th = 70.0; break;
+    case 3: r = 2.0; th = 80.0; break;
+    case 4: r = 2.0; th = 70.0; break;
+    default: break;
+  }
+  D2Geo g;
+  g.c = th == 90.0 ? 0.0 : cos(th * (M_PI / 180.0));
+  g.c2 = g.c * g.c;
+  g.inv_s2 = 1.0 / (1.0 - g.c2);
+  g.r = r;
+  const double k2sq = 1.0 / (r * r + 1.0 + 2.0 * r * g.c);   // (k2/k)^2
+  g.fb = k2sq;
+  g.fa = r * r * k2sq;
+  g.winther = variant == 5;
+  g.gr2 = variant == 6;
+  return g;
+}
+
+// GEO 0: r = 1, c = 0 (T1, Winther, GR): one extra chain, the T1 braces mu - B.
+// GEO 1: r = 1, c != 0: one extra chain (k1 = k2), full braces.
+// GEO 2: r != 1: chains at k1 and k2, full braces.
+template <int GEO> struct Layout {
+  static constexpr int NB = GEO == 2 ? 8 : 6;   // states per set: D1, D1s, Da, Das, (Db, Dbs,) D2, D2s
+  static constexpr int A = 2, B = GEO == 2 ? 4 : 2, D2 = GEO == 2 ? 6 : 4;
+};
+
+// right-hand side; y = [set] (+ [tangent set] when TAN)
+template <bool TAN, int GEO>
+__device__ __forceinline__ void rhs(const Bg& b, double k2, bool gr, const D2Geo& g, const double* y, double* dy) {
+  using L = Layout<GEO>;
+  constexpr int T = L::NB;
+  const double q = k2 * b.inv_a2, qa = q * g.fa, qb = q * g.fb;
+  double mu_k = 1.0, mu_a = 1.0, mu_b = 1.0, mu_kt = 0.0, mu_at = 0.0, mu_bt = 0.0, br = 1.0, brt = 0.0;
   if (!gr) {
-    const double rpk = 1.0 / (q + b.m2), rph = 1.0 / (qh + b.m2);
+    const double rpk = 1.0 / (q + b.m2), rpa = 1.0 / (qa + b.m2);
+    const double rpb = GEO == 2 ? 1.0 / (qb + b.m2) : rpa;
     mu_k = 1.0 + q * rpk * (1.0 / 3.0);
-    mu_h = 1.0 + qh * rph * (1.0 / 3.0);
-    B = b.bfac * q * rpk * rph * rph;
+    mu_a = 1.0 + qa * rpa * (1.0 / 3.0);
+    mu_b = GEO == 2 ? 1.0 + qb * rpb * (1.0 / 3.0) : mu_a;
+    const double B = b.bfac * q * rpk * rpa * rpb;
     if (TAN) {
       mu_kt = q * b.m2 * rpk * rpk * (1.0 / 3.0);
-      mu_ht = qh * b.m2 * rph * rph * (1.0 / 3.0);
-      Bt = B * (-2.0 + b.m2 * rpk + 2.0 * b.m2 * rph);
+      mu_at = qa * b.m2 * rpa * rpa * (1.0 / 3.0);
+      mu_bt = GEO == 2 ? qb * b.m2 * rpb * rpb * (1.0 / 3.0) : mu_at;
+    }
+    if (g.gr2) {             // the GR D2 variant: mu = 1 in its chains and equation
+      mu_a = mu_b = 1.0;
+      mu_at = mu_bt = 0.0;
+    } else if (GEO == 0) {
+      br = mu_k - B;
+      if (TAN) brt = mu_kt - B * (-2.0 + b.m2 * rpk + 2.0 * b.m2 * rpa);
+    } else {
+      const double G = b.m2 * rpk;
+      const double lin = 2.0 * g.c2 * (mu_a + mu_b - 2.0) + (g.c / g.r) * (mu_a - 1.0) + g.r * g.c * (mu_b - 1.0);
+      br = (mu_k - g.c2 * (mu_a + mu_b - mu_k) + G * lin - B) * g.inv_s2;
+      if (TAN) {
+        const double Gt = -G * q * rpk;
+        const double lint = 2.0 * g.c2 * (mu_at + mu_bt) + (g.c / g.r) * mu_at + g.r * g.c * mu_bt;
+        const double Bt = B * (-2.0 + b.m2 * rpk + b.m2 * rpa + b.m2 * rpb);
+        brt = (mu_kt - g.c2 * (mu_at + mu_bt - mu_kt) + Gt * lin + G * lint - Bt) * g.inv_s2;
+      }
     }
   }
-  const double src = mu_k - B;
+  const double mu_2 = g.gr2 ? 1.0 : mu_k, mu_2t = g.gr2 ? 0.0 : mu_kt;
+  // D1(k1) D1(k2) of the source (Winther: D1(k)^2)
+  const double Pa = g.winther ? y[0] : y[L::A], Pb = g.winther ? y[0] : y[L::B];
   dy[0] = y[1];
   dy[1] = -b.damp * y[1] + b.cc * mu_k * y[0];
-  dy[2] = y[3];
-  dy[3] = -b.damp * y[3] + b.cc * mu_h * y[2];
-  dy[4] = y[5];
-  dy[5] = -b.damp * y[5] + b.cc * mu_k * y[4] - b.cc * y[2] * y[2] * src;
+  dy[L::A] = y[L::A + 1];
+  dy[L::A + 1] = -b.damp * y[L::A + 1] + b.cc * mu_a * y[L::A];
+  if (GEO == 2) {
+    dy[L::B] = y[L::B + 1];
+    dy[L::B + 1] = -b.damp * y[L::B + 1] + b.cc * mu_b * y[L::B];
+  }
+  dy[L::D2] = y[L::D2 + 1];
+  dy[L::D2 + 1] = -b.damp * y[L::D2 + 1] + b.cc * mu_2 * y[L::D2] - b.cc * Pa * Pb * br;
   if (TAN) {
-    dy[6] = y[7];
-    dy[7] = -b.damp * y[7] + b.cc * (mu_k * y[6] + mu_kt * y[0]);
-    dy[8] = y[9];
-    dy[9] = -b.damp * y[9] + b.cc * (mu_h * y[8] + mu_ht * y[2]);
-    dy[10] = y[11];
-    dy[11] = -b.damp * y[11] + b.cc * (mu_k * y[10] + mu_kt * y[4]) -
-             b.cc * (2.0 * y[2] * y[8] * src + y[2] * y[2] * (mu_kt - Bt));
+    const double Pat = g.winther ? y[T] : y[T + L::A], Pbt = g.winther ? y[T] : y[T + L::B];
+    dy[T] = y[T + 1];
+    dy[T + 1] = -b.damp * y[T + 1] + b.cc * (mu_k * y[T] + mu_kt * y[0]);
+    dy[T + L::A] = y[T + L::A + 1];
+    dy[T + L::A + 1] = -b.damp * y[T + L::A + 1] + b.cc * (mu_a * y[T + L::A] + mu_at * y[L::A]);
+    if (GEO == 2) {
+      dy[T + L::B] = y[T + L::B + 1];
+      dy[T + L::B + 1] = -b.damp * y[T + L::B + 1] + b.cc * (mu_b * y[T + L::B] + mu_bt * y[L::B]);
+    }
+    dy[T + L::D2] = y[T + L::D2 + 1];
+    dy[T + L::D2 + 1] = -b.damp * y[T + L::D2 + 1] + b.cc * (mu_2 * y[T + L::D2] + mu_2t * y[L::D2]) -
+                        b.cc * ((Pat * Pb + Pa * Pbt) * br + Pa * Pb * brt);
   }
 }
 
-template <int NY, bool TAN>
-__device__ void rk4(const Bg* tab, int n_steps, double h, double k2, bool gr, double* y) {
+template <int NY, bool TAN, int GEO>
+__device__ void rk4(const Bg* tab, int n_steps, double h, double k2, bool gr, const D2Geo& g, double* y) {
   double k1[NY], k2v[NY], k3[NY], k4[NY], t[NY];
   for (int i = 0; i < n_steps; ++i) {
     const Bg& b0 = tab[2 * i];
     const Bg& bm = tab[2 * i + 1];
     const Bg& b1 = tab[2 * i + 2];
-    rhs<TAN>(b0, k2, gr, y, k1);
+    rhs<TAN, GEO>(b0, k2, gr, g, y, k1);
 #pragma unroll
     for (int j = 0; j < NY; ++j) t[j] = y[j] + 0.5 * h * k1[j];
-    rhs<TAN>(bm, k2, gr, t, k2v);
+    rhs<TAN, GEO>(bm, k2, gr, g, t, k2v);
 #pragma unroll
     for (int j = 0; j < NY; ++j) t[j] = y[j] + 0.5 * h * k2v[j];
-    rhs<TAN>(bm, k2, gr, t, k3);
+    rhs<TAN, GEO>(bm, k2, gr, g, t, k3);
 #pragma unroll
     for (int j = 0; j < NY; ++j) t[j] = y[j] + h * k3[j];
-    rhs<TAN>(b1, k2, gr, t, k4);
+    rhs<TAN, GEO>(b1, k2, gr, g, t, k4);
 #pragma unroll
     for (int j = 0; j < NY; ++j) y[j] = y[j] + (h / 6.0) * (k1[j] + 2.0 * k2v[j] + 2.0 * k3[j] + k4[j]);
   }
@@ -192,20 +263,22 @@ __device__ void fill_bg(Bg* tab, const GrowthParams& p, double s0, double h, int
   }
 }
 
-template <bool TAN>
+template <bool TAN, int GEO>
 __global__ void k_growth(GrowthParams p, double* tab, float* tabf) {
+  using L = Layout<GEO>;
   extern __shared__ Bg s_bg[];
   if (p.fr0s) p.fr0_abs = p.fr0s[blockIdx.y];     // instance blockIdx.y
   tab += (size_t)blockIdx.y * 4 * p.nk;
   tabf += (size_t)blockIdx.y * 4 * p.nk;
   const bool gr = (p.fr0_abs == 0.0);
+  const D2Geo geo = d2_geo(p.d2_variant);
   const double s0 = log(p.a_init);
   // GR normalisation D1_GR(a = 1)
   const double hg = (0.0 - s0) / p.n_steps;
   fill_bg(s_bg, p, s0, hg, p.n_steps, true);
   __syncthreads();
   double g[6] = {p.a_init, p.a_init, p.a_init, p.a_init, 0.0, 0.0};
-  rk4<6, false>(s_bg, p.n_steps, hg, 1.0, true, g);
+  rk4<6, false, 0>(s_bg, p.n_steps, hg, 1.0, true, d2_geo(0), g);
   const double norm = g[0];
   __syncthreads();
   const double h = (log(p.a_out) - s0) / p.n_steps;
@@ -214,35 +287,45 @@ __global__ void k_growth(GrowthParams p, double* tab, float* tabf) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= p.nk) return;
   const double k = p.k_min * pow(p.k_max / p.k_min, (double)t / (double)(p.nk - 1));
-  constexpr int NY = TAN ? 12 : 6;
+  constexpr int NY = TAN ? 2 * L::NB : L::NB;
   double y[NY];
 #pragma unroll
   for (int j = 0; j < NY; ++j) y[j] = 0.0;
-  y[0] = y[1] = y[2] = y[3] = p.a_init;
-  y[4] = -3.0 / 7.0 * p.a_init * p.a_init;
-  y[5] = -6.0 / 7.0 * p.a_init * p.a_init;
-  rk4<NY, TAN>(s_bg, p.n_steps, h, k * k, gr, y);
+#pragma unroll
+  for (int j = 0; j < L::D2; ++j) y[j] = p.a_init;
+  y[L::D2] = -3.0 / 7.0 * p.a_init * p.a_init;
+  y[L::D2 + 1] = -6.0 / 7.0 * p.a_init * p.a_init;
+  rk4<NY, TAN, GEO>(s_bg, p.n_steps, h, k * k, gr, geo, y);
   const int nk = p.nk;
+  const int T = L::NB;
   tab[t] = y[0] / norm;
-  tab[nk + t] = y[4] / (norm * norm);
-  tab[2 * nk + t] = TAN ? y[6] / norm : 0.0;
-  tab[3 * nk + t] = TAN ? y[10] / (norm * norm) : 0.0;
+  tab[nk + t] = y[L::D2] / (norm * norm);
+  tab[2 * nk + t] = TAN ? y[T] / norm : 0.0;
+  tab[3 * nk + t] = TAN ? y[T + L::D2] / (norm * norm) : 0.0;
   tabf[t] = (float)(y[0] / norm);
-  tabf[nk + t] = (float)(y[4] / (norm * norm));
+  tabf[nk + t] = (float)(y[L::D2] / (norm * norm));
   tabf[2 * nk + t] = (float)tab[2 * nk + t];
   tabf[3 * nk + t] = (float)tab[3 * nk + t];
 }
 
 #ifndef LPT2_GROWTH_THREADS
-#define LPT2_GROWTH_THREADS 32   // k nodes per block: the RK4 chains are FP64-bound, so spread them over SMs
+#define LPT2_GROWTH_THREADS 32   // k nodes per block (measured best: the RK4 chains are FP64-latency bound)
 #endif
-cudaError_t launch_growth(const GrowthParams& p, double* tab, float* tabf, cudaStream_t s) {
+template <int GEO>
+static cudaError_t launch_growth_geo(const GrowthParams& p, double* tab, float* tabf, cudaStream_t s) {
   const int threads = LPT2_GROWTH_THREADS;
   const int blocks = (p.nk + threads - 1) / threads;
   const size_t smem = (size_t)(2 * p.n_steps + 1) * sizeof(Bg);
-  cudaFuncSetAttribute(k_growth<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  k_growth<true><<<dim3(blocks, p.n_inst > 0 ? p.n_inst : 1), threads, smem, s>>>(p, tab, tabf);
+  cudaFuncSetAttribute(k_growth<true, GEO>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  k_growth<true, GEO><<<dim3(blocks, p.n_inst > 0 ? p.n_inst : 1), threads, smem, s>>>(p, tab, tabf);
   return cudaGetLastError();
+}
+
+cudaError_t launch_growth(const GrowthParams& p, double* tab, float* tabf, cudaStream_t s) {
+  const D2Geo g = d2_geo(p.d2_variant);
+  if (g.r != 1.0) return launch_growth_geo<2>(p, tab, tabf, s);
+  if (g.c != 0.0) return launch_growth_geo<1>(p, tab, tabf, s);
+  return launch_growth_geo<0>(p, tab, tabf, s);
 }
 
 // ------------------------------------------------------------- mode tables

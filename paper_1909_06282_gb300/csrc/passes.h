@@ -255,6 +255,7 @@ struct GrowthParams {
   int nk, n_steps;
   int n_inst;            // tables for n_inst instances (grid y)
   const double* fr0s;    // device |fR0| per instance, or null for fr0_abs
+  int d2_variant;        // triangle configuration of D2 (include/lpt2.h LPT2_D2_*)
 };
 int cosmo_partial_blocks();
 cudaError_t launch_cosmo_setup(const GrowthParams&, double* partials, DevCosmo* out, cudaStream_t);

@@ -1,0 +1,66 @@
+"""GPU growth tables and displacements for the D2 triangle variants (Sec. 3 triangle
+comparison; LPT2_D2_* in include/lpt2.h) against the FP64 oracle.
+  growth tables (FP64)   1e-10 relative (same RK4 step count on both sides)
+  Psi1, Psi2             relative L2 <= 2e-5, max |delta Psi| <= 1e-4 cell
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+STEPS = 256
+
+
+@pytest.fixture(scope="module")
+def lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1909_06282_gb300 import build as B
+    B.build()
+    import paper_1909_06282_gb300 as L
+    return L
+
+
+@pytest.mark.parametrize("variant", range(7))
+@pytest.mark.parametrize("fr0,a_out", [(1e-4, 1.0), (1e-6, 0.5)])
+def test_variant_growth_tables_against_oracle(lib, variant, fr0, a_out):
+    from oracle import growth as gr
+    c = W.COSMO.replace(fr0_abs=fr0, d2_variant=variant)
+    plan = lib.Plan(W.Instance(32, 100.0, 1, c, a_out=a_out), n_steps=STEPS)
+    d1, d2, dd1, dd2 = [t.cpu().numpy() for t in lib.lpt2_growth_tables(plan)]
+    ref = gr.growth_tables(c, a_out, n_steps=STEPS, variant=variant)
+    np.testing.assert_allclose(d1, ref["D1"], rtol=1e-10)
+    np.testing.assert_allclose(d2, ref["D2"], rtol=1e-10)
+    assert np.max(np.abs(dd1 - ref["dD1"])) <= 1e-10 * (np.max(np.abs(ref["dD1"])) + 1e-300)
+    assert np.max(np.abs(dd2 - ref["dD2"])) <= 1e-10 * (np.max(np.abs(ref["dD2"])) + 1e-300)
+
+
+def test_variants_differ_where_mg_acts(lib):
+    """At large k the triangles give different D2 (the point of the comparison); at small
+    k all of them reduce to the same GR growth."""
+    tabs = []
+    for v in range(6):
+        c = W.COSMO.replace(fr0_abs=1e-4, d2_variant=v)
+        plan = lib.Plan(W.Instance(32, 100.0, 1, c), n_steps=STEPS)
+        tabs.append(lib.lpt2_growth_tables(plan)[1].cpu().numpy())
+    tabs = np.array(tabs)
+    assert np.all(np.abs(tabs[:, 0] / tabs[0, 0] - 1) < 1e-4)
+    assert np.all(np.abs(np.diff(tabs[:, -1])) > 1e-4 * np.abs(tabs[0, -1]))
+
+
+@pytest.mark.parametrize("variant", [1, 3, 5])
+def test_variant_displacements_against_oracle(lib, variant):
+    from oracle import lpt2
+    n, box = 32, 128.0
+    c = W.COSMO.replace(fr0_abs=1e-4, d2_variant=variant)
+    plan = lib.Plan(W.Instance(n, box, 2, c), n_steps=STEPS)
+    out = lib.lpt2_displace(plan, psi1=True, psi2=True, pos=False)
+    ref = lpt2.run(n, box, c, seed=2, n_steps=STEPS)
+    cell = box / n
+    for key in ("psi1", "psi2"):
+        got, want = out[key].cpu().numpy(), ref[key]
+        r = float(np.linalg.norm((got - want).ravel()) / np.linalg.norm(want.ravel()))
+        assert r <= 2e-5, (key, r)
+        assert float(np.max(np.abs(got - want))) / cell <= 1e-4
