@@ -194,6 +194,19 @@ int lpt2_displace_vjp(lpt2_plan_t plan, const float* noise, const float* g_pos,
                       const float* g_density, const double* g_pk, int n_shells, float* g_noise,
                       double* g_log_fr0);
 
+/* Refinements of the P(k) estimator that Sec. 4 does not apply (its P(k) is the raw CIC
+ * estimate of lpt2_cic_pk); the method of Sefusatti et al. 2016:
+ *   LPT2_PK_DECONVOLVE  divide |delta(k)|^2 by the CIC window squared, W = prod_i sinc^2(pi n_i/N)
+ *   LPT2_PK_INTERLACE   deposit a second grid of the particles shifted by +h/2 along every
+ *                       axis (h = L/N) and use delta(k) = [F1 + F2 exp(i pi (nx+ny+nz)/N)] / 2,
+ *                       which cancels the odd aliasing images; needs pos (not NULL)
+ * Arguments, layouts and shells as lpt2_cic_pk (density, when given, is the first grid's
+ * contrast); flags = 0 gives the lpt2_cic_pk result.  Needs the workspace; not captured in
+ * a graph.  LPT2_EINVAL for unknown flags or interlacing without positions. */
+enum { LPT2_PK_DECONVOLVE = 1, LPT2_PK_INTERLACE = 2 };
+int lpt2_cic_pk_est(lpt2_plan_t plan, const float* pos, float* density, double* pk, double* k_mean,
+                    int64_t* n_modes, int n_shells, unsigned flags);
+
 /* Full second-order source term and its ratio to GR (Sec. 3, Eqs. full, s1-s4; the
  * diagnostic behind the paper's source-term figure, from which the T1 triangle was chosen).
  * With delta1(k) = D1(k,a) delta0(k) (a = the plan's a_out), phi = delta1/k^2 and

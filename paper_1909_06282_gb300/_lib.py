@@ -86,6 +86,7 @@ def load_library():
         "lpt2_launch_count": (i64, [vp]),
         "lpt2_device_status": (i, [vp]),
         "lpt2_source_ratio": (i, [vp, vp, i, vp, vp, vp, vp, vp, vp, vp]),
+        "lpt2_cic_pk_est": (i, [vp, vp, vp, vp, vp, vp, i, C.c_uint]),
         "lpt2_timing": (i, [vp, i]),
         "lpt2_cic_pk_noalloc": (i, [i, d, vp, vp, vp, vp, vp, i, vp]),
         "lpt2_set_fr0": (i, [vp, d]),
@@ -198,6 +199,25 @@ def lpt2_workspace_size(plan: Plan) -> int:
 
 def lpt2_launch_count(plan: Plan) -> int:
     return int(load_library().lpt2_launch_count(plan.handle))
+
+
+PK_DECONVOLVE, PK_INTERLACE = 1, 2
+
+
+def lpt2_cic_pk_est(plan: Plan, pos=None, density=False, n_shells=32, deconvolve=False, interlace=False):
+    """lpt2_cic_pk with the CIC window deconvolution and / or interlacing refinements."""
+    n = plan.n
+    sh = (n_shells,) if plan.n_inst == 1 else (plan.n_inst, n_shells)
+    res = dict(pk=torch.empty(sh, dtype=torch.float64, device="cuda"),
+               k_mean=torch.empty(sh, dtype=torch.float64, device="cuda"),
+               n_modes=torch.empty(sh, dtype=torch.int64, device="cuda"))
+    if torch.is_tensor(density) or density:
+        dsh = (n, n, n) if plan.n_inst == 1 else (plan.cells,)
+        res["density"] = density if torch.is_tensor(density) else torch.empty(dsh, dtype=torch.float32, device="cuda")
+    flags = (PK_DECONVOLVE if deconvolve else 0) | (PK_INTERLACE if interlace else 0)
+    _check(load_library().lpt2_cic_pk_est(plan.handle, _ptr(pos), _ptr(res.get("density")), _ptr(res["pk"]),
+                                          _ptr(res["k_mean"]), _ptr(res["n_modes"]), n_shells, flags))
+    return res
 
 
 def lpt2_source_ratio(plan: Plan, noise=None, n_bins=32, spectra=False):

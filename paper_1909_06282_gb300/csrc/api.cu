@@ -804,6 +804,64 @@ int lpt2_cic_pk(lpt2_plan_t p, const float* pos, float* density, double* pk, dou
   return run_graph(p, 1, key, body);
 }
 
+// P(k) estimator refinements: CIC window deconvolution and interlacing (see the header).
+int lpt2_cic_pk_est(lpt2_plan_t p, const float* pos, float* density, double* pk, double* k_mean, int64_t* n_modes,
+                    int n_shells, unsigned flags) {
+  int rc = check_plan_ws(p);
+  if (rc) return rc;
+  if (!pk) return fail(LPT2_EINVAL, "pk must not be null");
+  if (n_shells < 1 || n_shells > kMaxShells) return fail(LPT2_EINVAL, "n_shells must be in [1, 256]");
+  if (flags & ~(unsigned)(LPT2_PK_DECONVOLVE | LPT2_PK_INTERLACE)) return fail(LPT2_EINVAL, "unknown flags");
+  const bool inter = flags & LPT2_PK_INTERLACE;
+  if (inter && !pos) return fail(LPT2_EINVAL, "interlacing needs the positions (pos must not be null)");
+  for (int gi = 0; gi < (int)p->groups.size(); ++gi) {
+    rc = ensure_geometry(p, gi, n_shells);
+    if (rc) return rc;
+  }
+  for (int gi = 0; gi < (int)p->groups.size(); ++gi) {
+    set_group(p, gi);
+    const Group& gr = p->groups[gi];
+    const int n = p->n;
+    const Geo g = make_geo(p);
+    const size_t cells = (size_t)n * n * n * p->cur_batch;
+    const float* gpos = pos ? pos + 3 * gr.off : nullptr;
+    float* rho = rho_group(p);
+    float2* A = slot(p, S_A);
+    if (gpos) {
+      LAUNCH(p, "fill0", 4.0 * V3(p), launch_fill0(rho, cells, p->stream));
+      CicArgs c{g, gpos, rho, 0.f};
+      LAUNCH(p, "cic", 20.0 * V3(p), launch_cic(c, p->stream));
+    }
+    if ((rc = forward_zy(p, Z_DENSITY, rho, A))) return rc;
+    if (density)
+      LAUNCH(p, "contrast", 8.0 * V3(p), launch_contrast(rho, density + gr.off, cells, p->stream));
+    float2* B = slot(p, S_Y0);
+    if (inter) {   // second grid: the particles shifted by +h/2 along every axis
+      float* rho2 = reinterpret_cast<float*>(slot(p, S_X0));
+      LAUNCH(p, "fill0", 4.0 * V3(p), launch_fill0(rho2, cells, p->stream));
+      CicArgs c{g, gpos, rho2, 0.5f};
+      LAUNCH(p, "cic", 20.0 * V3(p), launch_cic(c, p->stream));
+      if ((rc = forward_zy(p, Z_DENSITY, rho2, B))) return rc;
+    }
+    XArgs x{};
+    x.g = g;
+    x.tw = p->tw;
+    x.mode = inter ? X_PKI : X_PKP;
+    x.in = A;
+    x.in2[0] = B;
+    x.cosmo = p->cosmo_dev;
+    x.pk_part = pk_part(p);
+    x.n_shells = n_shells;
+    x.pk_deconv = (flags & LPT2_PK_DECONVOLVE) ? 1 : 0;
+    LAUNCH(p, "x_pk", (inter ? 8.0 : 4.0) * V3(p), x_pass(n, x, p->stream));
+    LAUNCH(p, "pk_finalize", 0.0,
+           launch_pk_finalize_p(pk_part(p), x_blocks(n), n_shells, gr.geo_k, gr.geo_n, pk + (size_t)gr.inst0 * n_shells,
+                                k_mean ? k_mean + (size_t)gr.inst0 * n_shells : nullptr,
+                                n_modes ? n_modes + (size_t)gr.inst0 * n_shells : nullptr, p->stream, p->cur_batch));
+  }
+  return LPT2_OK;
+}
+
 // ------------------------------------------------------------ full-source diagnostic
 int lpt2_source_ratio(lpt2_plan_t p, const float* noise, int n_bins, double* mean, double* sigma, int64_t* count,
                       double* t1, double* k_mean, void* s_mg, void* s_gr) {

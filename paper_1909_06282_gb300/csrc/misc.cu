@@ -65,9 +65,9 @@ __global__ void __launch_bounds__(CIC_THREADS, LPT2_CIC_MINB) k_cic(CicArgs a) {
   __syncthreads();
 #pragma unroll
   for (int k = 0; k < CIC_PER; ++k) {
-    const float ux = wrapN<N>(u[k][0] * a.g.inv_cell);
-    const float uy = wrapN<N>(u[k][1] * a.g.inv_cell);
-    const float uz = wrapN<N>(u[k][2] * a.g.inv_cell);
+    const float ux = wrapN<N>(u[k][0] * a.g.inv_cell + a.shift);
+    const float uy = wrapN<N>(u[k][1] * a.g.inv_cell + a.shift);
+    const float uz = wrapN<N>(u[k][2] * a.g.inv_cell + a.shift);
     const float fx = floorf(ux), fy = floorf(uy), fz = floorf(uz);
     // window cell of the lower corner: periodic integer offset from the origin
     const int rx = wrap_cell<N>((int)fx - ox), ry = wrap_cell<N>((int)fy - oy), rz = wrap_cell<N>((int)fz - oz);

@@ -678,6 +678,18 @@ __device__ __forceinline__ int shell_of(int mx, int my, int mz, int ns, int& n2)
   return b;
 }
 
+// Square of the CIC window W = prod_i sinc^2(pi m_i / N) of mode (mx, my, mz).
+__device__ __forceinline__ float sinc2_pi(int m, int n) {
+  if (m == 0) return 1.f;
+  const float x = (float)m / (float)n;
+  const float s = sinpif(x) / (3.14159265358979f * x);
+  return s * s;
+}
+__device__ __forceinline__ float cic_window2(int mx, int my, int mz, int n) {
+  const float w = sinc2_pi(mx, n) * sinc2_pi(my, n) * sinc2_pi(mz, n);
+  return w * w;
+}
+
 // Sum of a float over the warp (all lanes participate).
 __device__ __forceinline__ float warp_sum(float x) {
 #pragma unroll
@@ -705,7 +717,7 @@ __global__ void __launch_bounds__(PassCfg<N>::XT) k_x(XArgs a) {
   const bool ny_nyq = (ky == C::H);
   const float kf = a.g.kf;
   const size_t blk = ((size_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
-  if (MODE == X_PK || MODE == X_PKP) {
+  if (MODE == X_PK || MODE == X_PKP || MODE == X_PKI) {
     float* s_accf = reinterpret_cast<float*>(s_acc);
     for (int i = threadIdx.x; i < NWARP * (MODE == X_PK ? 5 : 2) * a.n_shells; i += blockDim.x) s_accf[i] = 0.f;
   } else if (MODE == X_ADJ_SOURCE) {
@@ -776,7 +788,24 @@ __global__ void __launch_bounds__(PassCfg<N>::XT) k_x(XArgs a) {
     }
   }
 
-  if (MODE == X_PK || MODE == X_PKP) {
+  if (MODE == X_PKI) {
+    // interlacing: the second grid (particles shifted by +h/2 on every axis) sees the
+    // density at x - h/2; its spectrum is realigned by exp(+i pi (mx + my + mz) / N) and
+    // the two are averaged, which cancels the odd aliasing images of the first grid
+    float2 u[C::RMAX];
+#pragma unroll
+    for (int r = 0; r < C::RMAX; ++r) u[r] = a.in2[0][base + (size_t)(elem<N>(t, r)) * stride];
+    fft<N, false>(u, t, sm, s_tw);
+#pragma unroll
+    for (int r = 0; r < C::RMAX; ++r) {
+      const int mx = mode_of(elem<N>(t, r), N);
+      float sn, cs;
+      sincospif((float)(mx + my + mz) / (float)N, &sn, &cs);
+      const float2 w = cmul(u[r], make_float2(cs, sn));
+      v[r] = make_float2(0.5f * (v[r].x + w.x), 0.5f * (v[r].y + w.y));
+    }
+  }
+  if (MODE == X_PK || MODE == X_PKP || MODE == X_PKI) {
     // P(k) shells.  Lanes of a warp see neighbouring modes, so they fall in few
     // shells: for each distinct shell in the warp the lanes of that shell are
     // summed and one lane adds the sum to this warp's own accumulator, a
@@ -794,7 +823,8 @@ __global__ void __launch_bounds__(PassCfg<N>::XT) k_x(XArgs a) {
       int n2;
       const int b = shell_of<N>(mode_of(kx, N), my, mz, ns, n2);
       const int wgt = (b < 0) ? 0 : ((mz == 0) ? 1 : 2);
-      const float pv = (v[r].x * v[r].x + v[r].y * v[r].y) * pnorm * (float)wgt;
+      float pv = (v[r].x * v[r].x + v[r].y * v[r].y) * pnorm * (float)wgt;
+      if (MODE != X_PK && a.pk_deconv && b >= 0) pv /= cic_window2(mode_of(kx, N), my, mz, N);
       const float kv = GEO ? kf * sqrtf((float)n2) * (float)wgt : 0.f;
       unsigned todo = __ballot_sync(0xffffffffu, b >= 0);
       while (todo) {
@@ -1009,7 +1039,7 @@ template <int N, int MODE> cudaError_t launch_x_m(const XArgs& a, cudaStream_t s
   using C = PassCfg<N>;
   LPT2_CHECK_BATCH(a);
   const int smem = C::XSMEM + (MODE == X_PK ? (C::XT / 32) * 5 * a.n_shells * 4
-                            : MODE == X_PKP ? (C::XT / 32) * 2 * a.n_shells * 4
+                            : (MODE == X_PKP || MODE == X_PKI) ? (C::XT / 32) * 2 * a.n_shells * 4
                                             : (MODE == X_ADJ_SOURCE ? (C::XT / 32) * 8 : 0));
   cudaFuncSetAttribute(k_x<N, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   k_x<N, MODE><<<dim3(C::H / C::W, N, a.g.batch), C::XT, smem, s>>>(a);
@@ -1022,6 +1052,7 @@ template <int N> cudaError_t launch_x_t(const XArgs& a, cudaStream_t s) {
     case X_PK: return launch_x_m<N, X_PK>(a, s);
     case X_PKP: return launch_x_m<N, X_PKP>(a, s);
     case X_MUL: return launch_x_m<N, X_MUL>(a, s);
+    case X_PKI: return launch_x_m<N, X_PKI>(a, s);
     case X_FWD: return launch_x_m<N, X_FWD>(a, s);
     case X_INV: return launch_x_m<N, X_INV>(a, s);
     case X_PHI: return launch_x_m<N, X_PHI>(a, s);

@@ -130,6 +130,7 @@ enum XMode {
   X_ADJ_DELTA = 8,  // transpose of X_DELTA: s(k) (h_Psi + h_phi), inverse x
   X_PKP = 9,        // fwd x, shell sums of |delta|^2 only (mode counts and mean |k| cached)
   X_MUL = 10,       // k-space multiplier (i k)^ord g(|k|) of the full-source diagnostic, inverse x
+  X_PKI = 11,       // as X_PKP for two grids (the second shifted by h/2) combined by interlacing
 };
 struct XArgs {
   Geo g;
@@ -160,6 +161,7 @@ struct XArgs {
   double* theta_part;     // X_ADJ_SOURCE: per-block partial of dL/dln|fR0|
   // X_MUL: multiplier (i kx)^ord[0] (i ky)^ord[1] (i kz)^ord[2] g(|k|) / N^3, g one of MulG,
   // with m^2(a), 1/a^2 and D1_GR(a) for mu(k) and Pi(k)
+  int pk_deconv;          // X_PKP, X_PKI: divide |delta|^2 by the CIC window squared
   int mul_g;
   int mul_ord[3];
   float mul_m2a, mul_inv_a2, mul_d1gr;
@@ -178,6 +180,8 @@ struct CicArgs {
   Geo g;
   const float* pos;      // [3][N^3]
   float* rho;
+  float shift;           // added to every coordinate (cells) before the deposit; 0.5 for the
+                         // interlaced grid of the P(k) estimator
 };
 
 // Per grid size launchers (return cudaError_t of the launch).
