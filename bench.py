@@ -208,6 +208,36 @@ def profile_run(args):
     print(json.dumps({"profile_run": True, "grid": n, "box": box, "launches": L.lpt2_launch_count(plan)}))
 
 
+def bench_large(args, L, W, torch):
+    """The large configuration: 1024^3 particles, L = 2048 Mpc/h (the same 2 Mpc/h cell),
+    |fR0| = 1e-5, forward step (positions, CIC, 32-shell P(k)) on its own plan and stream."""
+    n = 1024
+    st = torch.cuda.Stream()
+    with torch.cuda.stream(st):
+        plan = L.Plan(W.Instance(n, 2048.0, 1, W.COSMO.replace(fr0_abs=1e-5)), n_steps=1024, stream=st)
+        pos = torch.empty((3, n, n, n), dtype=torch.float32, device="cuda")
+
+        def step():
+            L.lpt2_displace(plan, psi1=False, psi2=False, pos=pos)
+            return L.lpt2_cic_pk(plan, pos=None, n_shells=WORKLOAD["n_shells"])
+
+        for _ in range(2):
+            step()
+        st.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        k = 3
+        e0.record(st)
+        for _ in range(k):
+            step()
+        e1.record(st)
+        st.synchronize()
+        ms = e0.elapsed_time(e1) / k
+    del plan, pos
+    torch.cuda.empty_cache()
+    return {"particles_per_step": n ** 3, "ms_per_step": ms, "value": n ** 3 / (ms / 1e3), "unit": "particles/s",
+            "what": "1024^3, L = 2048 Mpc/h, |fR0| = 1e-5: positions + CIC + 32-shell P(k), 3 timed steps"}
+
+
 def bench_batched(args, L, W, torch, stream):
     """96 instances (32 each of 96^3/384, 128^3/512, 192^3/768 Mpc/h; seeds 1..96; |fR0|
     log-uniform in [1e-6, 1e-4]): one graph-captured batched plan vs the same instances
@@ -454,6 +484,7 @@ def bench_ours(args):
                            "transforms), per-mode ratio binned in 32 shells, T1 curve"}
 
         batched = bench_batched(args, L, W, torch, stream) if not args.no_batched else None
+        large = bench_large(args, L, W, torch) if not args.no_large else None
 
         # the same path with cuFFT transforms and unfused element-wise kernels
         cuf = None
@@ -576,6 +607,7 @@ def bench_ours(args):
             "batched": batched,
             "cufft_pipeline": cuf,
             "source_diagnostic": src,
+            "large_1024": large,
             "fwd_vjp": {"value": parts / (ms_fv / 1e3), "unit": "particles/s", "ms_per_step": ms_fv,
                         "vjp_over_fwd": (ms_fv - ms) / ms,
                         "what": "forward + loss cotangents + lpt2_displace_vjp (noise and ln|fR0| gradients)"},
@@ -608,6 +640,7 @@ def main():
     ap.add_argument("--no-batched", action="store_true", help="skip the 96-instance batched measurement")
     ap.add_argument("--no-cufft", action="store_true", help="skip the cuFFT comparison pipeline")
     ap.add_argument("--no-source", action="store_true", help="skip the full-source diagnostic timing")
+    ap.add_argument("--no-large", action="store_true", help="skip the 1024^3 forward timing")
     ap.add_argument("--profile", action="store_true",
                     help="forward-only run for ncu (no timing); grid from --grid")
     ap.add_argument("--grid", type=int, default=WORKLOAD["n"],

@@ -66,9 +66,9 @@ def delta_k_modes(n: int, box: float, cosmo, noise: np.ndarray, modes) -> np.nda
         if _is_zeroed(n, m[None, :])[0]:
             continue
         ex, ey, ez = (np.exp(-2j * np.pi * m[c] * x / n) for c in range(3))
-        s = np.einsum("ijk,k->ij", noise, ez)          # sum over z
-        s = np.einsum("ij,j->i", s, ey)                # over y
-        out[j] = np.dot(s, ex)                         # over x
+        s = (noise @ ez.real) + 1j * (noise @ ez.imag)   # sum over z (real products: no complex copy)
+        s = s @ ey                                       # over y
+        out[j] = np.dot(s, ex)                           # over x
         out[j] *= _scale(n, box, cosmo, np.array(kf * np.sqrt(float(m @ m))))
     return out
 

@@ -1,0 +1,71 @@
+"""GPU at the large configuration: 1024^3 particles, L = 2048 Mpc/h (the same 2 Mpc/h
+cell as the throughput workload), |fR0| = 1e-5.  The oracle computes delta(k) at sampled
+modes by direct DFT sums over all 1.07e9 cells of the Philox field (oracle/sampled.py);
+properties that hold at any size check the rest.
+  delta(k) at sampled modes    |GPU - oracle| <= 2e-5 rms|delta|
+  CIC density                  sum of the contrast = 0 (1e-6 N^3), contrast >= -1
+  P(k)                         every shell filled; mode counts as the exact shell count
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+N, BOX, SEED = 1024, 2048.0, 5
+
+
+@pytest.fixture(scope="module")
+def run():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1909_06282_gb300 import build as B
+    B.build()
+    import paper_1909_06282_gb300 as L
+    c = W.COSMO.replace(fr0_abs=1e-5)
+    plan = L.Plan(W.Instance(N, BOX, SEED, c), n_steps=512)
+    out = L.lpt2_displace(plan, psi1=False, psi2=False, pos=False, dk=True)
+    pk = L.lpt2_cic_pk(plan, pos=None, density=True, n_shells=32)
+    torch.cuda.synchronize()
+    L.lpt2_device_status(plan)
+    rng = np.random.default_rng(1024)
+    modes = np.column_stack([rng.integers(-N // 2 + 1, N // 2, 4), rng.integers(-N // 2 + 1, N // 2, 4),
+                             rng.integers(0, N // 2, 4)])
+    modes = np.vstack([modes, [[1, 0, 0], [0, 3, 2]]])
+    dk = out["dk"]
+    got = np.array([complex(dk[m[0] % N, m[1] % N, m[2]].item()) for m in modes])
+    rms = float(dk.abs().pow(2).mean().sqrt())
+    d = pk["density"]
+    res = dict(modes=modes, got=got, rms=rms, dsum=float(d.double().sum()), dmin=float(d.min()),
+               n_modes=pk["n_modes"].cpu().numpy(), cosmo=c)
+    del out, pk, d, dk, plan
+    torch.cuda.empty_cache()
+    return res
+
+
+def test_1024_delta_k_at_sampled_modes(run):
+    from oracle import sampled
+    noise = sampled.noise_grid(N, SEED, chunk_rows=8)
+    want = sampled.delta_k_modes(N, BOX, run["cosmo"], noise, run["modes"])
+    err = np.abs(run["got"] - want)
+    assert err.max() <= 2e-5 * run["rms"], (err / run["rms"], run["modes"])
+
+
+def test_1024_density_and_shells(run):
+    assert abs(run["dsum"]) <= 1e-6 * N ** 3
+    assert run["dmin"] >= -1.0 - 1e-6
+    from oracle import lpt2
+    m = lpt2.mode_numbers(N).astype(np.int64)
+    # exact shell counts of the full grid, summed plane by plane (every mode once)
+    cnt = np.zeros(32, dtype=np.int64)
+    for mx in m:
+        n2 = mx * mx + m[:, None] ** 2 + m[None, :] ** 2
+        ok = (n2 > 0) & (4 * n2 < N * N)
+        M = 4 * 32 * 32 * n2[ok]
+        r = np.floor(np.sqrt(M.astype(np.float64))).astype(np.int64)
+        r = np.where((r + 1) ** 2 <= M, r + 1, r)
+        r = np.where(r * r > M, r - 1, r)
+        cnt += np.bincount(r // N, minlength=32)
+    np.testing.assert_array_equal(run["n_modes"], cnt)
