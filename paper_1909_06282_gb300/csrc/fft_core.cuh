@@ -130,23 +130,34 @@ template <int R, bool INV> struct Dft {   // even R: split into even and odd hal
 };
 
 // --------------------------------------------------------- shared accessors
-// Z layout: one pencil per row of N + N/16 complex (one pad slot per 16).
-struct SmemRow {
+// Z layout: one pencil per row of N + N/16 complex (one pad slot per 16).  The row is
+// private to its pencil; when the pencil's threads lie in one warp (WARP), the exchange
+// between stages needs only a warp barrier.
+template <bool WARP = false> struct SmemRowT {
   float2* base;
   __device__ __forceinline__ void st(int n, float2 v) const { base[n + (n >> 4)] = v; }
   __device__ __forceinline__ float2 ld(int n) const { return base[n + (n >> 4)]; }
+  __device__ __forceinline__ void sync() const {
+    if (WARP) __syncwarp();
+    else __syncthreads();
+  }
   static __host__ __device__ constexpr int words(int n) { return n + n / 16; }
 };
-// Column layout: W pencils interleaved, element (n, w) at n * W + w.
+using SmemRow = SmemRowT<false>;
+// z-pass pencils of N points lie in one warp when N / RMAX <= 32 threads hold one
+template <int N> inline constexpr bool kRowWarp = (N / Cfg<N>::RMAX) <= 32;
+// Column layout: W pencils interleaved, element (n, w) at n * W + w (a pencil spans warps).
 template <int W> struct SmemCol {
   float2* base;   // already offset by w
   __device__ __forceinline__ void st(int n, float2 v) const { base[n * W] = v; }
   __device__ __forceinline__ float2 ld(int n) const { return base[n * W]; }
+  __device__ __forceinline__ void sync() const { __syncthreads(); }
 };
 
 // ------------------------------------------------------------ stage engine
 // Runs all stages on v (in: x[t + r TPP], out: X[t + r TPP]).  Every thread of
-// the CTA must call this the same number of times (it contains __syncthreads).
+// the CTA (of the warp, for a warp-private row layout) must call this the same number
+// of times (it contains the layout's barriers).
 template <int N, bool INV, int S, class SM>
 __device__ __forceinline__ void fft_stages(float2 (&v)[Cfg<N>::RMAX], int t, const SM& sm,
                                            const float2* __restrict__ tw) {
@@ -177,7 +188,7 @@ __device__ __forceinline__ void fft_stages(float2 (&v)[Cfg<N>::RMAX], int t, con
 #pragma unroll
       for (int r = 0; r < R; ++r) sm.st(d + r * NS, v[q * R + r]);
     }
-    __syncthreads();
+    sm.sync();
     constexpr int R2 = Cfg<N>::rad(S + 1);
 #pragma unroll
     for (int q = 0; q < RMAX / R2; ++q) {
@@ -185,7 +196,7 @@ __device__ __forceinline__ void fft_stages(float2 (&v)[Cfg<N>::RMAX], int t, con
 #pragma unroll
       for (int r = 0; r < R2; ++r) v[q * R2 + r] = sm.ld(b + r * (N / R2));
     }
-    __syncthreads();
+    sm.sync();
     fft_stages<N, INV, S + 1, SM>(v, t, sm, tw);
   }
 }

@@ -52,15 +52,15 @@ __device__ __forceinline__ float2 dconj(float2 v, float k, int m) {
 // ===================================================================== z pass
 // Thread layout: tid = p * TPP + t (pencil pair p, lane t within the pencil).
 
-template <int N>
-__device__ __forceinline__ void z_store_pair(const float2 (&v)[Cfg<N>::RMAX], int t, const SmemRow& sm,
+template <int N, class SM>
+__device__ __forceinline__ void z_store_pair(const float2 (&v)[Cfg<N>::RMAX], int t, const SM& sm,
                                              float2* __restrict__ outa, float2* __restrict__ outb) {
   // v holds Z = FFT(fa + i fb) at n = elem(t, r). Split into the two real spectra;
   // outputs k = t + r TPP, r < RMAX/2, cover [0, N/2) once.
   constexpr int RMAX = Cfg<N>::RMAX, TPP = N / RMAX, H = N / 2;
 #pragma unroll
   for (int r = 0; r < RMAX; ++r) sm.st(elem<N>(t, r), v[r]);
-  __syncthreads();
+  sm.sync();
 #pragma unroll
   for (int r = 0; r < RMAX / 2; ++r) {
     const int k = t + r * TPP;                      // < H
@@ -73,14 +73,14 @@ __device__ __forceinline__ void z_store_pair(const float2 (&v)[Cfg<N>::RMAX], in
 }
 
 // As z_store_pair, each output multiplied by conj((i k_z)^m) (transpose of a z derivative).
-template <int N>
-__device__ __forceinline__ void z_store_pair_d(const float2 (&v)[Cfg<N>::RMAX], int t, const SmemRow& sm,
+template <int N, class SM>
+__device__ __forceinline__ void z_store_pair_d(const float2 (&v)[Cfg<N>::RMAX], int t, const SM& sm,
                                                float2* __restrict__ outa, float2* __restrict__ outb,
                                                float kf, int ma, int mb) {
   constexpr int RMAX = Cfg<N>::RMAX, TPP = N / RMAX;
 #pragma unroll
   for (int r = 0; r < RMAX; ++r) sm.st(elem<N>(t, r), v[r]);
-  __syncthreads();
+  sm.sync();
 #pragma unroll
   for (int r = 0; r < RMAX / 2; ++r) {
     const int k = t + r * TPP;
@@ -115,7 +115,7 @@ __global__ void __launch_bounds__(PassCfg<N>::ZT, LPT2_Z_MINB) k_z_r2c(ZR2CArgs 
   float2* s_tw = smem;
   load_twiddles(s_tw, a.tw, N);
   const int p = threadIdx.x / C::TPP, t = threadIdx.x % C::TPP;
-  const SmemRow sm{smem + N + p * SmemRow::words(N)};
+  const SmemRowT<kRowWarp<N>> sm{smem + N + p * SmemRow::words(N)};
   const int pair = blockIdx.x * C::ZP + p;
   const int rowa = 2 * pair, rowb = rowa + 1;
   const size_t n3 = (size_t)N * N * N;                 // instance blockIdx.z of the batch
@@ -154,7 +154,7 @@ __global__ void __launch_bounds__(PassCfg<N>::ZT, LPT2_Z_MINB) k_z_c2r(ZC2RArgs 
   float2* s_tw = smem;
   load_twiddles(s_tw, a.tw, N);
   const int p = threadIdx.x / C::TPP, t = threadIdx.x % C::TPP;
-  const SmemRow sm{smem + N + p * SmemRow::words(N)};
+  const SmemRowT<kRowWarp<N>> sm{smem + N + p * SmemRow::words(N)};
   const int pair = blockIdx.x * C::ZP + p;
   const int rowa = 2 * pair, rowb = rowa + 1;
   const size_t n3 = (size_t)N * N * N;                 // instance blockIdx.z of the batch
@@ -227,7 +227,7 @@ __global__ void __launch_bounds__(PassCfg<N>::ZT, LPT2_Z_MINB) k_z_source(ZSourc
   float2* s_tw = reinterpret_cast<float2*>(zs_raw + Q::BAR_OFF + 64);
   __shared__ int s_fail;
   const int p = threadIdx.x / C::TPP, t = threadIdx.x % C::TPP;
-  const SmemRow sm{s_tw + N + p * SmemRow::words(N)};
+  const SmemRowT<kRowWarp<N>> sm{s_tw + N + p * SmemRow::words(N)};
   const size_t zoff = blockIdx.z * ((size_t)N * N * N / 2);   // instance blockIdx.z
   const size_t tile = (size_t)blockIdx.x * Q::STAGE_F2;        // first float2 of the tile in a field
   if (threadIdx.x == 0) {
@@ -352,7 +352,7 @@ __global__ void __launch_bounds__(PassCfg<N>::ZT, LPT2_Z_MINB) k_z_final(ZFinalA
   float2* s_tw = reinterpret_cast<float2*>(zs_raw + Q::BAR_OFF + 64);
   __shared__ int s_fail;
   const int p = threadIdx.x / C::TPP, t = threadIdx.x % C::TPP;
-  const SmemRow sm{s_tw + N + p * SmemRow::words(N)};
+  const SmemRowT<kRowWarp<N>> sm{s_tw + N + p * SmemRow::words(N)};
   const size_t n3 = (size_t)N * N * N;
   const size_t zs = blockIdx.z * (n3 / 2), zr = blockIdx.z * n3;   // instance blockIdx.z
   const size_t tile = (size_t)blockIdx.x * Q::STAGE_F2;
@@ -477,7 +477,7 @@ __global__ void __launch_bounds__(PassCfg<N>::ZT, LPT2_Z_MINB) k_z_adj_final(ZAd
   float2* s_tw = smem;
   load_twiddles(s_tw, a.tw, N);
   const int p = threadIdx.x / C::TPP, t = threadIdx.x % C::TPP;
-  const SmemRow sm{smem + N + p * SmemRow::words(N)};
+  const SmemRowT<kRowWarp<N>> sm{smem + N + p * SmemRow::words(N)};
   const int pair = blockIdx.x * C::ZP + p;
   const int rows[2] = {2 * pair, 2 * pair + 1};
   const size_t n3 = (size_t)N * N * N;
@@ -504,13 +504,13 @@ __global__ void __launch_bounds__(PassCfg<N>::ZT, LPT2_Z_MINB) k_z_adj_final(ZAd
     fft<N, false>(v, t, sm, s_tw);
     z_store_pair_d<N>(v, t, sm, a.gx + (size_t)rows[h] * C::H, a.gy + (size_t)rows[h] * C::H, kf, 0, 0);
     if (h == 1) {
-      __syncthreads();   // partner reads of the store above are done before smem is reused
+      sm.sync();   // partner reads of the store above are done before the row is reused
 #pragma unroll
       for (int r = 0; r < C::RMAX; ++r) v[r] = make_float2(gza[r], gzb[r]);
       fft<N, false>(v, t, sm, s_tw);
       z_store_pair_d<N>(v, t, sm, a.gz + (size_t)rows[0] * C::H, a.gz + (size_t)rows[1] * C::H, kf, 1, 1);
     } else {
-      __syncthreads();
+      sm.sync();
     }
   }
 }
@@ -527,7 +527,7 @@ __global__ void __launch_bounds__(PassCfg<N>::ZT, LPT2_Z_MINB) k_z_adj_source(ZA
   float2* s_tw = smem;
   load_twiddles(s_tw, a.tw, N);
   const int p = threadIdx.x / C::TPP, t = threadIdx.x % C::TPP;
-  const SmemRow sm{smem + N + p * SmemRow::words(N)};
+  const SmemRowT<kRowWarp<N>> sm{smem + N + p * SmemRow::words(N)};
   const int pair = blockIdx.x * C::ZP + p;
   const int rows[2] = {2 * pair, 2 * pair + 1};
   const float kf = a.g.kf;
@@ -570,12 +570,12 @@ __global__ void __launch_bounds__(PassCfg<N>::ZT, LPT2_Z_MINB) k_z_adj_source(ZA
     }
     fft<N, false>(A, t, sm, s_tw);
     z_store_pair_d<N>(A, t, sm, a.out[0] + off, a.out[1] + off, kf, a.ord[0], a.ord[1]);
-    __syncthreads();
+    sm.sync();
 #pragma unroll
     for (int r = 0; r < C::RMAX; ++r) B[r] = s_park[r * C::ZT];
     fft<N, false>(B, t, sm, s_tw);
     z_store_pair_d<N>(B, t, sm, a.out[2] + off, a.out[3] + off, kf, a.ord[2], a.ord[3]);
-    __syncthreads();
+    sm.sync();
 #pragma unroll
     for (int r = 0; r < C::RMAX; ++r)
       A[r] = z_assemble<N>(a.in[4] + off, a.in[5] + off, elem<N>(t, r), kf, a.ord[4], a.ord[5]);
@@ -587,7 +587,7 @@ __global__ void __launch_bounds__(PassCfg<N>::ZT, LPT2_Z_MINB) k_z_adj_source(ZA
     }
     fft<N, false>(A, t, sm, s_tw);
     z_store_pair_d<N>(A, t, sm, a.out[4] + off, a.out[5] + off, kf, a.ord[4], a.ord[5]);
-    __syncthreads();
+    sm.sync();
   }
 }
 
