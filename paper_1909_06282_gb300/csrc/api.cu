@@ -1231,7 +1231,11 @@ int lpt2_displace_vjp(lpt2_plan_t p, const float* noise, const float* g_pos, con
   ZAdjSourceArgs za{};
   za.g = g;
   za.tw = p->tw;
-  za.hs = S[13];
+  // g_S in real space (the positions of slots 18-20 are dead after the CIC transpose)
+  float* gsr = reinterpret_cast<float*>(S[S_POS]);
+  ZC2RArgs zg{g, p->tw, S[13], gsr, nullptr};
+  LAUNCH(p, "z_c2r_gs", 8.0 * V3(p), z_c2r(n, zg, p->stream));
+  za.gs = gsr;
   const float2* phi[6] = {S[10], S[7], S[5], S[9], S[8], S[6]};   // xx yy zz xy xz yz
   const int zord[6] = {0, 0, 2, 0, 1, 1};
   float2* gout[6] = {S[0], S[2], S[3], S[4], S[11], S[14]};
@@ -1240,7 +1244,7 @@ int lpt2_displace_vjp(lpt2_plan_t p, const float* noise, const float* g_pos, con
     za.ord[i] = zord[i];
     za.out[i] = gout[i];
   }
-  LAUNCH(p, "z_adj_source", 56.0 * V3(p), z_adj_source(n, za, p->stream));
+  LAUNCH(p, "z_adj_source", 52.0 * V3(p), z_adj_source(n, za, p->stream));
   // 9. y transpose: x-order 0 <- zz (y0) + yz (y1) + yy (y2); x-order 1 <- xz (y0) + xy (y1); 2 <- xx
   YArgs y6{};
   y6.g = g;

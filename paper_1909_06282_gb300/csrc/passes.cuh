@@ -515,79 +515,88 @@ __global__ void __launch_bounds__(PassCfg<N>::ZT, LPT2_Z_MINB) k_z_adj_final(ZAd
   }
 }
 
-// Transpose of k_z_source: g_S from h_S (inverse z), the six phi_ij recomputed
-// (inverse z), g_phi_ij = g_S dS/dphi_ij, forward z with conj z-derivatives.
-// g_S of both rows and the (g_zz, g_xy) products are parked in shared memory while
-// other transforms run (each thread reads back only its own elements), so that no
-// more than one 16-value transform is live in registers.
+// Transpose of k_z_source.  g_S = dL/dS is given in real space (the inverse z of h_S,
+// one z_c2r pass); the six phi_ij are recomputed (inverse z) and
+//   dL/dphi_ii = g_S (Tr - phi_ii),  Tr = phi_xx + phi_yy + phi_zz,   dL/dphi_ij = -2 g_S phi_ij,
+// each transformed forward with conj z-derivatives.  Tiles and copy ring as k_z_source
+// (rows 2p, 2p + 1 of one field per complex pencil); the diagonal fields are read twice,
+// first for Tr (kept in registers for both rows), then for their cotangents.
 template <int N>
 __global__ void __launch_bounds__(PassCfg<N>::ZT, LPT2_Z_MINB) k_z_adj_source(ZAdjSourceArgs a) {
   using C = PassCfg<N>;
-  extern __shared__ float2 smem[];
-  float2* s_tw = smem;
-  load_twiddles(s_tw, a.tw, N);
+  using Q = ZSrcCfg<N>;
+  constexpr int NQ = 9;                         // xx, yy, zz (trace), then xx .. yz (cotangents)
+  extern __shared__ __align__(128) unsigned char zs_raw[];
+  float2* ring = reinterpret_cast<float2*>(zs_raw);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(zs_raw + Q::BAR_OFF);
+  float2* s_tw = reinterpret_cast<float2*>(zs_raw + Q::BAR_OFF + 64);
+  __shared__ int s_fail;
   const int p = threadIdx.x / C::TPP, t = threadIdx.x % C::TPP;
-  const SmemRowT<kRowWarp<N>> sm{smem + N + p * SmemRow::words(N)};
-  const int pair = blockIdx.x * C::ZP + p;
-  const int rows[2] = {2 * pair, 2 * pair + 1};
+  const SmemRowT<kRowWarp<N>> sm{s_tw + N + p * SmemRow::words(N)};
+  const size_t n3 = (size_t)N * N * N;
+  const size_t zs = blockIdx.z * (n3 / 2), zr = blockIdx.z * n3;   // instance blockIdx.z
+  const size_t tile = (size_t)blockIdx.x * Q::STAGE_F2;
+  const int row = blockIdx.x * Q::ROWS + 2 * p;                    // rows `row`, `row` + 1
   const float kf = a.g.kf;
-  float* s_gs = reinterpret_cast<float*>(smem + N + C::ZP * SmemRow::words(N)) + p * 2 * N;   // [2][N]
-  float2* s_park = smem + N + C::ZP * SmemRow::words(N) + C::ZP * N + threadIdx.x;   // [RMAX][ZT]
+  auto field = [](int q) { return q < 3 ? q : q - 3; };
+  if (threadIdx.x == 0) {
+    s_fail = 0;
+    for (int st = 0; st < Q::STAGES; ++st) mbar_init(&bar[st], 1);
+    mbar_init_fence();
+  }
   __syncthreads();
-  {
-    float2 v[C::RMAX];
-#pragma unroll
-    for (int r = 0; r < C::RMAX; ++r)
-      v[r] = z_assemble<N>(a.hs + (size_t)rows[0] * C::H, a.hs + (size_t)rows[1] * C::H, elem<N>(t, r),
-                           kf, 0, 0);
-    fft<N, true>(v, t, sm, s_tw);
-#pragma unroll
-    for (int r = 0; r < C::RMAX; ++r) {
-      s_gs[elem<N>(t, r)] = v[r].x;
-      s_gs[N + elem<N>(t, r)] = v[r].y;
+  if (threadIdx.x == 0) {
+    for (int q = 0; q < Q::STAGES; ++q) {
+      mbar_expect_tx(&bar[q], Q::STAGE_BYTES);
+      bulk_load(ring + q * Q::STAGE_F2, a.in[field(q)] + zs + tile, Q::STAGE_BYTES, &bar[q]);
     }
   }
+  load_twiddles(s_tw, a.tw, N);
+  float T0[C::RMAX], T1[C::RMAX];
 #pragma unroll
-  for (int h = 0; h < 2; ++h) {
-    const size_t off = (size_t)rows[h] * C::H;
-    float2 A[C::RMAX], B[C::RMAX];
+  for (int q = 0; q < NQ; ++q) {
+    const int st = q % Q::STAGES;
+    const int f = field(q);
+    const bool ok = mbar_wait(&bar[st], (q / Q::STAGES) & 1);
+    if (!ok) s_fail = 1;
+    float2 v[C::RMAX];
+    const float2* ra = ring + st * Q::STAGE_F2 + (2 * p) * C::H;
 #pragma unroll
     for (int r = 0; r < C::RMAX; ++r)
-      A[r] = z_assemble<N>(a.in[0] + off, a.in[1] + off, elem<N>(t, r), kf, a.ord[0], a.ord[1]);
-    fft<N, true>(A, t, sm, s_tw);                       // (phi_xx, phi_yy)
+      v[r] = ok ? z_assemble_smem<N>(ra, ra + C::H, elem<N>(t, r), kf, a.ord[f]) : make_float2(0.f, 0.f);
+    __syncthreads();   // stage consumed by every thread (and, at q = 0, twiddles visible)
+    if (s_fail) {
+      if (threadIdx.x == 0) {
+        for (int g = q; g < NQ && g < q + Q::STAGES; ++g) mbar_wait(&bar[g % Q::STAGES], (g / Q::STAGES) & 1);
+        report_device_error(a.g.err, LPT2_DEV_ETIMEOUT_ZADJSOURCE);
+      }
+      return;
+    }
+    if (threadIdx.x == 0 && q + Q::STAGES < NQ) {
+      mbar_expect_tx(&bar[st], Q::STAGE_BYTES);
+      bulk_load(ring + st * Q::STAGE_F2, a.in[field(q + Q::STAGES)] + zs + tile, Q::STAGE_BYTES, &bar[st]);
+    }
+    fft<N, true>(v, t, sm, s_tw);
+    if (q < 3) {   // trace of the Hessian for both rows
 #pragma unroll
-    for (int r = 0; r < C::RMAX; ++r) s_park[r * C::ZT] = A[r];
-#pragma unroll
-    for (int r = 0; r < C::RMAX; ++r)
-      B[r] = z_assemble<N>(a.in[2] + off, a.in[3] + off, elem<N>(t, r), kf, a.ord[2], a.ord[3]);
-    fft<N, true>(B, t, sm, s_tw);                       // (phi_zz, phi_xy)
+      for (int r = 0; r < C::RMAX; ++r) {
+        T0[r] = q == 0 ? v[r].x : T0[r] + v[r].x;
+        T1[r] = q == 0 ? v[r].y : T1[r] + v[r].y;
+      }
+      continue;
+    }
+    const float* g0 = a.gs + zr + (size_t)row * N;
 #pragma unroll
     for (int r = 0; r < C::RMAX; ++r) {
-      A[r] = s_park[r * C::ZT];
-      const float xx = A[r].x, yy = A[r].y, zz = B[r].x, xy = B[r].y, g = s_gs[h * N + elem<N>(t, r)];
-      A[r] = make_float2(g * (yy + zz), g * (xx + zz));            // dS/dphi_xx, dS/dphi_yy
-      s_park[r * C::ZT] = make_float2(g * (xx + yy), -2.f * g * xy); // dS/dphi_zz, dS/dphi_xy
+      const int iz = elem<N>(t, r);
+      const float ga = __ldg(g0 + iz), gb = __ldg(g0 + N + iz);
+      v[r] = f < 3 ? make_float2(ga * (T0[r] - v[r].x), gb * (T1[r] - v[r].y))
+                   : make_float2(-2.f * ga * v[r].x, -2.f * gb * v[r].y);
     }
-    fft<N, false>(A, t, sm, s_tw);
-    z_store_pair_d<N>(A, t, sm, a.out[0] + off, a.out[1] + off, kf, a.ord[0], a.ord[1]);
-    sm.sync();
-#pragma unroll
-    for (int r = 0; r < C::RMAX; ++r) B[r] = s_park[r * C::ZT];
-    fft<N, false>(B, t, sm, s_tw);
-    z_store_pair_d<N>(B, t, sm, a.out[2] + off, a.out[3] + off, kf, a.ord[2], a.ord[3]);
-    sm.sync();
-#pragma unroll
-    for (int r = 0; r < C::RMAX; ++r)
-      A[r] = z_assemble<N>(a.in[4] + off, a.in[5] + off, elem<N>(t, r), kf, a.ord[4], a.ord[5]);
-    fft<N, true>(A, t, sm, s_tw);                       // (phi_xz, phi_yz)
-#pragma unroll
-    for (int r = 0; r < C::RMAX; ++r) {
-      const float g = s_gs[h * N + elem<N>(t, r)];
-      A[r] = make_float2(-2.f * g * A[r].x, -2.f * g * A[r].y);
-    }
-    fft<N, false>(A, t, sm, s_tw);
-    z_store_pair_d<N>(A, t, sm, a.out[4] + off, a.out[5] + off, kf, a.ord[4], a.ord[5]);
-    sm.sync();
+    fft<N, false>(v, t, sm, s_tw);
+    float2* out = a.out[f] + zs + tile + (size_t)(2 * p) * C::H;
+    z_store_pair_d<N>(v, t, sm, out, out + C::H, kf, a.ord[f], a.ord[f]);
+    sm.sync();   // the row's reads above are done before the next transform reuses it
   }
 }
 
@@ -1016,10 +1025,10 @@ template <int N> cudaError_t launch_z_adj_final_t(const ZAdjFinalArgs& a, cudaSt
 }
 template <int N> cudaError_t launch_z_adj_source_t(const ZAdjSourceArgs& a, cudaStream_t s) {
   using C = PassCfg<N>;
-  // + g_S of both rows per pencil pair + one parked 16-value transform per thread
-  const int smem = C::ZSMEM + C::ZP * 2 * N * (int)sizeof(float) + C::ZT * C::RMAX * (int)sizeof(float2);
-  cudaFuncSetAttribute(k_z_adj_source<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  k_z_adj_source<N><<<N * N / 2 / C::ZP, C::ZT, smem, s>>>(a);
+  using Q = ZSrcCfg<N>;
+  LPT2_CHECK_BATCH(a);
+  cudaFuncSetAttribute(k_z_adj_source<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, Q::SMEM);
+  k_z_adj_source<N><<<dim3(N * N / Q::ROWS, 1, a.g.batch), C::ZT, Q::SMEM, s>>>(a);
   return cudaGetLastError();
 }
 template <int N, int KIND> cudaError_t launch_y_k(const YArgs& a, cudaStream_t s) {

@@ -40,7 +40,7 @@ struct Geo {
 };
 
 // Codes a kernel writes into Geo::err when a bounded wait gives up.
-enum { LPT2_DEV_ETIMEOUT_ZSOURCE = 1, LPT2_DEV_ETIMEOUT_ZFINAL = 2 };
+enum { LPT2_DEV_ETIMEOUT_ZSOURCE = 1, LPT2_DEV_ETIMEOUT_ZFINAL = 2, LPT2_DEV_ETIMEOUT_ZADJSOURCE = 3 };
 
 enum ZSrc { Z_NOISE = 0, Z_REAL = 1, Z_DENSITY = 2 };
 
@@ -76,7 +76,7 @@ struct ZAdjFinalArgs { // transpose of k_z_final: CIC gather of dL/drho, forward
 struct ZAdjSourceArgs {  // transpose of k_z_source
   Geo g;
   const float2* tw;
-  const float2* hs;      // h_S after the inverse x and y passes
+  const float* gs;       // g_S = dL/dS in real space [N^3] (inverse z of h_S)
   const float2* in[6];   // phi_xx, phi_yy, phi_zz, phi_xy, phi_xz, phi_yz (recomputed, after y)
   int ord[6];            // their z derivative orders
   float2* out[6];        // conj z-derivative of FFT_z(g_phi_ij), same order
