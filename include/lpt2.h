@@ -172,6 +172,31 @@ int lpt2_displace(lpt2_plan_t plan, const float* noise, float* psi1, float* psi2
 int lpt2_cic_pk(lpt2_plan_t plan, const float* pos, float* density, double* pk,
                 double* k_mean, int64_t* n_modes, int n_shells);
 
+/* lpt2_displace_host: the forward step (lpt2_displace to positions, then the CIC shell
+ * P(k) of lpt2_cic_pk: Sec. 2.1 Eq. second-ini, Sec. 2.4, Sec. 4) end to end from and to
+ * HOST memory, for n_real realisations of a single-instance plan.  For r in [0, n_real):
+ *   noise_h + r * noise_stride  host float[N^3] white noise, or noise_h NULL to draw the
+ *                               plan's Philox noise on the device (nothing uploaded)
+ *   pos_h + r * pos_stride      host float[3][N^3] positions in [0, L), or pos_h NULL
+ *   pk_h + r * pk_stride        host double[n_shells] shell P(k), or pk_h NULL
+ * Strides are in elements; a stride of 0 makes every realisation use the one buffer
+ * (every copy still happens, and the last realisation's result is what remains);
+ * otherwise a stride is at least one realisation's size.  The steps are pipelined:
+ * while realisation r computes on the plan's stream, the upload of r + 1 and the
+ * download of r - 1 (and of r's positions, during r's P(k)) run on two copy streams of
+ * the plan, through two device buffer sets that the plan allocates on the first call
+ * (4 N^3 floats each, kept until lpt2_plan_destroy).  Page-locked host buffers
+ * (cudaHostAlloc, cudaHostRegister) let the copies overlap the kernels; pageable ones
+ * give the same results with less overlap.  The call returns when every result is in
+ * host memory.  It synchronises, so it cannot be captured in a CUDA graph; the plan's
+ * lpt2_displace / lpt2_cic_pk graphs are not used.  Needs the workspace.
+ * Errors: LPT2_EUNSUPPORTED for a batched plan; LPT2_EINVAL for n_real < 1, n_shells
+ * outside [1, 256], pos_h and pk_h both NULL, or a too-small non-zero stride;
+ * LPT2_ENOMEM if the buffer sets cannot be allocated; LPT2_ECUDA from a copy or launch
+ * (the call still waits for everything it queued before returning). */
+int lpt2_displace_host(lpt2_plan_t plan, int n_real, const float* noise_h, int64_t noise_stride,
+                       float* pos_h, int64_t pos_stride, double* pk_h, int64_t pk_stride, int n_shells);
+
 /* lpt2_set_fr0: change |f_R0| of the plan and recompute its growth tables
  * (the FP64 RK4 kernel) on the plan's stream.  fr0_abs >= 0 (0 = GR). */
 int lpt2_set_fr0(lpt2_plan_t plan, double fr0_abs);

@@ -91,6 +91,7 @@ def load_library():
         "lpt2_cic_pk_noalloc": (i, [i, d, vp, vp, vp, vp, vp, i, vp]),
         "lpt2_set_fr0": (i, [vp, d]),
         "lpt2_displace_vjp": (i, [vp, vp, vp, vp, vp, i, vp, vp]),
+        "lpt2_displace_host": (i, [vp, i, vp, i64, vp, i64, vp, i64, i]),
         "lpt2_timing_report": (i, [vp, C.POINTER(_KernelStat), i, C.POINTER(C.c_int)]),
     }
     for name, (res, args) in sig.items():
@@ -316,6 +317,43 @@ def lpt2_cic_pk(plan: Plan, pos=None, density=False, n_shells=32):
                                       _ptr(res["pk"]), _ptr(res["k_mean"]), _ptr(res["n_modes"]),
                                       int(n_shells)))
     return res
+
+
+def _hptr(t):
+    if t is None:
+        return None
+    if t.is_cuda or not t.is_contiguous():
+        raise ValueError("expected a contiguous host (CPU) tensor")
+    return C.c_void_p(t.data_ptr())
+
+
+def lpt2_displace_host(plan: Plan, n_real=1, noise=None, pos=None, pk=None, n_shells=32):
+    """The forward step end to end from and to host memory, n_real realisations,
+    pipelined (copies overlap the kernels).  noise: CPU float32 (N, N, N) used by every
+    realisation, or (n_real, N, N, N); None draws the plan's Philox noise on the device.
+    pos: CPU float32 (3, N, N, N) that every realisation overwrites, or (n_real, 3, N, N, N);
+    pk: CPU float64 (n_shells,) or (n_real, n_shells).  Pinned tensors (pin_memory())
+    overlap best.  Returns (pos, pk) as given."""
+    n = plan.n
+    n3 = n ** 3
+
+    def stride(t, dtype, one, name):
+        if t is None:
+            return 0
+        if t.dtype != dtype or t.is_cuda:
+            raise ValueError(f"{name} must be a host {dtype} tensor")
+        if t.numel() == one:
+            return 0
+        if t.numel() == n_real * one:
+            return one
+        raise ValueError(f"{name} must hold one realisation or n_real of them")
+
+    ns_ = stride(noise, torch.float32, n3, "noise")
+    ps_ = stride(pos, torch.float32, 3 * n3, "pos")
+    ks_ = stride(pk, torch.float64, int(n_shells), "pk")
+    _check(load_library().lpt2_displace_host(plan.handle, int(n_real), _hptr(noise), ns_, _hptr(pos), ps_,
+                                             _hptr(pk), ks_, int(n_shells)))
+    return pos, pk
 
 
 def lpt2_fft_r2c(plan: Plan, x, out=None):

@@ -62,6 +62,18 @@ struct GraphCache {  // one captured launch sequence per entry point (LPT2_GRAPH
   int64_t launches;
 };
 
+// Device side of lpt2_displace_host: two buffer sets (noise, positions, P(k)) so that
+// the copies of one realisation overlap the kernels of the next, two copy streams and
+// the events that order them.
+struct HostIO {
+  float* noise_d[2] = {};
+  float* pos_d[2] = {};
+  double* pk_d[2] = {};
+  cudaStream_t s_in = nullptr, s_out = nullptr;
+  cudaEvent_t start = nullptr, up_done[2] = {}, in_used[2] = {}, pos_ready[2] = {}, comp_done[2] = {},
+              down_done[2] = {};
+};
+
 struct lpt2_plan_s {
   // current group (set by set_group): grid side, box, twiddles, batch
   int n;
@@ -102,6 +114,7 @@ struct lpt2_plan_s {
   cudaEvent_t* ev;            // 2 * kMaxRec events, created on first enable
   const char* rec_name[kMaxRec];
   double rec_bytes[kMaxRec];
+  HostIO* hio = nullptr;      // lpt2_displace_host buffers and streams, made on first use
 };
 
 namespace {
@@ -281,6 +294,48 @@ int forward_zy(lpt2_plan_t p, int src, const float* in, float2* out) {
 
 int displace_impl(lpt2_plan_t p, const float* noise, float* psi1, float* psi2, float* pos, void* dk,
                   float2* s_keep);
+
+void free_host_io(lpt2_plan_t p) {
+  HostIO* h = p->hio;
+  if (!h) return;
+  for (int b = 0; b < 2; ++b) {
+    cudaFree(h->noise_d[b]);
+    cudaFree(h->pos_d[b]);
+    cudaFree(h->pk_d[b]);
+    for (cudaEvent_t e : {h->up_done[b], h->in_used[b], h->pos_ready[b], h->comp_done[b], h->down_done[b]})
+      if (e) cudaEventDestroy(e);
+  }
+  if (h->start) cudaEventDestroy(h->start);
+  if (h->s_in) cudaStreamDestroy(h->s_in);
+  if (h->s_out) cudaStreamDestroy(h->s_out);
+  delete h;
+  p->hio = nullptr;
+}
+
+// Buffers, streams and events of lpt2_displace_host (single-instance plan, grid n).
+int ensure_host_io(lpt2_plan_t p) {
+  if (p->hio) return LPT2_OK;
+  p->hio = new HostIO();
+  HostIO* h = p->hio;
+  const size_t n3 = (size_t)p->n * p->n * p->n;
+  cudaError_t e = cudaSuccess;
+  for (int b = 0; b < 2 && e == cudaSuccess; ++b) {
+    e = cudaMalloc(&h->noise_d[b], n3 * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&h->pos_d[b], 3 * n3 * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&h->pk_d[b], kMaxShells * sizeof(double));
+    for (cudaEvent_t* ev : {&h->up_done[b], &h->in_used[b], &h->pos_ready[b], &h->comp_done[b], &h->down_done[b]})
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
+  }
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->start, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->s_in, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->s_out, cudaStreamNonBlocking);
+  if (e != cudaSuccess) {
+    free_host_io(p);
+    return fail(e == cudaErrorMemoryAllocation ? LPT2_ENOMEM : LPT2_ECUDA, "host-io buffers: %s",
+                cudaGetErrorString(e));
+  }
+  return LPT2_OK;
+}
 
 // Shell geometry (mode counts, sum of |k|) of group gi for n_shells shells; made
 // once per shell count, outside any graph capture, and reused by every P(k).
@@ -567,6 +622,7 @@ int lpt2_plan_destroy(lpt2_plan_t p) {
     for (int i = 0; i < 2 * kMaxRec; ++i) cudaEventDestroy(p->ev[i]);
     delete[] p->ev;
   }
+  free_host_io(p);
   delete p;
   return LPT2_OK;
 }
@@ -802,6 +858,93 @@ int lpt2_cic_pk(lpt2_plan_t p, const float* pos, float* density, double* pk, dou
   if (!p->use_graph) return body();
   const void* key[8] = {pos, density, pk, k_mean, n_modes, p->ws, (const void*)(intptr_t)n_shells, nullptr};
   return run_graph(p, 1, key, body);
+}
+
+// The forward step from and to host memory, pipelined over realisations (see the header).
+int lpt2_displace_host(lpt2_plan_t p, int n_real, const float* noise_h, int64_t noise_stride, float* pos_h,
+                       int64_t pos_stride, double* pk_h, int64_t pk_stride, int n_shells) {
+  int rc = check_plan_ws(p);
+  if (rc) return rc;
+  if (p->n_inst != 1) return fail(LPT2_EUNSUPPORTED, "lpt2_displace_host needs a single-instance plan");
+  if (n_real < 1) return fail(LPT2_EINVAL, "n_real must be >= 1");
+  if (!pos_h && !pk_h) return fail(LPT2_EINVAL, "pos_h and pk_h are both null: nothing to return");
+  if (n_shells < 1 || n_shells > kMaxShells) return fail(LPT2_EINVAL, "n_shells must be in [1, 256]");
+  set_group(p, 0);
+  const int64_t n3 = (int64_t)p->n * p->n * p->n;
+  if ((noise_stride != 0 && noise_stride < n3) || (pos_stride != 0 && pos_stride < 3 * n3) ||
+      (pk_stride != 0 && pk_stride < n_shells))
+    return fail(LPT2_EINVAL, "a stride must be 0 (one shared buffer) or at least one realisation's size");
+  rc = ensure_host_io(p);
+  if (rc) return rc;
+  rc = ensure_geometry(p, 0, n_shells);
+  if (rc) return rc;
+  HostIO* h = p->hio;
+  cudaStream_t cs = p->stream;
+  auto ck = [&](cudaError_t e, const char* what) -> int {
+    return e == cudaSuccess ? LPT2_OK : fail(LPT2_ECUDA, "lpt2_displace_host %s: %s", what, cudaGetErrorString(e));
+  };
+  auto body = [&]() -> int {
+    // copies start after the work already queued on the plan's stream; both buffer sets start free
+    int r0 = ck(cudaEventRecord(h->start, cs), "event");
+    if (!r0) r0 = ck(cudaStreamWaitEvent(h->s_in, h->start, 0), "event");
+    if (!r0) r0 = ck(cudaStreamWaitEvent(h->s_out, h->start, 0), "event");
+    for (int b = 0; b < 2 && !r0; ++b) {
+      r0 = ck(cudaEventRecord(h->down_done[b], h->s_out), "event");
+      if (!r0) r0 = ck(cudaEventRecord(h->in_used[b], cs), "event");
+    }
+    if (r0) return r0;
+    const size_t nb = (size_t)n3 * sizeof(float);
+    if (noise_h) {
+      int r1 = ck(cudaMemcpyAsync(h->noise_d[0], noise_h, nb, cudaMemcpyHostToDevice, h->s_in), "upload");
+      if (!r1) r1 = ck(cudaEventRecord(h->up_done[0], h->s_in), "event");
+      if (r1) return r1;
+    }
+    for (int r = 0; r < n_real; ++r) {
+      const int b = r & 1;
+      int e = LPT2_OK;
+      if (noise_h && r + 1 < n_real) {   // prefetch the next realisation's noise into the other set
+        e = ck(cudaStreamWaitEvent(h->s_in, h->in_used[1 - b], 0), "event");
+        if (!e) e = ck(cudaMemcpyAsync(h->noise_d[1 - b], noise_h + (size_t)(r + 1) * noise_stride, nb,
+                                       cudaMemcpyHostToDevice, h->s_in), "upload");
+        if (!e) e = ck(cudaEventRecord(h->up_done[1 - b], h->s_in), "event");
+      }
+      if (!e && noise_h) e = ck(cudaStreamWaitEvent(cs, h->up_done[b], 0), "event");
+      if (!e) e = ck(cudaStreamWaitEvent(cs, h->down_done[b], 0), "event");   // set b copied out
+      if (e) return e;
+      e = displace_impl(p, noise_h ? h->noise_d[b] : nullptr, nullptr, nullptr, h->pos_d[b], nullptr, nullptr);
+      if (e) return e;
+      e = ck(cudaEventRecord(h->in_used[b], cs), "event");
+      if (!e) e = ck(cudaEventRecord(h->pos_ready[b], cs), "event");
+      if (e) return e;
+      // P(k) of the density that lpt2_displace deposited
+      e = cic_pk_group(p, 0, nullptr, nullptr, h->pk_d[b], nullptr, nullptr, n_shells);
+      if (e) return e;
+      e = ck(cudaEventRecord(h->comp_done[b], cs), "event");
+      if (!e && pos_h) {
+        e = ck(cudaStreamWaitEvent(h->s_out, h->pos_ready[b], 0), "event");
+        if (!e) e = ck(cudaMemcpyAsync(pos_h + (size_t)r * pos_stride, h->pos_d[b], 3 * nb, cudaMemcpyDeviceToHost,
+                                       h->s_out), "download");
+      }
+      if (!e && pk_h) {
+        e = ck(cudaStreamWaitEvent(h->s_out, h->comp_done[b], 0), "event");
+        if (!e) e = ck(cudaMemcpyAsync(pk_h + (size_t)r * pk_stride, h->pk_d[b], n_shells * sizeof(double),
+                                       cudaMemcpyDeviceToHost, h->s_out), "download");
+      }
+      if (!e) e = ck(cudaEventRecord(h->down_done[b], h->s_out), "event");
+      if (e) return e;
+    }
+    return LPT2_OK;
+  };
+  const int rb = body();
+  // wait for everything queued (also after an error, so no copy is left in flight)
+  const cudaError_t e1 = cudaStreamSynchronize(h->s_out);
+  const cudaError_t e2 = cudaStreamSynchronize(h->s_in);
+  const cudaError_t e3 = cudaStreamSynchronize(cs);
+  if (rb) return rb;
+  if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess)
+    return fail(LPT2_ECUDA, "lpt2_displace_host: %s",
+                cudaGetErrorString(e1 != cudaSuccess ? e1 : (e2 != cudaSuccess ? e2 : e3)));
+  return LPT2_OK;
 }
 
 // P(k) estimator refinements: CIC window deconvolution and interlacing (see the header).
