@@ -458,6 +458,31 @@ def bench_ours(args):
         stream.synchronize()
         ms_fv = e4.elapsed_time(e5) / vsteps
 
+        # several output times from one realisation: z = 1, 0.5, 0 with the a-independent
+        # prefix (noise -> delta(k) -> phi_ij -> S) once, against three forward steps
+        multi = None
+        if not args.no_multi_a:
+            a_list = [0.5, 2.0 / 3.0, 1.0]
+            L.lpt2_set_outputs(plan, a_list)
+            pos_m = torch.empty((len(a_list), 3, n, n, n), dtype=torch.float32, device="cuda")
+            for _ in range(args.warmup):
+                L.lpt2_displace_outputs(plan, pos=pos_m, n_shells=WORKLOAD["n_shells"])
+            stream.synchronize()
+            e8, e9 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            msteps = max(1, args.steps // 2)
+            e8.record(stream)
+            for _ in range(msteps):
+                L.lpt2_displace_outputs(plan, pos=pos_m, n_shells=WORKLOAD["n_shells"])
+            e9.record(stream)
+            stream.synchronize()
+            ms_m = e8.elapsed_time(e9) / msteps
+            multi = {"a_out": a_list, "ms_per_call": ms_m, "ms_per_output": ms_m / len(a_list),
+                     "particles_per_s": len(a_list) * n ** 3 / (ms_m / 1e3),
+                     "vs_separate_steps": len(a_list) * ms / ms_m,
+                     "what": "lpt2_displace_outputs: positions + 32-shell P(k) at each a; the noise -> "
+                             "delta(k) -> phi_ij -> S(k) prefix runs once per call"}
+            del pos_m
+
         # full second-order source term / GR diagnostic (Sec. 3), same plan and noise
         src = None
         if not args.no_source:
@@ -568,6 +593,7 @@ def bench_ours(args):
             "batched": batched,
             "cufft_pipeline": cuf,
             "source_diagnostic": src,
+            "multi_a": multi,
             "large_1024": large,
             "fwd_vjp": {"value": parts / (ms_fv / 1e3), "unit": "particles/s", "ms_per_step": ms_fv,
                         "vjp_over_fwd": (ms_fv - ms) / ms,
@@ -602,6 +628,7 @@ def main():
     ap.add_argument("--no-cufft", action="store_true", help="skip the cuFFT comparison pipeline")
     ap.add_argument("--no-source", action="store_true", help="skip the full-source diagnostic timing")
     ap.add_argument("--no-large", action="store_true", help="skip the 1024^3 forward timing")
+    ap.add_argument("--no-multi-a", action="store_true", help="skip the several-output-times timing")
     ap.add_argument("--profile", action="store_true",
                     help="forward-only run for ncu (no timing); grid from --grid")
     ap.add_argument("--grid", type=int, default=WORKLOAD["n"],

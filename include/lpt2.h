@@ -197,6 +197,36 @@ int lpt2_cic_pk(lpt2_plan_t plan, const float* pos, float* density, double* pk,
 int lpt2_displace_host(lpt2_plan_t plan, int n_real, const float* noise_h, int64_t noise_stride,
                        float* pos_h, int64_t pos_stride, double* pk_h, int64_t pk_stride, int n_shells);
 
+/* Several output times from one realisation (the paper evaluates its fields at one
+ * scale factor at a time; Sec. 2.4 and Eq. second-ini give the time dependence, which
+ * enters only through D1(k, a) and D2(k, a)).  The six phi_ij, and so S, are built from
+ * the z = 0 linear field delta_0 whatever the output time, so noise -> delta(k) -> phi_ij
+ * -> S(k) is the same for every a and is computed once; only the multipliers
+ * -S D2(k, a)/k^2 + delta D1(k, a)/k^2 and what follows them (Psi, positions, CIC,
+ * P(k)) are repeated per a.
+ *
+ * lpt2_set_outputs: the output scale factors a_out[0 .. n_a-1] (host array, each in
+ * (a_init, 1], any order, 1 <= n_a <= 64) of a single-instance plan.  Computes and
+ * keeps, per a_j, the FP64 RK4 growth tables from a_init to a_j (the plan's k table,
+ * step count, cosmology and D2 variant) and the per-|n|^2 multiplier tables, on the
+ * plan's stream; lpt2_set_fr0 refreshes them.  Replaces an earlier list.
+ * Errors: LPT2_EUNSUPPORTED for a batched plan, LPT2_EINVAL for a bad list, LPT2_ENOMEM. */
+int lpt2_set_outputs(lpt2_plan_t plan, int n_a, const double* a_out);
+
+/* lpt2_displace_outputs: one realisation at every output scale factor of
+ * lpt2_set_outputs (device pointers):
+ *   noise    float[N^3] white noise, or NULL for the plan's Philox noise
+ *   pos      float[n_a][3][N^3] positions in [0, L) at a_j, or NULL
+ *   pk       double[n_a][n_shells] CIC shell P(k) at a_j (as lpt2_cic_pk)
+ *   k_mean, n_modes  double / int64 [n_shells] (the same for every a_j), or NULL
+ * Each a_j's outputs equal those of lpt2_displace + lpt2_cic_pk on a plan made with
+ * a_out = a_j (the same kernels in the same order after the shared prefix).  The CIC
+ * density left in the workspace is the last a_j's.  Not graph-captured.  Needs the
+ * workspace.  Errors: LPT2_EINVAL if no output list is set, pk is NULL or n_shells is
+ * outside [1, 256]; LPT2_EUNSUPPORTED for a batched plan. */
+int lpt2_displace_outputs(lpt2_plan_t plan, const float* noise, float* pos, double* pk,
+                          double* k_mean, int64_t* n_modes, int n_shells);
+
 /* lpt2_set_fr0: change |f_R0| of the plan and recompute its growth tables
  * (the FP64 RK4 kernel) on the plan's stream.  fr0_abs >= 0 (0 = GR). */
 int lpt2_set_fr0(lpt2_plan_t plan, double fr0_abs);

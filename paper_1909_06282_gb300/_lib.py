@@ -92,6 +92,8 @@ def load_library():
         "lpt2_set_fr0": (i, [vp, d]),
         "lpt2_displace_vjp": (i, [vp, vp, vp, vp, vp, i, vp, vp]),
         "lpt2_displace_host": (i, [vp, i, vp, i64, vp, i64, vp, i64, i]),
+        "lpt2_set_outputs": (i, [vp, i, C.POINTER(d)]),
+        "lpt2_displace_outputs": (i, [vp, vp, vp, vp, vp, vp, i]),
         "lpt2_timing_report": (i, [vp, C.POINTER(_KernelStat), i, C.POINTER(C.c_int)]),
     }
     for name, (res, args) in sig.items():
@@ -316,6 +318,37 @@ def lpt2_cic_pk(plan: Plan, pos=None, density=False, n_shells=32):
     _check(load_library().lpt2_cic_pk(plan.handle, _ptr(pos), _ptr(res.get("density")),
                                       _ptr(res["pk"]), _ptr(res["k_mean"]), _ptr(res["n_modes"]),
                                       int(n_shells)))
+    return res
+
+
+def lpt2_set_outputs(plan: Plan, a_out):
+    """Output scale factors for lpt2_displace_outputs (each in (a_init, 1])."""
+    a = [float(x) for x in a_out]
+    arr = (C.c_double * len(a))(*a)
+    _check(load_library().lpt2_set_outputs(plan.handle, len(a), arr))
+    plan.out_a = a
+
+
+def lpt2_displace_outputs(plan: Plan, noise=None, pos=True, n_shells=32):
+    """One realisation at every output scale factor of lpt2_set_outputs.  Returns a dict
+    with pk (n_a, n_shells), k_mean and n_modes (n_shells,), and pos (n_a, 3, N, N, N)
+    when pos is True or a tensor."""
+    n = plan.n
+    n_a = len(getattr(plan, "out_a", ()))
+    if n_a == 0:
+        raise ValueError("call lpt2_set_outputs first")
+    res = dict(pk=torch.empty((n_a, n_shells), dtype=torch.float64, device="cuda"),
+               k_mean=torch.empty(n_shells, dtype=torch.float64, device="cuda"),
+               n_modes=torch.empty(n_shells, dtype=torch.int64, device="cuda"))
+    if torch.is_tensor(pos) or pos:
+        res["pos"] = pos if torch.is_tensor(pos) else torch.empty((n_a, 3, n, n, n), dtype=torch.float32,
+                                                                   device="cuda")
+        if res["pos"].dtype != torch.float32 or res["pos"].numel() != n_a * 3 * n ** 3:
+            raise ValueError("pos must be float32 with n_a * 3 N^3 elements")
+    if noise is not None and (noise.dtype != torch.float32 or noise.numel() != n ** 3):
+        raise ValueError("noise must be float32 with N^3 elements")
+    _check(load_library().lpt2_displace_outputs(plan.handle, _ptr(noise), _ptr(res.get("pos")), _ptr(res["pk"]),
+                                                _ptr(res["k_mean"]), _ptr(res["n_modes"]), int(n_shells)))
     return res
 
 

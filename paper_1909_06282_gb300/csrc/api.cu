@@ -36,6 +36,7 @@ bool supported_n(int n) {
 // 0-16 serve the forward map; 17-20 hold what the adjoint keeps of it.
 enum Slot { S_A = 0, S_DELTA = 1, S_X0 = 2, S_Y0 = 7, S_RHO = 16, S_SHAT = 17, S_POS = 18, N_SLOTS = 21 };
 constexpr int kMaxShells = 256;
+constexpr int kMaxOutputs = 64;   // output scale factors per plan (lpt2_set_outputs)
 constexpr int kMaxRec = 4096;
 
 }  // namespace
@@ -115,6 +116,14 @@ struct lpt2_plan_s {
   const char* rec_name[kMaxRec];
   double rec_bytes[kMaxRec];
   HostIO* hio = nullptr;      // lpt2_displace_host buffers and streams, made on first use
+  // output scale factors of lpt2_displace_outputs (lpt2_set_outputs): per a_j the growth
+  // tables [4][nk] (FP64, FP32) and the per-|n|^2 multiplier tables of the plan's grid
+  int n_out_a = 0;
+  std::vector<double> out_a;
+  double* tab_a = nullptr;
+  float* tabf_a = nullptr;
+  float4* mt0_a = nullptr;
+  float2* mt1_a = nullptr;
 };
 
 namespace {
@@ -295,6 +304,19 @@ int forward_zy(lpt2_plan_t p, int src, const float* in, float2* out) {
 int displace_impl(lpt2_plan_t p, const float* noise, float* psi1, float* psi2, float* pos, void* dk,
                   float2* s_keep);
 
+void free_outputs(lpt2_plan_t p) {
+  cudaFree(p->tab_a);
+  cudaFree(p->tabf_a);
+  cudaFree(p->mt0_a);
+  cudaFree(p->mt1_a);
+  p->tab_a = nullptr;
+  p->tabf_a = nullptr;
+  p->mt0_a = nullptr;
+  p->mt1_a = nullptr;
+  p->n_out_a = 0;
+  p->out_a.clear();
+}
+
 void free_host_io(lpt2_plan_t p) {
   HostIO* h = p->hio;
   if (!h) return;
@@ -352,12 +374,12 @@ int ensure_geometry(lpt2_plan_t p, int gi, int n_shells) {
 
 // CIC (when positions are given) and P(k) of the current group (geometry made).
 int cic_pk_group(lpt2_plan_t p, int gi, const float* pos, float* density, double* pk, double* k_mean,
-                 int64_t* n_modes, int n_shells) {
+                 int64_t* n_modes, int n_shells, float2* spec = nullptr) {
   const int n = p->n;
   const Geo g = make_geo(p);
   const size_t cells = (size_t)n * n * n * p->cur_batch;
   float* rho = rho_group(p);
-  float2* A = slot(p, S_A);
+  float2* A = spec ? spec : slot(p, S_A);   // density spectrum scratch
   if (pos) {
     LAUNCH(p, "fill0", 4.0 * V3(p), launch_fill0(rho, cells, p->stream));
     CicArgs c{g, pos, rho};
@@ -424,13 +446,27 @@ int run_graph(lpt2_plan_t p, int slot_i, const void* const key[8], F body) {
   return LPT2_OK;
 }
 
+// Growth and multiplier tables of every output scale factor (single-instance plan).
+int run_output_growth(lpt2_plan_t p) {
+  const size_t len = (size_t)mode_table_len(p->groups[0].n), nk4 = (size_t)4 * p->nk;
+  GrowthParams gp = growth_params(p);
+  for (int j = 0; j < p->n_out_a; ++j) {
+    gp.a_out = p->out_a[j];
+    LAUNCH(p, "growth", 0.0, launch_growth(gp, p->tab_a + j * nk4, p->tabf_a + j * nk4, p->stream));
+    LAUNCH(p, "mode_tables", 0.0,
+           launch_mode_tables(gp, p->cosmo_dev, p->tab_a + j * nk4, 0, 1, p->groups[0].n, p->groups[0].box,
+                              p->mt0_a + j * len, p->mt1_a + j * len, p->stream));
+  }
+  return LPT2_OK;
+}
+
 int run_growth(lpt2_plan_t p) {
   const GrowthParams gp = growth_params(p);
   LAUNCH(p, "growth", 0.0, launch_growth(gp, p->tab, p->tabf, p->stream));
   for (const Group& g : p->groups)
     LAUNCH(p, "mode_tables", 0.0,
            launch_mode_tables(gp, p->cosmo_dev, p->tab, g.inst0, g.count, g.n, g.box, g.mt0, g.mt1, p->stream));
-  return LPT2_OK;
+  return p->n_out_a > 0 ? run_output_growth(p) : LPT2_OK;   // |fR0| changed: output tables too
 }
 
 }  // namespace
@@ -623,6 +659,7 @@ int lpt2_plan_destroy(lpt2_plan_t p) {
     delete[] p->ev;
   }
   free_host_io(p);
+  free_outputs(p);
   delete p;
   return LPT2_OK;
 }
@@ -700,32 +737,41 @@ int lpt2_displace(lpt2_plan_t p, const float* noise, float* psi1, float* psi2, f
 namespace {
 
 // The forward map; s_keep (k space, may be null) receives S(k) for the adjoint.
-int displace_impl(lpt2_plan_t p, const float* noise, float* psi1, float* psi2, float* pos, void* dk,
-                  float2* s_keep) {
-  int rc = 0;
-  const int n = p->n;
-  const Geo g = make_geo(p);
-  const bool split = psi1 || psi2;
-  float2* A = slot(p, S_A);
-  float2* D = slot(p, S_DELTA);
+// Slots of the forward path: A (S_A) carries the noise / S spectrum, D (S_DELTA) delta(k),
+// X[0..4] the x-pass outputs, Y[0..8] the y-pass outputs.
+struct FwdSlots {
+  float2* A;
+  float2* D;
   float2* X[5];
   float2* Y[9];
-  for (int i = 0; i < 5; ++i) X[i] = slot(p, S_X0 + i);
-  for (int i = 0; i < 9; ++i) Y[i] = slot(p, S_Y0 + i);
-  float* rho = rho_group(p);
-  const size_t cells = (size_t)n * n * n * p->cur_batch;   // real elements of the group
+};
 
+FwdSlots fwd_slots(lpt2_plan_t p) {
+  FwdSlots f;
+  f.A = slot(p, S_A);
+  f.D = slot(p, S_DELTA);
+  for (int i = 0; i < 5; ++i) f.X[i] = slot(p, S_X0 + i);
+  for (int i = 0; i < 9; ++i) f.Y[i] = slot(p, S_Y0 + i);
+  return f;
+}
+
+// Steps that do not depend on the output scale factor: noise -> delta(k) (slot D) and
+// the phi potentials (+ Psi1 when split), the six phi_ij, the source term S and its z and
+// y forward transforms (slot A).
+int displace_prefix(lpt2_plan_t p, const FwdSlots& f, const float* noise, bool split) {
+  const int n = p->n;
+  const Geo g = make_geo(p);
   // 1. delta(k): noise -> z, y passes; x pass with sqrt(P) and the phi / Psi1 potentials
-  rc = forward_zy(p, noise ? Z_REAL : Z_NOISE, noise, A);
+  int rc = forward_zy(p, noise ? Z_REAL : Z_NOISE, noise, f.A);
   if (rc) return rc;
   XArgs x{};
   x.g = g;
   x.tw = p->tw;
   x.mode = X_DELTA;
   x.split = split;
-  x.in = A;
-  x.delta_out = D;
-  for (int i = 0; i < 5; ++i) x.out[i] = X[i];
+  x.in = f.A;
+  x.delta_out = f.D;
+  for (int i = 0; i < 5; ++i) x.out[i] = f.X[i];
   x.cosmo = p->cosmo_dev;
   x.mt0 = p->mt0;
   x.mt1 = p->mt1;
@@ -741,12 +787,12 @@ int displace_impl(lpt2_plan_t p, const float* noise, float* psi1, float* psi2, f
   y.tw = p->tw;
   y.inverse = 1;
   y.job.n_in = split ? 5 : 3;
-  for (int i = 0; i < 5; ++i) y.job.in[i] = X[i];
+  for (int i = 0; i < 5; ++i) y.job.in[i] = f.X[i];
   const int src[9] = {0, 0, 0, 1, 1, 2, 3, 3, 4};
   const int ord[9] = {0, 1, 2, 0, 1, 0, 0, 1, 0};
   y.job.n_out = split ? 9 : 6;
   for (int o = 0; o < 9; ++o) {
-    y.job.out[o] = Y[o];
+    y.job.out[o] = f.Y[o];
     y.job.src[o] = src[o];
     y.job.ord[o] = ord[o];
   }
@@ -756,13 +802,13 @@ int displace_impl(lpt2_plan_t p, const float* noise, float* psi1, float* psi2, f
   ZSourceArgs zs{};
   zs.g = g;
   zs.tw = p->tw;
-  const float2* phi[6] = {Y[5], Y[2], Y[0], Y[4], Y[3], Y[1]};   // xx yy zz xy xz yz
+  const float2* phi[6] = {f.Y[5], f.Y[2], f.Y[0], f.Y[4], f.Y[3], f.Y[1]};   // xx yy zz xy xz yz
   const int zord[6] = {0, 0, 2, 0, 1, 1};
   for (int i = 0; i < 6; ++i) {
     zs.in[i] = phi[i];
     zs.ord[i] = zord[i];
   }
-  zs.out = A;
+  zs.out = f.A;
   LAUNCH(p, "z_source", 28.0 * V3(p), z_source(n, zs, p->stream));
   YArgs yf{};
   yf.g = g;
@@ -770,19 +816,41 @@ int displace_impl(lpt2_plan_t p, const float* noise, float* psi1, float* psi2, f
   yf.inverse = 0;
   yf.job.n_in = 1;
   yf.job.n_out = 1;
-  yf.job.in[0] = A;
-  yf.job.out[0] = A;
+  yf.job.in[0] = f.A;
+  yf.job.out[0] = f.A;
   LAUNCH(p, "y_fwd", 8.0 * V3(p), y_pass(n, yf, p->stream));
+  return LPT2_OK;
+}
+
+// Steps of one output scale factor, whose D1(k, a), D2(k, a) enter through the
+// multiplier tables mt0 / mt1 and the growth tables tabf: S(k) -> phi2 (+ phi1 D1),
+// Psi, positions, CIC density (slots A and D are read, not written).
+int displace_suffix(lpt2_plan_t p, const FwdSlots& f, bool split, float* psi1, float* psi2, float* pos,
+                    float2* s_keep, const float4* mt0, const float2* mt1, const float* tabf) {
+  const int n = p->n;
+  const Geo g = make_geo(p);
+  float* rho = rho_group(p);
+  const size_t cells = (size_t)n * n * n * p->cur_batch;   // real elements of the group
 
   // 4. x pass: S(k) -> phi2 = -S D2/k^2 (+ D1 delta/k^2 when not split), x inverse
-  XArgs xs = x;
+  XArgs xs{};
+  xs.g = g;
+  xs.tw = p->tw;
   xs.mode = X_SOURCE;
-  xs.in = A;
+  xs.split = split;
+  xs.in = f.A;
   xs.s_out = s_keep;
   xs.delta_out = nullptr;
-  xs.delta_in = D;
-  xs.out[0] = X[0];
-  xs.out[1] = X[1];
+  xs.delta_in = f.D;
+  xs.out[0] = f.X[0];
+  xs.out[1] = f.X[1];
+  xs.cosmo = p->cosmo_dev;
+  xs.mt0 = mt0;
+  xs.mt1 = mt1;
+  xs.d1f = tabf;
+  xs.d2f = tabf + p->nk;
+  xs.t1f = tabf + 2 * p->nk;
+  xs.t2f = tabf + 3 * p->nk;
   LAUNCH(p, "x_source", (split ? 12.0 : 16.0) * V3(p), x_pass(n, xs, p->stream));
 
   // 5. y inverse: (x0 y0), (x0 y1), (x1 y0)
@@ -791,12 +859,12 @@ int displace_impl(lpt2_plan_t p, const float* noise, float* psi1, float* psi2, f
   y2.tw = p->tw;
   y2.inverse = 1;
   y2.job.n_in = 2;
-  y2.job.in[0] = X[0];
-  y2.job.in[1] = X[1];
+  y2.job.in[0] = f.X[0];
+  y2.job.in[1] = f.X[1];
   y2.job.n_out = 3;
   const int src2[3] = {0, 0, 1}, ord2[3] = {0, 1, 0};
   for (int o = 0; o < 3; ++o) {
-    y2.job.out[o] = Y[o];
+    y2.job.out[o] = f.Y[o];
     y2.job.src[o] = src2[o];
     y2.job.ord[o] = ord2[o];
   }
@@ -809,22 +877,34 @@ int displace_impl(lpt2_plan_t p, const float* noise, float* psi1, float* psi2, f
   zf.tw = p->tw;
   zf.split = split;
   for (int i = 0; i < 3; ++i) {
-    zf.a[i] = split ? Y[6 + i] : Y[i];
-    zf.b[i] = Y[i];
+    zf.a[i] = split ? f.Y[6 + i] : f.Y[i];
+    zf.b[i] = f.Y[i];
   }
   zf.psi1 = psi1;
   zf.psi2 = psi2;
   // The CIC deposit runs as its own kernel at full occupancy (atomic throughput
   // needs many warps in flight): z_final writes the positions (to the caller's
   // array, or to dead workspace slots 2-4) and k_cic reads them back.
-  float* posw = pos ? pos : reinterpret_cast<float*>(X[0]);
+  float* posw = pos ? pos : reinterpret_cast<float*>(f.X[0]);
   zf.pos = posw;
   LAUNCH(p, "z_final", ((split ? 24.0 : 12.0) + 12.0 + (psi1 ? 12.0 : 0.0) + (psi2 ? 12.0 : 0.0)) * V3(p),
          z_final(n, zf, p->stream));
   CicArgs ca{g, posw, rho};
   LAUNCH(p, "cic", 20.0 * V3(p), launch_cic(ca, p->stream));
+  return LPT2_OK;
+}
+
+int displace_impl(lpt2_plan_t p, const float* noise, float* psi1, float* psi2, float* pos, void* dk,
+                  float2* s_keep) {
+  const bool split = psi1 || psi2;
+  const FwdSlots f = fwd_slots(p);
+  int rc = displace_prefix(p, f, noise, split);
+  if (rc) return rc;
+  rc = displace_suffix(p, f, split, psi1, psi2, pos, s_keep, p->mt0, p->mt1, p->tabf);
+  if (rc) return rc;
   if (dk) {
-    cudaError_t e = cudaMemcpyAsync(dk, D, cells * sizeof(float), cudaMemcpyDeviceToDevice, p->stream);
+    const size_t cells = (size_t)p->n * p->n * p->n * p->cur_batch;
+    cudaError_t e = cudaMemcpyAsync(dk, f.D, cells * sizeof(float), cudaMemcpyDeviceToDevice, p->stream);
     if (e != cudaSuccess) return fail(LPT2_ECUDA, "dk copy: %s", cudaGetErrorString(e));
   }
   return LPT2_OK;
@@ -944,6 +1024,61 @@ int lpt2_displace_host(lpt2_plan_t p, int n_real, const float* noise_h, int64_t 
   if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess)
     return fail(LPT2_ECUDA, "lpt2_displace_host: %s",
                 cudaGetErrorString(e1 != cudaSuccess ? e1 : (e2 != cudaSuccess ? e2 : e3)));
+  return LPT2_OK;
+}
+
+// Output scale factors of lpt2_displace_outputs: growth and multiplier tables per a_j.
+int lpt2_set_outputs(lpt2_plan_t p, int n_a, const double* a_out) {
+  if (!p) return fail(LPT2_EINVAL, "null plan");
+  if (p->n_inst != 1) return fail(LPT2_EUNSUPPORTED, "lpt2_set_outputs needs a single-instance plan");
+  if (n_a < 1 || n_a > kMaxOutputs || !a_out) return fail(LPT2_EINVAL, "need 1 <= n_a <= %d and an a_out array", kMaxOutputs);
+  for (int j = 0; j < n_a; ++j)
+    if (!(a_out[j] > p->cosmo.a_init) || !(a_out[j] <= 1.0))
+      return fail(LPT2_EINVAL, "a_out[%d] = %g: need a_init < a_out <= 1", j, a_out[j]);
+  set_group(p, 0);
+  free_outputs(p);
+  const size_t len = (size_t)mode_table_len(p->n), nk4 = (size_t)4 * p->nk;
+  cudaError_t e = cudaMalloc(&p->tab_a, n_a * nk4 * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&p->tabf_a, n_a * nk4 * sizeof(float));
+  if (e == cudaSuccess) e = cudaMalloc(&p->mt0_a, n_a * len * sizeof(float4));
+  if (e == cudaSuccess) e = cudaMalloc(&p->mt1_a, n_a * len * sizeof(float2));
+  if (e != cudaSuccess) {
+    free_outputs(p);
+    return fail(e == cudaErrorMemoryAllocation ? LPT2_ENOMEM : LPT2_ECUDA, "output tables: %s", cudaGetErrorString(e));
+  }
+  p->out_a.assign(a_out, a_out + n_a);
+  p->n_out_a = n_a;
+  const int rc = run_output_growth(p);
+  if (rc) free_outputs(p);
+  return rc;
+}
+
+// One realisation at every output scale factor: the a-independent prefix once, then per
+// a_j the multipliers, positions, CIC and P(k) (see the header).
+int lpt2_displace_outputs(lpt2_plan_t p, const float* noise, float* pos, double* pk, double* k_mean,
+                          int64_t* n_modes, int n_shells) {
+  int rc = check_plan_ws(p);
+  if (rc) return rc;
+  if (p->n_inst != 1) return fail(LPT2_EUNSUPPORTED, "lpt2_displace_outputs needs a single-instance plan");
+  if (p->n_out_a < 1) return fail(LPT2_EINVAL, "no output scale factors: call lpt2_set_outputs first");
+  if (!pk) return fail(LPT2_EINVAL, "pk must not be null");
+  if (n_shells < 1 || n_shells > kMaxShells) return fail(LPT2_EINVAL, "n_shells must be in [1, 256]");
+  set_group(p, 0);
+  rc = ensure_geometry(p, 0, n_shells);
+  if (rc) return rc;
+  const FwdSlots f = fwd_slots(p);
+  rc = displace_prefix(p, f, noise, false);
+  if (rc) return rc;
+  const size_t n3 = (size_t)p->n * p->n * p->n, len = (size_t)mode_table_len(p->n), nk4 = (size_t)4 * p->nk;
+  for (int j = 0; j < p->n_out_a; ++j) {
+    rc = displace_suffix(p, f, false, nullptr, nullptr, pos ? pos + j * 3 * n3 : nullptr, nullptr,
+                         p->mt0_a + j * len, p->mt1_a + j * len, p->tabf_a + j * nk4);
+    if (rc) return rc;
+    // the density spectrum goes to a slot the suffix does not use (A and D stay intact)
+    rc = cic_pk_group(p, 0, nullptr, nullptr, pk + (size_t)j * n_shells, j == 0 ? k_mean : nullptr,
+                      j == 0 ? n_modes : nullptr, n_shells, f.Y[3]);
+    if (rc) return rc;
+  }
   return LPT2_OK;
 }
 
