@@ -208,6 +208,33 @@ def profile_run(args):
     print(json.dumps({"profile_run": True, "grid": n, "box": box, "launches": L.lpt2_launch_count(plan)}))
 
 
+def source_table(args):
+    """The full-source diagnostic over output times and |fR0| (`--source-table`): for
+    z = 0, 0.5, 1 and |fR0| = 1e-4, 1e-5, 1e-6 on one realisation (seed 1, the grid of
+    --grid at a 2 Mpc/h cell), the shell mean and scatter of Re(S_MG/S_GR) and the T1
+    ratio at each shell's mean |k|.  Prints one JSON line per (z, |fR0|)."""
+    import torch
+
+    import paper_1909_06282_gb300 as L
+    import workloads as W
+    n = args.grid
+    box = WORKLOAD["box"] * n / WORKLOAD["n"]
+    for z in (0.0, 0.5, 1.0):
+        a = 1.0 / (1.0 + z)
+        plan = L.Plan(W.Instance(n, box, 1, W.COSMO.replace(fr0_abs=1e-5), a_out=a), n_steps=1024)
+        for fr0 in (1e-4, 1e-5, 1e-6):
+            L.lpt2_set_fr0(plan, fr0)
+            t0 = time.perf_counter()
+            r = L.lpt2_source_ratio(plan, n_bins=WORKLOAD["n_shells"])
+            torch.cuda.synchronize()
+            ms = (time.perf_counter() - t0) * 1e3
+            L.lpt2_device_status(plan)
+            print(json.dumps({"source_table": True, "grid": n, "box": box, "z": z, "fr0": fr0, "ms": ms,
+                              **{k: v.cpu().tolist() for k, v in r.items()}}), flush=True)
+        del plan
+        torch.cuda.empty_cache()
+
+
 def bench_large(args, L, W, torch):
     """The large configuration: 1024^3 particles, L = 2048 Mpc/h (the same 2 Mpc/h cell),
     |fR0| = 1e-5, forward step (positions, CIC, 32-shell P(k)) on its own plan and stream."""
@@ -633,9 +660,15 @@ def main():
                     help="forward-only run for ncu (no timing); grid from --grid")
     ap.add_argument("--grid", type=int, default=WORKLOAD["n"],
                     help="grid side for --profile (cell size kept at 2 Mpc/h)")
+    ap.add_argument("--source-table", action="store_true",
+                    help="full-source diagnostic at z = 0, 0.5, 1 and |fR0| = 1e-4, 1e-5, 1e-6 (grid from "
+                         "--grid); prints one JSON line per case instead of the benchmark line")
     args = ap.parse_args()
     if args.profile:
         profile_run(args)
+        return
+    if args.source_table:
+        source_table(args)
         return
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3

@@ -45,7 +45,7 @@ def rel_l2(a, b):
 
 
 @pytest.mark.parametrize("n,box,fr0,a_out", [(32, 128.0, 1e-4, 1.0), (32, 200.0, 1e-5, 0.6667),
-                                             (64, 256.0, 1e-4, 1.0)])
+                                             (32, 64.0, 1e-6, 0.5), (64, 256.0, 1e-4, 1.0)])
 def test_source_ratio_against_oracle(lib, n, box, fr0, a_out):
     from oracle import fullsource as fs
     c = W.COSMO.replace(fr0_abs=fr0)
@@ -77,3 +77,17 @@ def test_source_ratio_gr_limit(lib):
     ok = res["count"].cpu().numpy() > 0
     assert np.abs(res["mean"].cpu().numpy()[ok] - 1.0).max() <= 1e-4
     np.testing.assert_allclose(res["t1"].cpu().numpy()[ok], 1.0, atol=1e-6)
+
+
+def test_source_ratio_after_set_fr0_equals_a_fresh_plan(lib):
+    """The diagnostic reads the plan's current tables: after lpt2_set_fr0 it equals a plan
+    made at that |fR0| (the GR reference is recomputed per call)."""
+    n, box, a = 32, 64.0, 0.5
+    plan = lib.Plan(W.Instance(n, box, 5, W.COSMO.replace(fr0_abs=1e-5), a), n_steps=STEPS)
+    lib.lpt2_set_fr0(plan, 1e-4)
+    got = lib.lpt2_source_ratio(plan, n_bins=16)
+    fresh = lib.Plan(W.Instance(n, box, 5, W.COSMO.replace(fr0_abs=1e-4), a), n_steps=STEPS)
+    want = lib.lpt2_source_ratio(fresh, n_bins=16)
+    for k in ("mean", "sigma", "t1", "k_mean"):
+        np.testing.assert_allclose(got[k].cpu().numpy(), want[k].cpu().numpy(), rtol=1e-6, atol=1e-12)
+    assert torch.equal(got["count"], want["count"])
