@@ -68,7 +68,10 @@ enum {
   LPT2_D2_R2_80 = 3,    /* k1 = 2 k2, theta = 80 deg                                         */
   LPT2_D2_R2_70 = 4,    /* k1 = 2 k2, theta = 70 deg                                         */
   LPT2_D2_WINTHER = 5,  /* T1 braces with D1(k)^2 in place of D1(k1) D1(k2) (Winther et al.) */
-  LPT2_D2_GR = 6        /* the D2 equation of GR (mu = 1): scale-independent                 */
+  LPT2_D2_GR = 6,       /* the D2 equation of GR (mu = 1): scale-independent                 */
+  LPT2_D2_ISO60 = 7,    /* k1 = k2, theta = 60 deg (the text's "equilateral", as printed)    */
+  LPT2_D2_SQUEEZED = 8, /* k1 = 1e-3 k2, theta = 90 deg (squeezed: k1 ~ 0, k2 ~ k)           */
+  LPT2_D2_LCDM_FIT = 9  /* Eq. lcdm-fit: D2 = -(3/7) D1(k,a)^2 Omega_m(a)^(-1/143), no D2 ODE */
 };
 
 /* Background cosmology and f(R) parameters. fr0_abs = |f_R0|; 0 selects GR
@@ -109,7 +112,7 @@ typedef struct lpt2_plan_s* lpt2_plan_t;
  * LPT2_EINVAL (null pointers, n_k < 2, k_min <= 0, k_max <= k_min, box <= 0,
  * a range, non-flat cosmology, fr0_abs < 0, n_steps < 1, instance ordering or
  * differing backgrounds, unknown flags), LPT2_EUNSUPPORTED (n not in the list
- * above, hs_n != 1, d2_variant outside LPT2_D2_T1 .. LPT2_D2_GR, differing boxes within a grid size),
+ * above, hs_n != 1, d2_variant outside LPT2_D2_T1 .. LPT2_D2_LCDM_FIT, differing boxes within a grid size),
  * LPT2_ENOMEM, LPT2_ECUDA.  lpt2_white_noise, lpt2_fft_*, lpt2_set_fr0 and
  * lpt2_displace_vjp need a single-instance plan. */
 int lpt2_plan(lpt2_plan_t* out, const lpt2_instance* inst, int n_inst, int n_k,

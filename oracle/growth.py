@@ -34,7 +34,12 @@ takes the geometric sin^2 theta of each mode pair from the GR source S).  Varian
   0 T1 (r = 1, 90 deg)   1 T2 (r = 1, 80 deg)   2 isosceles 70 deg
   3 r = 2, 80 deg        4 r = 2, 70 deg
   5 Winther: the T1 braces with D1(k)^2 in place of D1(k1) D1(k2)
-  6 GR: the D2 equation with mu = 1 and the GR braces (scale-independent D2).
+  6 GR: the D2 equation with mu = 1 and the GR braces (scale-independent D2)
+  7 isosceles 60 deg, the text's "equilateral" (k1 = k2, theta = 60 deg as printed)
+  8 squeezed, k1 = 1e-3 k2 at 90 deg (the text's k1 ~ 0, k2 = k; k1 = 0 exactly leaves
+    the k1.k2 terms 0/0, and at r = 1e-3 they are below 1e-6 of the braces)
+  9 the LCDM fit Eq. lcdm-fit, D2 = -(3/7) D1(k,a)^2 Omega_m(a)^(-1/143) with the D1 of
+    Eq. d1 (no D2 equation; tangent -(6/7) D1 dD1/dtheta Omega_m(a)^(-1/143)).
 
 The k table is k_t = k_min (k_max/k_min)^(t/(n_k-1)); lookups interpolate
 linearly in ln k between nodes and clamp outside the table (a reading: the
@@ -46,7 +51,7 @@ import numpy as np
 
 from . import cosmology as cm
 
-__all__ = ["k_table", "growth_tables", "interp_lnk", "d1_gr", "DEFAULT_STEPS", "VARIANTS",
+__all__ = ["k_table", "growth_tables", "interp_lnk", "d1_gr", "DEFAULT_STEPS", "VARIANTS", "BOUCHET",
            "triangle", "d2_braces"]
 
 DEFAULT_STEPS = 2048
@@ -66,8 +71,8 @@ def _background(c, s):
 
 # (r = k1 / k2, angle between k1 and k2 in degrees); 5 Winther and 6 GR use the T1 geometry
 VARIANTS = {0: (1.0, 90.0), 1: (1.0, 80.0), 2: (1.0, 70.0), 3: (2.0, 80.0), 4: (2.0, 70.0),
-            5: (1.0, 90.0), 6: (1.0, 90.0)}
-WINTHER, GR_D2 = 5, 6
+            5: (1.0, 90.0), 6: (1.0, 90.0), 7: (1.0, 60.0), 8: (1e-3, 90.0), 9: (1.0, 90.0)}
+WINTHER, GR_D2, BOUCHET = 5, 6, 9
 
 
 def triangle(k, variant):
@@ -187,8 +192,11 @@ def growth_tables(c, a_out=1.0, k=None, n_steps=DEFAULT_STEPS, variant=None):
         variant = int(getattr(c, "d2_variant", 0))
     y = _rk4(c, k, c.a_init, a_out, n_steps, variant)
     n1 = d1_gr(c, 1.0, n_steps)
-    return dict(k=k, D1=y[0] / n1, D2=y[6] / n1 ** 2,
-                dD1=y[8] / n1, dD2=y[14] / n1 ** 2, norm=n1)
+    D1, dD1 = y[0] / n1, y[8] / n1
+    if variant == BOUCHET:     # Eq. lcdm-fit with the scale-dependent D1 of Eq. d1
+        f = cm.omega_m_a(c, a_out) ** (-1.0 / 143.0)
+        return dict(k=k, D1=D1, D2=-3.0 / 7.0 * D1 * D1 * f, dD1=dD1, dD2=-6.0 / 7.0 * D1 * dD1 * f, norm=n1)
+    return dict(k=k, D1=D1, D2=y[6] / n1 ** 2, dD1=dD1, dD2=y[14] / n1 ** 2, norm=n1)
 
 
 def interp_lnk(table_k, table_v, kq):

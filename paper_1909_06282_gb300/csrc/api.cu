@@ -506,8 +506,8 @@ static int check_cosmo(const lpt2_instance* inst) {
     return fail(LPT2_EINVAL, "bad h / sigma8 / omega_b / t_cmb");
   if (!(c.fr0_abs >= 0) || !isfinite(c.fr0_abs)) return fail(LPT2_EINVAL, "fr0_abs must be >= 0");
   if (c.hs_n != 1) return fail(LPT2_EUNSUPPORTED, "only Hu-Sawicki n = 1 is supported");
-  if (c.d2_variant < LPT2_D2_T1 || c.d2_variant > LPT2_D2_GR)
-    return fail(LPT2_EUNSUPPORTED, "d2_variant must be one of LPT2_D2_T1 .. LPT2_D2_GR");
+  if (c.d2_variant < LPT2_D2_T1 || c.d2_variant > LPT2_D2_LCDM_FIT)
+    return fail(LPT2_EUNSUPPORTED, "d2_variant must be one of LPT2_D2_T1 .. LPT2_D2_LCDM_FIT");
   return LPT2_OK;
 }
 

@@ -134,6 +134,7 @@ __device__ Bg background(const GrowthParams& p, double s, bool gr) {
 struct D2Geo {
   double fa, fb, c, c2, inv_s2, r;
   int winther, gr2;
+  int fit;   // D2 from the LCDM fit Eq. lcdm-fit with the scale-dependent D1 (no D2 equation)
 };
 
 __host__ __device__ inline D2Geo d2_geo(int variant) {
@@ -144,7 +145,9 @@ __host__ __device__ inline D2Geo d2_geo(int variant) {
     case 2: th = 70.0; break;
     case 3: r = 2.0; th = 80.0; break;
     case 4: r = 2.0; th = 70.0; break;
-    default: break;
+    case 7: th = 60.0; break;    // isosceles 60 deg (the text's "equilateral")
+    case 8: r = 1e-3; break;     // squeezed: k1 = 1e-3 k2 at 90 deg (k1 ~ 0, k2 ~ k)
+    default: break;              // T1; Winther, GR and the LCDM fit use its geometry
   }
   D2Geo g;
   g.c = th == 90.0 ? 0.0 : cos(th * (M_PI / 180.0));
@@ -156,6 +159,7 @@ __host__ __device__ inline D2Geo d2_geo(int variant) {
   g.fa = r * r * k2sq;
   g.winther = variant == 5;
   g.gr2 = variant == 6;
+  g.fit = variant == 9;
   return g;
 }
 
@@ -302,8 +306,14 @@ __global__ void k_growth(GrowthParams p, double* tab, float* tabf) {
   tab[nk + t] = y[L::D2] / (norm * norm);
   tab[2 * nk + t] = TAN ? y[T] / norm : 0.0;
   tab[3 * nk + t] = TAN ? y[T + L::D2] / (norm * norm) : 0.0;
+  if (geo.fit) {   // D2 = -(3/7) D1^2 Omega_m(a)^(-1/143), tangent -(6/7) D1 dD1 Omega_m(a)^(-1/143)
+    const double a3 = 1.0 / (p.a_out * p.a_out * p.a_out);
+    const double f = pow(p.omega_m * a3 / (p.omega_m * a3 + p.omega_l), -1.0 / 143.0);
+    tab[nk + t] = -3.0 / 7.0 * tab[t] * tab[t] * f;
+    tab[3 * nk + t] = -6.0 / 7.0 * tab[t] * tab[2 * nk + t] * f;
+  }
   tabf[t] = (float)(y[0] / norm);
-  tabf[nk + t] = (float)(y[L::D2] / (norm * norm));
+  tabf[nk + t] = (float)tab[nk + t];
   tabf[2 * nk + t] = (float)tab[2 * nk + t];
   tabf[3 * nk + t] = (float)tab[3 * nk + t];
 }

@@ -48,7 +48,7 @@ def _inst(lib_mod, **over):
 
 @pytest.mark.parametrize("over,code", [
     (dict(n=100), -4), (dict(n=0), -4), (dict(n=2048), -4), (dict(box=0.0), -1), (dict(box=-5.0), -1),
-    (dict(hs_n=2), -4), (dict(d2_variant=7), -4), (dict(d2_variant=-1), -4), (dict(fr0_abs=-1e-5), -1),
+    (dict(hs_n=2), -4), (dict(d2_variant=10), -4), (dict(d2_variant=-1), -4), (dict(fr0_abs=-1e-5), -1),
     (dict(omega_m=0.3, omega_l=0.6), -1), (dict(a_out=1.5), -1), (dict(a_init=0.0), -1),
     (dict(a_out=1e-4), -1), (dict(sigma8=0.0), -1),
 ])

@@ -23,7 +23,7 @@ def lib():
     return L
 
 
-@pytest.mark.parametrize("variant", range(7))
+@pytest.mark.parametrize("variant", range(10))
 @pytest.mark.parametrize("fr0,a_out", [(1e-4, 1.0), (1e-6, 0.5)])
 def test_variant_growth_tables_against_oracle(lib, variant, fr0, a_out):
     from oracle import growth as gr
@@ -50,7 +50,7 @@ def test_variants_differ_where_mg_acts(lib):
     assert np.all(np.abs(np.diff(tabs[:, -1])) > 1e-4 * np.abs(tabs[0, -1]))
 
 
-@pytest.mark.parametrize("variant", [1, 3, 5])
+@pytest.mark.parametrize("variant", [1, 3, 5, 7, 8, 9])
 def test_variant_displacements_against_oracle(lib, variant):
     from oracle import lpt2
     n, box = 32, 128.0
@@ -64,3 +64,25 @@ def test_variant_displacements_against_oracle(lib, variant):
         r = float(np.linalg.norm((got - want).ravel()) / np.linalg.norm(want.ravel()))
         assert r <= 2e-5, (key, r)
         assert float(np.max(np.abs(got - want))) / cell <= 1e-4
+
+
+def test_fig_d2fit_tables(lib):
+    """Fig. d2fit from the GPU tables: D2 / (-3/7 D1^2) / Omega_m(a)^(-1/143) of T1 at
+    k = 1e-3, 1e-2, 0.1, 1 h/Mpc (the nodes of a 4-point k table) for |fR0| = 1e-4 equals
+    the oracle's to 1e-9, and the LCDM-fit variant gives exactly 1."""
+    from oracle import cosmology as cm
+    from oracle import growth as gr
+    k = np.array([1e-3, 1e-2, 0.1, 1.0])
+    for a in (0.25, 0.5, 1.0):
+        om = cm.omega_m_a(W.COSMO, a) ** (-1.0 / 143.0)
+        for v in (0, 9):
+            c = W.COSMO.replace(fr0_abs=1e-4, d2_variant=v)
+            plan = lib.Plan(W.Instance(32, 100.0, 1, c, a_out=a), n_k=4, k_min=1e-3, k_max=1.0,
+                            n_steps=STEPS, workspace=False)
+            d1, d2 = [t.cpu().numpy() for t in lib.lpt2_growth_tables(plan)[:2]]
+            got = d2 / (-3.0 / 7.0 * d1 * d1) / om
+            if v == 9:
+                np.testing.assert_allclose(got, 1.0, rtol=1e-13)
+            else:
+                ref = gr.growth_tables(c, a, k=k, n_steps=STEPS, variant=0)
+                np.testing.assert_allclose(got, ref["D2"] / (-3.0 / 7.0 * ref["D1"] ** 2) / om, rtol=1e-9)
