@@ -50,6 +50,7 @@ __global__ void __launch_bounds__(CIC_THREADS, LPT2_CIC_MINB) k_cic(CicArgs a) {
   const int b = blockIdx.x;
   const int x0 = (b / (NT * NT)) * CIC_T, y0 = ((b / NT) % NT) * CIC_T, z0 = (b % NT) * CIC_T;
   const int ox = x0 - CIC_H, oy = y0 - CIC_H, oz = z0 - CIC_HZ;   // window origin (may be < 0)
+  const bool wraps = ox < 0 || oy < 0 || oz < 0 || ox + CIC_E > N || oy + CIC_E > N || oz + CIC_EZ > N;
   // all position loads of this thread first: their latency overlaps the zeroing
   float u[CIC_PER][3];
 #pragma unroll
@@ -69,9 +70,15 @@ __global__ void __launch_bounds__(CIC_THREADS, LPT2_CIC_MINB) k_cic(CicArgs a) {
     const float uy = wrapN<N>(u[k][1] * a.g.inv_cell + a.shift);
     const float uz = wrapN<N>(u[k][2] * a.g.inv_cell + a.shift);
     const float fx = floorf(ux), fy = floorf(uy), fz = floorf(uz);
-    // window cell of the lower corner: periodic integer offset from the origin
-    const int rx = wrap_cell<N>((int)fx - ox), ry = wrap_cell<N>((int)fy - oy), rz = wrap_cell<N>((int)fz - oz);
-    if (rx < CIC_E - 1 && ry < CIC_E - 1 && rz < CIC_EZ - 1) {
+    // window cell of the lower corner: offset from the origin, periodic only for a window
+    // that crosses the grid boundary (elsewhere a negative offset is simply outside)
+    int rx = (int)fx - ox, ry = (int)fy - oy, rz = (int)fz - oz;
+    if (wraps) {
+      rx = wrap_cell<N>(rx);
+      ry = wrap_cell<N>(ry);
+      rz = wrap_cell<N>(rz);
+    }
+    if ((unsigned)rx < CIC_E - 1 && (unsigned)ry < CIC_E - 1 && (unsigned)rz < CIC_EZ - 1) {
       const float dx = ux - fx, dy = uy - fy, dz = uz - fz;   // exact
       const float wx0 = 1.f - dx, wy0 = 1.f - dy, wz0 = 1.f - dz;
       unsigned int* c = win + (rx * CIC_E + ry) * CIC_EZ + rz;
@@ -93,12 +100,26 @@ __global__ void __launch_bounds__(CIC_THREADS, LPT2_CIC_MINB) k_cic(CicArgs a) {
   }
   __syncthreads();
   const float inv_scale = 1.0f / CIC_SCALE;
+  // group q = (wx * CIC_E + wy) * CIC_QZ + qz, advanced by the CTA size without divisions
+  static_assert(CIC_THREADS / CIC_QZ / CIC_E < CIC_E, "flush stride must advance wx by less than a window");
+  constexpr int SQZ = CIC_THREADS % CIC_QZ, SR = CIC_THREADS / CIC_QZ;   // stride in (qz, row)
+  constexpr int SWY = SR % CIC_E, SWX = SR / CIC_E;                      // row stride in (wy, wx)
+  int qz = threadIdx.x % CIC_QZ, wy = (threadIdx.x / CIC_QZ) % CIC_E, wx = threadIdx.x / CIC_QZ / CIC_E;
   for (int q = threadIdx.x; q < CIC_E * CIC_E * CIC_QZ; q += blockDim.x) {
     const uint4 iv = reinterpret_cast<const uint4*>(win)[q];
+    const int cz = qz, cy = wy, cx = wx;
+    qz += SQZ;
+    wy += SWY;
+    wx += SWX;
+    if (qz >= CIC_QZ) { qz -= CIC_QZ; ++wy; }
+    if (wy >= CIC_E) { wy -= CIC_E; ++wx; }
     if ((iv.x | iv.y | iv.z | iv.w) == 0u) continue;
-    const int r = q / CIC_QZ, qz = q % CIC_QZ;
-    const int gx = wrap_cell<N>(ox + r / CIC_E), gy = wrap_cell<N>(oy + r % CIC_E);
-    const int gz = wrap_cell<N>(oz + 4 * qz);   // a multiple of 4: the group never straddles the wrap
+    int gx = ox + cx, gy = oy + cy, gz = oz + 4 * cz;   // gz a multiple of 4: the group never straddles the wrap
+    if (wraps) {
+      gx = wrap_cell<N>(gx);
+      gy = wrap_cell<N>(gy);
+      gz = wrap_cell<N>(gz);
+    }
     atomicAdd(reinterpret_cast<float4*>(a.rho + ((size_t)gx * N + gy) * N + gz),
               make_float4((float)iv.x * inv_scale, (float)iv.y * inv_scale, (float)iv.z * inv_scale,
                           (float)iv.w * inv_scale));
