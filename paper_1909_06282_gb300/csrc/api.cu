@@ -238,7 +238,6 @@ cudaError_t z_source(int n, const ZSourceArgs& a, cudaStream_t s) { DISPATCH(lau
 cudaError_t z_final(int n, const ZFinalArgs& a, cudaStream_t s) { DISPATCH(launch_z_final, n, a, s) }
 cudaError_t y_pass(int n, const YArgs& a, cudaStream_t s) { DISPATCH(launch_y, n, a, s) }
 cudaError_t x_pass(int n, const XArgs& a, cudaStream_t s) { DISPATCH(launch_x, n, a, s) }
-cudaError_t z_adj_final(int n, const ZAdjFinalArgs& a, cudaStream_t s) { DISPATCH(launch_z_adj_final, n, a, s) }
 cudaError_t z_adj_source(int n, const ZAdjSourceArgs& a, cudaStream_t s) { DISPATCH(launch_z_adj_source, n, a, s) }
 
 void timing_begin(lpt2_plan_s* p) {
@@ -1434,9 +1433,21 @@ int lpt2_displace_vjp(lpt2_plan_t p, const float* noise, const float* g_pos, con
   ZC2RArgs zc{g, p->tw, S[S_A], grho, g_density};
   LAUNCH(p, "z_c2r_grho", (g_density ? 12.0 : 8.0) * V3(p), z_c2r(n, zc, p->stream));
 
-  // 2-3. CIC transpose and forward z of g_Psi: slots 7 (z, order 1), 8 (y), 9 (x)
-  ZAdjFinalArgs zf{g, p->tw, grho, pos, g_pos, S[7], S[8], S[9]};
-  LAUNCH(p, "z_adj_final", 28.0 * V3(p), z_adj_final(n, zf, p->stream));
+  // 2-3. CIC transpose (tiled gather) into real g_Psi fields (slots 10-12), then their
+  // forward z transforms: slots 7 (z; its conj(i k_z) is applied in the y pass), 8 (y), 9 (x)
+  float* gps[3] = {reinterpret_cast<float*>(S[12]), reinterpret_cast<float*>(S[11]),
+                   reinterpret_cast<float*>(S[10])};   // x, y, z
+  CicGradArgs cg{g, grho, pos, g_pos, gps[0], gps[1], gps[2]};
+  LAUNCH(p, "cic_grad", (g_pos ? 40.0 : 28.0) * V3(p), launch_cic_grad(cg, p->stream));
+  ZR2CArgs zp{};
+  zp.g = g;
+  zp.tw = p->tw;
+  zp.src = Z_REAL;
+  for (int c = 0; c < 3; ++c) {   // z, y, x
+    zp.in = gps[2 - c];
+    zp.out = S[7 + c];
+    LAUNCH(p, "z_r2c_gpsi", 8.0 * V3(p), z_r2c(n, zp, p->stream));
+  }
   // 4. y transpose: x-order 0 group = Psi_z (y0) + Psi_y (y1); x-order 1 = Psi_x
   YArgs ys{};
   ys.g = g;
@@ -1447,7 +1458,7 @@ int lpt2_displace_vjp(lpt2_plan_t p, const float* noise, const float* g_pos, con
   ys.job.in[0] = S[7];
   ys.job.in[1] = S[8];
   ys.job.in[2] = S[9];
-  ys.job.dst[0] = 0; ys.job.ord[0] = 0;
+  ys.job.dst[0] = 0; ys.job.ord[0] = 0; ys.job.zord[0] = 1;
   ys.job.dst[1] = 0; ys.job.ord[1] = 1;
   ys.job.dst[2] = 1; ys.job.ord[2] = 0;
   ys.job.out[0] = S[10];

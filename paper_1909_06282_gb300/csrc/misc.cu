@@ -126,6 +126,122 @@ __global__ void __launch_bounds__(CIC_THREADS, LPT2_CIC_MINB) k_cic(CicArgs a) {
   }
 }
 
+// Transpose of the CIC deposit, tile by tile like k_cic: the CTA of a Lagrangian CIC_T^3
+// tile loads the window of dL/d(density) around it into shared memory (coalesced groups
+// of four along z) and each particle gathers the derivative of its eight CIC weights,
+//   dL/dx = (1/h) sum_corners g_c (+-1) w_y w_z   (and y, z alike),
+// from the window; a particle outside the window gathers from global memory.  The
+// three components go to real fields at the particle's Lagrangian cell.
+template <int N>
+__global__ void __launch_bounds__(CIC_THREADS, LPT2_CIC_MINB) k_cic_grad(CicGradArgs a) {
+  static_assert(N % CIC_T == 0 && N % 4 == 0, "grid side must be a multiple of the tile");
+  extern __shared__ __align__(16) float gw[];   // [CIC_E][CIC_E][CIC_EZ]
+  const size_t n3 = (size_t)N * N * N;
+  constexpr int NT = N / CIC_T;
+  const int b = blockIdx.x;
+  const int x0 = (b / (NT * NT)) * CIC_T, y0 = ((b / NT) % NT) * CIC_T, z0 = (b % NT) * CIC_T;
+  const int ox = x0 - CIC_H, oy = y0 - CIC_H, oz = z0 - CIC_HZ;
+  const bool wraps = ox < 0 || oy < 0 || oz < 0 || ox + CIC_E > N || oy + CIC_E > N || oz + CIC_EZ > N;
+  float u[CIC_PER][3];
+#pragma unroll
+  for (int k = 0; k < CIC_PER; ++k) {
+    const int p = threadIdx.x + k * CIC_THREADS;
+    const int i = p / (CIC_T * CIC_T), j = (p / CIC_T) % CIC_T, l = p % CIC_T;
+    const size_t e = ((size_t)(x0 + i) * N + (y0 + j)) * N + (z0 + l);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) u[k][c] = __ldg(a.pos + c * n3 + e);
+  }
+  // group q = (wx * CIC_E + wy) * CIC_QZ + qz, advanced by the CTA size without divisions
+  constexpr int SQZ = CIC_THREADS % CIC_QZ, SR = CIC_THREADS / CIC_QZ;
+  constexpr int SWY = SR % CIC_E, SWX = SR / CIC_E;
+  int qz = threadIdx.x % CIC_QZ, wy = (threadIdx.x / CIC_QZ) % CIC_E, wx = threadIdx.x / CIC_QZ / CIC_E;
+  for (int q = threadIdx.x; q < CIC_E * CIC_E * CIC_QZ; q += blockDim.x) {
+    int gx = ox + wx, gy = oy + wy, gz = oz + 4 * qz;   // gz a multiple of 4
+    qz += SQZ;
+    wy += SWY;
+    wx += SWX;
+    if (qz >= CIC_QZ) { qz -= CIC_QZ; ++wy; }
+    if (wy >= CIC_E) { wy -= CIC_E; ++wx; }
+    if (wraps) {
+      gx = wrap_cell<N>(gx);
+      gy = wrap_cell<N>(gy);
+      gz = wrap_cell<N>(gz);
+    }
+    reinterpret_cast<float4*>(gw)[q] = __ldg(reinterpret_cast<const float4*>(a.grho + ((size_t)gx * N + gy) * N + gz));
+  }
+  __syncthreads();
+  const float ic = a.g.inv_cell;
+#pragma unroll
+  for (int k = 0; k < CIC_PER; ++k) {
+    const int p = threadIdx.x + k * CIC_THREADS;
+    const int i = p / (CIC_T * CIC_T), j = (p / CIC_T) % CIC_T, l = p % CIC_T;
+    const size_t e = ((size_t)(x0 + i) * N + (y0 + j)) * N + (z0 + l);
+    const float ux = wrapN<N>(u[k][0] * ic), uy = wrapN<N>(u[k][1] * ic), uz = wrapN<N>(u[k][2] * ic);
+    const float fx = floorf(ux), fy = floorf(uy), fz = floorf(uz);
+    int rx = (int)fx - ox, ry = (int)fy - oy, rz = (int)fz - oz;
+    if (wraps) {
+      rx = wrap_cell<N>(rx);
+      ry = wrap_cell<N>(ry);
+      rz = wrap_cell<N>(rz);
+    }
+    float gxv, gyv, gzv;
+    if ((unsigned)rx < CIC_E - 1 && (unsigned)ry < CIC_E - 1 && (unsigned)rz < CIC_EZ - 1) {
+      const float dx = ux - fx, dy = uy - fy, dz = uz - fz;
+      const float wx[2] = {1.f - dx, dx}, wy[2] = {1.f - dy, dy}, wz[2] = {1.f - dz, dz};
+      const float* c = gw + (rx * CIC_E + ry) * CIC_EZ + rz;
+      float ax = 0.f, ay = 0.f, az = 0.f;
+#pragma unroll
+      for (int cx = 0; cx < 2; ++cx)
+#pragma unroll
+        for (int cy = 0; cy < 2; ++cy)
+#pragma unroll
+          for (int cz = 0; cz < 2; ++cz) {
+            const float gc = c[(cx * CIC_E + cy) * CIC_EZ + cz];
+            const float sx = cx ? 1.f : -1.f, sy = cy ? 1.f : -1.f, sz = cz ? 1.f : -1.f;
+            ax = fmaf(gc * sx, wy[cy] * wz[cz], ax);
+            ay = fmaf(gc * sy, wx[cx] * wz[cz], ay);
+            az = fmaf(gc * sz, wx[cx] * wy[cy], az);
+          }
+      gxv = ax * ic;
+      gyv = ay * ic;
+      gzv = az * ic;
+    } else {
+      cic_gather_grad<N>(a.grho, a.pos, e, n3, ic, gxv, gyv, gzv);
+    }
+    if (a.gpos) {
+      gxv += __ldg(a.gpos + e);
+      gyv += __ldg(a.gpos + n3 + e);
+      gzv += __ldg(a.gpos + 2 * n3 + e);
+    }
+    a.gx[e] = gxv;
+    a.gy[e] = gyv;
+    a.gz[e] = gzv;
+  }
+}
+
+template <int N>
+cudaError_t launch_cic_grad_n(const CicGradArgs& a, cudaStream_t s) {
+  cudaFuncSetAttribute(k_cic_grad<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, CIC_SMEM);
+  k_cic_grad<N><<<(unsigned)((N / CIC_T) * (N / CIC_T) * (N / CIC_T)), CIC_THREADS, CIC_SMEM, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cic_grad(const CicGradArgs& a, cudaStream_t s) {
+  if (a.g.batch != 1) return cudaErrorInvalidValue;
+  switch (a.g.n) {
+    case 16: return launch_cic_grad_n<16>(a, s);
+    case 32: return launch_cic_grad_n<32>(a, s);
+    case 64: return launch_cic_grad_n<64>(a, s);
+    case 96: return launch_cic_grad_n<96>(a, s);
+    case 128: return launch_cic_grad_n<128>(a, s);
+    case 192: return launch_cic_grad_n<192>(a, s);
+    case 256: return launch_cic_grad_n<256>(a, s);
+    case 512: return launch_cic_grad_n<512>(a, s);
+    case 1024: return launch_cic_grad_n<1024>(a, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
 template <int N>
 cudaError_t launch_cic_n(const CicArgs& a, cudaStream_t s) {
   cudaFuncSetAttribute(k_cic<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, CIC_SMEM);

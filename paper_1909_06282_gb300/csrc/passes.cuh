@@ -470,51 +470,6 @@ __device__ __forceinline__ void cic_gather_grad(const float* __restrict__ g, con
   gz = az * inv_cell;
 }
 
-template <int N>
-__global__ void __launch_bounds__(PassCfg<N>::ZT, LPT2_Z_MINB) k_z_adj_final(ZAdjFinalArgs a) {
-  using C = PassCfg<N>;
-  extern __shared__ float2 smem[];
-  float2* s_tw = smem;
-  load_twiddles(s_tw, a.tw, N);
-  const int p = threadIdx.x / C::TPP, t = threadIdx.x % C::TPP;
-  const SmemRowT<kRowWarp<N>> sm{smem + N + p * SmemRow::words(N)};
-  const int pair = blockIdx.x * C::ZP + p;
-  const int rows[2] = {2 * pair, 2 * pair + 1};
-  const size_t n3 = (size_t)N * N * N;
-  const float kf = a.g.kf;
-  float gza[C::RMAX];
-  __syncthreads();
-#pragma unroll
-  for (int h = 0; h < 2; ++h) {
-    float2 v[C::RMAX];
-    float gzb[C::RMAX];
-#pragma unroll
-    for (int r = 0; r < C::RMAX; ++r) {
-      float gx = 0.f, gy = 0.f, gz = 0.f;
-      const size_t e = (size_t)rows[h] * N + elem<N>(t, r);
-      if (a.grho) cic_gather_grad<N>(a.grho, a.pos, e, n3, a.g.inv_cell, gx, gy, gz);
-      if (a.gpos) {
-        gx += __ldg(a.gpos + e);
-        gy += __ldg(a.gpos + n3 + e);
-        gz += __ldg(a.gpos + 2 * n3 + e);
-      }
-      v[r] = make_float2(gx, gy);
-      if (h == 0) gza[r] = gz; else gzb[r] = gz;
-    }
-    fft<N, false>(v, t, sm, s_tw);
-    z_store_pair_d<N>(v, t, sm, a.gx + (size_t)rows[h] * C::H, a.gy + (size_t)rows[h] * C::H, kf, 0, 0);
-    if (h == 1) {
-      sm.sync();   // partner reads of the store above are done before the row is reused
-#pragma unroll
-      for (int r = 0; r < C::RMAX; ++r) v[r] = make_float2(gza[r], gzb[r]);
-      fft<N, false>(v, t, sm, s_tw);
-      z_store_pair_d<N>(v, t, sm, a.gz + (size_t)rows[0] * C::H, a.gz + (size_t)rows[1] * C::H, kf, 1, 1);
-    } else {
-      sm.sync();
-    }
-  }
-}
-
 // Transpose of k_z_source.  g_S = dL/dS is given in real space (the inverse z of h_S,
 // one z_c2r pass); the six phi_ij are recomputed (inverse z) and
 //   dL/dphi_ii = g_S (Tr - phi_ii),  Tr = phi_xx + phi_yy + phi_zz,   dL/dphi_ij = -2 g_S phi_ij,
@@ -632,10 +587,12 @@ __global__ void __launch_bounds__(PassCfg<N>::XT) k_y(YArgs a) {
 #pragma unroll
         for (int r = 0; r < C::RMAX; ++r) v[r] = a.job.in[i][base + (size_t)(elem<N>(t, r)) * C::H];
         fft<N, false>(v, t, sm, s_tw);
+        const int zo = a.job.zord[i];
 #pragma unroll
         for (int r = 0; r < C::RMAX; ++r) {
           const int n = elem<N>(t, r);
-          acc[r] = cadd(acc[r], dconj(v[r], a.g.kf * (float)mode_of(n, N), a.job.ord[i]));
+          const float2 u = dconj(v[r], a.g.kf * (float)mode_of(n, N), a.job.ord[i]);
+          acc[r] = cadd(acc[r], zo ? dconj(u, a.g.kf * (float)kz, zo) : u);
         }
       }
       float2* dst = a.job.out[o];
@@ -1017,12 +974,6 @@ template <int N> cudaError_t launch_z_final_t(const ZFinalArgs& a, cudaStream_t 
   k<<<dim3(N * N / Q::ROWS, 1, a.g.batch), C::ZT, Q::SMEM, s>>>(a);
   return cudaGetLastError();
 }
-template <int N> cudaError_t launch_z_adj_final_t(const ZAdjFinalArgs& a, cudaStream_t s) {
-  using C = PassCfg<N>;
-  cudaFuncSetAttribute(k_z_adj_final<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::ZSMEM);
-  k_z_adj_final<N><<<N * N / 2 / C::ZP, C::ZT, C::ZSMEM, s>>>(a);
-  return cudaGetLastError();
-}
 template <int N> cudaError_t launch_z_adj_source_t(const ZAdjSourceArgs& a, cudaStream_t s) {
   using C = PassCfg<N>;
   using Q = ZSrcCfg<N>;
@@ -1086,9 +1037,6 @@ template <int N> int x_blocks_t() { return (PassCfg<N>::H / PassCfg<N>::W) * N; 
     return launch_z_final_t<N>(a, s);                                                                \
   }                                                                                                  \
   cudaError_t launch_y_##N(const YArgs& a, cudaStream_t s) { return launch_y_t<N>(a, s); }           \
-  cudaError_t launch_z_adj_final_##N(const ZAdjFinalArgs& a, cudaStream_t s) {                       \
-    return launch_z_adj_final_t<N>(a, s);                                                            \
-  }                                                                                                  \
   cudaError_t launch_z_adj_source_##N(const ZAdjSourceArgs& a, cudaStream_t s) {                     \
     return launch_z_adj_source_t<N>(a, s);                                                           \
   }                                                                                                  \

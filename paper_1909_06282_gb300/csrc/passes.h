@@ -62,16 +62,17 @@ struct ZC2RArgs {      // inverse z pass of one field: half-spectrum rows -> rea
   const float* add_in;   // added to the result when not null
 };
 
-struct ZAdjFinalArgs { // transpose of k_z_final: CIC gather of dL/drho, forward z of g_Psi
+struct CicGradArgs {   // transpose of the CIC deposit: dL/d(position) of every particle
   Geo g;
-  const float2* tw;
-  const float* grho;   // dL/d(density contrast) per cell
+  const float* grho;   // dL/d(density contrast) per cell [N^3]
   const float* pos;    // [3][N^3] particle positions of the forward
   const float* gpos;   // [3][N^3] dL/dpositions added to the gathered gradient, or null
-  float2* gz;          // conj(i kz) FFT_z(g_Psi_z)
-  float2* gy;          // FFT_z(g_Psi_y)
-  float2* gx;          // FFT_z(g_Psi_x)
+  float* gx;           // [N^3] outputs at each particle's Lagrangian cell
+  float* gy;
+  float* gz;
 };
+cudaError_t launch_cic_grad(const CicGradArgs& a, cudaStream_t s);
+
 
 struct ZAdjSourceArgs {  // transpose of k_z_source
   Geo g;
@@ -107,9 +108,11 @@ struct YJob {          // y pass: each output = transform of (i k_y)^ord * input
   float2* out[9];
   int src[9];
   int ord[9];
-  // sum mode (transpose of the above): out[dst[i]] += conj((i k_y)^ord[i]) FFT_y(in[i])
+  // sum mode (transpose of the above): out[dst[i]] += conj((i k_y)^ord[i]) FFT_y(in[i]),
+  // times conj((i k_z)^zord[i]) (z-derivative of the transposed z pass, 0 = none)
   int sum;
   int dst[6];
+  int zord[6];
 };
 struct YArgs {
   Geo g;
@@ -191,7 +194,6 @@ struct CicArgs {
   cudaError_t launch_z_source_##N(const ZSourceArgs&, cudaStream_t);             \
   cudaError_t launch_z_final_##N(const ZFinalArgs&, cudaStream_t);               \
   cudaError_t launch_y_##N(const YArgs&, cudaStream_t);                          \
-  cudaError_t launch_z_adj_final_##N(const ZAdjFinalArgs&, cudaStream_t);        \
   cudaError_t launch_z_adj_source_##N(const ZAdjSourceArgs&, cudaStream_t);      \
   cudaError_t launch_x_##N(const XArgs&, cudaStream_t);                          \
   int x_blocks_##N();
