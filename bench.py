@@ -125,7 +125,7 @@ class ClockSampler:
 # its capture must be removed here (its traffic is then reported as null).
 TRAFFIC_512 = {
     "z_source": (402.789888 + 51.985152) * 1e6 * 8,
-    "cic": (270.263552 + 45.756416) * 1e6 * 8,
+    "cic": (270.254592 + 45.784320) * 1e6 * 8,
 }
 
 
