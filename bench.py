@@ -279,6 +279,19 @@ def bench_batched(args, L, W, torch, stream):
             L.lpt2_displace(plan, psi1=False, psi2=False, pos=pos)
             L.lpt2_cic_pk(plan, pos=None, n_shells=WORKLOAD["n_shells"])
 
+        # instances per launch of each grid-size group, tuned on this GPU (whole groups first)
+        for _ in range(args.warmup):
+            bstep()
+        stream.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(max(1, args.steps // 2)):
+            bstep()
+        e1.record(stream)
+        stream.synchronize()
+        ms_whole = e0.elapsed_time(e1) / max(1, args.steps // 2)
+        schedule = L.lpt2_autotune(plan, n_shells=WORKLOAD["n_shells"], reps=3)
+
         singles = [L.Plan(i, n_steps=1024, stream=stream) for i in insts]
         spos = [torch.empty((3, i.n, i.n, i.n), dtype=torch.float32, device="cuda") for i in insts]
 
@@ -307,8 +320,10 @@ def bench_batched(args, L, W, torch, stream):
             "ms_per_step": res["batched"],
             "one_by_one": {"value": parts / (res["one_by_one"] / 1e3), "ms_per_step": res["one_by_one"]},
             "speedup_vs_one_by_one": res["one_by_one"] / res["batched"],
+            "schedule": {"groups": ["96^3", "128^3", "192^3"], "instances_per_launch": schedule,
+                         "whole_group_ms_per_step": ms_whole},
             "what": "96 instances (32 x 96^3/384, 128^3/512, 192^3/768 Mpc/h), positions + CIC + P(k), "
-                    "one CUDA graph vs single-instance plans one by one"}
+                    "one CUDA graph with the autotuned launch schedule vs single-instance plans one by one"}
 
 
 def cufft_pipeline(plan, L, torch, n, box, n_shells):

@@ -230,6 +230,29 @@ int lpt2_set_outputs(lpt2_plan_t plan, int n_a, const double* a_out);
 int lpt2_displace_outputs(lpt2_plan_t plan, const float* noise, float* pos, double* pk,
                           double* k_mean, int64_t* n_modes, int n_shells);
 
+/* Launch schedule of a batched plan (no counterpart in the paper: how the batched form
+ * of the path is cut into launches).  Instances of one grid size form a group whose
+ * fields lie consecutively in every workspace slot; lpt2_displace and lpt2_cic_pk run a
+ * group in chunks of `chunk` instances per launch (default: the whole group), so that a
+ * chunk's fields can stay in L2 between the passes of small grids.  Outputs do not depend
+ * on the schedule (each instance's kernels are the same; the CIC float reductions may
+ * add in another order).
+ *
+ * lpt2_schedule: the number of groups (in order of the instances' first appearance) and,
+ * if chunk is not NULL, up to max_groups current chunk sizes.
+ * lpt2_set_schedule: chunk[n_groups] instances per launch (each >= 1, clamped to the
+ * group's size); drops the plan's captured graphs (recaptured on the next call).
+ * lpt2_autotune: times every group's forward step (Philox noise -> positions -> CIC ->
+ * n_shells-shell P(k)) on the plan's stream at chunk sizes count, ceil(count/2), ..., 1,
+ * `reps` timed repetitions after one warm-up each, keeps the fastest per group, and drops
+ * the captured graphs.  Plan-time work: it synchronises, allocates a small P(k) buffer
+ * (cudaMalloc) and overwrites the workspace; not capturable.  Needs the workspace.
+ * Errors: LPT2_EINVAL (bad count, chunk, n_shells, or reps outside [1, 100]),
+ * LPT2_ENOMEM, LPT2_ECUDA. */
+int lpt2_schedule(lpt2_plan_t plan, int* chunk, int max_groups, int* n_groups);
+int lpt2_set_schedule(lpt2_plan_t plan, const int* chunk, int n_groups);
+int lpt2_autotune(lpt2_plan_t plan, int n_shells, int reps);
+
 /* lpt2_set_fr0: change |f_R0| of the plan and recompute its growth tables
  * (the FP64 RK4 kernel) on the plan's stream.  fr0_abs >= 0 (0 = GR). */
 int lpt2_set_fr0(lpt2_plan_t plan, double fr0_abs);

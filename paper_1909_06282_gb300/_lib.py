@@ -93,6 +93,9 @@ def load_library():
         "lpt2_displace_vjp": (i, [vp, vp, vp, vp, vp, i, vp, vp]),
         "lpt2_displace_host": (i, [vp, i, vp, i64, vp, i64, vp, i64, i]),
         "lpt2_set_outputs": (i, [vp, i, C.POINTER(d)]),
+        "lpt2_schedule": (i, [vp, C.POINTER(i), i, C.POINTER(i)]),
+        "lpt2_set_schedule": (i, [vp, C.POINTER(i), i]),
+        "lpt2_autotune": (i, [vp, i, i]),
         "lpt2_displace_outputs": (i, [vp, vp, vp, vp, vp, vp, i]),
         "lpt2_timing_report": (i, [vp, C.POINTER(_KernelStat), i, C.POINTER(C.c_int)]),
     }
@@ -319,6 +322,28 @@ def lpt2_cic_pk(plan: Plan, pos=None, density=False, n_shells=32):
                                       _ptr(res["pk"]), _ptr(res["k_mean"]), _ptr(res["n_modes"]),
                                       int(n_shells)))
     return res
+
+
+def lpt2_schedule(plan: Plan):
+    """Instances per launch of each grid-size group of the plan (a list)."""
+    lib = load_library()
+    ng = C.c_int()
+    _check(lib.lpt2_schedule(plan.handle, None, 0, C.byref(ng)))
+    arr = (C.c_int * max(ng.value, 1))()
+    _check(lib.lpt2_schedule(plan.handle, arr, ng.value, C.byref(ng)))
+    return list(arr[: ng.value])
+
+
+def lpt2_set_schedule(plan: Plan, chunks):
+    arr = (C.c_int * len(chunks))(*[int(c) for c in chunks])
+    _check(load_library().lpt2_set_schedule(plan.handle, arr, len(chunks)))
+
+
+def lpt2_autotune(plan: Plan, n_shells=32, reps=3):
+    """Times each group's forward step at several instances-per-launch and keeps the
+    fastest; returns the chosen schedule."""
+    _check(load_library().lpt2_autotune(plan.handle, int(n_shells), int(reps)))
+    return lpt2_schedule(plan)
 
 
 def lpt2_set_outputs(plan: Plan, a_out):

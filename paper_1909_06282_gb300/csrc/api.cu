@@ -6,6 +6,7 @@
 #include <string.h>
 
 #include <string>
+#include <algorithm>
 #include <vector>
 
 #include "../../include/lpt2.h"
@@ -55,6 +56,7 @@ struct Group {
   double* geo_k;             // P(k) shell geometry for geo_ns shells: sum of |k| per shell
   unsigned long long* geo_n; // and mode count per shell [kMaxShells]
   int geo_ns;                // 0: not computed yet
+  int chunk = 0;             // instances per launch in lpt2_displace / lpt2_cic_pk (0: the whole group)
 };
 
 struct GraphCache {  // one captured launch sequence per entry point (LPT2_GRAPH)
@@ -83,6 +85,8 @@ struct lpt2_plan_s {
   const float4* mt0;
   const float2* mt1;
   int cur_batch, cur_inst0;
+  size_t cur_slot_off = 0;    // bytes into every workspace slot of the current instances (a chunk of a group)
+  size_t cur_rho_off = 0;     // floats into the density array of the current instances
   std::vector<Group> groups;
   int n_inst;
   uint64_t* seeds_dev;        // [n_inst]
@@ -142,7 +146,26 @@ void set_group(lpt2_plan_s* p, int gi) {
   p->mt1 = g.mt1;
   p->cur_batch = g.count;
   p->cur_inst0 = g.inst0;
+  p->cur_slot_off = 0;
+  p->cur_rho_off = g.off;
 }
+
+// Instances [c0, c0 + cnt) of group gi: the fields of a group's instances are consecutive
+// in every workspace slot (one N^3 real field, or half spectrum, per instance), so a chunk
+// is the group with offset slots, tables, seeds and density.
+void set_chunk(lpt2_plan_s* p, int gi, int c0, int cnt) {
+  set_group(p, gi);
+  const Group& g = p->groups[gi];
+  const size_t n3 = (size_t)g.n * g.n * g.n, len = (size_t)mode_table_len(g.n);
+  p->cur_batch = cnt;
+  p->cur_inst0 = g.inst0 + c0;
+  p->mt0 = g.mt0 + (size_t)c0 * len;
+  p->mt1 = g.mt1 + (size_t)c0 * len;
+  p->cur_slot_off = (size_t)c0 * n3 * sizeof(float);
+  p->cur_rho_off = g.off + (size_t)c0 * n3;
+}
+
+int chunk_of(const Group& g) { return g.chunk > 0 && g.chunk < g.count ? g.chunk : g.count; }
 
 int x_blocks(int n) {
   switch (n) {
@@ -164,10 +187,7 @@ int x_blocks(int n) {
 // CIC density of every instance (sum of n^3 floats) after the slots, then the tail.
 size_t rho_all_off(const lpt2_plan_s* p) { return N_SLOTS * slot_bytes(p); }
 float* rho_group(const lpt2_plan_s* p) {
-  const Group* g = nullptr;
-  for (const Group& x : p->groups)
-    if (x.inst0 == p->cur_inst0) g = &x;
-  return reinterpret_cast<float*>(p->ws + rho_all_off(p)) + (g ? g->off : 0);
+  return reinterpret_cast<float*>(p->ws + rho_all_off(p)) + p->cur_rho_off;
 }
 size_t tail_pk_part(const lpt2_plan_s* p) {
   return (rho_all_off(p) + p->total_cells * sizeof(float) + 255) / 256 * 256;
@@ -177,7 +197,9 @@ size_t tail_shw(const lpt2_plan_s* p) { return tail_pk(p) + 3 * kMaxShells * 8; 
 size_t tail_theta(const lpt2_plan_s* p) { return tail_shw(p) + kMaxShells * 4; }
 size_t ws_need(const lpt2_plan_s* p) { return tail_theta(p) + (size_t)p->xb_max * 8; }
 
-float2* slot(const lpt2_plan_s* p, int i) { return reinterpret_cast<float2*>(p->ws + i * slot_bytes(p)); }
+float2* slot(const lpt2_plan_s* p, int i) {
+  return reinterpret_cast<float2*>(p->ws + i * slot_bytes(p) + p->cur_slot_off);
+}
 double* pk_part(const lpt2_plan_s* p) { return reinterpret_cast<double*>(p->ws + tail_pk_part(p)); }
 
 Geo make_geo(const lpt2_plan_s* p) {
@@ -717,13 +739,18 @@ int lpt2_displace(lpt2_plan_t p, const float* noise, float* psi1, float* psi2, f
   if (dk && !aligned(dk, 16)) return fail(LPT2_EINVAL, "dk must be 16-byte aligned");
   auto body = [&]() -> int {
     for (int gi = 0; gi < (int)p->groups.size(); ++gi) {
-      set_group(p, gi);
-      const size_t off = p->groups[gi].off;   // real elements before the group
-      const int r = displace_impl(p, noise ? noise + off : nullptr, psi1 ? psi1 + 3 * off : nullptr,
-                                  psi2 ? psi2 + 3 * off : nullptr, pos ? pos + 3 * off : nullptr,
-                                  dk ? (char*)dk + off * sizeof(float) : nullptr, nullptr);
-      if (r) return r;
+      const Group& gr = p->groups[gi];
+      const size_t n3 = (size_t)gr.n * gr.n * gr.n;
+      for (int c0 = 0; c0 < gr.count; c0 += chunk_of(gr)) {
+        set_chunk(p, gi, c0, std::min(chunk_of(gr), gr.count - c0));
+        const size_t off = gr.off + (size_t)c0 * n3;   // real elements before the chunk
+        const int r = displace_impl(p, noise ? noise + off : nullptr, psi1 ? psi1 + 3 * off : nullptr,
+                                    psi2 ? psi2 + 3 * off : nullptr, pos ? pos + 3 * off : nullptr,
+                                    dk ? (char*)dk + off * sizeof(float) : nullptr, nullptr);
+        if (r) return r;
+      }
     }
+    set_group(p, 0);
     return LPT2_OK;
   };
   if (!p->use_graph) return body();
@@ -921,13 +948,19 @@ int lpt2_cic_pk(lpt2_plan_t p, const float* pos, float* density, double* pk, dou
   if (n_shells < 1 || n_shells > kMaxShells) return fail(LPT2_EINVAL, "n_shells must be in [1, 256]");
   auto body = [&]() -> int {
     for (int gi = 0; gi < (int)p->groups.size(); ++gi) {
-      set_group(p, gi);
       const Group& gr = p->groups[gi];
-      const int r = cic_pk_group(p, gi, pos ? pos + 3 * gr.off : nullptr, density ? density + gr.off : nullptr,
-                                 pk + (size_t)gr.inst0 * n_shells, k_mean ? k_mean + (size_t)gr.inst0 * n_shells : nullptr,
-                                 n_modes ? n_modes + (size_t)gr.inst0 * n_shells : nullptr, n_shells);
-      if (r) return r;
+      const size_t n3 = (size_t)gr.n * gr.n * gr.n;
+      for (int c0 = 0; c0 < gr.count; c0 += chunk_of(gr)) {
+        set_chunk(p, gi, c0, std::min(chunk_of(gr), gr.count - c0));
+        const size_t off = gr.off + (size_t)c0 * n3;
+        const size_t i0 = (size_t)gr.inst0 + c0;
+        const int r = cic_pk_group(p, gi, pos ? pos + 3 * off : nullptr, density ? density + off : nullptr,
+                                   pk + i0 * n_shells, k_mean ? k_mean + i0 * n_shells : nullptr,
+                                   n_modes ? n_modes + i0 * n_shells : nullptr, n_shells);
+        if (r) return r;
+      }
     }
+    set_group(p, 0);
     return LPT2_OK;
   };
   for (int gi = 0; gi < (int)p->groups.size(); ++gi) {
@@ -1079,6 +1112,94 @@ int lpt2_displace_outputs(lpt2_plan_t p, const float* noise, float* pos, double*
     if (rc) return rc;
   }
   return LPT2_OK;
+}
+
+// ------------------------------------------------------------ launch schedule
+int lpt2_schedule(lpt2_plan_t p, int* chunk, int max_groups, int* n_groups) {
+  if (!p || !n_groups) return fail(LPT2_EINVAL, "null argument");
+  *n_groups = (int)p->groups.size();
+  for (int gi = 0; gi < (int)p->groups.size() && gi < max_groups && chunk; ++gi) chunk[gi] = chunk_of(p->groups[gi]);
+  return LPT2_OK;
+}
+
+namespace {
+void drop_graphs(lpt2_plan_t p) {
+  for (auto& gc : p->graphs) {
+    if (gc.exec) cudaGraphExecDestroy(gc.exec);
+    gc.exec = nullptr;
+  }
+}
+}  // namespace
+
+int lpt2_set_schedule(lpt2_plan_t p, const int* chunk, int n_groups) {
+  if (!p || !chunk) return fail(LPT2_EINVAL, "null argument");
+  if (n_groups != (int)p->groups.size())
+    return fail(LPT2_EINVAL, "n_groups = %d, the plan has %d grid-size groups", n_groups, (int)p->groups.size());
+  for (int gi = 0; gi < n_groups; ++gi)
+    if (chunk[gi] < 1) return fail(LPT2_EINVAL, "chunk[%d] = %d: need >= 1", gi, chunk[gi]);
+  for (int gi = 0; gi < n_groups; ++gi) p->groups[gi].chunk = std::min(chunk[gi], p->groups[gi].count);
+  drop_graphs(p);
+  return LPT2_OK;
+}
+
+// Times every group's forward step (Philox noise, positions, CIC, P(k)) at chunk sizes
+// count, ceil(count/2), ceil(count/4), ..., 1 and keeps the fastest per group.
+int lpt2_autotune(lpt2_plan_t p, int n_shells, int reps) {
+  int rc = check_plan_ws(p);
+  if (rc) return rc;
+  if (n_shells < 1 || n_shells > kMaxShells) return fail(LPT2_EINVAL, "n_shells must be in [1, 256]");
+  if (reps < 1 || reps > 100) return fail(LPT2_EINVAL, "reps must be in [1, 100]");
+  double* pk = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t e = cudaMalloc(&pk, (size_t)p->n_inst * n_shells * sizeof(double));
+  if (e == cudaSuccess) e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  auto cleanup = [&]() {
+    cudaFree(pk);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    set_group(p, 0);
+  };
+  if (e != cudaSuccess) {
+    cleanup();
+    return fail(e == cudaErrorMemoryAllocation ? LPT2_ENOMEM : LPT2_ECUDA, "autotune: %s", cudaGetErrorString(e));
+  }
+  for (int gi = 0; gi < (int)p->groups.size() && !rc; ++gi) rc = ensure_geometry(p, gi, n_shells);
+  drop_graphs(p);
+  for (int gi = 0; gi < (int)p->groups.size() && !rc; ++gi) {
+    Group& gr = p->groups[gi];
+    auto step = [&]() -> int {
+      for (int c0 = 0; c0 < gr.count; c0 += chunk_of(gr)) {
+        set_chunk(p, gi, c0, std::min(chunk_of(gr), gr.count - c0));
+        int r = displace_impl(p, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr);
+        if (!r) r = cic_pk_group(p, gi, nullptr, nullptr, pk + ((size_t)gr.inst0 + c0) * n_shells, nullptr, nullptr,
+                                 n_shells);
+        if (r) return r;
+      }
+      return LPT2_OK;
+    };
+    int best = gr.count;
+    float best_ms = 0.f;
+    for (int c = gr.count, prev = 0; c != prev && !rc; prev = c, c = (c + 1) / 2) {
+      gr.chunk = c;
+      if ((rc = step())) break;   // warm-up
+      e = cudaEventRecord(e0, p->stream);
+      for (int k = 0; k < reps && !rc && e == cudaSuccess; ++k) rc = step();
+      if (e == cudaSuccess) e = cudaEventRecord(e1, p->stream);
+      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+      float ms = 0.f;
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+      if (e != cudaSuccess) rc = fail(LPT2_ECUDA, "autotune timing: %s", cudaGetErrorString(e));
+      if (!rc && (best_ms == 0.f || ms < best_ms)) {
+        best_ms = ms;
+        best = c;
+      }
+      if (c == 1) break;
+    }
+    gr.chunk = best;
+  }
+  cleanup();
+  return rc;
 }
 
 // P(k) estimator refinements: CIC window deconvolution and interlacing (see the header).
