@@ -20,7 +20,7 @@ namespace lpt2 {
 #define LPT2_Z_MINB 2   // minimum resident z-pass CTAs per SM (register cap)
 #endif
 #ifndef LPT2_W512
-#define LPT2_W512 16    // pencils per y/x CTA at N = 512
+#define LPT2_W512 8     // pencils per y/x CTA at N = 512 (measured: 8 beats 16 and 32)
 #endif
 
 template <int N> struct PassCfg {
@@ -33,6 +33,10 @@ template <int N> struct PassCfg {
   static constexpr int XT = TPP * W;                                  // y/x CTA threads
   static constexpr int ZSMEM = (N + ZP * SmemRow::words(N)) * 8;
   static constexpr int XSMEM = (N + N * W) * 8;
+  // resident x-pass CTAs per SM asked of the compiler: caps a thread at 128 registers for
+  // every CTA size (at 256 threads the multi-output modes would otherwise take 184 and
+  // halve the warps per SM)
+  static constexpr int XMINB = XT >= 512 ? 1 : 512 / XT;
 };
 
 // (i k)^m v for m = 0, 1, 2
@@ -663,9 +667,17 @@ __device__ __forceinline__ float warp_sum(float x) {
   return x;
 }
 
+// Minimum resident CTAs per SM for an x-pass mode: the one-transform shell-sum modes fit
+// in 64 registers a thread (twice the CTAs); the others are capped at 128.
+template <int N> constexpr int x_minb(int mode) {
+  return (mode == X_PK || mode == X_PKP)
+             ? (PassCfg<N>::XT >= 1024 ? 1 : 1024 / PassCfg<N>::XT)
+             : PassCfg<N>::XMINB;
+}
+
 // CTA = (kz block of W, fixed ky). Thread tid = t * W + w; kx = elem(t, r).
 template <int N, int MODE>
-__global__ void __launch_bounds__(PassCfg<N>::XT) k_x(XArgs a) {
+__global__ void __launch_bounds__(PassCfg<N>::XT, x_minb<N>(MODE)) k_x(XArgs a) {
   using C = PassCfg<N>;
   extern __shared__ float2 smem[];
   float2* s_tw = smem;
