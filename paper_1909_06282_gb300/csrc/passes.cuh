@@ -19,6 +19,9 @@ namespace lpt2 {
 #ifndef LPT2_Z_MINB
 #define LPT2_Z_MINB 2   // minimum resident z-pass CTAs per SM (register cap)
 #endif
+#ifndef LPT2_WSMALL
+#define LPT2_WSMALL 16  // pencils per y/x CTA for 32 <= N <= 256
+#endif
 #ifndef LPT2_W512
 #define LPT2_W512 8     // pencils per y/x CTA at N = 512 (measured: 8 beats 16 and 32)
 #endif
@@ -29,7 +32,7 @@ template <int N> struct PassCfg {
   static constexpr int H = N / 2;
   static constexpr int ZP = (256 / TPP) < 1 ? 1 : (256 / TPP);       // pencil pairs per z CTA
   static constexpr int ZT = ZP * TPP;                                 // z CTA threads
-  static constexpr int W = (N <= 16) ? 8 : (N >= 1024 ? 8 : (N == 512 ? LPT2_W512 : 16));       // pencils per y/x CTA
+  static constexpr int W = (N <= 16) ? 8 : (N >= 1024 ? 8 : (N == 512 ? LPT2_W512 : LPT2_WSMALL));   // pencils per y/x CTA
   static constexpr int XT = TPP * W;                                  // y/x CTA threads
   static constexpr int ZSMEM = (N + ZP * SmemRow::words(N)) * 8;
   static constexpr int XSMEM = (N + N * W) * 8;
