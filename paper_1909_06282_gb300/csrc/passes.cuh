@@ -16,8 +16,11 @@
 
 namespace lpt2 {
 
+#ifndef LPT2_ZTHREADS
+#define LPT2_ZTHREADS 256   // threads per z-pass CTA (pencil pairs per CTA = this / threads per pencil)
+#endif
 #ifndef LPT2_Z_MINB
-#define LPT2_Z_MINB 2   // minimum resident z-pass CTAs per SM (register cap)
+#define LPT2_Z_MINB (LPT2_ZTHREADS >= 512 ? 1 : 512 / LPT2_ZTHREADS)   // resident z-pass CTAs per SM asked: 128-register cap
 #endif
 #ifndef LPT2_WSMALL
 #define LPT2_WSMALL 16  // pencils per y/x CTA for 32 <= N <= 256
@@ -30,7 +33,7 @@ template <int N> struct PassCfg {
   static constexpr int RMAX = Cfg<N>::RMAX;
   static constexpr int TPP = N / RMAX;
   static constexpr int H = N / 2;
-  static constexpr int ZP = (256 / TPP) < 1 ? 1 : (256 / TPP);       // pencil pairs per z CTA
+  static constexpr int ZP = (LPT2_ZTHREADS / TPP) < 1 ? 1 : (LPT2_ZTHREADS / TPP);   // pencil pairs per z CTA
   static constexpr int ZT = ZP * TPP;                                 // z CTA threads
   static constexpr int W = (N <= 16) ? 8 : (N >= 1024 ? 8 : (N == 512 ? LPT2_W512 : LPT2_WSMALL));   // pencils per y/x CTA
   static constexpr int XT = TPP * W;                                  // y/x CTA threads
