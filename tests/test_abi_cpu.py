@@ -84,3 +84,16 @@ def test_null_pointers_rejected(lib):
     assert lib.lpt2_workspace_size(None, None) == -1
     assert lib.lpt2_philox_words(1, 0, 4, None, None) == -1
     assert lib.lpt2_plan_destroy(None) == 0
+
+
+def test_null_plan_rejected_by_the_newer_entry_points(lib):
+    """Host-buffer step, output times, launch schedule and autotuner refuse a null plan
+    before touching the device (no GPU needed)."""
+    ng = C.c_int(-1)
+    assert lib.lpt2_displace_host(None, 1, None, 0, None, 0, None, 0, 32) == -1
+    assert lib.lpt2_set_outputs(None, 1, (C.c_double * 1)(0.5)) == -1
+    assert lib.lpt2_displace_outputs(None, None, None, None, None, None, 32) == -1
+    assert lib.lpt2_schedule(None, None, 0, C.byref(ng)) == -1 and ng.value == -1
+    assert lib.lpt2_set_schedule(None, (C.c_int * 1)(1), 1) == -1
+    assert lib.lpt2_autotune(None, 32, 3) == -1
+    assert len(lib.lpt2_last_error()) > 0
