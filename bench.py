@@ -36,6 +36,14 @@ def workload_desc():
             f"{WORKLOAD['n_shells']}-shell P(k)")
 
 
+def workload_config(world):
+    """The `config` object of the JSON line; both arms report the same workload."""
+    return {"workload": workload_desc(), "grid": WORKLOAD["n"], "box_mpc_h": WORKLOAD["box"],
+            "fr0_abs": WORKLOAD["fr0"], "outputs": "positions, CIC density (in workspace), P(k)",
+            "l2": "inputs larger than L2 (every field 537 MB > 129 MB L2); no flush",
+            "parallelism": f"{world} independent realisation(s), one per GPU"}
+
+
 def dist_env():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -182,8 +190,8 @@ def bench_reference(args):
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": workload_desc(), "sample": f"{SAMPLE_N}^3 grid, L={SAMPLE_BOX:g} Mpc/h "
-                   "(same cell size), one realisation per step, growth tables precomputed"},
+        "config": dict(workload_config(world), sample=f"{SAMPLE_N}^3 grid, L={SAMPLE_BOX:g} Mpc/h "
+                       "(same cell size), one realisation per step, growth tables precomputed"),
         "cpu_baseline": {"value": value, "unit": "particles/s", "cores": 1, "kind": "oracle",
                          "sample": f"{SAMPLE_N}^3 sub-box at the workload's cell size, per step"},
         "e2e": {"value": value, "unit": "particles/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -619,10 +627,7 @@ def bench_ours(args):
             "metric": "particles_per_s", "value": value, "unit": "particles/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": workload_desc(), "grid": n, "box_mpc_h": box, "fr0_abs": WORKLOAD["fr0"],
-                       "outputs": "positions, CIC density (in workspace), P(k)",
-                       "l2": "inputs larger than L2 (every field 537 MB > 129 MB L2); no flush",
-                       "parallelism": f"{world} independent realisation(s), one per GPU"},
+            "config": workload_config(world),
             "roofline": {"bound": "hbm", "kernel": dname, "achieved": achieved, "peak": peak,
                          "peak_kind": f"hbm_gbs of {peak_kind}", "unit": "GB/s", "frac": achieved / peak,
                          "traffic": TRAFFIC_512.get(dname) if n == 512 else None,
