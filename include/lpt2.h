@@ -119,32 +119,39 @@ int lpt2_plan(lpt2_plan_t* out, const lpt2_instance* inst, int n_inst, int n_k,
               double k_min, double k_max, int n_steps, void* cuda_stream,
               unsigned flags);
 
+/* Frees the plan's device tables, captured graphs and the buffers made by
+ * lpt2_displace_host and lpt2_set_outputs (the caller's workspace stays the
+ * caller's).  NULL is a no-op.  Plan management: no counterpart in the paper. */
 int lpt2_plan_destroy(lpt2_plan_t plan);
 
 /* Bytes of caller-owned device scratch the plan needs: 21 slots of the largest
  * group (count N^3 floats each), the CIC density of every instance and small
- * per-block partial sums. */
+ * per-block partial sums.  Memory management: no counterpart in the paper. */
 int lpt2_workspace_size(lpt2_plan_t plan, size_t* bytes);
 
 /* Attach scratch: dev_ptr must be 256-byte aligned and >= lpt2_workspace_size
  * bytes; it must stay valid while calls using this plan are in flight. */
 int lpt2_set_workspace(lpt2_plan_t plan, void* dev_ptr, size_t bytes);
 
-/* lpt2_growth_tables: D1(k,a_out), D2(k,a_out) of the T1 configuration and
- * their derivatives with respect to ln|f_R0| (Eq. d1, Eq. full-d2 at k1 = k2 =
- * k/sqrt2, theta = 90 deg; D2 sign such that GR gives -3/7 D1^2), recomputed
+/* lpt2_growth_tables: D1(k,a_out), D2(k,a_out) of the plan's D2 variant (T1 by
+ * default) and their derivatives with respect to ln|f_R0| (Eq. d1, Eq. full-d2 at
+ * the variant's triangle, T1: k1 = k2 = k/sqrt2, theta = 90 deg; D2 sign such
+ * that GR gives -3/7 D1^2), recomputed
  * on the plan's stream by the batched FP64 RK4 kernel (one thread per
  * (instance, k)) and copied into the caller's device arrays double[n_inst][n_k]
  * (each pointer may be NULL). */
 int lpt2_growth_tables(lpt2_plan_t plan, double* d1, double* d2,
                        double* dd1_dlogf, double* dd2_dlogf);
 
-/* lpt2_white_noise: the unit Gaussian white noise the plan draws (Philox4x32-10
- * keyed by the seed, counter = flat cell index; Box-Muller on words 0 and 1),
+/* lpt2_white_noise: the unit Gaussian white noise the plan draws for the linear
+ * field of Sec. 3 (Philox4x32-10 of Salmon et al. 2011 keyed by the seed, counter
+ * = flat cell index; one Box-Muller transform of words 0 and 1 of the even cell
+ * (x, 2j, z) gives its cosine to that cell and its sine to (x, 2j+1, z)),
  * written to float[N^3]. */
 int lpt2_white_noise(lpt2_plan_t plan, float* noise);
 
-/* lpt2_philox_words: raw Philox4x32-10 output for counters (c, 0) with
+/* lpt2_philox_words: raw Philox4x32-10 output (Salmon et al. 2011; the generator
+ * behind lpt2_white_noise, exposed for bit-exact checks) for counters (c, 0) with
  * c in [first, first + count): uint32 out[count][4].  count <= 2^31. */
 int lpt2_philox_words(uint64_t seed, uint64_t first, int64_t count,
                       uint32_t* out, void* cuda_stream);
@@ -162,7 +169,8 @@ int lpt2_philox_words(uint64_t seed, uint64_t first, int64_t count,
 int lpt2_displace(lpt2_plan_t plan, const float* noise, float* psi1, float* psi2,
                   float* pos, void* dk);
 
-/* lpt2_cic_pk: cloud-in-cell density contrast of N^3 unit-mass particles and
+/* lpt2_cic_pk (Sec. 4, the power-spectrum comparison, here of the matter field):
+ * cloud-in-cell density contrast of N^3 unit-mass particles and
  * its power spectrum P(k) = V |delta(k)|^2 / N^6 averaged over n_shells linear
  * shells of width k_Ny / n_shells in [0, k_Ny) (DC excluded).
  *   pos     : float[3][N^3] positions in [0, L), or NULL to use the density
@@ -216,7 +224,8 @@ int lpt2_displace_host(lpt2_plan_t plan, int n_real, const float* noise_h, int64
  * Errors: LPT2_EUNSUPPORTED for a batched plan, LPT2_EINVAL for a bad list, LPT2_ENOMEM. */
 int lpt2_set_outputs(lpt2_plan_t plan, int n_a, const double* a_out);
 
-/* lpt2_displace_outputs: one realisation at every output scale factor of
+/* lpt2_displace_outputs (Sec. 2.4, the time dependence through D1(k,a), D2(k,a)):
+ * one realisation at every output scale factor of
  * lpt2_set_outputs (device pointers):
  *   noise    float[N^3] white noise, or NULL for the plan's Philox noise
  *   pos      float[n_a][3][N^3] positions in [0, L) at a_j, or NULL
@@ -253,7 +262,8 @@ int lpt2_schedule(lpt2_plan_t plan, int* chunk, int max_groups, int* n_groups);
 int lpt2_set_schedule(lpt2_plan_t plan, const int* chunk, int n_groups);
 int lpt2_autotune(lpt2_plan_t plan, int n_shells, int reps);
 
-/* lpt2_set_fr0: change |f_R0| of the plan and recompute its growth tables
+/* lpt2_set_fr0: change |f_R0| of the plan (it enters Eq. d1 and Eq. full-d2
+ * through m^2(a) and M2(a), Eq. mihusawicki) and recompute its growth tables
  * (the FP64 RK4 kernel) on the plan's stream.  fr0_abs >= 0 (0 = GR). */
 int lpt2_set_fr0(lpt2_plan_t plan, double fr0_abs);
 
@@ -314,7 +324,8 @@ int lpt2_cic_pk_est(lpt2_plan_t plan, const float* pos, float* density, double* 
 int lpt2_source_ratio(lpt2_plan_t plan, const float* noise, int n_bins, double* mean, double* sigma,
                       int64_t* count, double* t1, double* k_mean, void* s_mg, void* s_gr);
 
-/* lpt2_fft_r2c: forward 3-D transform of a real field (unnormalised,
+/* The path's three-pass transforms on their own (no counterpart in the paper).
+ * lpt2_fft_r2c: forward 3-D transform of a real field (unnormalised,
  * exp(-i k.x)) into the half spectrum; in and out may not alias.
  * lpt2_fft_c2r: inverse (exp(+i k.x), unnormalised: the result is N^3 times the
  * inverse DFT), treating the missing kz = N/2 plane as zero.  `in` is not
@@ -322,7 +333,8 @@ int lpt2_source_ratio(lpt2_plan_t plan, const float* noise, int n_bins, double* 
 int lpt2_fft_r2c(lpt2_plan_t plan, const float* in, void* out);
 int lpt2_fft_c2r(lpt2_plan_t plan, const void* in, float* out);
 
-/* Per-kernel timing.  lpt2_timing(plan, 1) clears the record and brackets each
+/* Per-kernel timing (instrumentation; no counterpart in the paper).
+ * lpt2_timing(plan, 1) clears the record and brackets each
  * later kernel launch of this plan with CUDA events on the plan's stream (up to
  * 4096 launches); lpt2_timing(plan, 0) stops recording.  lpt2_timing_report
  * waits for the recorded events and aggregates them by kernel name: launches,
@@ -362,10 +374,12 @@ int lpt2_timing_report(lpt2_plan_t plan, lpt2_kernel_stat* out, int max, int* n_
 int lpt2_cic_pk_noalloc(int n, double box, const float* pos, float* density, double* pk,
                         double* k_mean, int64_t* n_modes, int n_shells, void* cuda_stream);
 
-/* Message of the last failing call on this thread ("" if none). */
+/* Message of the last failing call on this thread ("" if none); error reporting,
+ * no counterpart in the paper. */
 const char* lpt2_last_error(void);
 
-/* Number of kernel launches issued by this plan since creation (counter kept on
+/* Instrumentation, no counterpart in the paper: the number of kernel launches
+ * issued by this plan since creation (counter kept on
  * the host; used to report launch counts). */
 int64_t lpt2_launch_count(lpt2_plan_t plan);
 
