@@ -22,7 +22,8 @@ import numpy as np
 H0_OVER_C = 1.0 / 2997.92458
 
 __all__ = ["H0_OVER_C", "E2", "omega_m_a", "four_pi_g_rho", "m2", "M2", "Pi", "mu",
-           "eh_nowiggle_T", "pk_shape", "sigma_r_sq", "pk_amplitude", "pk_linear"]
+           "eh_sound_horizon", "eh_alpha_gamma", "eh_gamma_eff", "eh_T0", "eh_nowiggle_T", "pk_shape",
+           "sigma_r_sq", "pk_amplitude", "pk_linear"]
 
 
 def E2(c, a):
@@ -65,22 +66,44 @@ def mu(c, k, a):
     return 1.0 + q / (3.0 * (q + m2(c, a)))
 
 
-def eh_nowiggle_T(c, k):
-    """Eisenstein & Hu (1998) no-wiggle transfer function T0(k), k in h/Mpc."""
-    k = np.asarray(k, dtype=np.float64)
-    h = c.h
-    wm = c.omega_m * h * h
-    wb = c.omega_b * h * h
+def eh_sound_horizon(c):
+    """Sound horizon fit s (Mpc, not Mpc/h) of Eisenstein & Hu (1998) Eq. 26."""
+    wm = c.omega_m * c.h * c.h
+    wb = c.omega_b * c.h * c.h
+    return 44.5 * np.log(9.83 / wm) / np.sqrt(1.0 + 10.0 * wb ** 0.75)
+
+
+def eh_alpha_gamma(c):
+    """Small-scale baryon suppression alpha_Gamma of Eisenstein & Hu (1998) Eq. 31."""
+    wm = c.omega_m * c.h * c.h
     fb = c.omega_b / c.omega_m
-    theta = c.t_cmb / 2.7
-    s = 44.5 * np.log(9.83 / wm) / np.sqrt(1.0 + 10.0 * wb ** 0.75)          # Mpc, Eq. 26
-    alpha = 1.0 - 0.328 * np.log(431.0 * wm) * fb + 0.38 * np.log(22.3 * wm) * fb * fb  # Eq. 31
-    k_mpc = k * h
-    gamma = c.omega_m * h * (alpha + (1.0 - alpha) / (1.0 + (0.43 * k_mpc * s) ** 4))  # Eq. 30
-    q = k * theta * theta / gamma                                             # Eq. 28
-    L0 = np.log(2.0 * np.e + 1.8 * q)                                         # Eq. 29
+    return 1.0 - 0.328 * np.log(431.0 * wm) * fb + 0.38 * np.log(22.3 * wm) * fb * fb
+
+
+def eh_gamma_eff(c, k):
+    """Effective shape Gamma_eff(k) of Eisenstein & Hu (1998) Eq. 30, k in h/Mpc.
+
+    The equation is written for k in Mpc^-1 (s is in Mpc): k_mpc = k h."""
+    k = np.asarray(k, dtype=np.float64)
+    alpha = eh_alpha_gamma(c)
+    k_mpc = k * c.h
+    return c.omega_m * c.h * (alpha + (1.0 - alpha) / (1.0 + (0.43 * k_mpc * eh_sound_horizon(c)) ** 4))
+
+
+def eh_T0(q):
+    """Zero-baryon transfer function of Eisenstein & Hu (1998) Eq. 29 at their q (Eq. 28)."""
+    q = np.asarray(q, dtype=np.float64)
+    L0 = np.log(2.0 * np.e + 1.8 * q)
     C0 = 14.2 + 731.0 / (1.0 + 62.5 * q)
     return L0 / (L0 + C0 * q * q)
+
+
+def eh_nowiggle_T(c, k):
+    """Eisenstein & Hu (1998) no-wiggle transfer function T0(k), k in h/Mpc (Eqs. 26, 28-31)."""
+    k = np.asarray(k, dtype=np.float64)
+    theta = c.t_cmb / 2.7
+    q = k * theta * theta / eh_gamma_eff(c, k)                                # Eq. 28
+    return eh_T0(q)
 
 
 def pk_shape(c, k):
