@@ -3,13 +3,14 @@
 // of fixed size (grids up to kNoAllocMaxN per side); the caller passes only
 // inputs and outputs.  The array is part of the library image, so every GPU
 // that loads the library holds it until the process exits.
+#include <cuda.h>   // CUcontext / CUresult types only; the driver calls are resolved at run time
 #include <math.h>
 
 #include <mutex>
 #include <string>
 
 #include "../../include/lpt2.h"
-#include "passes.h"
+#include "passes.cuh"
 
 using namespace lpt2;
 
@@ -18,8 +19,12 @@ namespace {
 constexpr int kNoAllocMaxN = 128;
 constexpr int kMaxShells = 256;
 constexpr size_t kGrid = (size_t)kNoAllocMaxN * kNoAllocMaxN * kNoAllocMaxN;
-// x-pass blocks for the largest grid: (N/2 / 16 kz per block) * N
-constexpr size_t kMaxXBlocks = (kNoAllocMaxN / 2 / 16) * kNoAllocMaxN;
+// x-pass blocks of a grid: (N/2 kz / W kz per block) * N, with W the pencils per CTA of this
+// build (a tuning macro); the partial-sum region is sized for the largest of the four grids
+template <int N> constexpr size_t xblocks_of() { return (size_t)(PassCfg<N>::H / PassCfg<N>::W) * N; }
+constexpr size_t cmax(size_t a, size_t b) { return a > b ? a : b; }
+constexpr size_t kMaxXBlocks =
+    cmax(cmax(xblocks_of<16>(), xblocks_of<32>()), cmax(xblocks_of<64>(), xblocks_of<128>()));
 constexpr size_t kRhoOff = 0;                                        // float[N^3]
 constexpr size_t kSpecOff = kRhoOff + kGrid * sizeof(float);         // float2[N^3/2]
 constexpr size_t kPartOff = kSpecOff + kGrid * sizeof(float);        // double[blocks][3][256]
@@ -37,8 +42,41 @@ static __device__ __align__(256) unsigned char g_lpt2_noalloc_scratch[kScratchBy
 
 namespace {
 
+// Device address of the scratch per device ordinal, valid for the context it was looked up
+// in: after cudaDeviceReset (or a release of the primary context) the library image is loaded
+// again into a new context and the address must be looked up again, so each entry records
+// the unique id of its context.
+struct ScratchAddr {
+  unsigned long long ctx_id = 0;
+  void* ptr = nullptr;
+};
 std::mutex g_mu;
-void* g_dev_ptr[128] = {};   // device address of the scratch, per device ordinal
+ScratchAddr g_addr[128];
+
+typedef CUresult (*PfnCtxGetCurrent)(CUcontext*);
+typedef CUresult (*PfnCtxGetId)(CUcontext, unsigned long long*);
+
+// Unique id of the calling thread's current context (0 if none is current yet).
+int current_ctx_id(unsigned long long* id) {
+  static PfnCtxGetCurrent get_current = nullptr;
+  static PfnCtxGetId get_id = nullptr;
+  if (!get_current || !get_id) {
+    void* f1 = nullptr;
+    void* f2 = nullptr;
+    cudaDriverEntryPointQueryResult q1, q2;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1) != cudaSuccess ||
+        cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2) != cudaSuccess ||
+        q1 != cudaDriverEntryPointSuccess || q2 != cudaDriverEntryPointSuccess || !f1 || !f2)
+      return -1;
+    get_current = (PfnCtxGetCurrent)f1;
+    get_id = (PfnCtxGetId)f2;
+  }
+  CUcontext ctx = nullptr;
+  if (get_current(&ctx) != CUDA_SUCCESS) return -1;
+  *id = 0;
+  if (ctx && get_id(ctx, id) != CUDA_SUCCESS) return -1;
+  return 0;
+}
 
 int fail(int code, const std::string& msg) {
   set_last_error(msg);   // reported by lpt2_last_error()
@@ -102,7 +140,12 @@ extern "C" int lpt2_cic_pk_noalloc(int n, double box, const float* pos, float* d
     return fail(LPT2_EINVAL, "lpt2_cic_pk_noalloc: misaligned pointer");
   cudaStream_t s = (cudaStream_t)cuda_stream;
 
-  // One-time set-up per device: the scratch symbol's device address.
+  // the shell partial sums of the P(k) pass must fit their region of the scratch
+  if ((size_t)xblocks_n(n) * 3 * n_shells > kMaxXBlocks * 3 * kMaxShells)
+    return fail(LPT2_EUNSUPPORTED, "lpt2_cic_pk_noalloc: shell partial sums exceed the static scratch");
+
+  // Set-up once per device (and again if the device's context was re-created): the
+  // scratch symbol's device address, looked up with that device current.
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return fail(LPT2_ECUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
@@ -110,14 +153,19 @@ extern "C" int lpt2_cic_pk_noalloc(int n, double box, const float* pos, float* d
   char* base = nullptr;
   {
     std::lock_guard<std::mutex> lk(g_mu);
-    if (!g_dev_ptr[dev]) {
+    unsigned long long ctx = 0;
+    if (current_ctx_id(&ctx)) return fail(LPT2_ECUDA, "lpt2_cic_pk_noalloc: cannot read the current context");
+    if (!g_addr[dev].ptr || ctx == 0 || ctx != g_addr[dev].ctx_id) {
       void* p = nullptr;
-      e = cudaGetSymbolAddress(&p, g_lpt2_noalloc_scratch);
+      e = cudaGetSymbolAddress(&p, g_lpt2_noalloc_scratch);   // makes the device's context current
       if (e != cudaSuccess)
         return fail(LPT2_ECUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
-      g_dev_ptr[dev] = p;
+      if (current_ctx_id(&ctx) || ctx == 0)
+        return fail(LPT2_ECUDA, "lpt2_cic_pk_noalloc: no current context after the set-up");
+      g_addr[dev].ptr = p;
+      g_addr[dev].ctx_id = ctx;
     }
-    base = (char*)g_dev_ptr[dev];
+    base = (char*)g_addr[dev].ptr;
   }
   float* rho = reinterpret_cast<float*>(base + kRhoOff);
   float2* spec = reinterpret_cast<float2*>(base + kSpecOff);
@@ -137,6 +185,7 @@ extern "C" int lpt2_cic_pk_noalloc(int n, double box, const float* pos, float* d
   g.batch = 1;        // one grid per call
   g.inst0 = 0;
   g.tab_stride = 0;
+  g.wait = LPT2_WAIT_CYCLES;   // none of these passes waits on a barrier
   const size_t n3 = (size_t)n * n * n;
 
 #define NA_CHECK(expr)                                                                     \
