@@ -441,7 +441,7 @@ def bench_ours(args):
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
         t0 = time.perf_counter()
-        plan = L.Plan(inst, n_steps=1024, stream=stream)
+        plan = L.Plan(inst, n_steps=1024, stream=stream, host_io=True, max_outputs=3)
         g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         g0.record(stream)
         L.lpt2_growth_tables(plan)
@@ -463,7 +463,6 @@ def bench_ours(args):
             dist.barrier()
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        L.lpt2_timing(plan, True)
         c0 = L.lpt2_launch_count(plan)
         with ClockSampler(local) as clk:
             e0.record(stream)
@@ -472,10 +471,16 @@ def bench_ours(args):
             e1.record(stream)
             stream.synchronize()
         launches = L.lpt2_launch_count(plan) - c0
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / args.steps
+        # the per-kernel split (CUDA events around every launch) comes from a second run of
+        # the same steps, so that the headline above is timed without that instrumentation
+        L.lpt2_timing(plan, True)
+        for _ in range(args.steps):
+            step()
         kstats = L.lpt2_timing_report(plan)
         L.lpt2_timing(plan, False)
         torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1) / args.steps
 
         # forward + adjoint (loss: mean squared density difference to the seed-7 field
         # plus the squared log P(k) ratio; cotangents formed by torch on the device)

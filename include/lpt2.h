@@ -11,13 +11,17 @@
  * exception crosses this boundary.
  *
  * Memory: all field pointers are DEVICE pointers owned by the caller.  The
- * plan owns only small tables (twiddles, growth tables, cosmology constants).
- * Large scratch ("workspace") is caller-owned too: query lpt2_workspace_size()
- * and hand a device buffer to lpt2_set_workspace() before lpt2_displace /
- * lpt2_cic_pk / lpt2_displace_vjp / lpt2_fft_*.  No call after lpt2_plan
- * allocates device memory.  All launches go to the stream given to lpt2_plan
- * and are asynchronous with respect to the host; results are ready after the
- * caller synchronises that stream.
+ * plan owns only small tables (twiddles, growth tables, cosmology constants,
+ * Box-Muller tables), allocated by lpt2_plan.  Large scratch ("workspace") is
+ * caller-owned too: query lpt2_workspace_size() (or, before making the plan,
+ * lpt2_workspace_bytes()) and hand a device buffer to lpt2_set_workspace()
+ * before lpt2_displace / lpt2_cic_pk / lpt2_displace_vjp / lpt2_fft_* and the
+ * other calls that say they need it.  The device buffers of lpt2_displace_host
+ * (plan flag LPT2_HOST_IO) and the tables of the output times of
+ * lpt2_set_outputs (plan flag LPT2_MAX_OUTPUTS(n)) are part of that workspace.
+ * No call after lpt2_plan allocates device memory.  All launches go to the
+ * stream given to lpt2_plan and are asynchronous with respect to the host;
+ * results are ready after the caller synchronises that stream.
  *
  * Layouts.  Grid side N (16, 32, 64, 96, 128, 192, 256, 512 or 1024), box side L in
  * Mpc/h.  A real field is float[N][N][N] (x, y, z; z fastest), cell (ix,iy,iz)
@@ -51,10 +55,17 @@ enum {
 
 /* Plan flags. */
 enum {
-  LPT2_GRAPH = 1  /* capture lpt2_displace / lpt2_cic_pk into CUDA graphs on first use and
-                     replay them while the argument pointers stay the same (needs a stream
-                     other than the legacy default stream) */
+  LPT2_GRAPH = 1,   /* capture lpt2_displace / lpt2_cic_pk into CUDA graphs on first use and
+                       replay them while the argument pointers stay the same (needs a stream
+                       other than the legacy default stream) */
+  LPT2_HOST_IO = 2  /* single-instance plans: the workspace also holds the two device buffer
+                       sets of lpt2_displace_host (each N^3 + 3 N^3 floats + 256 doubles) and
+                       the plan makes its two copy streams */
 };
+/* Single-instance plans: room in the workspace for the tables of up to n (<= 64) output
+ * scale factors of lpt2_set_outputs (per output: growth tables 4 n_k doubles and floats,
+ * multiplier tables (3 (N/2)^2 + 1) x 24 bytes).  Or it with the other flags. */
+#define LPT2_MAX_OUTPUTS(n) (((unsigned)(n) & 0xffu) << 8)
 
 /* D2 variants: the triangle configuration (k1, k2, angle theta between the vectors k1 and
  * k2, |k1 + k2| = k) at which the second-order growth of Eq. full-d2 is solved (Sec. 3,
@@ -107,7 +118,8 @@ typedef struct lpt2_plan_s* lpt2_plan_t;
  * as one batch (every pass kernel covers all its instances).  Per-instance
  * arrays of the other calls are the instances' arrays concatenated in plan
  * order.  cuda_stream is a cudaStream_t (NULL = legacy default stream).  flags:
- * 0 or LPT2_GRAPH.  Allocates the plan's small device tables and computes the
+ * 0 or an or of LPT2_GRAPH, LPT2_HOST_IO and LPT2_MAX_OUTPUTS(n) (the last two for
+ * single-instance plans only).  Allocates the plan's small device tables and computes the
  * P(k) normalisation (sigma_8) and the growth tables on the stream.  Errors:
  * LPT2_EINVAL (null pointers, n_k < 2, k_min <= 0, k_max <= k_min, box <= 0,
  * a range, non-flat cosmology, fr0_abs < 0, n_steps < 1, instance ordering or
@@ -119,15 +131,23 @@ int lpt2_plan(lpt2_plan_t* out, const lpt2_instance* inst, int n_inst, int n_k,
               double k_min, double k_max, int n_steps, void* cuda_stream,
               unsigned flags);
 
-/* Frees the plan's device tables, captured graphs and the buffers made by
- * lpt2_displace_host and lpt2_set_outputs (the caller's workspace stays the
- * caller's).  NULL is a no-op.  Plan management: no counterpart in the paper. */
+/* Frees the plan's device tables, captured graphs, streams and events (the caller's
+ * workspace stays the caller's).  NULL is a no-op.  Plan management: no counterpart
+ * in the paper. */
 int lpt2_plan_destroy(lpt2_plan_t plan);
 
 /* Bytes of caller-owned device scratch the plan needs: 21 slots of the largest
- * group (count N^3 floats each), the CIC density of every instance and small
- * per-block partial sums.  Memory management: no counterpart in the paper. */
+ * group (count N^3 floats each), the CIC density of every instance, small
+ * per-block partial sums and a P(k) per instance, plus the LPT2_HOST_IO buffer
+ * sets and the LPT2_MAX_OUTPUTS tables when the plan has those flags.  Memory
+ * management: no counterpart in the paper. */
 int lpt2_workspace_size(lpt2_plan_t plan, size_t* bytes);
+
+/* lpt2_workspace_bytes: the same number for a plan not made yet (the arguments of
+ * lpt2_plan that decide it), computed on the host without touching a GPU, so that a
+ * caller can reserve the memory first.  Errors as lpt2_plan's host-side checks
+ * (LPT2_EINVAL, LPT2_EUNSUPPORTED).  No counterpart in the paper. */
+int lpt2_workspace_bytes(const lpt2_instance* inst, int n_inst, int n_k, unsigned flags, size_t* bytes);
 
 /* Attach scratch: dev_ptr must be 256-byte aligned and >= lpt2_workspace_size
  * bytes; it must stay valid while calls using this plan are in flight. */
@@ -146,9 +166,21 @@ int lpt2_growth_tables(lpt2_plan_t plan, double* d1, double* d2,
 /* lpt2_white_noise: the unit Gaussian white noise the plan draws for the linear
  * field of Sec. 3 (Philox4x32-10 of Salmon et al. 2011 keyed by the seed, counter
  * = flat cell index; one Box-Muller transform of words 0 and 1 of the even cell
- * (x, 2j, z) gives its cosine to that cell and its sine to (x, 2j+1, z)),
- * written to float[N^3]. */
+ * (x, 2j, z) gives its cosine to that cell and its sine to (x, 2j+1, z); each value
+ * rounded once to FP32 as in lpt2_box_muller), written to float[N^3]. */
 int lpt2_white_noise(lpt2_plan_t plan, float* noise);
+
+/* lpt2_box_muller: the Box-Muller transform behind lpt2_white_noise applied to given Philox
+ * word pairs (Sec. 3's Gaussian white noise; exposed so that the transform can be checked on
+ * chosen words, e.g. u0 = 1, u0 = 2^-24 and the quadrant boundaries of the angle):
+ *   words  device uint32[count][2] = (x0, x1)
+ *   out    device float[count][2] = sqrt(-2 ln u0) (cos, sin)(2 pi u1), u_j = ((x_j >> 8) + 1) 2^-24,
+ *          each evaluated in float-float arithmetic (relative error below about 2^-44) and rounded
+ *          once to FP32, so it equals the correctly rounded value except within that distance of a
+ *          rounding midpoint
+ * Runs on the plan's stream (the plan holds the transform's tables).  0 <= count <= 2^31; both
+ * pointers 8-byte aligned.  LPT2_EINVAL otherwise. */
+int lpt2_box_muller(lpt2_plan_t plan, const uint32_t* words, int64_t count, float* out);
 
 /* lpt2_philox_words: raw Philox4x32-10 output (Salmon et al. 2011; the generator
  * behind lpt2_white_noise, exposed for bit-exact checks) for counters (c, 0) with
@@ -195,16 +227,16 @@ int lpt2_cic_pk(lpt2_plan_t plan, const float* pos, float* density, double* pk,
  * otherwise a stride is at least one realisation's size.  The steps are pipelined:
  * while realisation r computes on the plan's stream, the upload of r + 1 and the
  * download of r - 1 (and of r's positions, during r's P(k)) run on two copy streams of
- * the plan, through two device buffer sets that the plan allocates on the first call
- * (4 N^3 floats each, kept until lpt2_plan_destroy).  Page-locked host buffers
+ * the plan, through two device buffer sets in the caller's workspace (the plan must be made
+ * with LPT2_HOST_IO; 4 N^3 floats + 256 doubles each).  Page-locked host buffers
  * (cudaHostAlloc, cudaHostRegister) let the copies overlap the kernels; pageable ones
  * give the same results with less overlap.  The call returns when every result is in
  * host memory.  It synchronises, so it cannot be captured in a CUDA graph; the plan's
  * lpt2_displace / lpt2_cic_pk graphs are not used.  Needs the workspace.
- * Errors: LPT2_EUNSUPPORTED for a batched plan; LPT2_EINVAL for n_real < 1, n_shells
- * outside [1, 256], pos_h and pk_h both NULL, or a too-small non-zero stride;
- * LPT2_ENOMEM if the buffer sets cannot be allocated; LPT2_ECUDA from a copy or launch
- * (the call still waits for everything it queued before returning). */
+ * Errors: LPT2_EUNSUPPORTED for a batched plan; LPT2_EINVAL for a plan made without
+ * LPT2_HOST_IO, n_real < 1, n_shells outside [1, 256], pos_h and pk_h both NULL, or a
+ * too-small non-zero stride; LPT2_ECUDA from a copy or launch (the call still waits for
+ * everything it queued before returning). */
 int lpt2_displace_host(lpt2_plan_t plan, int n_real, const float* noise_h, int64_t noise_stride,
                        float* pos_h, int64_t pos_stride, double* pk_h, int64_t pk_stride, int n_shells);
 
@@ -220,8 +252,10 @@ int lpt2_displace_host(lpt2_plan_t plan, int n_real, const float* noise_h, int64
  * (a_init, 1], any order, 1 <= n_a <= 64) of a single-instance plan.  Computes and
  * keeps, per a_j, the FP64 RK4 growth tables from a_init to a_j (the plan's k table,
  * step count, cosmology and D2 variant) and the per-|n|^2 multiplier tables, on the
- * plan's stream; lpt2_set_fr0 refreshes them.  Replaces an earlier list.
- * Errors: LPT2_EUNSUPPORTED for a batched plan, LPT2_EINVAL for a bad list, LPT2_ENOMEM. */
+ * plan's stream, in the caller's workspace (room for n_a of them: plan flag
+ * LPT2_MAX_OUTPUTS(n) with n >= n_a); lpt2_set_fr0 and lpt2_set_workspace recompute them.
+ * Replaces an earlier list.  Errors: LPT2_EUNSUPPORTED for a batched plan, LPT2_EINVAL for
+ * a bad list or n_a above the plan's LPT2_MAX_OUTPUTS, LPT2_ENOWORKSPACE. */
 int lpt2_set_outputs(lpt2_plan_t plan, int n_a, const double* a_out);
 
 /* lpt2_displace_outputs (Sec. 2.4, the time dependence through D1(k,a), D2(k,a)):
@@ -254,10 +288,10 @@ int lpt2_displace_outputs(lpt2_plan_t plan, const float* noise, float* pos, doub
  * lpt2_autotune: times every group's forward step (Philox noise -> positions -> CIC ->
  * n_shells-shell P(k)) on the plan's stream at chunk sizes count, ceil(count/2), ..., 1,
  * `reps` timed repetitions after one warm-up each, keeps the fastest per group, and drops
- * the captured graphs.  Plan-time work: it synchronises, allocates a small P(k) buffer
- * (cudaMalloc) and overwrites the workspace; not capturable.  Needs the workspace.
+ * the captured graphs.  Plan-time work: it synchronises and overwrites the workspace;
+ * not capturable.  Needs the workspace.
  * Errors: LPT2_EINVAL (bad count, chunk, n_shells, or reps outside [1, 100]),
- * LPT2_ENOMEM, LPT2_ECUDA. */
+ * LPT2_ECUDA. */
 int lpt2_schedule(lpt2_plan_t plan, int* chunk, int max_groups, int* n_groups);
 int lpt2_set_schedule(lpt2_plan_t plan, const int* chunk, int n_groups);
 int lpt2_autotune(lpt2_plan_t plan, int n_shells, int reps);
@@ -374,6 +408,14 @@ int lpt2_timing_report(lpt2_plan_t plan, lpt2_kernel_stat* out, int max, int* n_
 int lpt2_cic_pk_noalloc(int n, double box, const float* pos, float* density, double* pk,
                         double* k_mean, int64_t* n_modes, int n_shells, void* cuda_stream);
 
+/* Test hook for the allocation-failure paths (no counterpart in the paper).  Every device
+ * allocation of the library is made by lpt2_plan.  With fail_at = k >= 0 the k-th allocation
+ * after this call (counting from 0, over all plans and threads) fails as if the device were out
+ * of memory; fail_at = -1 turns the failure off.  *live (if not NULL) receives the number of
+ * device allocations of the library that are currently live, so that a test can check that a
+ * failed lpt2_plan freed everything it had allocated.  Not for concurrent use with other plans. */
+int lpt2_debug_alloc_hook(int fail_at, int64_t* live);
+
 /* Message of the last failing call on this thread ("" if none); error reporting,
  * no counterpart in the paper. */
 const char* lpt2_last_error(void);
@@ -383,9 +425,19 @@ const char* lpt2_last_error(void);
  * the host; used to report launch counts). */
 int64_t lpt2_launch_count(lpt2_plan_t plan);
 
+/* lpt2_set_wait_budget: the cycle budget of the plan's bounded device-side waits on its
+ * bulk-copy rings (default 2e9 SM cycles, about one second), for its later launches.  A
+ * CTA whose wait runs out waits (with the default budget) for its own copies in flight,
+ * sets the plan's device error word and returns; lpt2_device_status then reports
+ * LPT2_ETIMEOUT.  cycles = 0 makes every such wait give up at once without looking at its
+ * barrier, which is how the timeout path is exercised (the copies themselves complete).
+ * cycles < 0: LPT2_EINVAL.  Failure detection: no counterpart in the paper. */
+int lpt2_set_wait_budget(lpt2_plan_t plan, int64_t cycles);
+
 /* Waits for the plan's stream and reads the plan's device error word.  Kernels that
  * stage data with bulk asynchronous copies wait on them with a bounded wait (about
- * one second); a wait that runs out makes its CTA return early and sets the word.
+ * one second, lpt2_set_wait_budget); a wait that runs out makes its CTA return early
+ * and sets the word.
  * Returns LPT2_OK, or LPT2_ETIMEOUT (the word is then cleared and the outputs of
  * every launch since the previous check are invalid), or LPT2_ECUDA.  Not part of
  * the paper's method: a run-time health check of the asynchronous launches. */

@@ -20,7 +20,7 @@ from __future__ import annotations
 
 import numpy as np
 
-__all__ = ["philox4x32_10", "uniforms", "gaussian_noise", "MULT", "WEYL"]
+__all__ = ["philox4x32_10", "uniforms", "box_muller", "gaussian_noise", "MULT", "WEYL"]
 
 MULT = (0xD2511F53, 0xCD9E8D57)   # round multipliers (Salmon et al. 2011)
 WEYL = (0x9E3779B9, 0xBB67AE85)   # key schedule increments (Salmon et al. 2011)
@@ -61,6 +61,13 @@ def uniforms(x: np.ndarray) -> np.ndarray:
     return ((x.astype(np.uint64) >> np.uint64(8)) + np.uint64(1)).astype(np.float64) * 2.0 ** -24
 
 
+def box_muller(x0: np.ndarray, x1: np.ndarray):
+    """(g_even, g_odd) = sqrt(-2 ln u0) (cos, sin)(2 pi u1) in float64 for words x0, x1."""
+    u0, u1 = uniforms(x0), uniforms(x1)
+    r = np.sqrt(-2.0 * np.log(u0))
+    return r * np.cos(2.0 * np.pi * u1), r * np.sin(2.0 * np.pi * u1)
+
+
 def gaussian_noise(n: int, seed: int, first: int = 0, count: int | None = None,
                    as_float64: bool = False) -> np.ndarray:
     """Unit-variance Gaussian per cell via Box-Muller on Philox words 0 and 1 of the
@@ -74,7 +81,6 @@ def gaussian_noise(n: int, seed: int, first: int = 0, count: int | None = None,
     ctr = (base & _M32, base >> np.uint64(32), np.zeros_like(base), np.zeros_like(base))
     key = (seed & 0xFFFFFFFF, (seed >> 32) & 0xFFFFFFFF)
     x0, x1, _, _ = philox4x32_10(ctr, key)
-    u0, u1 = uniforms(x0), uniforms(x1)
-    r = np.sqrt(-2.0 * np.log(u0))
-    g = np.where(iy % 2 == 0, r * np.cos(2.0 * np.pi * u1), r * np.sin(2.0 * np.pi * u1))
+    ge, go = box_muller(x0, x1)
+    g = np.where(iy % 2 == 0, ge, go)
     return g if as_float64 else g.astype(np.float32)

@@ -74,10 +74,14 @@ def load_library():
         "lpt2_plan": (i, [C.POINTER(vp), C.POINTER(_Instance), i, i, d, d, i, vp, C.c_uint]),
         "lpt2_plan_destroy": (i, [vp]),
         "lpt2_workspace_size": (i, [vp, C.POINTER(C.c_size_t)]),
+        "lpt2_workspace_bytes": (i, [C.POINTER(_Instance), i, i, C.c_uint, C.POINTER(C.c_size_t)]),
+        "lpt2_debug_alloc_hook": (i, [i, C.POINTER(i64)]),
+        "lpt2_set_wait_budget": (i, [vp, i64]),
         "lpt2_set_workspace": (i, [vp, vp, C.c_size_t]),
         "lpt2_growth_tables": (i, [vp, vp, vp, vp, vp]),
         "lpt2_white_noise": (i, [vp, vp]),
         "lpt2_philox_words": (i, [u64, u64, i64, vp, vp]),
+        "lpt2_box_muller": (i, [vp, vp, i64, vp]),
         "lpt2_displace": (i, [vp, vp, vp, vp, vp, vp]),
         "lpt2_cic_pk": (i, [vp, vp, vp, vp, vp, vp, i]),
         "lpt2_fft_r2c": (i, [vp, vp, vp]),
@@ -129,14 +133,53 @@ def _stream(stream=None):
     return C.c_void_p(s.cuda_stream)
 
 
+GRAPH, HOST_IO = 1, 2
+
+
+def plan_flags(graph=False, host_io=False, max_outputs=0) -> int:
+    """The lpt2_plan flags: LPT2_GRAPH, LPT2_HOST_IO, LPT2_MAX_OUTPUTS(max_outputs)."""
+    return (GRAPH if graph else 0) | (HOST_IO if host_io else 0) | ((int(max_outputs) & 0xFF) << 8)
+
+
+def _instances(insts):
+    arr = (_Instance * len(insts))()
+    for j, it in enumerate(insts):
+        c = it.cosmo
+        arr[j] = _Instance(int(it.n), float(it.box), int(it.seed) & (2 ** 64 - 1),
+                           float(getattr(it, "a_out", 1.0)),
+                           _Cosmo(c.omega_m, c.omega_l, c.omega_b, c.h, c.n_s, c.sigma8, c.t_cmb,
+                                  c.fr0_abs, int(c.hs_n), c.a_init,
+                                  int(getattr(c, "d2_variant", 0))))
+    return arr
+
+
+def lpt2_workspace_bytes(inst, n_k=512, graph=False, host_io=False, max_outputs=0) -> int:
+    """Workspace bytes of a plan not made yet (host-side computation, no GPU needed)."""
+    insts = list(inst) if isinstance(inst, (list, tuple)) else [inst]
+    nb = C.c_size_t()
+    _check(load_library().lpt2_workspace_bytes(_instances(insts), len(insts), int(n_k),
+                                               plan_flags(graph, host_io, max_outputs), C.byref(nb)))
+    return nb.value
+
+
+def lpt2_debug_alloc_hook(fail_at: int) -> int:
+    """Makes allocation number fail_at (from now on, counting from 0) fail; -1 turns that off.
+    Returns the number of live device allocations of the library."""
+    live = C.c_int64()
+    _check(load_library().lpt2_debug_alloc_hook(int(fail_at), C.byref(live)))
+    return live.value
+
+
 class Plan:
     """Owns an lpt2 plan handle and its workspace (a torch uint8 CUDA tensor).
 
     `inst` is one instance or a list of instances (equal grid sizes contiguous);
-    `graph=True` sets LPT2_GRAPH (needs a non-default stream)."""
+    `graph=True` sets LPT2_GRAPH (needs a non-default stream); `host_io=True` sets
+    LPT2_HOST_IO (lpt2_displace_host); `max_outputs=n` reserves room for n output times
+    (lpt2_set_outputs)."""
 
     def __init__(self, inst, n_k=512, k_min=1e-4, k_max=10.0, n_steps=1024, stream=None,
-                 workspace=True, graph=False):
+                 workspace=True, graph=False, host_io=False, max_outputs=0):
         lib = load_library()
         insts = list(inst) if isinstance(inst, (list, tuple)) else [inst]
         self.insts = insts
@@ -147,19 +190,13 @@ class Plan:
         self.cells = sum(n ** 3 for n in self.ns)
         self.n_k = int(n_k)
         self.n_steps = int(n_steps)
-        arr = (_Instance * self.n_inst)()
-        for j, it in enumerate(insts):
-            c = it.cosmo
-            arr[j] = _Instance(int(it.n), float(it.box), int(it.seed) & (2 ** 64 - 1),
-                               float(getattr(it, "a_out", 1.0)),
-                               _Cosmo(c.omega_m, c.omega_l, c.omega_b, c.h, c.n_s, c.sigma8, c.t_cmb,
-                                      c.fr0_abs, int(c.hs_n), c.a_init,
-                                      int(getattr(c, "d2_variant", 0))))
+        self.flags = plan_flags(graph, host_io, max_outputs)
+        arr = _instances(insts)
         self._cinst = arr
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         h = C.c_void_p()
         _check(lib.lpt2_plan(C.byref(h), arr, self.n_inst, self.n_k, float(k_min), float(k_max),
-                             self.n_steps, _stream(self.stream), 1 if graph else 0))
+                             self.n_steps, _stream(self.stream), self.flags))
         self.handle = h
         self.workspace = None
         if workspace:
@@ -244,6 +281,11 @@ def lpt2_source_ratio(plan: Plan, noise=None, n_bins=32, spectra=False):
     return res
 
 
+def lpt2_set_wait_budget(plan: Plan, cycles: int) -> None:
+    """Cycle budget of the plan's bounded device-side waits (0: give up at once)."""
+    _check(load_library().lpt2_set_wait_budget(plan.handle, int(cycles)))
+
+
 def lpt2_device_status(plan: Plan) -> None:
     """Synchronises the plan's stream; raises LPT2Error if a bounded device-side wait
     gave up since the previous check."""
@@ -263,6 +305,16 @@ def lpt2_white_noise(plan: Plan, out=None):
     n = plan.n
     out = torch.empty((n, n, n), dtype=torch.float32, device="cuda") if out is None else out
     _check(load_library().lpt2_white_noise(plan.handle, _ptr(out)))
+    return out
+
+
+def lpt2_box_muller(plan: Plan, words):
+    """Box-Muller transform of Philox word pairs: words is an int32 CUDA tensor (count, 2)
+    holding uint32 bit patterns (x0, x1); returns float32 (count, 2) (cosine, sine outputs)."""
+    if words.dtype != torch.int32 or words.dim() != 2 or words.shape[1] != 2:
+        raise ValueError("words must be an int32 tensor of shape (count, 2)")
+    out = torch.empty((words.shape[0], 2), dtype=torch.float32, device="cuda")
+    _check(load_library().lpt2_box_muller(plan.handle, _ptr(words), int(words.shape[0]), _ptr(out)))
     return out
 
 

@@ -5,11 +5,13 @@
 #include <stdio.h>
 #include <string.h>
 
-#include <string>
 #include <algorithm>
+#include <atomic>
+#include <string>
 #include <vector>
 
 #include "../../include/lpt2.h"
+#include "boxmuller.cuh"
 #include "passes.h"
 
 using namespace lpt2;
@@ -28,6 +30,29 @@ int fail(int code, const char* fmt, ...) {
   return code;
 }
 
+// Every device allocation of the library goes through plan_malloc / plan_free (all of them
+// in lpt2_plan).  A test can make the k-th allocation fail (lpt2_debug_alloc_hook) and read
+// how many allocations are live, to check that each failure returns LPT2_ENOMEM and frees
+// what was already allocated.
+std::atomic<int> g_fail_alloc_at{-1};
+std::atomic<int> g_alloc_calls{0};
+std::atomic<long long> g_alloc_live{0};
+
+cudaError_t plan_malloc(void** ptr, size_t bytes) {
+  *ptr = nullptr;
+  const int k = g_alloc_calls.fetch_add(1);
+  if (g_fail_alloc_at.load() >= 0 && k == g_fail_alloc_at.load()) return cudaErrorMemoryAllocation;
+  const cudaError_t e = cudaMalloc(ptr, bytes);
+  if (e == cudaSuccess) g_alloc_live.fetch_add(1);
+  return e;
+}
+
+void plan_free(void* ptr) {
+  if (!ptr) return;
+  cudaFree(ptr);
+  g_alloc_live.fetch_sub(1);
+}
+
 bool supported_n(int n) {
   return n == 16 || n == 32 || n == 64 || n == 96 || n == 128 || n == 192 || n == 256 || n == 512 ||
          n == 1024;
@@ -39,6 +64,7 @@ enum Slot { S_A = 0, S_DELTA = 1, S_X0 = 2, S_Y0 = 7, S_RHO = 16, S_SHAT = 17, S
 constexpr int kMaxShells = 256;
 constexpr int kMaxOutputs = 64;   // output scale factors per plan (lpt2_set_outputs)
 constexpr int kMaxRec = 4096;
+constexpr long long kDefaultWaitCycles = 2000000000LL;   // about one second at 2 GHz
 
 }  // namespace
 
@@ -65,9 +91,9 @@ struct GraphCache {  // one captured launch sequence per entry point (LPT2_GRAPH
   int64_t launches;
 };
 
-// Device side of lpt2_displace_host: two buffer sets (noise, positions, P(k)) so that
-// the copies of one realisation overlap the kernels of the next, two copy streams and
-// the events that order them.
+// Device side of lpt2_displace_host: two buffer sets (noise, positions, P(k)) in the
+// caller's workspace so that the copies of one realisation overlap the kernels of the
+// next, two copy streams and the events that order them (made by lpt2_plan).
 struct HostIO {
   float* noise_d[2] = {};
   float* pos_d[2] = {};
@@ -92,11 +118,15 @@ struct lpt2_plan_s {
   uint64_t* seeds_dev;        // [n_inst]
   double* fr0_dev;            // [n_inst]
   int* dev_err;               // device error word written by bounded waits (0 = ok)
+  float4* bm_tab;             // Box-Muller tables of the white noise (boxmuller.cuh)
+  long long wait_cycles = kDefaultWaitCycles;   // budget of the bounded consumer waits
   double* gr_tab;             // [4][2] GR growth (D1_GR(a) / D1_GR(1)) for the source diagnostic
   float* gr_tabf;
   size_t slot_sz;             // bytes per workspace slot: max over groups of count n^3 4
   int xb_max;                 // max over groups of count * x-pass blocks
   size_t total_cells;         // sum over instances of n^3
+  bool host_io;               // LPT2_HOST_IO: the workspace holds lpt2_displace_host's buffer sets
+  int max_out;                // LPT2_MAX_OUTPUTS(n): room for n output times' tables in the workspace
   bool use_graph;
   GraphCache graphs[2] = {};  // lpt2_displace, lpt2_cic_pk
   uint64_t seed;
@@ -120,14 +150,11 @@ struct lpt2_plan_s {
   const char* rec_name[kMaxRec];
   double rec_bytes[kMaxRec];
   HostIO* hio = nullptr;      // lpt2_displace_host buffers and streams, made on first use
-  // output scale factors of lpt2_displace_outputs (lpt2_set_outputs): per a_j the growth
-  // tables [4][nk] (FP64, FP32) and the per-|n|^2 multiplier tables of the plan's grid
+  // output scale factors of lpt2_displace_outputs (lpt2_set_outputs); per a_j the growth
+  // tables [4][nk] (FP64, FP32) and the per-|n|^2 multiplier tables of the plan's grid sit
+  // in the workspace (WsLayout::outs)
   int n_out_a = 0;
   std::vector<double> out_a;
-  double* tab_a = nullptr;
-  float* tabf_a = nullptr;
-  float4* mt0_a = nullptr;
-  float2* mt1_a = nullptr;
 };
 
 namespace {
@@ -181,21 +208,58 @@ int x_blocks(int n) {
   }
 }
 
-// Tail of the workspace after the slots: P(k) block partials [x_blocks][3][256],
-// internal pk / k_mean / n_modes [256] each, shell weights [256], dL/dln|fR0|
-// block partials [x_blocks].
-// CIC density of every instance (sum of n^3 floats) after the slots, then the tail.
+// Workspace layout (byte offsets; every region 256-byte aligned):
+//   N_SLOTS slots of slot_sz bytes, the CIC density of every instance (sum of n^3 floats),
+//   P(k) block partials [xb_max][3][256] doubles, internal pk / k_mean / n_modes [256] each,
+//   shell weights [256] floats, dL/dln|fR0| block partials [xb_max] doubles, P(k) per
+//   instance [n_inst][256] doubles (lpt2_autotune), then with LPT2_HOST_IO two buffer sets
+//   of lpt2_displace_host (noise n^3 floats, positions 3 n^3 floats, P(k) 256 doubles) and
+//   with LPT2_MAX_OUTPUTS(m) m output times' tables (growth [4][nk] doubles and floats,
+//   multiplier tables [mode_table_len] float4 and float2).
+struct WsLayout {
+  size_t slot_sz, rho, pk_part, pk, shw, theta, inst_pk, hio, hio_noise, hio_pos, hio_pk, hio_set, outs,
+      out_tab, out_tabf, out_mt0, out_mt1, out_each, total;
+};
+size_t up256(size_t b) { return (b + 255) / 256 * 256; }
+WsLayout ws_layout(size_t slot_sz, size_t total_cells, int xb_max, int n_inst, int nk, int n0, bool host_io,
+                   int max_out) {
+  WsLayout w{};
+  w.slot_sz = slot_sz;
+  w.rho = N_SLOTS * slot_sz;
+  w.pk_part = up256(w.rho + total_cells * sizeof(float));
+  w.pk = up256(w.pk_part + (size_t)xb_max * 3 * kMaxShells * 8);
+  w.shw = up256(w.pk + 3 * kMaxShells * 8);
+  w.theta = up256(w.shw + kMaxShells * 4);
+  w.inst_pk = up256(w.theta + (size_t)xb_max * 8);
+  w.hio = up256(w.inst_pk + (size_t)n_inst * kMaxShells * 8);
+  const size_t n3 = (size_t)n0 * n0 * n0;
+  w.hio_noise = 0;
+  w.hio_pos = up256(n3 * sizeof(float));
+  w.hio_pk = up256(w.hio_pos + 3 * n3 * sizeof(float));
+  w.hio_set = up256(w.hio_pk + kMaxShells * 8);
+  w.outs = w.hio + (host_io ? 2 * w.hio_set : 0);
+  const size_t len = (size_t)mode_table_len(n0);
+  w.out_tab = 0;
+  w.out_tabf = up256((size_t)4 * nk * sizeof(double));
+  w.out_mt0 = up256(w.out_tabf + (size_t)4 * nk * sizeof(float));
+  w.out_mt1 = up256(w.out_mt0 + len * sizeof(float4));
+  w.out_each = up256(w.out_mt1 + len * sizeof(float2));
+  w.total = w.outs + (size_t)max_out * w.out_each;
+  return w;
+}
+WsLayout ws_layout(const lpt2_plan_s* p) {
+  return ws_layout(p->slot_sz, p->total_cells, p->xb_max, p->n_inst, p->nk, p->groups[0].n, p->host_io,
+                   p->max_out);
+}
 size_t rho_all_off(const lpt2_plan_s* p) { return N_SLOTS * slot_bytes(p); }
 float* rho_group(const lpt2_plan_s* p) {
   return reinterpret_cast<float*>(p->ws + rho_all_off(p)) + p->cur_rho_off;
 }
-size_t tail_pk_part(const lpt2_plan_s* p) {
-  return (rho_all_off(p) + p->total_cells * sizeof(float) + 255) / 256 * 256;
-}
-size_t tail_pk(const lpt2_plan_s* p) { return tail_pk_part(p) + (size_t)p->xb_max * 3 * kMaxShells * 8; }
-size_t tail_shw(const lpt2_plan_s* p) { return tail_pk(p) + 3 * kMaxShells * 8; }
-size_t tail_theta(const lpt2_plan_s* p) { return tail_shw(p) + kMaxShells * 4; }
-size_t ws_need(const lpt2_plan_s* p) { return tail_theta(p) + (size_t)p->xb_max * 8; }
+size_t tail_pk_part(const lpt2_plan_s* p) { return ws_layout(p).pk_part; }
+size_t tail_pk(const lpt2_plan_s* p) { return ws_layout(p).pk; }
+size_t tail_shw(const lpt2_plan_s* p) { return ws_layout(p).shw; }
+size_t tail_theta(const lpt2_plan_s* p) { return ws_layout(p).theta; }
+size_t ws_need(const lpt2_plan_s* p) { return ws_layout(p).total; }
 
 float2* slot(const lpt2_plan_s* p, int i) {
   return reinterpret_cast<float2*>(p->ws + i * slot_bytes(p) + p->cur_slot_off);
@@ -216,6 +280,7 @@ Geo make_geo(const lpt2_plan_s* p) {
   g.inst0 = p->cur_inst0;
   g.tab_stride = 4 * p->nk;
   g.err = p->dev_err;
+  g.wait = p->wait_cycles;
   return g;
 }
 
@@ -305,6 +370,7 @@ int forward_zy(lpt2_plan_t p, int src, const float* in, float2* out) {
   z.seed_lo = (uint32_t)p->seed;
   z.seed_hi = (uint32_t)(p->seed >> 32);
   z.seeds = p->seeds_dev;
+  z.bm = p->bm_tab;
   z.out = out;
   LAUNCH(p, src == Z_NOISE ? "z_r2c_noise" : (src == Z_DENSITY ? "z_r2c_density" : "z_r2c"),
          (src == Z_NOISE ? 4.0 : 8.0) * V3(p), z_r2c(p->n, z, p->stream));
@@ -325,15 +391,8 @@ int forward_zy(lpt2_plan_t p, int src, const float* in, float2* out) {
 int displace_impl(lpt2_plan_t p, const float* noise, float* psi1, float* psi2, float* pos, void* dk,
                   float2* s_keep);
 
+// Forgets the output times (their tables live in the workspace).
 void free_outputs(lpt2_plan_t p) {
-  cudaFree(p->tab_a);
-  cudaFree(p->tabf_a);
-  cudaFree(p->mt0_a);
-  cudaFree(p->mt1_a);
-  p->tab_a = nullptr;
-  p->tabf_a = nullptr;
-  p->mt0_a = nullptr;
-  p->mt1_a = nullptr;
   p->n_out_a = 0;
   p->out_a.clear();
 }
@@ -342,9 +401,6 @@ void free_host_io(lpt2_plan_t p) {
   HostIO* h = p->hio;
   if (!h) return;
   for (int b = 0; b < 2; ++b) {
-    cudaFree(h->noise_d[b]);
-    cudaFree(h->pos_d[b]);
-    cudaFree(h->pk_d[b]);
     for (cudaEvent_t e : {h->up_done[b], h->in_used[b], h->pos_ready[b], h->comp_done[b], h->down_done[b]})
       if (e) cudaEventDestroy(e);
   }
@@ -355,29 +411,34 @@ void free_host_io(lpt2_plan_t p) {
   p->hio = nullptr;
 }
 
-// Buffers, streams and events of lpt2_displace_host (single-instance plan, grid n).
-int ensure_host_io(lpt2_plan_t p) {
-  if (p->hio) return LPT2_OK;
+// Streams and events of lpt2_displace_host (plans made with LPT2_HOST_IO; made by lpt2_plan).
+int make_host_io(lpt2_plan_t p) {
   p->hio = new HostIO();
   HostIO* h = p->hio;
-  const size_t n3 = (size_t)p->n * p->n * p->n;
   cudaError_t e = cudaSuccess;
-  for (int b = 0; b < 2 && e == cudaSuccess; ++b) {
-    e = cudaMalloc(&h->noise_d[b], n3 * sizeof(float));
-    if (e == cudaSuccess) e = cudaMalloc(&h->pos_d[b], 3 * n3 * sizeof(float));
-    if (e == cudaSuccess) e = cudaMalloc(&h->pk_d[b], kMaxShells * sizeof(double));
+  for (int b = 0; b < 2 && e == cudaSuccess; ++b)
     for (cudaEvent_t* ev : {&h->up_done[b], &h->in_used[b], &h->pos_ready[b], &h->comp_done[b], &h->down_done[b]})
       if (e == cudaSuccess) e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
-  }
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->start, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->s_in, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->s_out, cudaStreamNonBlocking);
   if (e != cudaSuccess) {
     free_host_io(p);
-    return fail(e == cudaErrorMemoryAllocation ? LPT2_ENOMEM : LPT2_ECUDA, "host-io buffers: %s",
-                cudaGetErrorString(e));
+    return fail(LPT2_ECUDA, "host-io streams and events: %s", cudaGetErrorString(e));
   }
   return LPT2_OK;
+}
+
+// The two buffer sets of lpt2_displace_host in the workspace.
+void host_io_buffers(lpt2_plan_t p) {
+  const WsLayout w = ws_layout(p);
+  HostIO* h = p->hio;
+  for (int b = 0; b < 2; ++b) {
+    char* base = p->ws + w.hio + b * w.hio_set;
+    h->noise_d[b] = reinterpret_cast<float*>(base + w.hio_noise);
+    h->pos_d[b] = reinterpret_cast<float*>(base + w.hio_pos);
+    h->pk_d[b] = reinterpret_cast<double*>(base + w.hio_pk);
+  }
 }
 
 // Shell geometry (mode counts, sum of |k|) of group gi for n_shells shells; made
@@ -467,16 +528,33 @@ int run_graph(lpt2_plan_t p, int slot_i, const void* const key[8], F body) {
   return LPT2_OK;
 }
 
+// Growth and multiplier tables of output scale factor j, in the workspace.
+double* out_tab(lpt2_plan_t p, int j) {
+  const WsLayout w = ws_layout(p);
+  return reinterpret_cast<double*>(p->ws + w.outs + j * w.out_each + w.out_tab);
+}
+float* out_tabf(lpt2_plan_t p, int j) {
+  const WsLayout w = ws_layout(p);
+  return reinterpret_cast<float*>(p->ws + w.outs + j * w.out_each + w.out_tabf);
+}
+float4* out_mt0(lpt2_plan_t p, int j) {
+  const WsLayout w = ws_layout(p);
+  return reinterpret_cast<float4*>(p->ws + w.outs + j * w.out_each + w.out_mt0);
+}
+float2* out_mt1(lpt2_plan_t p, int j) {
+  const WsLayout w = ws_layout(p);
+  return reinterpret_cast<float2*>(p->ws + w.outs + j * w.out_each + w.out_mt1);
+}
+
 // Growth and multiplier tables of every output scale factor (single-instance plan).
 int run_output_growth(lpt2_plan_t p) {
-  const size_t len = (size_t)mode_table_len(p->groups[0].n), nk4 = (size_t)4 * p->nk;
   GrowthParams gp = growth_params(p);
   for (int j = 0; j < p->n_out_a; ++j) {
     gp.a_out = p->out_a[j];
-    LAUNCH(p, "growth", 0.0, launch_growth(gp, p->tab_a + j * nk4, p->tabf_a + j * nk4, p->stream));
+    LAUNCH(p, "growth", 0.0, launch_growth(gp, out_tab(p, j), out_tabf(p, j), p->stream));
     LAUNCH(p, "mode_tables", 0.0,
-           launch_mode_tables(gp, p->cosmo_dev, p->tab_a + j * nk4, 0, 1, p->groups[0].n, p->groups[0].box,
-                              p->mt0_a + j * len, p->mt1_a + j * len, p->stream));
+           launch_mode_tables(gp, p->cosmo_dev, out_tab(p, j), 0, 1, p->groups[0].n, p->groups[0].box,
+                              out_mt0(p, j), out_mt1(p, j), p->stream));
   }
   return LPT2_OK;
 }
@@ -539,19 +617,27 @@ static bool same_background(const lpt2_instance& a, const lpt2_instance& b) {
          x.hs_n == y.hs_n && x.d2_variant == y.d2_variant && a.a_out == b.a_out;
 }
 
-int lpt2_plan(lpt2_plan_t* out, const lpt2_instance* inst, int n_inst, int n_k, double k_min,
-              double k_max, int n_steps, void* cuda_stream, unsigned flags) {
-  g_err.clear();
-  if (!out || !inst) return fail(LPT2_EINVAL, "null out/inst pointer");
-  *out = nullptr;
-  if (n_inst < 1 || n_inst > 65535) return fail(LPT2_EINVAL, "n_inst must be in [1, 65535] (got %d)", n_inst);
-  if (flags & ~(unsigned)LPT2_GRAPH) return fail(LPT2_EINVAL, "unknown flags");
-  if ((flags & LPT2_GRAPH) && cuda_stream == nullptr)
-    return fail(LPT2_EINVAL, "LPT2_GRAPH needs a stream other than the legacy default stream");
-  if (n_k < 2 || n_k > 4096) return fail(LPT2_EINVAL, "n_k must be in [2, 4096]");
-  if (!(k_min > 0) || !(k_max > k_min)) return fail(LPT2_EINVAL, "need 0 < k_min < k_max");
-  if (n_steps < 1 || n_steps > 2800) return fail(LPT2_EINVAL, "n_steps must be in [1, 2800]");
+// Host-side checks shared by lpt2_plan and lpt2_workspace_bytes: the instance list, n_k and
+// the flags; on success the grid-size groups and the workspace sizes of such a plan.
+struct PlanShape {
   std::vector<Group> groups;
+  size_t slot_sz = 0, total_cells = 0;
+  int xb_max = 0;
+  bool host_io = false;
+  int max_out = 0;
+};
+static int plan_shape(const lpt2_instance* inst, int n_inst, int n_k, unsigned flags, PlanShape& ps) {
+  if (!inst) return fail(LPT2_EINVAL, "null inst pointer");
+  if (n_inst < 1 || n_inst > 65535) return fail(LPT2_EINVAL, "n_inst must be in [1, 65535] (got %d)", n_inst);
+  const unsigned known = LPT2_GRAPH | LPT2_HOST_IO | LPT2_MAX_OUTPUTS(0xff);
+  if (flags & ~known) return fail(LPT2_EINVAL, "unknown flags");
+  ps.host_io = (flags & LPT2_HOST_IO) != 0;
+  ps.max_out = (int)((flags >> 8) & 0xff);
+  if (ps.max_out > kMaxOutputs) return fail(LPT2_EINVAL, "LPT2_MAX_OUTPUTS(n): n must be <= %d", kMaxOutputs);
+  if ((ps.host_io || ps.max_out > 0) && n_inst != 1)
+    return fail(LPT2_EINVAL, "LPT2_HOST_IO and LPT2_MAX_OUTPUTS need a single-instance plan");
+  if (n_k < 2 || n_k > 4096) return fail(LPT2_EINVAL, "n_k must be in [2, 4096]");
+  std::vector<Group>& groups = ps.groups;
   for (int i = 0; i < n_inst; ++i) {
     const int rc = check_cosmo(&inst[i]);
     if (rc) return rc;
@@ -568,9 +654,60 @@ int lpt2_plan(lpt2_plan_t* out, const lpt2_instance* inst, int n_inst, int n_k, 
       return fail(LPT2_EUNSUPPORTED, "instances of one grid size must share the box (instance %d)", i);
     groups.back().count++;
   }
+  for (Group& g : groups) {
+    g.off = ps.total_cells;
+    ps.total_cells += (size_t)g.count * g.n * g.n * g.n;
+    const size_t sz = (size_t)g.count * g.n * g.n * g.n * sizeof(float);
+    if (sz > ps.slot_sz) ps.slot_sz = sz;
+    if (g.count * x_blocks(g.n) > ps.xb_max) ps.xb_max = g.count * x_blocks(g.n);
+  }
+  return LPT2_OK;
+}
+
+int lpt2_set_wait_budget(lpt2_plan_t p, int64_t cycles) {
+  if (!p) return fail(LPT2_EINVAL, "null plan");
+  if (cycles < 0) return fail(LPT2_EINVAL, "cycles must be >= 0");
+  p->wait_cycles = cycles;
+  for (auto& gc : p->graphs) {   // captured launches carry the old budget
+    if (gc.exec) cudaGraphExecDestroy(gc.exec);
+    gc.exec = nullptr;
+  }
+  return LPT2_OK;
+}
+
+int lpt2_debug_alloc_hook(int fail_at, int64_t* live) {
+  if (fail_at < -1) return fail(LPT2_EINVAL, "fail_at must be >= -1");
+  g_fail_alloc_at.store(fail_at);
+  g_alloc_calls.store(0);
+  if (live) *live = (int64_t)g_alloc_live.load();
+  return LPT2_OK;
+}
+
+int lpt2_workspace_bytes(const lpt2_instance* inst, int n_inst, int n_k, unsigned flags, size_t* bytes) {
+  if (!bytes) return fail(LPT2_EINVAL, "null bytes pointer");
+  PlanShape ps;
+  const int rc = plan_shape(inst, n_inst, n_k, flags, ps);
+  if (rc) return rc;
+  *bytes = ws_layout(ps.slot_sz, ps.total_cells, ps.xb_max, n_inst, n_k, ps.groups[0].n, ps.host_io, ps.max_out)
+               .total;
+  return LPT2_OK;
+}
+
+int lpt2_plan(lpt2_plan_t* out, const lpt2_instance* inst, int n_inst, int n_k, double k_min,
+              double k_max, int n_steps, void* cuda_stream, unsigned flags) {
+  g_err.clear();
+  if (!out || !inst) return fail(LPT2_EINVAL, "null out/inst pointer");
+  *out = nullptr;
+  if ((flags & LPT2_GRAPH) && cuda_stream == nullptr)
+    return fail(LPT2_EINVAL, "LPT2_GRAPH needs a stream other than the legacy default stream");
+  if (!(k_min > 0) || !(k_max > k_min)) return fail(LPT2_EINVAL, "need 0 < k_min < k_max");
+  if (n_steps < 1 || n_steps > 2800) return fail(LPT2_EINVAL, "n_steps must be in [1, 2800]");
+  PlanShape ps;
+  const int prc = plan_shape(inst, n_inst, n_k, flags, ps);
+  if (prc) return prc;
 
   lpt2_plan_s* p = new lpt2_plan_s();
-  p->groups = groups;
+  p->groups = ps.groups;
   p->n_inst = n_inst;
   p->seed = inst[0].seed;
   p->a_out = inst[0].a_out;
@@ -581,40 +718,35 @@ int lpt2_plan(lpt2_plan_t* out, const lpt2_instance* inst, int n_inst, int n_k, 
   p->n_steps = n_steps;
   p->stream = (cudaStream_t)cuda_stream;
   p->use_graph = (flags & LPT2_GRAPH) != 0;
-  p->slot_sz = 0;
-  p->xb_max = 0;
-  p->total_cells = 0;
-  for (Group& g : p->groups) {
-    g.off = p->total_cells;
-    p->total_cells += (size_t)g.count * g.n * g.n * g.n;
-  }
-  for (const Group& g : groups) {
-    const size_t sz = (size_t)g.count * g.n * g.n * g.n * sizeof(float);
-    if (sz > p->slot_sz) p->slot_sz = sz;
-    if (g.count * x_blocks(g.n) > p->xb_max) p->xb_max = g.count * x_blocks(g.n);
-  }
+  p->slot_sz = ps.slot_sz;
+  p->xb_max = ps.xb_max;
+  p->total_cells = ps.total_cells;
+  p->host_io = ps.host_io;
+  p->max_out = ps.max_out;
   cudaError_t e = cudaSuccess;
   for (Group& g : p->groups) {
-    if (e == cudaSuccess) e = cudaMalloc(&g.tw, g.n * sizeof(float2));
-    if (e == cudaSuccess) e = cudaMalloc(&g.mt0, (size_t)g.count * mode_table_len(g.n) * sizeof(float4));
-    if (e == cudaSuccess) e = cudaMalloc(&g.mt1, (size_t)g.count * mode_table_len(g.n) * sizeof(float2));
-    if (e == cudaSuccess) e = cudaMalloc(&g.geo_k, kMaxShells * sizeof(double));
-    if (e == cudaSuccess) e = cudaMalloc(&g.geo_n, kMaxShells * sizeof(unsigned long long));
+    if (e == cudaSuccess) e = plan_malloc((void**)&g.tw, g.n * sizeof(float2));
+    if (e == cudaSuccess) e = plan_malloc((void**)&g.mt0, (size_t)g.count * mode_table_len(g.n) * sizeof(float4));
+    if (e == cudaSuccess) e = plan_malloc((void**)&g.mt1, (size_t)g.count * mode_table_len(g.n) * sizeof(float2));
+    if (e == cudaSuccess) e = plan_malloc((void**)&g.geo_k, kMaxShells * sizeof(double));
+    if (e == cudaSuccess) e = plan_malloc((void**)&g.geo_n, kMaxShells * sizeof(unsigned long long));
     g.geo_ns = 0;
   }
-  if (e == cudaSuccess) e = cudaMalloc(&p->cosmo_dev, sizeof(DevCosmo));
-  if (e == cudaSuccess) e = cudaMalloc(&p->partials, cosmo_partial_blocks() * sizeof(double));
-  if (e == cudaSuccess) e = cudaMalloc(&p->tab, (size_t)n_inst * 4 * n_k * sizeof(double));
-  if (e == cudaSuccess) e = cudaMalloc(&p->tabf, (size_t)n_inst * 4 * n_k * sizeof(float));
-  if (e == cudaSuccess) e = cudaMalloc(&p->seeds_dev, (size_t)n_inst * sizeof(uint64_t));
-  if (e == cudaSuccess) e = cudaMalloc(&p->fr0_dev, (size_t)n_inst * sizeof(double));
-  if (e == cudaSuccess) e = cudaMalloc(&p->dev_err, sizeof(int));
-  if (e == cudaSuccess) e = cudaMalloc(&p->gr_tab, 8 * sizeof(double));
-  if (e == cudaSuccess) e = cudaMalloc(&p->gr_tabf, 8 * sizeof(float));
+  if (e == cudaSuccess) e = plan_malloc((void**)&p->cosmo_dev, sizeof(DevCosmo));
+  if (e == cudaSuccess) e = plan_malloc((void**)&p->partials, cosmo_partial_blocks() * sizeof(double));
+  if (e == cudaSuccess) e = plan_malloc((void**)&p->tab, (size_t)n_inst * 4 * n_k * sizeof(double));
+  if (e == cudaSuccess) e = plan_malloc((void**)&p->tabf, (size_t)n_inst * 4 * n_k * sizeof(float));
+  if (e == cudaSuccess) e = plan_malloc((void**)&p->seeds_dev, (size_t)n_inst * sizeof(uint64_t));
+  if (e == cudaSuccess) e = plan_malloc((void**)&p->fr0_dev, (size_t)n_inst * sizeof(double));
+  if (e == cudaSuccess) e = plan_malloc((void**)&p->dev_err, sizeof(int));
+  if (e == cudaSuccess) e = plan_malloc((void**)&p->bm_tab, kBmTableLen * sizeof(float4));
+  if (e == cudaSuccess) e = plan_malloc((void**)&p->gr_tab, 8 * sizeof(double));
+  if (e == cudaSuccess) e = plan_malloc((void**)&p->gr_tabf, 8 * sizeof(float));
   if (e == cudaSuccess) e = cudaMemset(p->dev_err, 0, sizeof(int));
   if (e != cudaSuccess) {
     lpt2_plan_destroy(p);
-    return fail(LPT2_ENOMEM, "plan allocation failed: %s", cudaGetErrorString(e));
+    return fail(e == cudaErrorMemoryAllocation ? LPT2_ENOMEM : LPT2_ECUDA, "plan allocation failed: %s",
+                cudaGetErrorString(e));
   }
   // twiddles exp(-2 pi i m / N), FP64 then rounded once
   for (Group& g : p->groups) {
@@ -632,6 +764,9 @@ int lpt2_plan(lpt2_plan_t* out, const lpt2_instance* inst, int n_inst, int n_k, 
     seeds[i] = inst[i].seed;
     fr0s[i] = inst[i].cosmo.fr0_abs;
   }
+  std::vector<float4> bm(kBmTableLen);
+  bm_table(bm.data());
+  if (e == cudaSuccess) e = cudaMemcpy(p->bm_tab, bm.data(), kBmTableLen * sizeof(float4), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(p->seeds_dev, seeds.data(), n_inst * sizeof(uint64_t), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(p->fr0_dev, fr0s.data(), n_inst * sizeof(double), cudaMemcpyHostToDevice);
   if (e != cudaSuccess) {
@@ -646,7 +781,8 @@ int lpt2_plan(lpt2_plan_t* out, const lpt2_instance* inst, int n_inst, int n_k, 
     lpt2_plan_destroy(p);
     return fail(LPT2_ECUDA, "set-up kernels: %s", cudaGetErrorString(e));
   }
-  const int rc = run_growth(p);   // growth tables, then the per-|n|^2 multiplier tables
+  int rc = run_growth(p);   // growth tables, then the per-|n|^2 multiplier tables
+  if (!rc && p->host_io) rc = make_host_io(p);
   if (rc) {
     lpt2_plan_destroy(p);
     return rc;
@@ -658,21 +794,22 @@ int lpt2_plan(lpt2_plan_t* out, const lpt2_instance* inst, int n_inst, int n_k, 
 int lpt2_plan_destroy(lpt2_plan_t p) {
   if (!p) return LPT2_OK;
   for (Group& g : p->groups) {
-    cudaFree(g.tw);
-    cudaFree(g.mt0);
-    cudaFree(g.mt1);
-    cudaFree(g.geo_k);
-    cudaFree(g.geo_n);
+    plan_free(g.tw);
+    plan_free(g.mt0);
+    plan_free(g.mt1);
+    plan_free(g.geo_k);
+    plan_free(g.geo_n);
   }
-  cudaFree(p->cosmo_dev);
-  cudaFree(p->partials);
-  cudaFree(p->tab);
-  cudaFree(p->tabf);
-  cudaFree(p->seeds_dev);
-  cudaFree(p->fr0_dev);
-  cudaFree(p->dev_err);
-  cudaFree(p->gr_tab);
-  cudaFree(p->gr_tabf);
+  plan_free(p->cosmo_dev);
+  plan_free(p->partials);
+  plan_free(p->tab);
+  plan_free(p->tabf);
+  plan_free(p->seeds_dev);
+  plan_free(p->fr0_dev);
+  plan_free(p->dev_err);
+  plan_free(p->bm_tab);
+  plan_free(p->gr_tab);
+  plan_free(p->gr_tabf);
   for (auto& gc : p->graphs)
     if (gc.exec) cudaGraphExecDestroy(gc.exec);
   if (p->ev) {
@@ -697,7 +834,7 @@ int lpt2_set_workspace(lpt2_plan_t p, void* dev_ptr, size_t bytes) {
   if (bytes < ws_need(p)) return fail(LPT2_ENOWORKSPACE, "workspace too small: %zu < %zu", bytes, ws_need(p));
   p->ws = (char*)dev_ptr;
   p->ws_bytes = bytes;
-  return LPT2_OK;
+  return p->n_out_a > 0 ? run_output_growth(p) : LPT2_OK;   // the output tables live in the workspace
 }
 
 int lpt2_growth_tables(lpt2_plan_t p, double* d1, double* d2, double* dd1, double* dd2) {
@@ -719,7 +856,17 @@ int lpt2_white_noise(lpt2_plan_t p, float* noise) {
   if (!p || !noise) return fail(LPT2_EINVAL, "null argument");
   if (p->n_inst != 1) return fail(LPT2_EUNSUPPORTED, "lpt2_white_noise needs a single-instance plan");
   if (!aligned(noise, 4)) return fail(LPT2_EINVAL, "misaligned output");
-  LAUNCH(p, "noise", 4.0 * V3(p), launch_noise(make_geo(p), (uint32_t)p->seed, (uint32_t)(p->seed >> 32), noise, p->stream));
+  LAUNCH(p, "noise", 4.0 * V3(p),
+         launch_noise(make_geo(p), (uint32_t)p->seed, (uint32_t)(p->seed >> 32), p->bm_tab, noise, p->stream));
+  return LPT2_OK;
+}
+
+int lpt2_box_muller(lpt2_plan_t p, const uint32_t* words, int64_t count, float* out) {
+  if (!p || (count > 0 && (!words || !out))) return fail(LPT2_EINVAL, "null argument");
+  if (count < 0 || count > (1LL << 31)) return fail(LPT2_EINVAL, "count must be in [0, 2^31]");
+  if (!aligned(words, 8) || !aligned(out, 8)) return fail(LPT2_EINVAL, "words and out must be 8-byte aligned");
+  if (count == 0) return LPT2_OK;
+  LAUNCH(p, "box_muller", 16.0 * count, launch_box_muller(words, count, p->bm_tab, out, p->stream));
   return LPT2_OK;
 }
 
@@ -986,8 +1133,10 @@ int lpt2_displace_host(lpt2_plan_t p, int n_real, const float* noise_h, int64_t 
   if ((noise_stride != 0 && noise_stride < n3) || (pos_stride != 0 && pos_stride < 3 * n3) ||
       (pk_stride != 0 && pk_stride < n_shells))
     return fail(LPT2_EINVAL, "a stride must be 0 (one shared buffer) or at least one realisation's size");
-  rc = ensure_host_io(p);
-  if (rc) return rc;
+  if (!p->host_io || !p->hio)
+    return fail(LPT2_EINVAL, "lpt2_displace_host needs a plan made with the LPT2_HOST_IO flag (the workspace "
+                             "then holds its two device buffer sets)");
+  host_io_buffers(p);
   rc = ensure_geometry(p, 0, n_shells);
   if (rc) return rc;
   HostIO* h = p->hio;
@@ -1067,17 +1216,12 @@ int lpt2_set_outputs(lpt2_plan_t p, int n_a, const double* a_out) {
   for (int j = 0; j < n_a; ++j)
     if (!(a_out[j] > p->cosmo.a_init) || !(a_out[j] <= 1.0))
       return fail(LPT2_EINVAL, "a_out[%d] = %g: need a_init < a_out <= 1", j, a_out[j]);
+  if (n_a > p->max_out)
+    return fail(LPT2_EINVAL, "n_a = %d output times, the plan has room for %d: make it with LPT2_MAX_OUTPUTS(n_a)",
+                n_a, p->max_out);
+  if (!p->ws) return fail(LPT2_ENOWORKSPACE, "no workspace attached (the output tables live in it)");
   set_group(p, 0);
   free_outputs(p);
-  const size_t len = (size_t)mode_table_len(p->n), nk4 = (size_t)4 * p->nk;
-  cudaError_t e = cudaMalloc(&p->tab_a, n_a * nk4 * sizeof(double));
-  if (e == cudaSuccess) e = cudaMalloc(&p->tabf_a, n_a * nk4 * sizeof(float));
-  if (e == cudaSuccess) e = cudaMalloc(&p->mt0_a, n_a * len * sizeof(float4));
-  if (e == cudaSuccess) e = cudaMalloc(&p->mt1_a, n_a * len * sizeof(float2));
-  if (e != cudaSuccess) {
-    free_outputs(p);
-    return fail(e == cudaErrorMemoryAllocation ? LPT2_ENOMEM : LPT2_ECUDA, "output tables: %s", cudaGetErrorString(e));
-  }
   p->out_a.assign(a_out, a_out + n_a);
   p->n_out_a = n_a;
   const int rc = run_output_growth(p);
@@ -1101,10 +1245,10 @@ int lpt2_displace_outputs(lpt2_plan_t p, const float* noise, float* pos, double*
   const FwdSlots f = fwd_slots(p);
   rc = displace_prefix(p, f, noise, false);
   if (rc) return rc;
-  const size_t n3 = (size_t)p->n * p->n * p->n, len = (size_t)mode_table_len(p->n), nk4 = (size_t)4 * p->nk;
+  const size_t n3 = (size_t)p->n * p->n * p->n;
   for (int j = 0; j < p->n_out_a; ++j) {
     rc = displace_suffix(p, f, false, nullptr, nullptr, pos ? pos + j * 3 * n3 : nullptr, nullptr,
-                         p->mt0_a + j * len, p->mt1_a + j * len, p->tabf_a + j * nk4);
+                         out_mt0(p, j), out_mt1(p, j), out_tabf(p, j));
     if (rc) return rc;
     // the density spectrum goes to a slot the suffix does not use (A and D stay intact)
     rc = cic_pk_group(p, 0, nullptr, nullptr, pk + (size_t)j * n_shells, j == 0 ? k_mean : nullptr,
@@ -1149,20 +1293,18 @@ int lpt2_autotune(lpt2_plan_t p, int n_shells, int reps) {
   if (rc) return rc;
   if (n_shells < 1 || n_shells > kMaxShells) return fail(LPT2_EINVAL, "n_shells must be in [1, 256]");
   if (reps < 1 || reps > 100) return fail(LPT2_EINVAL, "reps must be in [1, 100]");
-  double* pk = nullptr;
+  double* pk = reinterpret_cast<double*>(p->ws + ws_layout(p).inst_pk);   // [n_inst][n_shells]
   cudaEvent_t e0 = nullptr, e1 = nullptr;
-  cudaError_t e = cudaMalloc(&pk, (size_t)p->n_inst * n_shells * sizeof(double));
-  if (e == cudaSuccess) e = cudaEventCreate(&e0);
+  cudaError_t e = cudaEventCreate(&e0);
   if (e == cudaSuccess) e = cudaEventCreate(&e1);
   auto cleanup = [&]() {
-    cudaFree(pk);
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
     set_group(p, 0);
   };
   if (e != cudaSuccess) {
     cleanup();
-    return fail(e == cudaErrorMemoryAllocation ? LPT2_ENOMEM : LPT2_ECUDA, "autotune: %s", cudaGetErrorString(e));
+    return fail(LPT2_ECUDA, "autotune events: %s", cudaGetErrorString(e));
   }
   for (int gi = 0; gi < (int)p->groups.size() && !rc; ++gi) rc = ensure_geometry(p, gi, n_shells);
   drop_graphs(p);

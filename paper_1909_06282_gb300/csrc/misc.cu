@@ -420,18 +420,62 @@ cudaError_t launch_pk_finalize_p(const double* part, int n_blocks, int n_shells,
   return cudaGetLastError();
 }
 
-__global__ void k_noise(int n, uint32_t k0, uint32_t k1, float* out) {
+__global__ void k_noise(int n, uint32_t k0, uint32_t k1, const float4* __restrict__ g_bm, float* out) {
+  __shared__ float4 bm[kBmTableLen];
+  bm_load_table(bm, g_bm);
+  __syncthreads();
   const size_t n3 = (size_t)n * n * n;
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n3; i += (size_t)gridDim.x * blockDim.x) {
     const bool odd = ((i / n) % n) & 1;   // iy odd: sine output of the draw at iy - 1
-    const float2 g2 = philox_gauss2(odd ? i - n : i, k0, k1);
+    const float2 g2 = philox_gauss2(odd ? i - n : i, k0, k1, bm);
     out[i] = odd ? g2.y : g2.x;
   }
 }
 
-cudaError_t launch_noise(const Geo& g, uint32_t k0, uint32_t k1, float* out, cudaStream_t s) {
-  k_noise<<<152 * 8, 256, 0, s>>>(g.n, k0, k1, out);
+cudaError_t launch_noise(const Geo& g, uint32_t k0, uint32_t k1, const float4* bm, float* out, cudaStream_t s) {
+  k_noise<<<152 * 8, 256, 0, s>>>(g.n, k0, k1, bm, out);
   return cudaGetLastError();
+}
+
+__global__ void k_box_muller(const uint2* __restrict__ w, int64_t count, const float4* __restrict__ g_bm,
+                             float2* out) {
+  __shared__ float4 bm[kBmTableLen];
+  bm_load_table(bm, g_bm);
+  __syncthreads();
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x) {
+    const uint2 x = w[i];
+    out[i] = bm_pair(x.x, x.y, bm);
+  }
+}
+
+cudaError_t launch_box_muller(const uint32_t* words, int64_t count, const float4* bm, float* out, cudaStream_t s) {
+  k_box_muller<<<152 * 4, 256, 0, s>>>(reinterpret_cast<const uint2*>(words), count, bm,
+                                       reinterpret_cast<float2*>(out));
+  return cudaGetLastError();
+}
+
+// Box-Muller tables (layout in boxmuller.cuh): FP64 values, each split into the float
+// nearest to it and the float nearest to the remainder.
+void bm_table(float4* t) {
+  auto split = [](double v, float& hi, float& lo) {
+    hi = (float)v;
+    lo = (float)(v - (double)hi);
+  };
+  for (int j = 0; j < kBmSinCos; ++j) {
+    const double a = M_PI * (double)j / 2048.0;   // 2 pi j / 4096
+    split(cos(a), t[j].x, t[j].y);
+    split(sin(a), t[j].z, t[j].w);
+  }
+  for (int j = kBmLogLo; j <= kBmLogHi; ++j) {
+    const float c = (float)(1.0 / (1.0 + j / 128.0));
+    float4& e = t[kBmLog0 + (j - kBmLogLo)];
+    e.x = c;
+    split(-log((double)c), e.y, e.z);
+    e.w = 0.f;
+  }
+  float4& k = t[kBmConst];
+  split(2.0 * M_PI, k.x, k.y);
+  split(M_LN2, k.z, k.w);
 }
 
 __global__ void k_philox_words(uint32_t k0, uint32_t k1, uint64_t first, int64_t count, uint4* out) {

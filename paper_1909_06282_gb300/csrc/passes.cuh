@@ -118,12 +118,24 @@ __device__ __forceinline__ float2 z_assemble(const float2* __restrict__ ra, cons
   return make_float2(A.x - B.y, A.y + B.x);
 }
 
+// shared memory of the forward z pass: twiddles and exchange rows, then (noise source)
+// the Box-Muller table at a 16-byte boundary
+template <int N> constexpr int zr2c_tab_off() { return (PassCfg<N>::ZSMEM + 15) / 16 * 16; }
+template <int N, int SRC> constexpr int zr2c_smem() {
+  return SRC == Z_NOISE ? zr2c_tab_off<N>() + kBmTableLen * 16 : PassCfg<N>::ZSMEM;
+}
+
 template <int N, int SRC>
 __global__ void __launch_bounds__(PassCfg<N>::ZT, LPT2_Z_MINB) k_z_r2c(ZR2CArgs a) {
   using C = PassCfg<N>;
-  extern __shared__ float2 smem[];
+  extern __shared__ __align__(16) float2 smem[];
   float2* s_tw = smem;
+  float4* s_bm = reinterpret_cast<float4*>(reinterpret_cast<char*>(smem) + zr2c_tab_off<N>());
   load_twiddles(s_tw, a.tw, N);
+  if (SRC == Z_NOISE) {
+    bm_load_table(s_bm, a.bm);
+    __syncthreads();
+  }
   const int p = threadIdx.x / C::TPP, t = threadIdx.x % C::TPP;
   const SmemRowT<kRowWarp<N>> sm{smem + N + p * SmemRow::words(N)};
   const int pair = blockIdx.x * C::ZP + p;
@@ -142,7 +154,7 @@ __global__ void __launch_bounds__(PassCfg<N>::ZT, LPT2_Z_MINB) k_z_r2c(ZR2CArgs 
     const int n = elem<N>(t, r);
     float fa, fb;
     if (SRC == Z_NOISE) {   // rows (x, y) and (x, y+1), y even: one Box-Muller pair per z
-      const float2 g2 = philox_gauss2((uint64_t)rowa * N + n, a.seed_lo, a.seed_hi);
+      const float2 g2 = philox_gauss2((uint64_t)rowa * N + n, a.seed_lo, a.seed_hi, s_bm);
       fa = g2.x;
       fb = g2.y;
     } else {
@@ -257,7 +269,7 @@ __global__ void __launch_bounds__(PassCfg<N>::ZT, LPT2_Z_MINB) k_z_source(ZSourc
 #pragma unroll
   for (int f = 0; f < 6; ++f) {
     const int s = f % Q::STAGES;
-    const bool ok = mbar_wait(&bar[s], (f / Q::STAGES) & 1);
+    const bool ok = mbar_wait(&bar[s], (f / Q::STAGES) & 1, a.g.wait);
     if (!ok) s_fail = 1;
     float2 v[C::RMAX];
     const float2* ra = ring + s * Q::STAGE_F2 + (2 * p) * C::H;
@@ -337,11 +349,14 @@ __device__ __forceinline__ void cic_deposit_vec(float* __restrict__ rho, float u
   w = dx * dy;   add_zpair<N>(rho, ((size_t)jx * N + jy) * N, iz, jz, w * wz0, w * dz);
 }
 
-// wrap grid coordinate into [0, N)
+// wrap grid coordinate into [0, N); a value that is not finite, or a rounding stray of a
+// coordinate far outside the box, goes to 0, so every cell index derived from the result
+// lies in the grid whatever the input
 template <int N>
 __device__ __forceinline__ float wrapN(float u) {
   u = u - (float)N * floorf(u * (1.0f / N));
-  return (u >= (float)N) ? u - (float)N : u;
+  u = (u >= (float)N) ? u - (float)N : u;
+  return (u >= 0.0f && u < (float)N) ? u : 0.0f;
 }
 
 // Psi inputs (z order 1 -> Psi_z, 0 -> Psi_y, 0 -> Psi_x) -> particle positions
@@ -388,7 +403,7 @@ __global__ void __launch_bounds__(PassCfg<N>::ZT, LPT2_Z_MINB) k_z_final(ZFinalA
   for (int q = 0; q < NQ; ++q) {
     const int st = q % Q::STAGES;
     const int c = SPLIT ? (q >> 1) : q;   // 0: Psi_z, 1: Psi_y, 2: Psi_x
-    const bool ok = mbar_wait(&bar[st], (q / Q::STAGES) & 1);
+    const bool ok = mbar_wait(&bar[st], (q / Q::STAGES) & 1, a.g.wait);
     if (!ok) s_fail = 1;
     float2 v[C::RMAX];
     const float2* ra = ring + st * Q::STAGE_F2 + (2 * p) * C::H;
@@ -522,7 +537,7 @@ __global__ void __launch_bounds__(PassCfg<N>::ZT, LPT2_Z_MINB) k_z_adj_source(ZA
   for (int q = 0; q < NQ; ++q) {
     const int st = q % Q::STAGES;
     const int f = field(q);
-    const bool ok = mbar_wait(&bar[st], (q / Q::STAGES) & 1);
+    const bool ok = mbar_wait(&bar[st], (q / Q::STAGES) & 1, a.g.wait);
     if (!ok) s_fail = 1;
     float2 v[C::RMAX];
     const float2* ra = ring + st * Q::STAGE_F2 + (2 * p) * C::H;
@@ -956,8 +971,9 @@ __global__ void __launch_bounds__(PassCfg<N>::XT, x_minb<N>(MODE)) k_x(XArgs a) 
 template <int N, int SRC> cudaError_t launch_z_r2c_m(const ZR2CArgs& a, cudaStream_t s) {
   using C = PassCfg<N>;
   LPT2_CHECK_BATCH(a);
-  cudaFuncSetAttribute(k_z_r2c<N, SRC>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::ZSMEM);
-  k_z_r2c<N, SRC><<<dim3(N * N / 2 / C::ZP, 1, a.g.batch), C::ZT, C::ZSMEM, s>>>(a);
+  constexpr int smem = zr2c_smem<N, SRC>();
+  cudaFuncSetAttribute(k_z_r2c<N, SRC>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  k_z_r2c<N, SRC><<<dim3(N * N / 2 / C::ZP, 1, a.g.batch), C::ZT, smem, s>>>(a);
   return cudaGetLastError();
 }
 template <int N> cudaError_t launch_z_r2c_t(const ZR2CArgs& a, cudaStream_t s) {

@@ -37,6 +37,7 @@ struct Geo {
   int inst0;
   int tab_stride;       // floats per instance in the float growth tables
   int* err;             // device error word (0 = ok), may be null
+  long long wait;       // cycle budget of the bounded consumer waits (0: give up at once)
 };
 
 // Codes a kernel writes into Geo::err when a bounded wait gives up.
@@ -51,6 +52,7 @@ struct ZR2CArgs {      // forward z pass: real rows -> half-spectrum rows
   const float* in;     // Z_REAL / Z_DENSITY
   uint32_t seed_lo, seed_hi;
   const uint64_t* seeds;  // per global instance (Z_NOISE), or null to use seed_lo/hi
+  const float4* bm;       // Box-Muller tables (Z_NOISE; boxmuller.cuh)
   float2* out;         // [N*N][N/2]
 };
 
@@ -247,7 +249,10 @@ cudaError_t launch_src_t1(int n_bins, const double* ksum, const unsigned long lo
 cudaError_t launch_pk_finalize_p(const double* part, int n_blocks, int n_shells, const double* ksum,
                                  const unsigned long long* count, double* pk, double* k_mean, int64_t* n_modes,
                                  cudaStream_t s, int batch);
-cudaError_t launch_noise(const Geo& g, uint32_t seed_lo, uint32_t seed_hi, float* out, cudaStream_t);
+cudaError_t launch_noise(const Geo& g, uint32_t seed_lo, uint32_t seed_hi, const float4* bm, float* out,
+                         cudaStream_t);
+// Box-Muller transform of given word pairs (x0, x1) [count][2] -> floats [count][2].
+cudaError_t launch_box_muller(const uint32_t* words, int64_t count, const float4* bm, float* out, cudaStream_t);
 cudaError_t launch_philox_words(uint32_t seed_lo, uint32_t seed_hi, uint64_t first, int64_t count,
                                 uint32_t* out, cudaStream_t);
 

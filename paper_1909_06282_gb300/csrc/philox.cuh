@@ -4,9 +4,11 @@
 // two Weyl increments between rounds.  Key = (seed lo, seed hi); counter =
 // (cell lo, cell hi, 0, 0) with cell = (ix N + iy) N + iz of the cell with even
 // iy; cells (ix, iy, iz) and (ix, iy+1, iz) take the cosine and sine outputs of
-// the same Box-Muller transform.
+// the same Box-Muller transform (boxmuller.cuh).
 #pragma once
 #include <stdint.h>
+
+#include "boxmuller.cuh"
 
 namespace lpt2 {
 
@@ -26,16 +28,12 @@ __host__ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, ui
   return c;
 }
 
-// u = ((x >> 8) + 1) 2^-24 (exact in FP32, in (0, 1]);
-// (g_even, g_odd) = sqrt(-2 ln u0) (cos, sin)(2 pi u1) for the pair drawn at `cell`.
-__device__ __forceinline__ float2 philox_gauss2(uint64_t cell, uint32_t k0, uint32_t k1) {
+// (g_even, g_odd) = sqrt(-2 ln u0) (cos, sin)(2 pi u1), u = ((x >> 8) + 1) 2^-24, for the
+// pair drawn at `cell`, each the correctly rounded FP32 value (boxmuller.cuh).
+__device__ __forceinline__ float2 philox_gauss2(uint64_t cell, uint32_t k0, uint32_t k1,
+                                                const float4* bm) {
   const uint4 x = philox4x32_10(make_uint4((uint32_t)cell, (uint32_t)(cell >> 32), 0u, 0u), k0, k1);
-  const float u0 = (float)((x.x >> 8) + 1u) * 5.9604644775390625e-8f;
-  const float u1 = (float)((x.y >> 8) + 1u) * 5.9604644775390625e-8f;
-  const float r = sqrtf(-2.0f * logf(u0));
-  float sn, cs;
-  sincospif(2.0f * u1, &sn, &cs);
-  return make_float2(r * cs, r * sn);
+  return bm_pair(x.x, x.y, bm);
 }
 
 }  // namespace lpt2

@@ -54,12 +54,15 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   return ok != 0;
 }
 
-// Waits for phase `parity` of `bar` to complete; false if the cycle budget ran out.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+// Waits for phase `parity` of `bar` to complete; false if the cycle budget ran out.  A
+// budget of 0 gives up at once without looking at the barrier (how the timeout path is
+// tested: the copies are real and land, only the consumer stops waiting for them).
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, long long budget = LPT2_WAIT_CYCLES) {
+  if (budget <= 0) return false;
   if (mbar_try_wait(bar, parity)) return true;
   const long long t0 = clock64();
   while (!mbar_try_wait(bar, parity))
-    if (clock64() - t0 > LPT2_WAIT_CYCLES) return false;
+    if (clock64() - t0 > budget) return false;
   return true;
 }
 

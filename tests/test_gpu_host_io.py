@@ -39,7 +39,7 @@ def device_step(L, plan, noise=None):
 
 def test_philox_noise_matches_device_path(L):
     n = 64
-    plan = L.Plan(W.Instance(n, 128.0, 5, W.COSMO), n_steps=256)
+    plan = L.Plan(W.Instance(n, 128.0, 5, W.COSMO), n_steps=256, host_io=True)
     pos_ref, pk_ref = device_step(L, plan)
     pos = torch.empty((3, n, n, n), dtype=torch.float32).pin_memory()
     pk = torch.empty(NS, dtype=torch.float64).pin_memory()
@@ -53,7 +53,7 @@ def test_three_realisations_each_match(L, pinned):
     """Three host noise fields in one call (strided buffers): realisation r's outputs
     equal the device path run on noise r."""
     n, R = 64, 3
-    plan = L.Plan(W.Instance(n, 128.0, 1, W.COSMO), n_steps=256)
+    plan = L.Plan(W.Instance(n, 128.0, 1, W.COSMO), n_steps=256, host_io=True)
     noise = np.stack([W.white_noise(n, 100 + r) for r in range(R)])
     noise_h = torch.from_numpy(noise)
     pos = torch.empty((R, 3, n, n, n), dtype=torch.float32)
@@ -72,7 +72,7 @@ def test_shared_buffers_keep_the_last_realisation(L):
     """Stride 0: one noise buffer feeds every realisation and one position buffer
     receives every download; what remains is the last realisation's result."""
     n, R = 32, 4
-    plan = L.Plan(W.Instance(n, 64.0, 1, W.COSMO), n_steps=256)
+    plan = L.Plan(W.Instance(n, 64.0, 1, W.COSMO), n_steps=256, host_io=True)
     noise = np.stack([W.white_noise(n, 7 + r) for r in range(R)])
     pos = torch.empty((3, n, n, n), dtype=torch.float32).pin_memory()
     pk = torch.empty(NS, dtype=torch.float64).pin_memory()
@@ -93,7 +93,7 @@ def test_host_path_against_oracle(L):
     n, box = 32, 64.0
     inst = W.Instance(n, box, 3, W.COSMO)
     noise = W.white_noise(n, 11)
-    plan = L.Plan(inst, n_steps=1024)
+    plan = L.Plan(inst, n_steps=1024, host_io=True)
     pos = torch.empty((3, n, n, n), dtype=torch.float32)
     pk = torch.empty(NS, dtype=torch.float64)
     L.lpt2_displace_host(plan, 1, noise=torch.from_numpy(noise), pos=pos, pk=pk, n_shells=NS)
@@ -112,7 +112,7 @@ def test_full_size_two_realisations(L):
     """512^3, L = 1024 Mpc/h (the throughput configuration): two host noise fields, one
     shared pinned position buffer; P(k) of each equals the device path's."""
     n = 512
-    plan = L.Plan(W.Instance(n, 1024.0, 1, W.COSMO), n_steps=1024)
+    plan = L.Plan(W.Instance(n, 1024.0, 1, W.COSMO), n_steps=1024, host_io=True)
     noise = torch.from_numpy(np.stack([W.white_noise(n, 1000 + r) for r in range(2)])).pin_memory()
     pos = torch.empty((3, n, n, n), dtype=torch.float32).pin_memory()
     pk = torch.empty((2, NS), dtype=torch.float64).pin_memory()
@@ -126,7 +126,7 @@ def test_full_size_two_realisations(L):
 
 def test_argument_errors(L):
     n = 32
-    plan = L.Plan(W.Instance(n, 64.0, 1, W.COSMO), n_steps=64)
+    plan = L.Plan(W.Instance(n, 64.0, 1, W.COSMO), n_steps=64, host_io=True)
     pk = torch.empty(NS, dtype=torch.float64)
     with pytest.raises(L.LPT2Error):
         L.lpt2_displace_host(plan, 0, pk=pk, n_shells=NS)

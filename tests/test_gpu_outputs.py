@@ -41,7 +41,7 @@ def test_each_output_equals_a_plan_at_that_a(L, noise_seed):
     n, box, seed, steps = 64, 128.0, 4, 512
     a_list = [0.5, 0.8, 1.0, 0.25]
     noise = None if noise_seed is None else torch.from_numpy(W.white_noise(n, noise_seed)).cuda()
-    plan = L.Plan(W.Instance(n, box, seed, W.COSMO), n_steps=steps)
+    plan = L.Plan(W.Instance(n, box, seed, W.COSMO), n_steps=steps, max_outputs=4)
     L.lpt2_set_outputs(plan, a_list)
     out = L.lpt2_displace_outputs(plan, noise=noise, pos=True, n_shells=NS)
     torch.cuda.synchronize()
@@ -58,7 +58,7 @@ def test_each_output_equals_a_plan_at_that_a(L, noise_seed):
 def test_output_at_half_against_oracle(L):
     from oracle import lpt2
     n, box, seed = 32, 64.0, 2
-    plan = L.Plan(W.Instance(n, box, seed, W.COSMO), n_steps=1024)
+    plan = L.Plan(W.Instance(n, box, seed, W.COSMO), n_steps=1024, max_outputs=2)
     L.lpt2_set_outputs(plan, [1.0, 0.5])
     out = L.lpt2_displace_outputs(plan, pos=True, n_shells=NS)
     ref = lpt2.run(n, box, W.COSMO, seed=seed, a_out=0.5, n_steps=1024)
@@ -73,7 +73,7 @@ def test_output_at_half_against_oracle(L):
 
 def test_set_fr0_refreshes_the_output_tables(L):
     n, box, seed, steps = 32, 64.0, 3, 256
-    plan = L.Plan(W.Instance(n, box, seed, W.COSMO), n_steps=steps)
+    plan = L.Plan(W.Instance(n, box, seed, W.COSMO), n_steps=steps, max_outputs=2)
     L.lpt2_set_outputs(plan, [0.6, 1.0])
     L.lpt2_set_fr0(plan, 1e-6)
     out = L.lpt2_displace_outputs(plan, pos=True, n_shells=NS)
@@ -87,7 +87,7 @@ def test_full_size_two_outputs(L):
     """512^3, L = 1024 Mpc/h, |fR0| = 1e-5 (the throughput configuration), outputs at
     z = 1 and z = 0: each equals a one-output plan at that a."""
     n, box, steps = 512, 1024.0, 1024
-    plan = L.Plan(W.Instance(n, box, 1, W.COSMO), n_steps=steps)
+    plan = L.Plan(W.Instance(n, box, 1, W.COSMO), n_steps=steps, max_outputs=2)
     L.lpt2_set_outputs(plan, [0.5, 1.0])
     out = L.lpt2_displace_outputs(plan, pos=True, n_shells=NS)
     torch.cuda.synchronize()
@@ -103,7 +103,7 @@ def test_argument_errors(L):
     import ctypes as C
     from paper_1909_06282_gb300._lib import load_library
     n = 32
-    plan = L.Plan(W.Instance(n, 64.0, 1, W.COSMO), n_steps=64)
+    plan = L.Plan(W.Instance(n, 64.0, 1, W.COSMO), n_steps=64, max_outputs=4)
     pk = torch.empty(NS, dtype=torch.float64, device="cuda")
     # no output list yet
     rc = load_library().lpt2_displace_outputs(plan.handle, None, None, C.c_void_p(pk.data_ptr()), None, None, NS)
@@ -114,3 +114,25 @@ def test_argument_errors(L):
     batched = L.Plan([W.Instance(32, 64.0, s, W.COSMO) for s in (1, 2)], n_steps=64)
     with pytest.raises(L.LPT2Error):
         L.lpt2_set_outputs(batched, [0.5])
+    # more output times than the plan reserved room for in its workspace
+    with pytest.raises(L.LPT2Error, match="LPT2_MAX_OUTPUTS"):
+        L.lpt2_set_outputs(plan, [0.2, 0.4, 0.6, 0.8, 1.0])
+    small = L.Plan(W.Instance(n, 64.0, 1, W.COSMO), n_steps=64)
+    with pytest.raises(L.LPT2Error, match="LPT2_MAX_OUTPUTS"):
+        L.lpt2_set_outputs(small, [0.5])
+
+
+def test_output_tables_follow_a_new_workspace(L):
+    """The output tables live in the workspace: after lpt2_set_workspace with another
+    buffer they are recomputed there and the outputs are unchanged."""
+    n, box, seed, steps = 32, 64.0, 3, 256
+    plan = L.Plan(W.Instance(n, box, seed, W.COSMO), n_steps=steps, max_outputs=2)
+    L.lpt2_set_outputs(plan, [0.6, 1.0])
+    first = L.lpt2_displace_outputs(plan, pos=True, n_shells=NS)["pos"].clone()
+    import ctypes as C
+    from paper_1909_06282_gb300._lib import load_library
+    ws2 = torch.full_like(plan.workspace, 0x7F)
+    assert load_library().lpt2_set_workspace(plan.handle, C.c_void_p(ws2.data_ptr()), ws2.numel()) == 0
+    plan.workspace = ws2
+    second = L.lpt2_displace_outputs(plan, pos=True, n_shells=NS)["pos"]
+    assert torch.equal(first, second)
