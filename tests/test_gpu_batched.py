@@ -88,3 +88,32 @@ def test_batched_rejects_bad_orderings():
     p = L.Plan([a, b])
     with pytest.raises(L.LPT2Error):
         L.lpt2_displace_vjp(p)
+
+
+def test_batched_96_workload_one_instance_per_size_against_oracle():
+    """The real 96-instance batched workload (32 x 96^3/384, 128^3/512, 192^3/768 Mpc/h,
+    seeds 1-96, |fR0| log-uniform in [1e-6, 1e-4]) as one plan, in the launch configuration
+    the benchmark times (one CUDA graph): one instance of every grid size against the FP64
+    oracle (Psi1, Psi2 within the parity tolerances, P(k) of its density per shell)."""
+    from oracle import lpt2
+    L = lp()
+    insts = W.batched_96()
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        plan = L.Plan(insts, n_steps=1024, stream=stream, graph=True)
+        out = L.lpt2_displace(plan, psi1=True, psi2=True, pos=False)
+        pk = L.lpt2_cic_pk(plan, pos=None, n_shells=32)
+        stream.synchronize()
+    L.lpt2_device_status(plan)
+    for j in (5, 32 + 17, 64 + 30):     # one 96^3, one 128^3, one 192^3 instance
+        it = insts[j]
+        ref = lpt2.run(it.n, it.box, it.cosmo, seed=it.seed, n_steps=1024)
+        cell = it.box / it.n
+        for key in ("psi1", "psi2"):
+            got = plan.split(out[key], 3)[j].reshape(3, it.n, it.n, it.n).cpu().numpy()
+            rel = np.linalg.norm(got - ref[key]) / np.linalg.norm(ref[key])
+            mx = np.abs(got - ref[key]).max() / cell
+            assert rel <= 2e-5 and mx <= 1e-4, (j, key, rel, mx)
+        ok = ref["n_modes"] > 0
+        np.testing.assert_array_equal(pk["n_modes"][j].cpu().numpy(), ref["n_modes"])
+        np.testing.assert_allclose(pk["pk"][j].cpu().numpy()[ok], ref["pk"][ok], rtol=1e-4)

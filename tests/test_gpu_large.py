@@ -3,8 +3,14 @@ cell as the throughput workload), |fR0| = 1e-5.  The oracle computes delta(k) at
 modes by direct DFT sums over all 1.07e9 cells of the Philox field (oracle/sampled.py);
 properties that hold at any size check the rest.
   delta(k) at sampled modes    |GPU - oracle| <= 2e-5 rms|delta|
+  Psi1, Psi2 at 10 sampled     max |GPU - oracle| <= 1e-4 cell per component (oracle: the six
+  particles                    phi_ij and S on the full grid with a library real FFT in FP64,
+                               then direct inverse-DFT sums at the particles; about 70 GB of
+                               host memory); positions q + Psi1 + Psi2 within 2e-4 cell
   CIC density                  sum of the contrast = 0 (1e-6 N^3), contrast >= -1
   P(k)                         every shell filled; mode counts as the exact shell count
+This is the path of the large configuration: radix 16-4-16 pencils, z pencils of 64
+threads exchanging through CTA barriers, 8 pencils per y/x CTA.
 """
 import numpy as np
 import pytest
@@ -45,9 +51,55 @@ def run():
     return res
 
 
-def test_1024_delta_k_at_sampled_modes(run):
+@pytest.fixture(scope="module")
+def noise():
     from oracle import sampled
-    noise = sampled.noise_grid(N, SEED, chunk_rows=8)
+    return sampled.noise_grid(N, SEED, chunk_rows=8)
+
+
+CELLS = np.vstack([np.random.default_rng(2048).integers(0, N, size=(8, 3)), [[0, 0, 0], [N - 1, N - 1, N - 1]]])
+
+
+@pytest.fixture(scope="module")
+def psi_run():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1909_06282_gb300 import build as B
+    B.build()
+    import paper_1909_06282_gb300 as L
+    c = W.COSMO.replace(fr0_abs=1e-5)
+    plan = L.Plan(W.Instance(N, BOX, SEED, c), n_steps=512)
+    out = L.lpt2_displace(plan, psi1=True, psi2=True, pos=True)
+    torch.cuda.synchronize()
+    L.lpt2_device_status(plan)
+    res = {}
+    for key in ("psi1", "psi2", "pos"):
+        f = out[key].reshape(3, N, N, N)
+        res[key] = np.stack([f[:, x, y, z].double().cpu().numpy() for x, y, z in CELLS])
+    del out, f, plan
+    torch.cuda.empty_cache()
+    return res
+
+
+def test_1024_psi_at_sampled_particles(psi_run, noise):
+    from oracle import growth, sampled
+    c = W.COSMO.replace(fr0_abs=1e-5)
+    tab = growth.growth_tables(c, 1.0, n_steps=512)
+    p1, p2 = sampled.displacements_at(N, BOX, c, noise, tab, CELLS)
+    cell = BOX / N
+    e1 = np.abs(psi_run["psi1"] - p1).max() / cell
+    e2 = np.abs(psi_run["psi2"] - p2).max() / cell
+    q = CELLS.astype(np.float64) * cell
+    d = psi_run["pos"] - (q + p1 + p2)
+    d -= BOX * np.round(d / BOX)
+    print(f"1024^3, {len(CELLS)} particles: max |dPsi1| {e1:.2e}, |dPsi2| {e2:.2e}, |dx| "
+          f"{np.abs(d).max() / cell:.2e} cell")
+    assert e1 <= 1e-4 and e2 <= 1e-4, (e1, e2)
+    assert np.abs(d).max() <= 2e-4 * cell
+
+
+def test_1024_delta_k_at_sampled_modes(run, noise):
+    from oracle import sampled
     want = sampled.delta_k_modes(N, BOX, run["cosmo"], noise, run["modes"])
     err = np.abs(run["got"] - want)
     assert err.max() <= 2e-5 * run["rms"], (err / run["rms"], run["modes"])

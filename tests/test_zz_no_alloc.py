@@ -72,6 +72,23 @@ def test_noalloc_matches_plan_entry_point_two_calls(lib, n, box):
     check_same(call_noalloc(lib, n, box, pos_a), want_a)
 
 
+def test_noalloc_against_oracle_128(lib):
+    """The no-allocation entry point against the FP64 oracle directly (CIC density and
+    shell P(k) of seeded lattice-plus-jitter positions at 128^3), on two calls in a row."""
+    from oracle import lpt2
+    n, box = 128, 512.0
+    for seed in (31, 32):
+        pos = W.random_positions(n, box, seed)
+        got = call_noalloc(lib, n, box, torch.from_numpy(pos).cuda())
+        want = lpt2.cic_density(n, box, pos.astype(np.float64))
+        assert np.max(np.abs(got["density"] - want.reshape(n, n, n))) < 2e-5 * max(1.0, np.abs(want).max())
+        pk, km, cnt = lpt2.power_spectrum(n, box, want, 32)
+        np.testing.assert_array_equal(got["n_modes"], cnt)
+        ok = cnt > 0
+        np.testing.assert_allclose(got["pk"][ok], pk[ok], rtol=PK_REL)
+        np.testing.assert_allclose(got["k_mean"][ok], km[ok], rtol=1e-6)
+
+
 def test_noalloc_rejects_sizes_beyond_its_static_scratch(lib):
     L = lib
     pk = torch.empty(32, dtype=torch.float64, device="cuda")
