@@ -1,23 +1,41 @@
-"""GPU adjoint (lpt2_displace_vjp) against the FP64 oracle adjoint and against
-central finite differences of the GPU forward map.
+"""GPU adjoint (lpt2_displace_vjp) against the FP64 oracle adjoint and against central
+finite differences of a float64 forward map, at the 1e-3 bar.
 
-Loss: L = sum (delta - delta_t)^2 / N^3 + sum_b (ln P_b - ln P_t,b)^2, the target
-from seed 7.  Tolerances: gradient vs FP64 oracle gradient (relative L2 of g_noise,
-relative dL/dln|fR0|) 1e-5 for position cotangents, 1e-4 (32^3) / 2e-3 (64^3) for the
-full loss; directional central differences of the FP32 forward along a random
-unit-variance direction: smooth position loss (step 0.05) within 1e-4, density +
-P(k) loss (step 1e-4) within 2e-3 on average over four directions, ln|fR0| (step
-1e-2) within 1e-3.
+Loss (the differentiable configuration): L = sum (delta - delta_t)^2 / N^3 +
+sum_b (ln P_b - ln P_t,b)^2, the target from seed 7.
 
-CIC face crossings: the transpose of the CIC deposit is discontinuous at cell
-faces (one-sided derivatives differ).  A particle whose FP32 and FP64 positions
-(about 1e-5 cell apart) fall on opposite sides of a face takes a different, equally
-valid, one-sided derivative; at 64^3 a few of the 786k coordinates do, which moves
-the density-term gradient by ~1e-3 in relative L2.  The smooth part of the adjoint
-(position cotangents, no CIC) is therefore compared at 1e-5 at every size; the
-full loss is compared at 1e-4 at 32^3 and 2e-3 at 64^3.
-Per-cell differences are checked on the oracle in FP64 (tests/test_oracle_vjp.py):
-in FP32 a single cell moves the loss by ~1e-9 of itself, below FP32 resolution.
+  oracle gradient (FP64 hand adjoint, full loss)       rel. L2 of g_noise and rel. dL/dln|fR0|
+                                                       <= 1e-3 at 32^3 and 64^3 (measured
+                                                       4e-6 and 1.1e-4)
+  CIC transpose, masked                                <= 1e-4 (see below)
+  finite differences (64 random noise cells, step 1e-3, rel. L2 over the cells <= 1e-3,
+  and dL/dln|fR0| with step 1e-3)                      at 64^3 and at 512^3, L = 1024 Mpc/h,
+                                                       |fR0| = 1e-5, Philox seed 1
+
+The loss is piecewise smooth in the noise: the CIC deposit is linear within a cell and
+its derivative jumps where a particle crosses a cell face.  Two effects follow.
+- Differences: between w - h e_c and w + h e_c a few particles may cross a face.  The
+  float64 forward map of tests/fd64.py deposits every particle with the lower-corner
+  cell it has at w (the weights 1 - d, d extended linearly), so each difference stays on
+  the branch at w; the test states how many particles would have changed cell.
+- FP32 against FP64: a particle whose FP32 position (the GPU's: rounding of the absolute
+  coordinate and of the transforms, up to about 3e-5 of a cell at 512^3) and FP64
+  position lie on opposite sides of a face takes the other one-sided derivative.  Both
+  are valid gradients of the piecewise-linear map, so what is compared is the part that
+  is unique, and the branch of those particles is checked separately:
+  * oracle comparison at 64^3: 2 such particles move the full-loss gradient by 1.1e-4;
+    for the density term alone, whose gradient norm is small, they dominate (1.5e-3), and
+    the masked check removes them by replacing the density cotangent g at the cells
+    around every particle within 1e-5 cell of a face (the oracle's positions) by its
+    linear interpolation across the face, g_c = (g_{c-1} + g_{c+1}) / 2, which makes the
+    two one-sided derivatives equal; both adjoints then get that same cotangent;
+  * central differences: for every particle whose FP32 cell differs from the FP64 one, the
+    test takes the difference of its two one-sided CIC derivatives (dL/dx at the GPU's
+    position and cell minus at the FP64 ones, from the float64 density cotangent) and
+    removes its effect from the GPU gradient with the GPU's own position-cotangent adjoint
+    (checked against the oracle at 1e-5 above).  Both the raw and the corrected relative
+    error are printed; the corrected one must be <= 1e-3 and the correction itself must
+    stay below 5e-3 of the gradient (at 512^3: 4216 of 134M particles, 1.8e-3).
 """
 import numpy as np
 import pytest
@@ -77,27 +95,186 @@ def test_vjp_position_cotangent_against_oracle(n, box, fr0):
     assert abs(float(g_t) - want_t) <= 1e-5 * abs(want_t), (float(g_t), want_t)
 
 
-@pytest.mark.parametrize("n,box,fr0,tol", [(32, 128.0, 1e-4, 1e-4), (64, 256.0, 1e-5, 2e-3)])
-def test_vjp_against_oracle(n, box, fr0, tol):
+def oracle_setup(n, box, fr0, noise_seed=3):
     from oracle import growth as gr
     from oracle import philox
     from oracle import vjp as ov
     c = W.COSMO.replace(fr0_abs=fr0)
     tab = gr.growth_tables(c, 1.0, n_steps=STEPS)
     tgt = ov.forward_state(n, box, c, philox.gaussian_noise(n, 7, as_float64=True).reshape(n, n, n), tab, NS)
-    noise = W.white_noise(n, 3)
+    noise = W.white_noise(n, noise_seed)
     st = ov.forward_state(n, box, c, noise.astype(np.float64), tab, NS)
+    return c, tab, tgt, noise, st
+
+
+@pytest.mark.parametrize("n,box,fr0", [(32, 128.0, 1e-4), (64, 256.0, 1e-5)])
+def test_vjp_against_oracle(n, box, fr0):
+    from oracle import vjp as ov
+    c, tab, tgt, noise, st = oracle_setup(n, box, fr0)
     _, gd, gp = ov.loss_and_cotangents(st["density"], st["pk"], tgt["density"], tgt["pk"])
     want_w, want_t = ov.vjp(n, box, st, tab, gd, gp, NS)
-
     plan = lp().Plan(W.Instance(n, box, 1, c), n_steps=STEPS)
     g_noise, g_t = lp().lpt2_displace_vjp(plan, g_density=torch.from_numpy(gd.astype(np.float32)).cuda(),
                                           g_pk=torch.from_numpy(gp).cuda(),
                                           noise=torch.from_numpy(noise).cuda(), n_shells=NS)
     got = g_noise.cpu().numpy()
     rel = np.linalg.norm(got - want_w) / np.linalg.norm(want_w)
-    assert rel < tol, rel
-    assert abs(float(g_t) - want_t) <= tol * abs(want_t), (float(g_t), want_t)
+    # particles whose GPU and oracle positions lie on opposite sides of a cell face
+    pos = lp().lpt2_displace(plan, noise=torch.from_numpy(noise).cuda(), psi1=False, psi2=False,
+                             pos=True)["pos"].cpu().numpy().reshape(3, -1).astype(np.float64)
+    sides = int(np.sum(np.any(np.floor(pos * (n / box)) % n != np.floor(st["pos"] * (n / box)) % n, axis=0)))
+    print(f"vjp {n}^3 full loss: rel L2 {rel:.2e}, dL/dln|fR0| {abs(float(g_t) - want_t) / abs(want_t):.2e}, "
+          f"{sides} particles on the other side of a face")
+    assert rel < 1e-3, rel
+    assert abs(float(g_t) - want_t) <= 1e-3 * abs(want_t), (float(g_t), want_t)
+
+
+def linearise_near_faces(n, box, pos, g, eps=1e-5):
+    """The density cotangent with g at the cells around every particle within eps of a cell
+    face replaced by its linear interpolation across that face (see the module docstring).
+    Returns the new cotangent and the number of (particle, axis) pairs treated."""
+    g = g.reshape(n, n, n).copy()
+    u = pos * (n / box)
+    fl = np.floor(u)
+    frac = u - fl
+    count = 0
+    for a in range(3):
+        near = np.nonzero((frac[a] < eps) | (frac[a] > 1.0 - eps))[0]
+        others = [o for o in range(3) if o != a]
+        for p in near:
+            face = int(np.rint(u[a, p])) % n
+            for t0 in (0, 1):
+                for t1 in (0, 1):
+                    idx = [0, 0, 0]
+                    idx[others[0]] = int(fl[others[0], p] + t0) % n
+                    idx[others[1]] = int(fl[others[1], p] + t1) % n
+                    lo, mid, hi = list(idx), list(idx), list(idx)
+                    lo[a], mid[a], hi[a] = (face - 1) % n, face, (face + 1) % n
+                    g[tuple(mid)] = 0.5 * (g[tuple(lo)] + g[tuple(hi)])
+            count += 1
+    return g, count
+
+
+def test_vjp_cic_transpose_masked_against_oracle():
+    """Density term alone, with the cotangent made linear across the faces near which the
+    FP32 and FP64 positions may disagree on the cell: the adjoints must then agree to FP32
+    rounding."""
+    from oracle import vjp as ov
+    n, box = 64, 256.0
+    c, tab, tgt, noise, st = oracle_setup(n, box, 1e-5)
+    _, gd, _ = ov.loss_and_cotangents(st["density"], st["pk"], tgt["density"], tgt["pk"])
+    gm, count = linearise_near_faces(n, box, st["pos"], gd)
+    want_w, want_t = ov.vjp(n, box, st, tab, gm, np.zeros(NS), NS)
+    plan = lp().Plan(W.Instance(n, box, 1, c), n_steps=STEPS)
+    g_noise, g_t = lp().lpt2_displace_vjp(plan, g_density=torch.from_numpy(gm.astype(np.float32)).cuda(),
+                                          noise=torch.from_numpy(noise).cuda(), n_shells=NS)
+    got = g_noise.cpu().numpy()
+    rel = np.linalg.norm(got - want_w) / np.linalg.norm(want_w)
+    print(f"vjp {n}^3 density term, {count} particle-axis pairs within 1e-5 cell of a face masked: "
+          f"rel L2 {rel:.2e}")
+    assert rel < 1e-4, rel
+    assert abs(float(g_t) - want_t) <= 1e-4 * abs(want_t), (float(g_t), want_t)
+
+
+def _fd_check(n, box, fr0, noise_np, n_cells=64, h=1e-3, steps=STEPS, seed_cells=2024):
+    """GPU adjoint against central differences of the float64 forward map (tests/fd64.py)
+    at n_cells random noise cells and in ln|fR0|; returns the relative errors and counts."""
+    from oracle import growth as gr
+    from oracle import philox
+    from fd64 import Forward64
+    c = W.COSMO.replace(fr0_abs=fr0)
+    tab = gr.growth_tables(c, 1.0, n_steps=steps)
+    F = Forward64(n, box, c, tab, NS)
+    w = torch.from_numpy(noise_np.astype(np.float64)).cuda().reshape(-1)
+    tw = torch.from_numpy(philox.gaussian_noise(n, 7, as_float64=True)).cuda()
+    ut = F.lattice_coords(tw)
+    dt = F.density(ut)
+    pt = F.power(dt)
+    del ut
+    u0 = F.lattice_coords(w)
+    base = torch.floor(u0).long()
+    d0 = F.density(u0, base)
+    p0 = F.power(d0)
+    gd, gp = F.cotangents(d0, p0, dt, pt)
+    plan = lp().Plan(W.Instance(n, box, 1, c), n_steps=steps)
+    nz32 = w.float().reshape(n, n, n).contiguous()
+    g_noise, g_t = lp().lpt2_displace_vjp(plan, g_density=gd.float().contiguous(), g_pk=gp.contiguous(),
+                                          noise=nz32, n_shells=NS)
+    # particles on the other side of a face in the GPU's FP32 positions, and the branch
+    # correction: the GPU adjoint of the difference of their one-sided CIC derivatives
+    pos = lp().lpt2_displace(plan, noise=nz32, psi1=False, psi2=False, pos=True)["pos"].reshape(3, -1)
+    ug = pos.double() * (n / box)
+    bg = torch.floor(ug).long()
+    swap = torch.any(torch.remainder(bg, n) != torch.remainder(base, n), dim=0)
+    sides = int(swap.sum())
+    idx = torch.nonzero(swap).reshape(-1)
+    g_rho = F.density_cotangent(d0, gd, gp)
+    # the FP64 particle at its own cell, shifted by whole boxes to the GPU's image
+    shift = torch.round((ug[:, idx] - u0[:, idx]) / n) * n
+    delta = F.cic_transpose(ug[:, idx], bg[:, idx], g_rho) - F.cic_transpose(u0[:, idx] + shift, base[:, idx] + shift.long(), g_rho)
+    g_pos = torch.zeros((3, n ** 3), dtype=torch.float32, device="cuda")
+    g_pos[:, idx] = delta.float()
+    corr, _ = lp().lpt2_displace_vjp(plan, g_pos=g_pos, noise=nz32, n_shells=NS)
+    del pos, ug, bg, g_pos
+    rng = np.random.default_rng(seed_cells)
+    cells = rng.choice(n ** 3, size=n_cells, replace=False)
+    fd = np.zeros(n_cells)
+    crossed = 0
+    for j, cidx in enumerate(cells):
+        ls = []
+        for sgn in (1.0, -1.0):
+            wp = w.clone()
+            wp[cidx] += sgn * h
+            up = F.lattice_coords(wp)
+            crossed += int(torch.any(torch.floor(up).long() != base, dim=0).sum())
+            dp = F.density(up, base)
+            ls.append(F.loss(dp, F.power(dp), dt, pt))
+            del up, dp
+        fd[j] = (ls[0] - ls[1]) / (2 * h)
+    sel = torch.from_numpy(cells).cuda()
+    an = g_noise.reshape(-1)[sel].double().cpu().numpy()
+    cr = corr.reshape(-1)[sel].double().cpu().numpy()
+    raw = np.linalg.norm(an - fd) / np.linalg.norm(fd)
+    rel = np.linalg.norm(an - cr - fd) / np.linalg.norm(fd)
+    size = np.linalg.norm(cr) / np.linalg.norm(fd)
+    # ln|fR0|: the growth tables at |fR0| e^{+-h}
+    lt = []
+    for sgn in (1.0, -1.0):
+        F.set_tables(gr.growth_tables(c.replace(fr0_abs=fr0 * np.exp(sgn * h)), 1.0, n_steps=steps))
+        up = F.lattice_coords(w)
+        dp = F.density(up, base)
+        lt.append(F.loss(dp, F.power(dp), dt, pt))
+        del up, dp
+    fdt = (lt[0] - lt[1]) / (2 * h)
+    rel_t = abs(float(g_t) - fdt) / abs(fdt)
+    return dict(rel=rel, raw=raw, size=size, rel_t=rel_t, sides=sides, crossed=crossed)
+
+
+def report(n, r):
+    print(f"vjp {n}^3 vs central differences (64 cells, step 1e-3): rel L2 {r['rel']:.2e} "
+          f"(raw {r['raw']:.2e}, branch correction {r['size']:.2e} for {r['sides']} particles on the other "
+          f"side of a face in FP32), dL/dln|fR0| {r['rel_t']:.2e}; {r['crossed']} face crossings frozen")
+    assert r["rel"] <= 1e-3, r
+    assert r["size"] <= 5e-3, r
+    assert r["rel_t"] <= 1e-3, r
+
+
+def test_vjp_against_central_differences_64():
+    n, box = 64, 256.0
+    r = _fd_check(n, box, 1e-5, W.white_noise(n, 3))
+    report(n, r)
+
+
+def test_vjp_against_central_differences_512():
+    """The differentiable configuration: 512^3, L = 1024 Mpc/h, |fR0| = 1e-5, the Philox
+    noise of seed 1 (drawn by the library, FP32, exact in FP64), target seed 7; central
+    differences (step 1e-3) at 64 random noise cells (host RNG seed 2024) and in ln|fR0|."""
+    n, box = 512, 1024.0
+    plan = lp().Plan(W.Instance(n, box, 1, W.COSMO.replace(fr0_abs=1e-5)), n_steps=16)
+    noise = lp().lpt2_white_noise(plan).cpu().numpy()
+    del plan
+    r = _fd_check(n, box, 1e-5, noise, steps=1024)
+    report(n, r)
 
 
 def _loss_setup(n, box):
@@ -136,41 +313,6 @@ def test_vjp_directional_fd_smooth_position_loss():
     fd = (L(noise + h * d) - L(noise - h * d)) / (2 * h)
     an = float((g_noise.double() * d.double()).sum())
     assert abs(fd - an) <= 1e-4 * abs(fd), (fd, an)
-
-
-def test_vjp_directional_fd_density_pk_loss():
-    """Density + P(k) loss. CIC is piecewise linear, so the step is kept small (1e-4)
-    to limit the cell-face crossings inside the difference.  Particles that cross a
-    face within +-h (about 0.2 % of them at this step) still make each central
-    difference uncertain at the 1e-3 level, with a sign that varies from direction to
-    direction, so the check averages the relative error over four random directions
-    (mean <= 2e-3, each <= 5e-3); the smooth loss above checks the same adjoint at
-    1e-4 and the oracle comparison checks the CIC transpose itself."""
-    n, box = 64, 256.0
-    plan, tgt_d, tgt_pk, noise = _loss_setup(n, box)
-    L0, d, pk = gpu_loss(plan, noise, tgt_d, tgt_pk)
-    gd, gp = _cotangents(d, pk, tgt_d, tgt_pk)
-    g_noise, g_t = lp().lpt2_displace_vjp(plan, g_density=gd, g_pk=gp, noise=noise, n_shells=NS)
-    h = 1e-4
-    errs = []
-    for dseed in (11, 12, 13, 14):
-        v = torch.from_numpy(W.white_noise(n, dseed)).cuda()
-        lp_, _, _ = gpu_loss(plan, (noise + h * v).contiguous(), tgt_d, tgt_pk)
-        lm_, _, _ = gpu_loss(plan, (noise - h * v).contiguous(), tgt_d, tgt_pk)
-        fd = (lp_ - lm_) / (2 * h)
-        an = float((g_noise.double() * v.double()).sum())
-        errs.append(abs(fd - an) / abs(fd))
-    assert np.mean(errs) <= 2e-3 and max(errs) <= 5e-3, errs
-    # d/dln|fR0| by central differences of the GPU forward (tables recomputed).  Step 1e-2:
-    # the multiplier tables are FP32, whose rounding (6e-8 of D1) is 1e-3 of the change a
-    # 1e-3 step makes; the O(h^2) truncation of a 1e-2 step is ~1e-5.
-    hf = 1e-2
-    lp().lpt2_set_fr0(plan, 1e-5 * np.exp(hf))
-    lpf, _, _ = gpu_loss(plan, noise, tgt_d, tgt_pk)
-    lp().lpt2_set_fr0(plan, 1e-5 * np.exp(-hf))
-    lmf, _, _ = gpu_loss(plan, noise, tgt_d, tgt_pk)
-    fdt = (lpf - lmf) / (2 * hf)
-    assert abs(fdt - float(g_t)) <= 1e-3 * abs(fdt), (fdt, float(g_t))
 
 
 def test_autograd_function_matches_vjp():
