@@ -151,49 +151,96 @@ import json, sys, time
 sys.path.insert(0, {root!r})
 import workloads as W
 from oracle import growth, lpt2
-n, box, reps = {n}, {box}, {reps}
+n, box, reps, seed0 = {n}, {box}, {reps}, {seed0}
 c = W.COSMO.replace(fr0_abs={fr0})
 tables = growth.growth_tables(c, 1.0, n_steps=1024)
+sys.stdout.write("ready\n")
+sys.stdout.flush()
+sys.stdin.readline()                   # start together with the other processes
 t0 = time.perf_counter()
 for r in range(reps):
-    out = lpt2.run(n, box, c, seed=1 + r, tables=tables, n_shells={ns})
+    out = lpt2.run(n, box, c, seed=seed0 + r, tables=tables, n_shells={ns})
 dt = time.perf_counter() - t0
 print(json.dumps(dict(seconds=dt, particles=reps * n ** 3)))
 """
 
 
-def run_oracle_sample(reps, n=SAMPLE_N, box=SAMPLE_BOX):
-    """Runs the oracle in a fresh single-threaded process (spawned, never forked)."""
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def cpu_model():
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
+def run_oracle_sample(reps, n=SAMPLE_N, box=SAMPLE_BOX, procs=1):
+    """Runs the oracle in `procs` fresh single-threaded processes at once (exec'd, never
+    forked from this one), each on `reps` realisations of its own seeds; returns the
+    particles of all of them and the wall time from the common start to the last finish."""
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
                CUDA_VISIBLE_DEVICES="")
-    code = ORACLE_SAMPLE_CODE.format(root=ROOT, n=n, box=box, reps=reps, fr0=WORKLOAD["fr0"],
-                                     ns=WORKLOAD["n_shells"])
-    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=900)
-    if r.returncode != 0:
-        raise RuntimeError("oracle sample failed: " + r.stderr[-2000:])
-    return json.loads(r.stdout.strip().splitlines()[-1])
+    ps = []
+    for i in range(procs):
+        code = ORACLE_SAMPLE_CODE.format(root=ROOT, n=n, box=box, reps=reps, seed0=1 + i * reps,
+                                         fr0=WORKLOAD["fr0"], ns=WORKLOAD["n_shells"])
+        ps.append(subprocess.Popen([sys.executable, "-c", code], stdin=subprocess.PIPE, stdout=subprocess.PIPE,
+                                   stderr=subprocess.PIPE, text=True, env=env))
+    for p in ps:                         # every process has its tables: start them together
+        if p.stdout.readline().strip() != "ready":
+            raise RuntimeError("oracle sample failed: " + p.stderr.read()[-2000:])
+    t0 = time.perf_counter()
+    for p in ps:
+        p.stdin.write("go\n")
+        p.stdin.flush()
+    results = []
+    for p in ps:
+        out, err = p.communicate(timeout=1800)
+        if p.returncode != 0:
+            raise RuntimeError("oracle sample failed: " + err[-2000:])
+        results.append(json.loads(out.strip().splitlines()[-1]))
+    wall = time.perf_counter() - t0
+    return dict(seconds=wall, particles=sum(r["particles"] for r in results), procs=procs)
 
 
 def bench_reference(args):
     world, rank, _ = dist_env()
     if rank != 0:
         return
+    cores = host_cores()
     per = []
     for i in range(args.warmup + args.steps):
-        res = run_oracle_sample(1)
+        res = run_oracle_sample(1, procs=cores)   # one realisation per host core, all at once
         if i >= args.warmup:
             per.append(res["seconds"])
     sec = sum(per) / len(per)
-    value = SAMPLE_N ** 3 / sec
+    value = cores * SAMPLE_N ** 3 / sec
     line = {
         "impl": "reference", "metric": "particles_per_s", "value": value, "unit": "particles/s",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
         "config": dict(workload_config(world), sample=f"{SAMPLE_N}^3 grid, L={SAMPLE_BOX:g} Mpc/h "
-                       "(same cell size), one realisation per step, growth tables precomputed"),
-        "cpu_baseline": {"value": value, "unit": "particles/s", "cores": 1, "kind": "oracle",
-                         "sample": f"{SAMPLE_N}^3 sub-box at the workload's cell size, per step"},
+                       f"(same cell size), one realisation per host core ({cores}) per step, growth "
+                       "tables precomputed"),
+        "cpu_baseline": {"value": value, "unit": "particles/s", "cores": cores, "kind": "oracle",
+                         "cpu_model": cpu_model(),
+                         "sample": f"{SAMPLE_N}^3 sub-box at the workload's cell size, one per core per step"},
         "e2e": {"value": value, "unit": "particles/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -656,13 +703,28 @@ def bench_ours(args):
             "clocks": clk.summary(),
         }
         if not args.no_cpu_baseline:
-            reps = 3
-            res = run_oracle_sample(reps)
-            line["cpu_baseline"] = {"value": res["particles"] / res["seconds"], "unit": "particles/s",
-                                    "cores": 1, "kind": "oracle",
-                                    "sample": f"{reps} realisations of a {SAMPLE_N}^3 grid at the workload's "
-                                              f"cell size (L={SAMPLE_BOX:g} Mpc/h), growth tables precomputed, "
-                                              f"{res['seconds']:.1f} s"}
+            # the oracle on every host core (one process per core, independent realisations)
+            # and on one core, 64^3 samples at the workload's cell size
+            reps, cores = 3, host_cores()
+            res = run_oracle_sample(reps, procs=cores)
+            one = run_oracle_sample(reps)
+            line["cpu_baseline"] = {
+                "value": res["particles"] / res["seconds"], "unit": "particles/s", "cores": cores,
+                "kind": "oracle", "cpu_model": cpu_model(),
+                "sample": f"{reps} realisations of a {SAMPLE_N}^3 grid at the workload's cell size "
+                          f"(L={SAMPLE_BOX:g} Mpc/h) per core, {cores} single-threaded processes at once, "
+                          f"growth tables precomputed, {res['seconds']:.1f} s",
+                "one_core": {"value": one["particles"] / one["seconds"], "unit": "particles/s",
+                             "sample": f"{reps} realisations of {SAMPLE_N}^3, {one['seconds']:.1f} s"}}
+            if args.oracle_256:
+                n2, b2 = 256, WORKLOAD["box"] * 256 / WORKLOAD["n"]
+                r1 = run_oracle_sample(1, n=n2, box=b2)
+                ra = run_oracle_sample(1, n=n2, box=b2, procs=cores)
+                line["cpu_baseline"]["at_256"] = {
+                    "one_core": r1["particles"] / r1["seconds"], "all_cores": ra["particles"] / ra["seconds"],
+                    "unit": "particles/s",
+                    "sample": f"one 256^3 realisation (L={b2:g} Mpc/h) on one core ({r1['seconds']:.0f} s) "
+                              f"and one per core on {cores} cores ({ra['seconds']:.0f} s)"}
         print(json.dumps(line), flush=True)
     if dist:
         dist.barrier()
@@ -676,6 +738,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--oracle-256", action="store_true",
+                    help="also time the oracle on a 256^3 realisation, on one core and on every core "
+                         "(minutes of CPU time)")
     ap.add_argument("--no-batched", action="store_true", help="skip the 96-instance batched measurement")
     ap.add_argument("--no-cufft", action="store_true", help="skip the cuFFT comparison pipeline")
     ap.add_argument("--no-source", action="store_true", help="skip the full-source diagnostic timing")
