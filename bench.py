@@ -247,8 +247,9 @@ def bench_reference(args):
 
 
 def profile_run(args):
-    """A short forward-only run for profilers (`--profile`): plan, args.warmup + args.steps
-    forward steps, no timing output beyond one line."""
+    """A short run for profilers (`--profile`): plan, args.warmup + args.steps forward steps
+    (with --profile-vjp each followed by the adjoint of the density + P(k) loss against
+    zero targets), no timing output beyond one line."""
     import torch
 
     import paper_1909_06282_gb300 as L
@@ -258,7 +259,11 @@ def profile_run(args):
     plan = L.Plan(W.Instance(n, box, 1, W.COSMO.replace(fr0_abs=WORKLOAD["fr0"])), n_steps=1024)
     for _ in range(args.warmup + args.steps):
         L.lpt2_displace(plan, psi1=False, psi2=False, pos=True)
-        L.lpt2_cic_pk(plan, pos=None, n_shells=WORKLOAD["n_shells"])
+        r = L.lpt2_cic_pk(plan, pos=None, density=args.profile_vjp, n_shells=WORKLOAD["n_shells"])
+        if args.profile_vjp:
+            gd = (2.0 / r["density"].numel()) * r["density"]
+            L.lpt2_displace_vjp(plan, g_density=gd.contiguous(), g_pk=(1.0 / r["pk"].clamp_min(1e-30)).contiguous(),
+                                n_shells=WORKLOAD["n_shells"])
     torch.cuda.synchronize()
     print(json.dumps({"profile_run": True, "grid": n, "box": box, "launches": L.lpt2_launch_count(plan)}))
 
@@ -746,6 +751,7 @@ def main():
     ap.add_argument("--no-source", action="store_true", help="skip the full-source diagnostic timing")
     ap.add_argument("--no-large", action="store_true", help="skip the 1024^3 forward timing")
     ap.add_argument("--no-multi-a", action="store_true", help="skip the several-output-times timing")
+    ap.add_argument("--profile-vjp", action="store_true", help="with --profile: run the adjoint after each step")
     ap.add_argument("--profile", action="store_true",
                     help="forward-only run for ncu (no timing); grid from --grid")
     ap.add_argument("--grid", type=int, default=WORKLOAD["n"],

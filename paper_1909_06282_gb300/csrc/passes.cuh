@@ -125,8 +125,12 @@ template <int N, int SRC> constexpr int zr2c_smem() {
   return SRC == Z_NOISE ? zr2c_tab_off<N>() + kBmTableLen * 16 : PassCfg<N>::ZSMEM;
 }
 
+#ifndef LPT2_ZNOISE_MINB
+#define LPT2_ZNOISE_MINB 3   // resident noise-pass CTAs per SM asked: 80 registers (it is issue bound)
+#endif
 template <int N, int SRC>
-__global__ void __launch_bounds__(PassCfg<N>::ZT, LPT2_Z_MINB) k_z_r2c(ZR2CArgs a) {
+__global__ void __launch_bounds__(PassCfg<N>::ZT, SRC == Z_NOISE ? LPT2_ZNOISE_MINB : LPT2_Z_MINB)
+    k_z_r2c(ZR2CArgs a) {
   using C = PassCfg<N>;
   extern __shared__ __align__(16) float2 smem[];
   float2* s_tw = smem;
@@ -265,48 +269,65 @@ __global__ void __launch_bounds__(PassCfg<N>::ZT, LPT2_Z_MINB) k_z_source(ZSourc
     }
   }
   load_twiddles(s_tw, a.tw, N);
-  float S0[C::RMAX], S1[C::RMAX], T0[C::RMAX], T1[C::RMAX];
-#pragma unroll
-  for (int f = 0; f < 6; ++f) {
+  // field f of the ring into v, then the copy of field f + STAGES; false if a wait ran out
+  // (the CTA has then drained its copies and reported, and must return)
+  auto fetch = [&](int f, float2 (&v)[C::RMAX]) -> bool {
     const int s = f % Q::STAGES;
     const bool ok = mbar_wait(&bar[s], (f / Q::STAGES) & 1, a.g.wait);
     if (!ok) s_fail = 1;
-    float2 v[C::RMAX];
     const float2* ra = ring + s * Q::STAGE_F2 + (2 * p) * C::H;
+    const int m = a.ord[f];
 #pragma unroll
     for (int r = 0; r < C::RMAX; ++r)
-      v[r] = ok ? z_assemble_smem<N>(ra, ra + C::H, elem<N>(t, r), a.g.kf, a.ord[f]) : make_float2(0.f, 0.f);
+      v[r] = ok ? z_assemble_smem<N>(ra, ra + C::H, elem<N>(t, r), a.g.kf, m) : make_float2(0.f, 0.f);
     __syncthreads();   // stage s consumed by every thread (and, at f = 0, twiddles visible)
     if (s_fail) {      // a copy never landed: wait (bounded) for the copies in flight, report
       if (threadIdx.x == 0) {
         for (int g = f; g < 6 && g < f + Q::STAGES; ++g) mbar_wait(&bar[g % Q::STAGES], (g / Q::STAGES) & 1);
         report_device_error(a.g.err, LPT2_DEV_ETIMEOUT_ZSOURCE);
       }
-      return;
+      return false;
     }
     if (threadIdx.x == 0 && f + Q::STAGES < 6) {
       mbar_expect_tx(&bar[s], Q::STAGE_BYTES);
       bulk_load(ring + s * Q::STAGE_F2, a.in[f + Q::STAGES] + zoff + tile, Q::STAGE_BYTES, &bar[s]);
     }
+    return true;
+  };
+  float S0[C::RMAX], S1[C::RMAX], T0[C::RMAX], T1[C::RMAX];
+#pragma unroll
+  for (int f = 0; f < 3; ++f) {   // phi_xx, phi_yy, phi_zz
+    float2 v[C::RMAX];
+    if (!fetch(f, v)) return;
     fft<N, true>(v, t, sm, s_tw);
 #pragma unroll
     for (int r = 0; r < C::RMAX; ++r) {
       const float e = v[r].x, g = v[r].y;   // rows 2p and 2p + 1
-      if (f == 0) {            // phi_xx
+      if (f == 0) {
         S0[r] = e;
         S1[r] = g;
-      } else if (f == 1) {     // phi_yy
+      } else if (f == 1) {
         T0[r] = S0[r] + e;
         T1[r] = S1[r] + g;
         S0[r] *= e;
         S1[r] *= g;
-      } else if (f == 2) {     // phi_zz
+      } else {
         S0[r] = fmaf(T0[r], e, S0[r]);
         S1[r] = fmaf(T1[r], g, S1[r]);
-      } else {                 // phi_xy, phi_xz, phi_yz
-        S0[r] = fmaf(-e, e, S0[r]);
-        S1[r] = fmaf(-g, g, S1[r]);
       }
+    }
+  }
+  // phi_xy, phi_xz, phi_yz: one loop body (three unrolled copies of the transform push the
+  // kernel out of the instruction cache)
+#pragma unroll 1
+  for (int f = 3; f < 6; ++f) {
+    float2 v[C::RMAX];
+    if (!fetch(f, v)) return;
+    fft<N, true>(v, t, sm, s_tw);
+#pragma unroll
+    for (int r = 0; r < C::RMAX; ++r) {
+      S0[r] = fmaf(-v[r].x, v[r].x, S0[r]);
+      S1[r] = fmaf(-v[r].y, v[r].y, S1[r]);
     }
   }
   float2 v[C::RMAX];
@@ -532,46 +553,68 @@ __global__ void __launch_bounds__(PassCfg<N>::ZT, LPT2_Z_MINB) k_z_adj_source(ZA
     }
   }
   load_twiddles(s_tw, a.tw, N);
-  float T0[C::RMAX], T1[C::RMAX];
-#pragma unroll
-  for (int q = 0; q < NQ; ++q) {
+  // Stage q of the ring into v (z_assemble with the field's z-derivative order), then the
+  // copy of stage q + STAGES; false if a wait ran out (the CTA has then drained its copies
+  // and reported, and must return).
+  auto fetch = [&](int q, float2 (&v)[C::RMAX]) -> bool {
     const int st = q % Q::STAGES;
-    const int f = field(q);
     const bool ok = mbar_wait(&bar[st], (q / Q::STAGES) & 1, a.g.wait);
     if (!ok) s_fail = 1;
-    float2 v[C::RMAX];
     const float2* ra = ring + st * Q::STAGE_F2 + (2 * p) * C::H;
+    const int m = a.ord[field(q)];
 #pragma unroll
     for (int r = 0; r < C::RMAX; ++r)
-      v[r] = ok ? z_assemble_smem<N>(ra, ra + C::H, elem<N>(t, r), kf, a.ord[f]) : make_float2(0.f, 0.f);
+      v[r] = ok ? z_assemble_smem<N>(ra, ra + C::H, elem<N>(t, r), kf, m) : make_float2(0.f, 0.f);
     __syncthreads();   // stage consumed by every thread (and, at q = 0, twiddles visible)
     if (s_fail) {
       if (threadIdx.x == 0) {
         for (int g = q; g < NQ && g < q + Q::STAGES; ++g) mbar_wait(&bar[g % Q::STAGES], (g / Q::STAGES) & 1);
         report_device_error(a.g.err, LPT2_DEV_ETIMEOUT_ZADJSOURCE);
       }
-      return;
+      return false;
     }
     if (threadIdx.x == 0 && q + Q::STAGES < NQ) {
       mbar_expect_tx(&bar[st], Q::STAGE_BYTES);
       bulk_load(ring + st * Q::STAGE_F2, a.in[field(q + Q::STAGES)] + zs + tile, Q::STAGE_BYTES, &bar[st]);
     }
-    fft<N, true>(v, t, sm, s_tw);
-    if (q < 3) {   // trace of the Hessian for both rows
+    return true;
+  };
+  // trace of the Hessian for both rows (fields xx, yy, zz)
+  float T0[C::RMAX], T1[C::RMAX];
 #pragma unroll
-      for (int r = 0; r < C::RMAX; ++r) {
-        T0[r] = q == 0 ? v[r].x : T0[r] + v[r].x;
-        T1[r] = q == 0 ? v[r].y : T1[r] + v[r].y;
-      }
-      continue;
-    }
-    const float* g0 = a.gs + zr + (size_t)row * N;
+  for (int q = 0; q < 3; ++q) {
+    float2 v[C::RMAX];
+    if (!fetch(q, v)) return;
+    fft<N, true>(v, t, sm, s_tw);
 #pragma unroll
     for (int r = 0; r < C::RMAX; ++r) {
-      const int iz = elem<N>(t, r);
-      const float ga = __ldg(g0 + iz), gb = __ldg(g0 + N + iz);
-      v[r] = f < 3 ? make_float2(ga * (T0[r] - v[r].x), gb * (T1[r] - v[r].y))
-                   : make_float2(-2.f * ga * v[r].x, -2.f * gb * v[r].y);
+      T0[r] = q == 0 ? v[r].x : T0[r] + v[r].x;
+      T1[r] = q == 0 ? v[r].y : T1[r] + v[r].y;
+    }
+  }
+  // the six cotangents: one loop body (not unrolled: nine copies of the two transforms
+  // overflow the instruction cache)
+  const float* g0 = a.gs + zr + (size_t)row * N;
+#pragma unroll 1
+  for (int q = 3; q < NQ; ++q) {
+    float2 v[C::RMAX];
+    if (!fetch(q, v)) return;
+    const int f = q - 3;
+    fft<N, true>(v, t, sm, s_tw);
+    if (f < 3) {
+#pragma unroll
+      for (int r = 0; r < C::RMAX; ++r) {
+        const int iz = elem<N>(t, r);
+        const float ga = __ldg(g0 + iz), gb = __ldg(g0 + N + iz);
+        v[r] = make_float2(ga * (T0[r] - v[r].x), gb * (T1[r] - v[r].y));
+      }
+    } else {
+#pragma unroll
+      for (int r = 0; r < C::RMAX; ++r) {
+        const int iz = elem<N>(t, r);
+        const float ga = __ldg(g0 + iz), gb = __ldg(g0 + N + iz);
+        v[r] = make_float2(-2.f * ga * v[r].x, -2.f * gb * v[r].y);
+      }
     }
     fft<N, false>(v, t, sm, s_tw);
     float2* out = a.out[f] + zs + tile + (size_t)(2 * p) * C::H;
@@ -718,7 +761,7 @@ __global__ void __launch_bounds__(PassCfg<N>::XT, x_minb<N>(MODE)) k_x(XArgs a) 
   const size_t blk = ((size_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
   if (MODE == X_PK || MODE == X_PKP || MODE == X_PKI) {
     float* s_accf = reinterpret_cast<float*>(s_acc);
-    for (int i = threadIdx.x; i < NWARP * (MODE == X_PK ? 5 : 2) * a.n_shells; i += blockDim.x) s_accf[i] = 0.f;
+    for (int i = threadIdx.x; i < NWARP * (MODE == X_PK ? 5 : 1) * a.n_shells; i += blockDim.x) s_accf[i] = 0.f;
   } else if (MODE == X_ADJ_SOURCE) {
     for (int i = threadIdx.x; i < NWARP; i += blockDim.x) s_acc[i] = 0.0;
   }
@@ -804,15 +847,59 @@ __global__ void __launch_bounds__(PassCfg<N>::XT, x_minb<N>(MODE)) k_x(XArgs a) 
       v[r] = make_float2(0.5f * (v[r].x + w.x), 0.5f * (v[r].y + w.y));
     }
   }
-  if (MODE == X_PK || MODE == X_PKP || MODE == X_PKI) {
+  if (MODE == X_PKP || MODE == X_PKI) {
+    // P(k) shells (mode counts and mean |k| come from the cached shell geometry).  At one
+    // register slot a warp holds a compact patch of modes (consecutive kx and kz), which
+    // mostly falls in one or two shells: the warp finds its smallest and largest shell
+    // (two reductions), sums V |delta|^2 / N^6 over the lanes of each (warp sums) and one
+    // lane adds the sums to the warp's own FP32 histogram in shared memory; a patch over
+    // more shells takes them one at a time.  At most 32 x RMAX values per shell and warp
+    // (relative error below 4e-5 even when every rounding goes one way); the sums over
+    // warps and blocks are FP64.
+    const float pnorm = a.g.box * a.g.box * a.g.box * a.g.inv_n3 * a.g.inv_n3;
+    const int ns = a.n_shells;
+    float* s_mine = reinterpret_cast<float*>(s_acc) + warp * ns;
+#pragma unroll
+    for (int r = 0; r < C::RMAX; ++r) {
+      const int kx = elem<N>(t, r);
+      int n2;
+      const int b = shell_of<N>(mode_of(kx, N), my, mz, ns, n2);
+      float pv = 0.f;
+      if (b >= 0) {
+        pv = (v[r].x * v[r].x + v[r].y * v[r].y) * pnorm * (mz == 0 ? 1.f : 2.f);
+        if (a.pk_deconv) pv /= cic_window2(mode_of(kx, N), my, mz, N);
+      }
+      const int lo = (int)__reduce_min_sync(0xffffffffu, (unsigned)(b < 0 ? 0x7fffffff : b));
+      const int hi = (int)__reduce_max_sync(0xffffffffu, (unsigned)(b < 0 ? 0 : b + 1)) - 1;
+      if (lo > hi) continue;                         // no mode of the patch in a shell
+      const float s0 = warp_sum(b == lo ? pv : 0.f);
+      if (lane == 0) s_mine[lo] += s0;
+      if (hi == lo) continue;
+      const float s1 = warp_sum(b == hi ? pv : 0.f);
+      if (lane == 0) s_mine[hi] += s1;
+      for (int k = lo + 1; k < hi; ++k) {            // shells strictly between (rare)
+        const float sk = warp_sum(b == k ? pv : 0.f);
+        if (lane == 0) s_mine[k] += sk;
+      }
+    }
+    __syncthreads();
+    const float* s_all = reinterpret_cast<const float*>(s_acc);
+    for (int b = threadIdx.x; b < ns; b += blockDim.x) {
+      double acc = 0.0;
+      for (int wi = 0; wi < NWARP; ++wi) acc += (double)s_all[wi * ns + b];   // fixed order
+      a.pk_part[blk * ns + b] = acc;
+    }
+    return;
+  }
+  if (MODE == X_PK) {
     // P(k) shells.  Lanes of a warp see neighbouring modes, so they fall in few
     // shells: for each distinct shell in the warp the lanes of that shell are
     // summed and one lane adds the sum to this warp's own accumulator, a
     // Kahan-compensated FP32 pair (FP64-class accuracy without FP64 adds, which
     // are slow on this part); the sums over warps and blocks are FP64.  X_PK also
     // sums |k| and the mode counts; X_PKP leaves them to the cached shell geometry.
-    constexpr bool GEO = (MODE == X_PK);
-    constexpr int NQ = GEO ? 5 : 2;   // per warp: P, its compensation (, |k|, compensation, count)
+    constexpr bool GEO = true;
+    constexpr int NQ = 5;             // per warp: P, its compensation, |k|, compensation, count
     const float pnorm = a.g.box * a.g.box * a.g.box * a.g.inv_n3 * a.g.inv_n3;
     const int ns = a.n_shells;
     float* s_mine = reinterpret_cast<float*>(s_acc) + warp * NQ * ns;
@@ -822,9 +909,8 @@ __global__ void __launch_bounds__(PassCfg<N>::XT, x_minb<N>(MODE)) k_x(XArgs a) 
       int n2;
       const int b = shell_of<N>(mode_of(kx, N), my, mz, ns, n2);
       const int wgt = (b < 0) ? 0 : ((mz == 0) ? 1 : 2);
-      float pv = (v[r].x * v[r].x + v[r].y * v[r].y) * pnorm * (float)wgt;
-      if (MODE != X_PK && a.pk_deconv && b >= 0) pv /= cic_window2(mode_of(kx, N), my, mz, N);
-      const float kv = GEO ? kf * sqrtf((float)n2) * (float)wgt : 0.f;
+      const float pv = (v[r].x * v[r].x + v[r].y * v[r].y) * pnorm * (float)wgt;
+      const float kv = kf * sqrtf((float)n2) * (float)wgt;
       unsigned todo = __ballot_sync(0xffffffffu, b >= 0);
       while (todo) {
         const int leader = __ffs(todo) - 1;
@@ -1033,7 +1119,7 @@ template <int N, int MODE> cudaError_t launch_x_m(const XArgs& a, cudaStream_t s
   using C = PassCfg<N>;
   LPT2_CHECK_BATCH(a);
   const int smem = C::XSMEM + (MODE == X_PK ? (C::XT / 32) * 5 * a.n_shells * 4
-                            : (MODE == X_PKP || MODE == X_PKI) ? (C::XT / 32) * 2 * a.n_shells * 4
+                            : (MODE == X_PKP || MODE == X_PKI) ? (C::XT / 32) * a.n_shells * 4
                                             : (MODE == X_ADJ_SOURCE ? (C::XT / 32) * 8 : 0));
   cudaFuncSetAttribute(k_x<N, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   k_x<N, MODE><<<dim3(C::H / C::W, N, a.g.batch), C::XT, smem, s>>>(a);
