@@ -10,6 +10,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>   // header-only: ranges cost a pointer test unless a profiler is attached
+
 #include "../../include/lpt2.h"
 #include "boxmuller.cuh"
 #include "passes.h"
@@ -342,15 +344,25 @@ void timing_end(lpt2_plan_s* p, const char* name, double bytes) {
 
 // Every kernel launch goes through LAUNCH(plan, name, algorithmic bytes, call):
 // counts it and, when timing is on, brackets it with CUDA events on the plan's stream.
+// counts it and, when timing is on, brackets it with CUDA events on the plan's stream; an
+// NVTX range named after the pass marks the launch for timeline profilers.
 #define LAUNCH(plan, name, bytes, expr)                                               \
   do {                                                                                \
+    nvtxRangePushA(name);                                                             \
     timing_begin((plan));                                                             \
     cudaError_t e_ = (expr);                                                          \
     (plan)->launches++;                                                               \
     timing_end((plan), (name), (double)(bytes));                                      \
+    nvtxRangePop();                                                                   \
     if (e_ != cudaSuccess)                                                            \
       return fail(LPT2_ECUDA, "%s: %s", #expr, cudaGetErrorString(e_));               \
   } while (0)
+
+// NVTX range around one C-ABI call (the whole call, host side).
+struct AbiRange {
+  explicit AbiRange(const char* name) { nvtxRangePushA(name); }
+  ~AbiRange() { nvtxRangePop(); }
+};
 
 bool aligned(const void* p, size_t a) { return ((uintptr_t)p % a) == 0; }
 
@@ -695,6 +707,7 @@ int lpt2_workspace_bytes(const lpt2_instance* inst, int n_inst, int n_k, unsigne
 
 int lpt2_plan(lpt2_plan_t* out, const lpt2_instance* inst, int n_inst, int n_k, double k_min,
               double k_max, int n_steps, void* cuda_stream, unsigned flags) {
+  AbiRange nvtx_range("lpt2_plan");
   g_err.clear();
   if (!out || !inst) return fail(LPT2_EINVAL, "null out/inst pointer");
   *out = nullptr;
@@ -838,6 +851,7 @@ int lpt2_set_workspace(lpt2_plan_t p, void* dev_ptr, size_t bytes) {
 }
 
 int lpt2_growth_tables(lpt2_plan_t p, double* d1, double* d2, double* dd1, double* dd2) {
+  AbiRange nvtx_range("lpt2_growth_tables");
   if (!p) return fail(LPT2_EINVAL, "null plan");
   int rc = run_growth(p);
   if (rc) return rc;
@@ -881,6 +895,7 @@ int lpt2_philox_words(uint64_t seed, uint64_t first, int64_t count, uint32_t* ou
 }
 
 int lpt2_displace(lpt2_plan_t p, const float* noise, float* psi1, float* psi2, float* pos, void* dk) {
+  AbiRange nvtx_range("lpt2_displace");
   int rc = check_plan_ws(p);
   if (rc) return rc;
   if (dk && !aligned(dk, 16)) return fail(LPT2_EINVAL, "dk must be 16-byte aligned");
@@ -1089,6 +1104,7 @@ extern "C" {
 
 int lpt2_cic_pk(lpt2_plan_t p, const float* pos, float* density, double* pk, double* k_mean,
                 int64_t* n_modes, int n_shells) {
+  AbiRange nvtx_range("lpt2_cic_pk");
   int rc = check_plan_ws(p);
   if (rc) return rc;
   if (!pk) return fail(LPT2_EINVAL, "pk must not be null");
@@ -1122,6 +1138,7 @@ int lpt2_cic_pk(lpt2_plan_t p, const float* pos, float* density, double* pk, dou
 // The forward step from and to host memory, pipelined over realisations (see the header).
 int lpt2_displace_host(lpt2_plan_t p, int n_real, const float* noise_h, int64_t noise_stride, float* pos_h,
                        int64_t pos_stride, double* pk_h, int64_t pk_stride, int n_shells) {
+  AbiRange nvtx_range("lpt2_displace_host");
   int rc = check_plan_ws(p);
   if (rc) return rc;
   if (p->n_inst != 1) return fail(LPT2_EUNSUPPORTED, "lpt2_displace_host needs a single-instance plan");
@@ -1210,6 +1227,7 @@ int lpt2_displace_host(lpt2_plan_t p, int n_real, const float* noise_h, int64_t 
 
 // Output scale factors of lpt2_displace_outputs: growth and multiplier tables per a_j.
 int lpt2_set_outputs(lpt2_plan_t p, int n_a, const double* a_out) {
+  AbiRange nvtx_range("lpt2_set_outputs");
   if (!p) return fail(LPT2_EINVAL, "null plan");
   if (p->n_inst != 1) return fail(LPT2_EUNSUPPORTED, "lpt2_set_outputs needs a single-instance plan");
   if (n_a < 1 || n_a > kMaxOutputs || !a_out) return fail(LPT2_EINVAL, "need 1 <= n_a <= %d and an a_out array", kMaxOutputs);
@@ -1233,6 +1251,7 @@ int lpt2_set_outputs(lpt2_plan_t p, int n_a, const double* a_out) {
 // a_j the multipliers, positions, CIC and P(k) (see the header).
 int lpt2_displace_outputs(lpt2_plan_t p, const float* noise, float* pos, double* pk, double* k_mean,
                           int64_t* n_modes, int n_shells) {
+  AbiRange nvtx_range("lpt2_displace_outputs");
   int rc = check_plan_ws(p);
   if (rc) return rc;
   if (p->n_inst != 1) return fail(LPT2_EUNSUPPORTED, "lpt2_displace_outputs needs a single-instance plan");
@@ -1289,6 +1308,7 @@ int lpt2_set_schedule(lpt2_plan_t p, const int* chunk, int n_groups) {
 // Times every group's forward step (Philox noise, positions, CIC, P(k)) at chunk sizes
 // count, ceil(count/2), ceil(count/4), ..., 1 and keeps the fastest per group.
 int lpt2_autotune(lpt2_plan_t p, int n_shells, int reps) {
+  AbiRange nvtx_range("lpt2_autotune");
   int rc = check_plan_ws(p);
   if (rc) return rc;
   if (n_shells < 1 || n_shells > kMaxShells) return fail(LPT2_EINVAL, "n_shells must be in [1, 256]");
@@ -1347,6 +1367,7 @@ int lpt2_autotune(lpt2_plan_t p, int n_shells, int reps) {
 // P(k) estimator refinements: CIC window deconvolution and interlacing (see the header).
 int lpt2_cic_pk_est(lpt2_plan_t p, const float* pos, float* density, double* pk, double* k_mean, int64_t* n_modes,
                     int n_shells, unsigned flags) {
+  AbiRange nvtx_range("lpt2_cic_pk_est");
   int rc = check_plan_ws(p);
   if (rc) return rc;
   if (!pk) return fail(LPT2_EINVAL, "pk must not be null");
@@ -1405,6 +1426,7 @@ int lpt2_cic_pk_est(lpt2_plan_t p, const float* pos, float* density, double* pk,
 // ------------------------------------------------------------ full-source diagnostic
 int lpt2_source_ratio(lpt2_plan_t p, const float* noise, int n_bins, double* mean, double* sigma, int64_t* count,
                       double* t1, double* k_mean, void* s_mg, void* s_gr) {
+  AbiRange nvtx_range("lpt2_source_ratio");
   int rc = check_plan_ws(p);
   if (rc) return rc;
   if (p->n_inst != 1) return fail(LPT2_EUNSUPPORTED, "lpt2_source_ratio needs a single-instance plan");
@@ -1575,6 +1597,7 @@ int lpt2_source_ratio(lpt2_plan_t p, const float* noise, int n_bins, double* mea
 }
 
 int lpt2_fft_r2c(lpt2_plan_t p, const float* in, void* out) {
+  AbiRange nvtx_range("lpt2_fft_r2c");
   int rc = check_plan_ws(p);
   if (rc) return rc;
   if (p->n_inst != 1) return fail(LPT2_EUNSUPPORTED, "lpt2_fft_r2c needs a single-instance plan");
@@ -1594,6 +1617,7 @@ int lpt2_fft_r2c(lpt2_plan_t p, const float* in, void* out) {
 }
 
 int lpt2_fft_c2r(lpt2_plan_t p, const void* in, float* out) {
+  AbiRange nvtx_range("lpt2_fft_c2r");
   int rc = check_plan_ws(p);
   if (rc) return rc;
   if (p->n_inst != 1) return fail(LPT2_EUNSUPPORTED, "lpt2_fft_c2r needs a single-instance plan");
@@ -1636,6 +1660,7 @@ int lpt2_set_fr0(lpt2_plan_t p, double fr0_abs) {
 
 int lpt2_displace_vjp(lpt2_plan_t p, const float* noise, const float* g_pos, const float* g_density,
                       const double* g_pk, int n_shells, float* g_noise, double* g_log_fr0) {
+  AbiRange nvtx_range("lpt2_displace_vjp");
   int rc = check_plan_ws(p);
   if (rc) return rc;
   if (p->n_inst != 1) return fail(LPT2_EUNSUPPORTED, "lpt2_displace_vjp needs a single-instance plan");

@@ -454,6 +454,31 @@ cudaError_t launch_box_muller(const uint32_t* words, int64_t count, const float4
   return cudaGetLastError();
 }
 
+// Bulk-tensor map of an x-pass input (see passes.h).  cuTensorMapEncodeTiled is a
+// host-only driver call, resolved through the runtime (no link against the driver).
+bool encode_x_tile_map(CUtensorMap* map, const void* base, int n, int w, int batch) {
+  typedef CUresult (*Encode)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                             const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                             CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+  static Encode encode = nullptr;
+  if (!encode) {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !f)
+      return false;
+    encode = (Encode)f;
+  }
+  const cuuint64_t nn = (cuuint64_t)n;
+  const cuuint64_t dims[4] = {nn, nn, nn, (cuuint64_t)batch};                  // kz floats, ky, kx, instance
+  const cuuint64_t strides[3] = {nn * 4, nn * nn * 4, nn * nn * nn * 4};       // bytes of dims 1..3
+  const cuuint32_t box[4] = {(cuuint32_t)(2 * w), 1u, (cuuint32_t)(n > 256 ? 256 : n), 1u};
+  const cuuint32_t estr[4] = {1u, 1u, 1u, 1u};
+  return encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<void*>(base), dims, strides, box, estr,
+                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 // Box-Muller tables (layout in boxmuller.cuh): FP64 values, each split into the float
 // nearest to it and the float nearest to the remainder.
 void bm_table(float4* t) {

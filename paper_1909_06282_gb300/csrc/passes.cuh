@@ -9,6 +9,8 @@
 // x pass, which sees full (kx, ky, kz) and runs the forward transform, the
 // multiplier and the first inverse transform back to back in registers.
 #pragma once
+#include <algorithm>
+
 #include "fft_core.cuh"
 #include "passes.h"
 #include "philox.cuh"
@@ -739,35 +741,26 @@ template <int N> constexpr int x_minb(int mode) {
              : PassCfg<N>::XMINB;
 }
 
-// CTA = (kz block of W, fixed ky). Thread tid = t * W + w; kx = elem(t, r).
+// One x-pass tile: kz block kzb (W consecutive kz), fixed ky, instance inst, all kx.
+// Thread tid = t * W + w; kx = elem(t, r).  v holds the tile's input (non-adjoint modes;
+// the adjoint modes load their x-order groups here), sm is the tile's exchange buffer,
+// s_acc the per-warp accumulators (zeroed by the caller), blk the tile's linear index.
 template <int N, int MODE>
-__global__ void __launch_bounds__(PassCfg<N>::XT, x_minb<N>(MODE)) k_x(XArgs a) {
+__device__ __forceinline__ void x_tile(const XArgs& a, float2 (&v)[PassCfg<N>::RMAX], int kzb, int ky, int inst,
+                                       size_t blk, const SmemCol<PassCfg<N>::W>& sm, const float2* s_tw,
+                                       double* s_acc) {
   using C = PassCfg<N>;
-  extern __shared__ float2 smem[];
-  float2* s_tw = smem;
-  load_twiddles(s_tw, a.tw, N);
   const int w = threadIdx.x % C::W, t = threadIdx.x / C::W;
-  const SmemCol<C::W> sm{smem + N + w};
-  double* s_acc = reinterpret_cast<double*>(smem + N + N * C::W);   // per-warp FP64 accumulators
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   constexpr int NWARP = C::XT / 32;
-  const int kz = blockIdx.x * C::W + w;
-  const int ky = blockIdx.y;
-  const size_t base = blockIdx.z * ((size_t)N * N * C::H) + (size_t)ky * C::H + kz;   // + kx * N * H
+  const int kz = kzb * C::W + w;
+  const size_t base = inst * ((size_t)N * N * C::H) + (size_t)ky * C::H + kz;   // + kx * N * H
   const size_t stride = (size_t)N * C::H;
   const int my = mode_of(ky, N), mz = kz;
   const bool ny_nyq = (ky == C::H);
   const float kf = a.g.kf;
-  const size_t blk = ((size_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
-  if (MODE == X_PK || MODE == X_PKP || MODE == X_PKI) {
-    float* s_accf = reinterpret_cast<float*>(s_acc);
-    for (int i = threadIdx.x; i < NWARP * (MODE == X_PK ? 5 : 1) * a.n_shells; i += blockDim.x) s_accf[i] = 0.f;
-  } else if (MODE == X_ADJ_SOURCE) {
-    for (int i = threadIdx.x; i < NWARP; i += blockDim.x) s_acc[i] = 0.0;
-  }
-  __syncthreads();
-
-  float2 v[C::RMAX];
+  (void)warp;
+  (void)lane;
   const bool adjoint = (MODE == X_ADJ_SOURCE || MODE == X_ADJ_DELTA);
   if (adjoint) {
     // forward x transform of each x-order group, summed with conj((i kx)^m)
@@ -786,10 +779,8 @@ __global__ void __launch_bounds__(PassCfg<N>::XT, x_minb<N>(MODE)) k_x(XArgs a) 
       }
     }
   } else {
-#pragma unroll
-    for (int r = 0; r < C::RMAX; ++r) v[r] = a.in[base + (size_t)(elem<N>(t, r)) * stride];
     if (MODE == X_MUL) {   // full-source diagnostic: multiplier, then inverse x
-      const size_t toff = (size_t)blockIdx.z * mode_table_len(N);
+      const size_t toff = (size_t)inst * mode_table_len(N);
 #pragma unroll
       for (int r = 0; r < C::RMAX; ++r) {
         const int kx = elem<N>(t, r);
@@ -978,7 +969,7 @@ __global__ void __launch_bounds__(PassCfg<N>::XT, x_minb<N>(MODE)) k_x(XArgs a) 
   }
 
   // k-space multipliers from the per-|n|^2 tables.  g = potential to transform back along x.
-  const size_t toff = (size_t)blockIdx.z * mode_table_len(N);
+  const size_t toff = (size_t)inst * mode_table_len(N);
   float2 g[C::RMAX], hpot[C::RMAX];
   float theta = 0.f;
 #pragma unroll
@@ -1046,6 +1037,119 @@ __global__ void __launch_bounds__(PassCfg<N>::XT, x_minb<N>(MODE)) k_x(XArgs a) 
     double acc = 0.0;
     for (int wi = 0; wi < NWARP; ++wi) acc += s_acc[wi];   // fixed order (barriers inside fft)
     a.theta_part[blk] = acc;
+  }
+}
+
+// Tile loads from global memory (one CTA per tile): the adjoint modes, whose tiles are sums
+// over several inputs, and any mode when the bulk-tensor path is off.
+template <int N, int MODE>
+__global__ void __launch_bounds__(PassCfg<N>::XT, x_minb<N>(MODE)) k_x(XArgs a) {
+  using C = PassCfg<N>;
+  extern __shared__ float2 smem[];
+  float2* s_tw = smem;
+  load_twiddles(s_tw, a.tw, N);
+  const int w = threadIdx.x % C::W, t = threadIdx.x / C::W;
+  const SmemCol<C::W> sm{smem + N + w};
+  double* s_acc = reinterpret_cast<double*>(smem + N + N * C::W);   // per-warp accumulators
+  constexpr int NWARP = C::XT / 32;
+  if (MODE == X_PK || MODE == X_PKP || MODE == X_PKI) {
+    float* s_accf = reinterpret_cast<float*>(s_acc);
+    for (int i = threadIdx.x; i < NWARP * (MODE == X_PK ? 5 : 1) * a.n_shells; i += blockDim.x) s_accf[i] = 0.f;
+  } else if (MODE == X_ADJ_SOURCE) {
+    for (int i = threadIdx.x; i < NWARP; i += blockDim.x) s_acc[i] = 0.0;
+  }
+  __syncthreads();
+  float2 v[C::RMAX];
+  if (MODE != X_ADJ_SOURCE && MODE != X_ADJ_DELTA) {
+    const size_t base = blockIdx.z * ((size_t)N * N * C::H) + (size_t)blockIdx.y * C::H + blockIdx.x * C::W + w;
+#pragma unroll
+    for (int r = 0; r < C::RMAX; ++r) v[r] = a.in[base + (size_t)(elem<N>(t, r)) * ((size_t)N * C::H)];
+  }
+  const size_t blk = ((size_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+  x_tile<N, MODE>(a, v, blockIdx.x, blockIdx.y, blockIdx.z, blk, sm, s_tw, s_acc);
+}
+
+// Tile loads by the tensor-memory accelerator: a persistent CTA walks the tiles
+// blockIdx.x, blockIdx.x + gridDim.x, ... and keeps two in flight in a shared-memory ring
+// (cp.async.bulk.tensor on an mbarrier: no registers, no load instructions), so the load
+// of the next tile overlaps the transforms of the current one.  A tile lands in the
+// layout of the FFT exchange buffer (kx major, the W kz of a row contiguous), which the
+// tile's transforms then use in place.  Every wait is bounded; a CTA whose wait runs out
+// waits (default budget) for its copies in flight, sets the error word and returns.
+#ifndef LPT2_X_TMA
+#define LPT2_X_TMA 1
+#endif
+template <int N> struct XTmaCfg {
+  using C = PassCfg<N>;
+  static constexpr int TILE = N * C::W;                 // float2 per tile
+  static constexpr int NBOX = N > 256 ? N / 256 : 1;    // bulk-tensor boxes per tile (<= 256 kx each)
+  static constexpr int BOXROWS = N / NBOX;
+  static constexpr int KZB = C::H / C::W;               // kz blocks per (ky, instance)
+  static constexpr int BAR_OFF = (N + 2 * TILE) * 8;    // bytes: twiddles, ring, then two barriers
+  static constexpr int ACC_OFF = BAR_OFF + 16;
+  static_assert((2 * C::W * 4) % 16 == 0, "the box's innermost extent must be a multiple of 16 bytes");
+};
+
+template <int N, int MODE>
+__global__ void __launch_bounds__(PassCfg<N>::XT, x_minb<N>(MODE)) k_x_tma(const __grid_constant__ XArgs a) {
+  using C = PassCfg<N>;
+  using Q = XTmaCfg<N>;
+  extern __shared__ __align__(128) unsigned char xs_raw[];
+  float2* s_tw = reinterpret_cast<float2*>(xs_raw);
+  float2* ring = s_tw + N;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(xs_raw + Q::BAR_OFF);
+  double* s_acc = reinterpret_cast<double*>(xs_raw + Q::ACC_OFF);
+  __shared__ int s_fail;
+  constexpr int NWARP = C::XT / 32;
+  const int w = threadIdx.x % C::W, t = threadIdx.x / C::W;
+  const int ntiles = Q::KZB * N * a.g.batch;
+  auto issue = [&](int st, int tile) {   // one thread
+    const int kzb = tile % Q::KZB, ky = (tile / Q::KZB) % N, inst = tile / (Q::KZB * N);
+    mbar_expect_tx(&bar[st], Q::TILE * 8u);
+#pragma unroll
+    for (int j = 0; j < Q::NBOX; ++j)
+      tensor_load_4d(ring + st * Q::TILE + j * Q::BOXROWS * C::W, &a.tmap, 2 * kzb * C::W, ky, j * Q::BOXROWS,
+                     inst, &bar[st]);
+  };
+  if (threadIdx.x == 0) {
+    s_fail = 0;
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    mbar_init_fence();
+    for (int i = 0; i < 2; ++i)
+      if (blockIdx.x + i * gridDim.x < ntiles) issue(i, blockIdx.x + i * gridDim.x);
+  }
+  load_twiddles(s_tw, a.tw, N);
+  __syncthreads();
+  for (int i = 0, tile = blockIdx.x; tile < ntiles; ++i, tile += gridDim.x) {
+    const int st = i & 1;
+    if (MODE == X_PK || MODE == X_PKP) {
+      float* s_accf = reinterpret_cast<float*>(s_acc);
+      for (int k = threadIdx.x; k < NWARP * (MODE == X_PK ? 5 : 1) * a.n_shells; k += blockDim.x) s_accf[k] = 0.f;
+    }
+    const bool ok = mbar_wait(&bar[st], (i >> 1) & 1, a.g.wait);
+    if (!ok) s_fail = 1;
+    float2 v[C::RMAX];
+    const float2* tl = ring + st * Q::TILE;
+#pragma unroll
+    for (int r = 0; r < C::RMAX; ++r) v[r] = ok ? tl[elem<N>(t, r) * C::W + w] : make_float2(0.f, 0.f);
+    __syncthreads();   // tile read by every thread before the transforms reuse the buffer
+    if (s_fail) {
+      if (threadIdx.x == 0) {
+        mbar_wait(&bar[st], (i >> 1) & 1);                                           // this tile's copy
+        if (tile + gridDim.x < ntiles) mbar_wait(&bar[st ^ 1], ((i + 1) >> 1) & 1);  // the next tile's
+        report_device_error(a.g.err, LPT2_DEV_ETIMEOUT_X);
+      }
+      return;
+    }
+    const int kzb = tile % Q::KZB, ky = (tile / Q::KZB) % N, inst = tile / (Q::KZB * N);
+    const SmemCol<C::W> sm{ring + st * Q::TILE + w};
+    x_tile<N, MODE>(a, v, kzb, ky, inst, (size_t)tile, sm, s_tw, s_acc);
+    __syncthreads();   // ring stage and accumulators free
+    if (threadIdx.x == 0 && tile + 2 * gridDim.x < ntiles) {
+      fence_proxy_async_smem();
+      issue(st, tile + 2 * gridDim.x);
+    }
   }
 }
 
@@ -1118,11 +1222,33 @@ template <int N> cudaError_t launch_y_t(const YArgs& a, cudaStream_t s) {
 template <int N, int MODE> cudaError_t launch_x_m(const XArgs& a, cudaStream_t s) {
   using C = PassCfg<N>;
   LPT2_CHECK_BATCH(a);
-  const int smem = C::XSMEM + (MODE == X_PK ? (C::XT / 32) * 5 * a.n_shells * 4
-                            : (MODE == X_PKP || MODE == X_PKI) ? (C::XT / 32) * a.n_shells * 4
-                                            : (MODE == X_ADJ_SOURCE ? (C::XT / 32) * 8 : 0));
-  cudaFuncSetAttribute(k_x<N, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  k_x<N, MODE><<<dim3(C::H / C::W, N, a.g.batch), C::XT, smem, s>>>(a);
+  const int acc = MODE == X_PK ? (C::XT / 32) * 5 * a.n_shells * 4
+                  : (MODE == X_PKP || MODE == X_PKI) ? (C::XT / 32) * a.n_shells * 4
+                                                     : (MODE == X_ADJ_SOURCE ? (C::XT / 32) * 8 : 0);
+  // bulk-tensor tiles where they measured faster at 512^3 (x_delta 0.91 -> 0.86 ms); the
+  // one-transform shell-sum modes keep the global-load kernel at twice the CTAs per SM, and
+  // the source multiplier, which also reads delta(k) per mode, measured 0.73 -> 0.76 ms
+  constexpr bool tma = LPT2_X_TMA && (MODE == X_DELTA || MODE == X_PHI);
+  if constexpr (tma) {
+    using Q = XTmaCfg<N>;
+    XArgs b = a;
+    if (!encode_x_tile_map(&b.tmap, a.in, N, C::W, a.g.batch)) return cudaErrorInvalidValue;
+    const int smem = Q::ACC_OFF + acc;
+    cudaError_t e = cudaFuncSetAttribute(k_x_tma<N, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    int dev = 0, sms = 0, per_sm = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_x_tma<N, MODE>, C::XT, smem)) != cudaSuccess)
+      return e;
+    const long long tiles = (long long)Q::KZB * N * a.g.batch;
+    const int grid = (int)std::min<long long>(tiles, (long long)sms * std::max(per_sm, 1));
+    k_x_tma<N, MODE><<<grid, C::XT, smem, s>>>(b);
+  } else {
+    const int smem = C::XSMEM + acc;
+    cudaFuncSetAttribute(k_x<N, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    k_x<N, MODE><<<dim3(C::H / C::W, N, a.g.batch), C::XT, smem, s>>>(a);
+  }
   return cudaGetLastError();
 }
 template <int N> cudaError_t launch_x_t(const XArgs& a, cudaStream_t s) {

@@ -1,6 +1,7 @@
 // Host/device shared declarations of the pass kernels' argument blocks and the
 // per-grid-size launcher entry points (instantiated in inst_<N>.cu).
 #pragma once
+#include <cuda.h>   // CUtensorMap (a plain 128-byte descriptor; no driver call is linked)
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -41,7 +42,8 @@ struct Geo {
 };
 
 // Codes a kernel writes into Geo::err when a bounded wait gives up.
-enum { LPT2_DEV_ETIMEOUT_ZSOURCE = 1, LPT2_DEV_ETIMEOUT_ZFINAL = 2, LPT2_DEV_ETIMEOUT_ZADJSOURCE = 3 };
+enum { LPT2_DEV_ETIMEOUT_ZSOURCE = 1, LPT2_DEV_ETIMEOUT_ZFINAL = 2, LPT2_DEV_ETIMEOUT_ZADJSOURCE = 3,
+       LPT2_DEV_ETIMEOUT_X = 4 };
 
 enum ZSrc { Z_NOISE = 0, Z_REAL = 1, Z_DENSITY = 2 };
 
@@ -170,7 +172,13 @@ struct XArgs {
   int mul_g;
   int mul_ord[3];
   float mul_m2a, mul_inv_a2, mul_d1gr;
+  CUtensorMap tmap;       // bulk-tensor map of `in` (set by the launcher; encode_x_tile_map)
 };
+
+// Bulk-tensor map of a batch of half spectra float2[batch][N][N][N/2] seen as floats
+// (kz re/im: N floats, ky, kx, instance) whose box is one x-pass tile: 2w floats (w
+// consecutive kz) x 1 ky x min(N, 256) kx x 1 instance.  False if the driver refuses it.
+bool encode_x_tile_map(CUtensorMap* map, const void* base, int n, int w, int batch);
 
 // Radial factors of the full-source diagnostic (Sec. 3, Eqs. s1-s4):
 enum MulG {
