@@ -127,13 +127,18 @@ class ClockSampler:
 
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the kernels
-# that can dominate the 512^3 step, from one ncu capture each of the 256^3 case of the same
-# kernel scaled by the cell count (x 8; the traffic of these passes is proportional to
-# N^3).  Sources: profiles/z_source_256.md, profiles/cic_256.md.  A kernel changed since
-# its capture must be removed here (its traffic is then reported as null).
+# that can dominate the 512^3 step, from one ncu capture of the 256^3 case of the same
+# kernels scaled by the cell count (x 8; the traffic of these passes is proportional to
+# N^3, except that at 256^3 a field fits in L2, so the scaled figures are lower bounds).
+# Source: profiles/kernels_256.md.  A kernel changed since its capture must be removed here
+# (its traffic is then reported as null).
 TRAFFIC_512 = {
-    "z_source": (402.789888 + 51.985152) * 1e6 * 8,
-    "cic": (270.254592 + 45.784320) * 1e6 * 8,
+    "z_source": (402.768896 + 52.556544) * 1e6 * 8,
+    "cic": (270.255104 + 45.323008) * 1e6 * 8,
+    "y_phi": (201.832704 + 345.711104) * 1e6 * 8,
+    "x_delta": (68.005888 + 208.239104) * 1e6 * 8,
+    "x_source": (135.116288 + 84.932864) * 1e6 * 8,
+    "z_final": (201.371392 + 152.319744) * 1e6 * 8,
 }
 
 
