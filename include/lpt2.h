@@ -58,9 +58,13 @@ enum {
   LPT2_GRAPH = 1,   /* capture lpt2_displace / lpt2_cic_pk into CUDA graphs on first use and
                        replay them while the argument pointers stay the same (needs a stream
                        other than the legacy default stream) */
-  LPT2_HOST_IO = 2  /* single-instance plans: the workspace also holds the two device buffer
+  LPT2_HOST_IO = 2, /* single-instance plans: the workspace also holds the two device buffer
                        sets of lpt2_displace_host (each N^3 + 3 N^3 floats + 256 doubles) and
                        the plan makes its two copy streams */
+  LPT2_KEEP_STATE = 4 /* single-instance plans: lpt2_displace to the CIC density only (psi1, psi2
+                       and pos NULL) also keeps S(k) and the positions in the workspace, so that
+                       a following lpt2_displace_vjp with the same noise starts from the kept
+                       forward map instead of recomputing it (see lpt2_displace_vjp) */
 };
 /* Single-instance plans: room in the workspace for the tables of up to n (<= 64) output
  * scale factors of lpt2_set_outputs (per output: growth tables 4 n_k doubles and floats,
@@ -307,7 +311,14 @@ int lpt2_set_fr0(lpt2_plan_t plan, double fr0_abs);
  * no gradients: this is the transpose
  * of the steps of Sec. 2.1 Eq. second-ini and Sec. 2.4 taken in reverse order).
  * The forward map is recomputed inside (only delta(k) is kept; the six phi_ij
- * are recomputed from it for the source-term transpose).
+ * are recomputed from it for the source-term transpose), except on a plan made with
+ * LPT2_KEEP_STATE whose last lpt2_displace (to the density only) used the same noise
+ * pointer and whose workspace no call has overwritten since (lpt2_cic_pk of that density
+ * keeps it too, and also leaves the density spectrum the adjoint needs): then the adjoint
+ * starts from that forward map.  The noise buffer must still hold the values it had then;
+ * a call that overwrites the kept state (lpt2_displace, lpt2_cic_pk with positions,
+ * lpt2_displace_vjp itself, lpt2_set_fr0, lpt2_set_workspace, ...) makes the next adjoint
+ * recompute the forward map.
  *   noise      float[N^3] white noise, or NULL for the plan's Philox noise
  *   g_pos      float[3][N^3] dL/d(positions), or NULL (zero)
  *   g_density  float[N^3] dL/d(density contrast), or NULL (zero)

@@ -133,12 +133,13 @@ def _stream(stream=None):
     return C.c_void_p(s.cuda_stream)
 
 
-GRAPH, HOST_IO = 1, 2
+GRAPH, HOST_IO, KEEP_STATE = 1, 2, 4
 
 
-def plan_flags(graph=False, host_io=False, max_outputs=0) -> int:
-    """The lpt2_plan flags: LPT2_GRAPH, LPT2_HOST_IO, LPT2_MAX_OUTPUTS(max_outputs)."""
-    return (GRAPH if graph else 0) | (HOST_IO if host_io else 0) | ((int(max_outputs) & 0xFF) << 8)
+def plan_flags(graph=False, host_io=False, max_outputs=0, keep_state=False) -> int:
+    """The lpt2_plan flags: LPT2_GRAPH, LPT2_HOST_IO, LPT2_KEEP_STATE, LPT2_MAX_OUTPUTS(max_outputs)."""
+    return ((GRAPH if graph else 0) | (HOST_IO if host_io else 0) | (KEEP_STATE if keep_state else 0)
+            | ((int(max_outputs) & 0xFF) << 8))
 
 
 def _instances(insts):
@@ -176,10 +177,11 @@ class Plan:
     `inst` is one instance or a list of instances (equal grid sizes contiguous);
     `graph=True` sets LPT2_GRAPH (needs a non-default stream); `host_io=True` sets
     LPT2_HOST_IO (lpt2_displace_host); `max_outputs=n` reserves room for n output times
-    (lpt2_set_outputs)."""
+    (lpt2_set_outputs); `keep_state=True` sets LPT2_KEEP_STATE (the adjoint reuses the
+    forward map of the last lpt2_displace)."""
 
     def __init__(self, inst, n_k=512, k_min=1e-4, k_max=10.0, n_steps=1024, stream=None,
-                 workspace=True, graph=False, host_io=False, max_outputs=0):
+                 workspace=True, graph=False, host_io=False, max_outputs=0, keep_state=False):
         lib = load_library()
         insts = list(inst) if isinstance(inst, (list, tuple)) else [inst]
         self.insts = insts
@@ -190,7 +192,7 @@ class Plan:
         self.cells = sum(n ** 3 for n in self.ns)
         self.n_k = int(n_k)
         self.n_steps = int(n_steps)
-        self.flags = plan_flags(graph, host_io, max_outputs)
+        self.flags = plan_flags(graph, host_io, max_outputs, keep_state)
         arr = _instances(insts)
         self._cinst = arr
         self.stream = stream if stream is not None else torch.cuda.current_stream()

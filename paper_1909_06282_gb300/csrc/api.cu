@@ -128,6 +128,12 @@ struct lpt2_plan_s {
   int xb_max;                 // max over groups of count * x-pass blocks
   size_t total_cells;         // sum over instances of n^3
   bool host_io;               // LPT2_HOST_IO: the workspace holds lpt2_displace_host's buffer sets
+  bool keep_state;            // LPT2_KEEP_STATE: lpt2_displace keeps what the adjoint needs
+  // what the workspace holds of the last forward map (LPT2_KEEP_STATE): fwd = delta(k), S(k),
+  // positions and CIC density of lpt2_displace with noise `kept_noise`; spec = also the
+  // density spectrum after the z and y passes (a later lpt2_cic_pk of that density)
+  bool kept_fwd = false, kept_spec = false;
+  const float* kept_noise = nullptr;
   int max_out;                // LPT2_MAX_OUTPUTS(n): room for n output times' tables in the workspace
   bool use_graph;
   GraphCache graphs[2] = {};  // lpt2_displace, lpt2_cic_pk
@@ -258,7 +264,6 @@ float* rho_group(const lpt2_plan_s* p) {
   return reinterpret_cast<float*>(p->ws + rho_all_off(p)) + p->cur_rho_off;
 }
 size_t tail_pk_part(const lpt2_plan_s* p) { return ws_layout(p).pk_part; }
-size_t tail_pk(const lpt2_plan_s* p) { return ws_layout(p).pk; }
 size_t tail_shw(const lpt2_plan_s* p) { return ws_layout(p).shw; }
 size_t tail_theta(const lpt2_plan_s* p) { return ws_layout(p).theta; }
 size_t ws_need(const lpt2_plan_s* p) { return ws_layout(p).total; }
@@ -401,7 +406,13 @@ int forward_zy(lpt2_plan_t p, int src, const float* in, float2* out) {
 }
 
 int displace_impl(lpt2_plan_t p, const float* noise, float* psi1, float* psi2, float* pos, void* dk,
-                  float2* s_keep);
+                  float2* s_keep, float* pos_scratch = nullptr);
+
+// Forgets the forward state kept for the adjoint (a call has overwritten the workspace).
+void drop_state(lpt2_plan_t p) {
+  p->kept_fwd = false;
+  p->kept_spec = false;
+}
 
 // Forgets the output times (their tables live in the workspace).
 void free_outputs(lpt2_plan_t p) {
@@ -641,13 +652,13 @@ struct PlanShape {
 static int plan_shape(const lpt2_instance* inst, int n_inst, int n_k, unsigned flags, PlanShape& ps) {
   if (!inst) return fail(LPT2_EINVAL, "null inst pointer");
   if (n_inst < 1 || n_inst > 65535) return fail(LPT2_EINVAL, "n_inst must be in [1, 65535] (got %d)", n_inst);
-  const unsigned known = LPT2_GRAPH | LPT2_HOST_IO | LPT2_MAX_OUTPUTS(0xff);
+  const unsigned known = LPT2_GRAPH | LPT2_HOST_IO | LPT2_KEEP_STATE | LPT2_MAX_OUTPUTS(0xff);
   if (flags & ~known) return fail(LPT2_EINVAL, "unknown flags");
   ps.host_io = (flags & LPT2_HOST_IO) != 0;
   ps.max_out = (int)((flags >> 8) & 0xff);
   if (ps.max_out > kMaxOutputs) return fail(LPT2_EINVAL, "LPT2_MAX_OUTPUTS(n): n must be <= %d", kMaxOutputs);
-  if ((ps.host_io || ps.max_out > 0) && n_inst != 1)
-    return fail(LPT2_EINVAL, "LPT2_HOST_IO and LPT2_MAX_OUTPUTS need a single-instance plan");
+  if ((ps.host_io || ps.max_out > 0 || (flags & LPT2_KEEP_STATE)) && n_inst != 1)
+    return fail(LPT2_EINVAL, "LPT2_HOST_IO, LPT2_KEEP_STATE and LPT2_MAX_OUTPUTS need a single-instance plan");
   if (n_k < 2 || n_k > 4096) return fail(LPT2_EINVAL, "n_k must be in [2, 4096]");
   std::vector<Group>& groups = ps.groups;
   for (int i = 0; i < n_inst; ++i) {
@@ -735,6 +746,7 @@ int lpt2_plan(lpt2_plan_t* out, const lpt2_instance* inst, int n_inst, int n_k, 
   p->xb_max = ps.xb_max;
   p->total_cells = ps.total_cells;
   p->host_io = ps.host_io;
+  p->keep_state = (flags & LPT2_KEEP_STATE) != 0;
   p->max_out = ps.max_out;
   cudaError_t e = cudaSuccess;
   for (Group& g : p->groups) {
@@ -842,6 +854,7 @@ int lpt2_workspace_size(lpt2_plan_t p, size_t* bytes) {
 }
 
 int lpt2_set_workspace(lpt2_plan_t p, void* dev_ptr, size_t bytes) {
+  if (p) drop_state(p);   // overwrites the state kept for the adjoint
   if (!p || !dev_ptr) return fail(LPT2_EINVAL, "null argument");
   if (!aligned(dev_ptr, 256)) return fail(LPT2_EINVAL, "workspace must be 256-byte aligned");
   if (bytes < ws_need(p)) return fail(LPT2_ENOWORKSPACE, "workspace too small: %zu < %zu", bytes, ws_need(p));
@@ -851,6 +864,7 @@ int lpt2_set_workspace(lpt2_plan_t p, void* dev_ptr, size_t bytes) {
 }
 
 int lpt2_growth_tables(lpt2_plan_t p, double* d1, double* d2, double* dd1, double* dd2) {
+  if (p) drop_state(p);   // overwrites the state kept for the adjoint
   AbiRange nvtx_range("lpt2_growth_tables");
   if (!p) return fail(LPT2_EINVAL, "null plan");
   int rc = run_growth(p);
@@ -899,6 +913,10 @@ int lpt2_displace(lpt2_plan_t p, const float* noise, float* psi1, float* psi2, f
   int rc = check_plan_ws(p);
   if (rc) return rc;
   if (dk && !aligned(dk, 16)) return fail(LPT2_EINVAL, "dk must be 16-byte aligned");
+  drop_state(p);
+  // with LPT2_KEEP_STATE a forward to the CIC density only (no Psi, no positions out) also
+  // keeps S(k) and the positions in the slots the adjoint reads them from
+  const bool keep = p->keep_state && !psi1 && !psi2 && !pos;
   auto body = [&]() -> int {
     for (int gi = 0; gi < (int)p->groups.size(); ++gi) {
       const Group& gr = p->groups[gi];
@@ -908,16 +926,22 @@ int lpt2_displace(lpt2_plan_t p, const float* noise, float* psi1, float* psi2, f
         const size_t off = gr.off + (size_t)c0 * n3;   // real elements before the chunk
         const int r = displace_impl(p, noise ? noise + off : nullptr, psi1 ? psi1 + 3 * off : nullptr,
                                     psi2 ? psi2 + 3 * off : nullptr, pos ? pos + 3 * off : nullptr,
-                                    dk ? (char*)dk + off * sizeof(float) : nullptr, nullptr);
+                                    dk ? (char*)dk + off * sizeof(float) : nullptr,
+                                    keep ? slot(p, S_SHAT) : nullptr,
+                                    keep ? reinterpret_cast<float*>(slot(p, S_POS)) : nullptr);
         if (r) return r;
       }
     }
     set_group(p, 0);
     return LPT2_OK;
   };
-  if (!p->use_graph) return body();
   const void* key[8] = {noise, psi1, psi2, pos, dk, p->ws, nullptr, nullptr};
-  return run_graph(p, 0, key, body);
+  const int r = p->use_graph ? run_graph(p, 0, key, body) : body();
+  if (!r && keep) {
+    p->kept_fwd = true;
+    p->kept_noise = noise;
+  }
+  return r;
 }
 
 }  // extern "C"
@@ -1014,7 +1038,8 @@ int displace_prefix(lpt2_plan_t p, const FwdSlots& f, const float* noise, bool s
 // multiplier tables mt0 / mt1 and the growth tables tabf: S(k) -> phi2 (+ phi1 D1),
 // Psi, positions, CIC density (slots A and D are read, not written).
 int displace_suffix(lpt2_plan_t p, const FwdSlots& f, bool split, float* psi1, float* psi2, float* pos,
-                    float2* s_keep, const float4* mt0, const float2* mt1, const float* tabf) {
+                    float2* s_keep, const float4* mt0, const float2* mt1, const float* tabf,
+                    float* pos_scratch = nullptr) {
   const int n = p->n;
   const Geo g = make_geo(p);
   float* rho = rho_group(p);
@@ -1073,7 +1098,7 @@ int displace_suffix(lpt2_plan_t p, const FwdSlots& f, bool split, float* psi1, f
   // The CIC deposit runs as its own kernel at full occupancy (atomic throughput
   // needs many warps in flight): z_final writes the positions (to the caller's
   // array, or to dead workspace slots 2-4) and k_cic reads them back.
-  float* posw = pos ? pos : reinterpret_cast<float*>(f.X[0]);
+  float* posw = pos ? pos : (pos_scratch ? pos_scratch : reinterpret_cast<float*>(f.X[0]));
   zf.pos = posw;
   LAUNCH(p, "z_final", ((split ? 24.0 : 12.0) + 12.0 + (psi1 ? 12.0 : 0.0) + (psi2 ? 12.0 : 0.0)) * V3(p),
          z_final(n, zf, p->stream));
@@ -1083,12 +1108,12 @@ int displace_suffix(lpt2_plan_t p, const FwdSlots& f, bool split, float* psi1, f
 }
 
 int displace_impl(lpt2_plan_t p, const float* noise, float* psi1, float* psi2, float* pos, void* dk,
-                  float2* s_keep) {
+                  float2* s_keep, float* pos_scratch) {
   const bool split = psi1 || psi2;
   const FwdSlots f = fwd_slots(p);
   int rc = displace_prefix(p, f, noise, split);
   if (rc) return rc;
-  rc = displace_suffix(p, f, split, psi1, psi2, pos, s_keep, p->mt0, p->mt1, p->tabf);
+  rc = displace_suffix(p, f, split, psi1, psi2, pos, s_keep, p->mt0, p->mt1, p->tabf, pos_scratch);
   if (rc) return rc;
   if (dk) {
     const size_t cells = (size_t)p->n * p->n * p->n * p->cur_batch;
@@ -1130,14 +1155,17 @@ int lpt2_cic_pk(lpt2_plan_t p, const float* pos, float* density, double* pk, dou
     rc = ensure_geometry(p, gi, n_shells);
     if (rc) return rc;
   }
-  if (!p->use_graph) return body();
+  if (pos) drop_state(p);   // a new deposit replaces the kept density
   const void* key[8] = {pos, density, pk, k_mean, n_modes, p->ws, (const void*)(intptr_t)n_shells, nullptr};
-  return run_graph(p, 1, key, body);
+  const int r = p->use_graph ? run_graph(p, 1, key, body) : body();
+  if (!r && !pos && p->kept_fwd) p->kept_spec = true;   // slot A now holds the density spectrum
+  return r;
 }
 
 // The forward step from and to host memory, pipelined over realisations (see the header).
 int lpt2_displace_host(lpt2_plan_t p, int n_real, const float* noise_h, int64_t noise_stride, float* pos_h,
                        int64_t pos_stride, double* pk_h, int64_t pk_stride, int n_shells) {
+  if (p) drop_state(p);   // overwrites the state kept for the adjoint
   AbiRange nvtx_range("lpt2_displace_host");
   int rc = check_plan_ws(p);
   if (rc) return rc;
@@ -1251,6 +1279,7 @@ int lpt2_set_outputs(lpt2_plan_t p, int n_a, const double* a_out) {
 // a_j the multipliers, positions, CIC and P(k) (see the header).
 int lpt2_displace_outputs(lpt2_plan_t p, const float* noise, float* pos, double* pk, double* k_mean,
                           int64_t* n_modes, int n_shells) {
+  if (p) drop_state(p);   // overwrites the state kept for the adjoint
   AbiRange nvtx_range("lpt2_displace_outputs");
   int rc = check_plan_ws(p);
   if (rc) return rc;
@@ -1308,6 +1337,7 @@ int lpt2_set_schedule(lpt2_plan_t p, const int* chunk, int n_groups) {
 // Times every group's forward step (Philox noise, positions, CIC, P(k)) at chunk sizes
 // count, ceil(count/2), ceil(count/4), ..., 1 and keeps the fastest per group.
 int lpt2_autotune(lpt2_plan_t p, int n_shells, int reps) {
+  if (p) drop_state(p);   // overwrites the state kept for the adjoint
   AbiRange nvtx_range("lpt2_autotune");
   int rc = check_plan_ws(p);
   if (rc) return rc;
@@ -1367,6 +1397,7 @@ int lpt2_autotune(lpt2_plan_t p, int n_shells, int reps) {
 // P(k) estimator refinements: CIC window deconvolution and interlacing (see the header).
 int lpt2_cic_pk_est(lpt2_plan_t p, const float* pos, float* density, double* pk, double* k_mean, int64_t* n_modes,
                     int n_shells, unsigned flags) {
+  if (p) drop_state(p);   // overwrites the state kept for the adjoint
   AbiRange nvtx_range("lpt2_cic_pk_est");
   int rc = check_plan_ws(p);
   if (rc) return rc;
@@ -1426,6 +1457,7 @@ int lpt2_cic_pk_est(lpt2_plan_t p, const float* pos, float* density, double* pk,
 // ------------------------------------------------------------ full-source diagnostic
 int lpt2_source_ratio(lpt2_plan_t p, const float* noise, int n_bins, double* mean, double* sigma, int64_t* count,
                       double* t1, double* k_mean, void* s_mg, void* s_gr) {
+  if (p) drop_state(p);   // overwrites the state kept for the adjoint
   AbiRange nvtx_range("lpt2_source_ratio");
   int rc = check_plan_ws(p);
   if (rc) return rc;
@@ -1617,6 +1649,7 @@ int lpt2_fft_r2c(lpt2_plan_t p, const float* in, void* out) {
 }
 
 int lpt2_fft_c2r(lpt2_plan_t p, const void* in, float* out) {
+  if (p) p->kept_spec = false;   // slot A is overwritten
   AbiRange nvtx_range("lpt2_fft_c2r");
   int rc = check_plan_ws(p);
   if (rc) return rc;
@@ -1647,6 +1680,7 @@ int lpt2_fft_c2r(lpt2_plan_t p, const void* in, float* out) {
 }
 
 int lpt2_set_fr0(lpt2_plan_t p, double fr0_abs) {
+  if (p) drop_state(p);   // overwrites the state kept for the adjoint
   if (!p) return fail(LPT2_EINVAL, "null plan");
   if (p->n_inst != 1) return fail(LPT2_EUNSUPPORTED, "lpt2_set_fr0 needs a single-instance plan");
   if (!(fr0_abs >= 0) || !isfinite(fr0_abs)) return fail(LPT2_EINVAL, "fr0_abs must be >= 0");
@@ -1672,33 +1706,36 @@ int lpt2_displace_vjp(lpt2_plan_t p, const float* noise, const float* g_pos, con
   for (int i = 0; i < N_SLOTS; ++i) S[i] = slot(p, i);
   float* pos = reinterpret_cast<float*>(S[S_POS]);            // 3 consecutive slots
   float* rho = rho_group(p);
-  double* pk = reinterpret_cast<double*>(p->ws + tail_pk(p));
-  double* kmean = pk + kMaxShells;
-  int64_t* nmodes = reinterpret_cast<int64_t*>(pk + 2 * kMaxShells);
   float* shw = reinterpret_cast<float*>(p->ws + tail_shw(p));
   double* thp = reinterpret_cast<double*>(p->ws + tail_theta(p));
   const double V3d = (double)n * n * n;
 
-  // forward, keeping delta(k) (slot 1), S(k), positions and the CIC density
-  rc = displace_impl(p, noise, nullptr, nullptr, pos, nullptr, S[S_SHAT]);
+  // The forward map, keeping delta(k) (slot 1), S(k), positions and the CIC density, unless
+  // the last lpt2_displace of a LPT2_KEEP_STATE plan left them for this noise; then the
+  // delta_rho spectrum after the z and y passes, unless a later lpt2_cic_pk left it in slot A.
+  const bool reuse = p->keep_state && p->kept_fwd && p->kept_noise == noise;
+  const bool reuse_spec = reuse && p->kept_spec;
+  drop_state(p);   // this call overwrites the kept slots
+  if (!reuse) {
+    rc = displace_impl(p, noise, nullptr, nullptr, nullptr, nullptr, S[S_SHAT], pos);
+    if (rc) return rc;
+  }
+  if (!reuse_spec) {
+    rc = forward_zy(p, Z_DENSITY, rho, S[S_A]);
+    if (rc) return rc;
+  }
+  // the P(k) transpose needs the mode count per shell (cached geometry), not P(k) itself
+  rc = ensure_geometry(p, 0, n_shells);
   if (rc) return rc;
-  // P(k) of the density: shell counts and the delta_rho spectrum after z, y
-  rc = forward_zy(p, Z_DENSITY, rho, S[S_A]);
-  if (rc) return rc;
+  static_assert(sizeof(unsigned long long) == sizeof(int64_t), "mode counts are 64-bit");
+  const int64_t* nmodes = reinterpret_cast<const int64_t*>(p->groups[0].geo_n);
   XArgs xp{};
   xp.g = g;
   xp.tw = p->tw;
-  xp.mode = X_PKP;
   xp.in = S[S_A];
   xp.cosmo = p->cosmo_dev;
   xp.pk_part = pk_part(p);
   xp.n_shells = n_shells;
-  LAUNCH(p, "x_pk", 4.0 * V3(p), x_pass(n, xp, p->stream));
-  rc = ensure_geometry(p, 0, n_shells);
-  if (rc) return rc;
-  LAUNCH(p, "pk_finalize", 0.0,
-         launch_pk_finalize_p(pk_part(p), x_blocks(n), n_shells, p->groups[0].geo_k, p->groups[0].geo_n, pk, kmean,
-                              nmodes, p->stream, 1));
 
   // 1. density cotangent: g_density + IDFT[w_b delta_rho(k)]
   const double v_over_n6 = p->box * p->box * p->box / (V3d * V3d);

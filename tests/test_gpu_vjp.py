@@ -332,3 +332,56 @@ def test_autograd_function_matches_vjp():
     rel = float((noise.grad.double() - g_noise.double()).norm() / g_noise.double().norm())
     assert rel < 1e-5, rel
     assert abs(float(logf.grad) - float(g_t)) <= 1e-5 * abs(float(g_t)), (float(logf.grad), float(g_t))
+
+
+def test_vjp_reuses_the_kept_forward_map():
+    """LPT2_KEEP_STATE: after lpt2_displace (density only) and lpt2_cic_pk of that density
+    the adjoint starts from the kept forward map (fewer launches) and gives the adjoint of a
+    plan that recomputes it; a deposit of other positions, a different noise buffer or an
+    adjoint in between make it recompute, with the same result."""
+    n, box = 64, 256.0
+    c = W.COSMO.replace(fr0_abs=1e-5)
+    keep = lp().Plan(W.Instance(n, box, 1, c), n_steps=STEPS, keep_state=True)
+    plain = lp().Plan(W.Instance(n, box, 1, c), n_steps=STEPS)
+    noise = torch.from_numpy(W.white_noise(n, 3)).cuda()
+    other = torch.from_numpy(W.white_noise(n, 4)).cuda()
+    gd = torch.from_numpy(W.random_field((n, n, n), 5) * 1e-6).cuda()
+    gp = torch.from_numpy(W.random_field((NS,), 6).astype(np.float64) * 1e-3).cuda()
+
+    def fwd(plan, nz):
+        lp().lpt2_displace(plan, noise=nz, psi1=False, psi2=False, pos=False)
+        return lp().lpt2_cic_pk(plan, pos=None, density=True, n_shells=NS)
+
+    def vjp(plan, nz):
+        c0 = lp().lpt2_launch_count(plan)
+        g, t = lp().lpt2_displace_vjp(plan, noise=nz, g_density=gd, g_pk=gp, n_shells=NS)
+        torch.cuda.synchronize()
+        return g.clone(), float(t), lp().lpt2_launch_count(plan) - c0
+
+    fwd(plain, noise)
+    want, want_t, full = vjp(plain, noise)
+
+    def same(g, t):
+        assert float((g.double() - want.double()).norm() / want.double().norm()) < 1e-6
+        assert abs(t - want_t) <= 1e-6 * abs(want_t)
+
+    fwd(keep, noise)
+    g, t, l_reuse = vjp(keep, noise)           # kept forward map and density spectrum
+    same(g, t)
+    assert l_reuse < full, (l_reuse, full)
+    g, t, l = vjp(keep, noise)                 # the adjoint overwrote the state: recompute
+    same(g, t)
+    assert l == full
+    fwd(keep, noise)
+    lp().lpt2_cic_pk(keep, pos=torch.from_numpy(W.random_positions(n, box, 9)).cuda(), n_shells=NS)
+    g, t, l = vjp(keep, noise)                 # another deposit replaced the density
+    same(g, t)
+    assert l == full
+    fwd(keep, other)
+    g, t, l = vjp(keep, noise)                 # kept for another noise buffer
+    same(g, t)
+    assert l == full
+    lp().lpt2_displace(keep, noise=noise, psi1=False, psi2=False, pos=False)
+    g, t, l = vjp(keep, noise)                 # forward kept, density spectrum recomputed
+    same(g, t)
+    assert l_reuse < l < full
