@@ -47,6 +47,20 @@ template <int N> struct PassCfg {
   static constexpr int XMINB = XT >= 512 ? 1 : 512 / XT;
 };
 
+// y passes: their own pencils per CTA (the y tile rows are 2 KB apart, the x tile rows a
+// whole (ky, kz) plane apart, and the two passes hold different working sets)
+#ifndef LPT2_WY512
+#define LPT2_WY512 LPT2_W512
+#endif
+template <int N> struct YCfg {
+  static constexpr int RMAX = Cfg<N>::RMAX;
+  static constexpr int TPP = N / RMAX;
+  static constexpr int H = N / 2;
+  static constexpr int W = N == 512 ? LPT2_WY512 : PassCfg<N>::W;
+  static constexpr int XT = TPP * W;
+  static constexpr int XSMEM = (N + N * W) * 8;
+};
+
 // (i k)^m v for m = 0, 1, 2
 __device__ __forceinline__ float2 deriv(float2 v, float k, int m) {
   if (m == 0) return v;
@@ -635,8 +649,8 @@ __global__ void __launch_bounds__(PassCfg<N>::ZT, LPT2_Z_MINB) k_z_adj_source(ZA
 enum YKind { Y_MULTI = 0, Y_SUM = 1, Y_ONE = 2 };
 
 template <int N, int KIND>
-__global__ void __launch_bounds__(PassCfg<N>::XT) k_y(YArgs a) {
-  using C = PassCfg<N>;
+__global__ void __launch_bounds__(YCfg<N>::XT) k_y(YArgs a) {
+  using C = YCfg<N>;
   extern __shared__ float2 smem[];
   float2* s_tw = smem;
   load_twiddles(s_tw, a.tw, N);
@@ -1207,7 +1221,7 @@ template <int N> cudaError_t launch_z_adj_source_t(const ZAdjSourceArgs& a, cuda
   return cudaGetLastError();
 }
 template <int N, int KIND> cudaError_t launch_y_k(const YArgs& a, cudaStream_t s) {
-  using C = PassCfg<N>;
+  using C = YCfg<N>;
   LPT2_CHECK_BATCH(a);
   cudaFuncSetAttribute(k_y<N, KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::XSMEM);
   k_y<N, KIND><<<dim3(C::H / C::W, N, a.g.batch), C::XT, C::XSMEM, s>>>(a);
