@@ -122,8 +122,8 @@ typedef struct lpt2_plan_s* lpt2_plan_t;
  * as one batch (every pass kernel covers all its instances).  Per-instance
  * arrays of the other calls are the instances' arrays concatenated in plan
  * order.  cuda_stream is a cudaStream_t (NULL = legacy default stream).  flags:
- * 0 or an or of LPT2_GRAPH, LPT2_HOST_IO and LPT2_MAX_OUTPUTS(n) (the last two for
- * single-instance plans only).  Allocates the plan's small device tables and computes the
+ * 0 or an or of LPT2_GRAPH, LPT2_HOST_IO, LPT2_KEEP_STATE and LPT2_MAX_OUTPUTS(n) (the
+ * last three for single-instance plans only).  Allocates the plan's small device tables and computes the
  * P(k) normalisation (sigma_8) and the growth tables on the stream.  Errors:
  * LPT2_EINVAL (null pointers, n_k < 2, k_min <= 0, k_max <= k_min, box <= 0,
  * a range, non-flat cosmology, fr0_abs < 0, n_steps < 1, instance ordering or
