@@ -289,15 +289,24 @@ int lpt2_displace_outputs(lpt2_plan_t plan, const float* noise, float* pos, doub
  * if chunk is not NULL, up to max_groups current chunk sizes.
  * lpt2_set_schedule: chunk[n_groups] instances per launch (each >= 1, clamped to the
  * group's size); drops the plan's captured graphs (recaptured on the next call).
+ * lpt2_tiles: the number of groups and, where the arrays are not NULL, up to max_groups
+ * tile choices per group: ytile = pencils per CTA of the y passes (0 = build default, 8 or
+ * 16) and xtile = tile path of the x passes that fill the phi potentials (0 = build
+ * default, 1 = bulk-tensor tiles staged in shared memory, 2 = global loads).
+ * lpt2_set_tiles: sets them for every group (ytile 16 needs N >= 32); results are the
+ * same bit for bit for every choice, only the speed differs.  Drops the captured graphs.
  * lpt2_autotune: times every group's forward step (Philox noise -> positions -> CIC ->
  * n_shells-shell P(k)) on the plan's stream at chunk sizes count, ceil(count/2), ..., 1,
- * `reps` timed repetitions after one warm-up each, keeps the fastest per group, and drops
- * the captured graphs.  Plan-time work: it synchronises and overwrites the workspace;
- * not capturable.  Needs the workspace.
- * Errors: LPT2_EINVAL (bad count, chunk, n_shells, or reps outside [1, 100]),
+ * `reps` timed repetitions after one warm-up each, keeps the fastest per group; then, at
+ * that chunk size, tries ytile 8 and 16 and xtile 1 and 2 in turn and keeps what is faster;
+ * and drops the captured graphs.  Plan-time work: it synchronises and overwrites the
+ * workspace; not capturable.  Needs the workspace.
+ * Errors: LPT2_EINVAL (bad count, chunk, tile choice, n_shells, or reps outside [1, 100]),
  * LPT2_ECUDA. */
 int lpt2_schedule(lpt2_plan_t plan, int* chunk, int max_groups, int* n_groups);
 int lpt2_set_schedule(lpt2_plan_t plan, const int* chunk, int n_groups);
+int lpt2_tiles(lpt2_plan_t plan, int* ytile, int* xtile, int max_groups, int* n_groups);
+int lpt2_set_tiles(lpt2_plan_t plan, const int* ytile, const int* xtile, int n_groups);
 int lpt2_autotune(lpt2_plan_t plan, int n_shells, int reps);
 
 /* lpt2_set_fr0: change |f_R0| of the plan (it enters Eq. d1 and Eq. full-d2

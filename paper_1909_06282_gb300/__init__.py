@@ -14,6 +14,7 @@ from ._lib import (  # noqa: F401
     lpt2_plan, lpt2_plan_destroy, lpt2_workspace_size, lpt2_growth_tables, lpt2_white_noise,
     lpt2_philox_words, lpt2_box_muller, lpt2_displace, lpt2_cic_pk, lpt2_fft_r2c, lpt2_fft_c2r, lpt2_last_error,
     lpt2_launch_count, lpt2_device_status, lpt2_set_wait_budget, lpt2_source_ratio, lpt2_cic_pk_est, lpt2_timing, lpt2_timing_report, lpt2_set_fr0, lpt2_displace_vjp,
-    lpt2_displace_host, lpt2_set_outputs, lpt2_displace_outputs, lpt2_schedule, lpt2_set_schedule, lpt2_autotune,
+    lpt2_displace_host, lpt2_set_outputs, lpt2_displace_outputs, lpt2_schedule, lpt2_set_schedule, lpt2_tiles,
+    lpt2_set_tiles, lpt2_autotune,
     Displace, HEADER_FUNCTIONS,
 )

@@ -99,6 +99,8 @@ def load_library():
         "lpt2_set_outputs": (i, [vp, i, C.POINTER(d)]),
         "lpt2_schedule": (i, [vp, C.POINTER(i), i, C.POINTER(i)]),
         "lpt2_set_schedule": (i, [vp, C.POINTER(i), i]),
+        "lpt2_tiles": (i, [vp, C.POINTER(i), C.POINTER(i), i, C.POINTER(i)]),
+        "lpt2_set_tiles": (i, [vp, C.POINTER(i), C.POINTER(i), i]),
         "lpt2_autotune": (i, [vp, i, i]),
         "lpt2_displace_outputs": (i, [vp, vp, vp, vp, vp, vp, i]),
         "lpt2_timing_report": (i, [vp, C.POINTER(_KernelStat), i, C.POINTER(C.c_int)]),
@@ -393,9 +395,29 @@ def lpt2_set_schedule(plan: Plan, chunks):
     _check(load_library().lpt2_set_schedule(plan.handle, arr, len(chunks)))
 
 
+def lpt2_tiles(plan: Plan):
+    """Tile choices of each grid-size group: (ytile list, xtile list); 0 = build default."""
+    lib = load_library()
+    ng = C.c_int()
+    _check(lib.lpt2_tiles(plan.handle, None, None, 0, C.byref(ng)))
+    yt = (C.c_int * max(ng.value, 1))()
+    xt = (C.c_int * max(ng.value, 1))()
+    _check(lib.lpt2_tiles(plan.handle, yt, xt, ng.value, C.byref(ng)))
+    return list(yt[: ng.value]), list(xt[: ng.value])
+
+
+def lpt2_set_tiles(plan: Plan, ytile, xtile):
+    if len(ytile) != len(xtile):
+        raise ValueError("ytile and xtile need one entry per group each")
+    yt = (C.c_int * len(ytile))(*[int(v) for v in ytile])
+    xt = (C.c_int * len(xtile))(*[int(v) for v in xtile])
+    _check(load_library().lpt2_set_tiles(plan.handle, yt, xt, len(ytile)))
+
+
 def lpt2_autotune(plan: Plan, n_shells=32, reps=3):
-    """Times each group's forward step at several instances-per-launch and keeps the
-    fastest; returns the chosen schedule."""
+    """Times each group's forward step at several instances-per-launch, then y-pass
+    pencils per CTA and x-pass tile paths, and keeps the fastest; returns the chosen
+    instances per launch (lpt2_tiles gives the tile choices)."""
     _check(load_library().lpt2_autotune(plan.handle, int(n_shells), int(reps)))
     return lpt2_schedule(plan)
 

@@ -85,6 +85,8 @@ struct Group {
   unsigned long long* geo_n; // and mode count per shell [kMaxShells]
   int geo_ns;                // 0: not computed yet
   int chunk = 0;             // instances per launch in lpt2_displace / lpt2_cic_pk (0: the whole group)
+  int ytile = 0;             // y-pass pencils per CTA (0: build default, 8, 16)
+  int xtile = 0;             // x-pass tile path of the delta/phi modes (0: default, 1: bulk-tensor, 2: global)
 };
 
 struct GraphCache {  // one captured launch sequence per entry point (LPT2_GRAPH)
@@ -113,6 +115,7 @@ struct lpt2_plan_s {
   const float4* mt0;
   const float2* mt1;
   int cur_batch, cur_inst0;
+  int cur_ytile = 0, cur_xtile = 0;   // tile schedule of the current group
   size_t cur_slot_off = 0;    // bytes into every workspace slot of the current instances (a chunk of a group)
   size_t cur_rho_off = 0;     // floats into the density array of the current instances
   std::vector<Group> groups;
@@ -181,6 +184,8 @@ void set_group(lpt2_plan_s* p, int gi) {
   p->mt1 = g.mt1;
   p->cur_batch = g.count;
   p->cur_inst0 = g.inst0;
+  p->cur_ytile = g.ytile;
+  p->cur_xtile = g.xtile;
   p->cur_slot_off = 0;
   p->cur_rho_off = g.off;
 }
@@ -288,6 +293,8 @@ Geo make_geo(const lpt2_plan_s* p) {
   g.tab_stride = 4 * p->nk;
   g.err = p->dev_err;
   g.wait = p->wait_cycles;
+  g.ytile = p->cur_ytile;
+  g.xtile = p->cur_xtile;
   return g;
 }
 
@@ -1334,8 +1341,43 @@ int lpt2_set_schedule(lpt2_plan_t p, const int* chunk, int n_groups) {
   return LPT2_OK;
 }
 
+namespace {
+// y-pass pencils per CTA a group of grid size n can take: the build default (0), or 8 and
+// 16 where they tile the n/2 kz of the half spectrum (n >= 32; at n = 16 only the default 8)
+bool valid_ytile(int n, int v) { return v == 0 || v == 8 || (v == 16 && n >= 32); }
+}  // namespace
+
+int lpt2_tiles(lpt2_plan_t p, int* ytile, int* xtile, int max_groups, int* n_groups) {
+  if (!p || !n_groups) return fail(LPT2_EINVAL, "null argument");
+  *n_groups = (int)p->groups.size();
+  for (int gi = 0; gi < (int)p->groups.size() && gi < max_groups; ++gi) {
+    if (ytile) ytile[gi] = p->groups[gi].ytile;
+    if (xtile) xtile[gi] = p->groups[gi].xtile;
+  }
+  return LPT2_OK;
+}
+
+int lpt2_set_tiles(lpt2_plan_t p, const int* ytile, const int* xtile, int n_groups) {
+  if (!p || !ytile || !xtile) return fail(LPT2_EINVAL, "null argument");
+  if (n_groups != (int)p->groups.size())
+    return fail(LPT2_EINVAL, "n_groups = %d, the plan has %d grid-size groups", n_groups, (int)p->groups.size());
+  for (int gi = 0; gi < n_groups; ++gi) {
+    if (!valid_ytile(p->groups[gi].n, ytile[gi]))
+      return fail(LPT2_EINVAL, "ytile[%d] = %d: need 0, 8 or 16 (16 needs N >= 32)", gi, ytile[gi]);
+    if (xtile[gi] < 0 || xtile[gi] > 2) return fail(LPT2_EINVAL, "xtile[%d] = %d: need 0, 1 or 2", gi, xtile[gi]);
+  }
+  for (int gi = 0; gi < n_groups; ++gi) {
+    p->groups[gi].ytile = ytile[gi];
+    p->groups[gi].xtile = xtile[gi];
+  }
+  drop_graphs(p);
+  return LPT2_OK;
+}
+
 // Times every group's forward step (Philox noise, positions, CIC, P(k)) at chunk sizes
-// count, ceil(count/2), ceil(count/4), ..., 1 and keeps the fastest per group.
+// count, ceil(count/2), ceil(count/4), ..., 1 and keeps the fastest per group; then, at
+// that chunk size, the y-pass pencils per CTA (8, 16) and the x-pass tile path of the
+// delta and phi modes (bulk-tensor, global loads), one after the other.
 int lpt2_autotune(lpt2_plan_t p, int n_shells, int reps) {
   if (p) drop_state(p);   // overwrites the state kept for the adjoint
   AbiRange nvtx_range("lpt2_autotune");
@@ -1370,25 +1412,49 @@ int lpt2_autotune(lpt2_plan_t p, int n_shells, int reps) {
       }
       return LPT2_OK;
     };
+    auto timed = [&](float& ms) -> int {   // one warm-up, then reps timed steps
+      int r = step();
+      if (r) return r;
+      e = cudaEventRecord(e0, p->stream);
+      for (int k = 0; k < reps && !r && e == cudaSuccess; ++k) r = step();
+      if (r) return r;
+      if (e == cudaSuccess) e = cudaEventRecord(e1, p->stream);
+      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+      if (e != cudaSuccess) return fail(LPT2_ECUDA, "autotune timing: %s", cudaGetErrorString(e));
+      return LPT2_OK;
+    };
     int best = gr.count;
     float best_ms = 0.f;
     for (int c = gr.count, prev = 0; c != prev && !rc; prev = c, c = (c + 1) / 2) {
       gr.chunk = c;
-      if ((rc = step())) break;   // warm-up
-      e = cudaEventRecord(e0, p->stream);
-      for (int k = 0; k < reps && !rc && e == cudaSuccess; ++k) rc = step();
-      if (e == cudaSuccess) e = cudaEventRecord(e1, p->stream);
-      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
       float ms = 0.f;
-      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
-      if (e != cudaSuccess) rc = fail(LPT2_ECUDA, "autotune timing: %s", cudaGetErrorString(e));
-      if (!rc && (best_ms == 0.f || ms < best_ms)) {
+      if ((rc = timed(ms))) break;
+      if (best_ms == 0.f || ms < best_ms) {
         best_ms = ms;
         best = c;
       }
       if (c == 1) break;
     }
     gr.chunk = best;
+    for (int yt : {8, 16}) {   // y-pass pencils per CTA
+      if (rc || !valid_ytile(gr.n, yt)) continue;
+      const int keep = gr.ytile;
+      gr.ytile = yt;
+      float ms = 0.f;
+      if ((rc = timed(ms))) break;
+      if (ms < best_ms) best_ms = ms;
+      else gr.ytile = keep;
+    }
+    for (int xt : {1, 2}) {    // x-pass tile path of the delta and phi modes
+      if (rc) break;
+      const int keep = gr.xtile;
+      gr.xtile = xt;
+      float ms = 0.f;
+      if ((rc = timed(ms))) break;
+      if (ms < best_ms) best_ms = ms;
+      else gr.xtile = keep;
+    }
   }
   cleanup();
   return rc;

@@ -48,17 +48,20 @@ template <int N> struct PassCfg {
 };
 
 // y passes: their own pencils per CTA (the y tile rows are 2 KB apart, the x tile rows a
-// whole (ky, kz) plane apart, and the two passes hold different working sets)
+// whole (ky, kz) plane apart, and the two passes hold different working sets).  WY = 0 is
+// the build default; the launcher also has WY = 8 and 16 compiled, which a plan's tile
+// schedule (Geo::ytile) selects per grid-size group.
 #ifndef LPT2_WY512
 #define LPT2_WY512 LPT2_W512
 #endif
-template <int N> struct YCfg {
+template <int N, int WY = 0> struct YCfg {
   static constexpr int RMAX = Cfg<N>::RMAX;
   static constexpr int TPP = N / RMAX;
   static constexpr int H = N / 2;
-  static constexpr int W = N == 512 ? LPT2_WY512 : PassCfg<N>::W;
+  static constexpr int W = WY ? WY : (N == 512 ? LPT2_WY512 : PassCfg<N>::W);
   static constexpr int XT = TPP * W;
   static constexpr int XSMEM = (N + N * W) * 8;
+  static_assert(H % W == 0, "a CTA's kz block must tile the half spectrum");
 };
 
 // (i k)^m v for m = 0, 1, 2
@@ -648,9 +651,9 @@ __global__ void __launch_bounds__(PassCfg<N>::ZT, LPT2_Z_MINB) k_z_adj_source(ZA
 //       Y_ONE    one input, one output, no derivative (forward or inverse).
 enum YKind { Y_MULTI = 0, Y_SUM = 1, Y_ONE = 2 };
 
-template <int N, int KIND>
-__global__ void __launch_bounds__(YCfg<N>::XT) k_y(YArgs a) {
-  using C = YCfg<N>;
+template <int N, int KIND, int WY>
+__global__ void __launch_bounds__(YCfg<N, WY>::XT) k_y(YArgs a) {
+  using C = YCfg<N, WY>;
   extern __shared__ float2 smem[];
   float2* s_tw = smem;
   load_twiddles(s_tw, a.tw, N);
@@ -1220,18 +1223,29 @@ template <int N> cudaError_t launch_z_adj_source_t(const ZAdjSourceArgs& a, cuda
   k_z_adj_source<N><<<dim3(N * N / Q::ROWS, 1, a.g.batch), C::ZT, Q::SMEM, s>>>(a);
   return cudaGetLastError();
 }
-template <int N, int KIND> cudaError_t launch_y_k(const YArgs& a, cudaStream_t s) {
-  using C = YCfg<N>;
+template <int N, int KIND, int WY> cudaError_t launch_y_k(const YArgs& a, cudaStream_t s) {
+  using C = YCfg<N, WY>;
   LPT2_CHECK_BATCH(a);
-  cudaFuncSetAttribute(k_y<N, KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::XSMEM);
-  k_y<N, KIND><<<dim3(C::H / C::W, N, a.g.batch), C::XT, C::XSMEM, s>>>(a);
+  cudaFuncSetAttribute(k_y<N, KIND, WY>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::XSMEM);
+  k_y<N, KIND, WY><<<dim3(C::H / C::W, N, a.g.batch), C::XT, C::XSMEM, s>>>(a);
   return cudaGetLastError();
 }
-template <int N> cudaError_t launch_y_t(const YArgs& a, cudaStream_t s) {
-  if (a.job.sum) return launch_y_k<N, Y_SUM>(a, s);
+template <int N, int WY> cudaError_t launch_y_w(const YArgs& a, cudaStream_t s) {
+  if (a.job.sum) return launch_y_k<N, Y_SUM, WY>(a, s);
   if (a.job.n_in == 1 && a.job.n_out == 1 && a.job.ord[0] == 0 && a.job.src[0] == 0)
-    return launch_y_k<N, Y_ONE>(a, s);
-  return launch_y_k<N, Y_MULTI>(a, s);
+    return launch_y_k<N, Y_ONE, WY>(a, s);
+  return launch_y_k<N, Y_MULTI, WY>(a, s);
+}
+// y pencils per CTA: Geo::ytile 0 (build default), 8 or 16 (where they tile N/2)
+template <int N> cudaError_t launch_y_t(const YArgs& a, cudaStream_t s) {
+  if constexpr (N >= 32 && YCfg<N>::W != 8) {
+    if (a.g.ytile == 8) return launch_y_w<N, 8>(a, s);
+  }
+  if constexpr (N >= 32 && YCfg<N>::W != 16) {
+    if (a.g.ytile == 16) return launch_y_w<N, 16>(a, s);
+  }
+  if (a.g.ytile != 0 && a.g.ytile != YCfg<N>::W) return cudaErrorInvalidValue;
+  return launch_y_w<N, 0>(a, s);
 }
 template <int N, int MODE> cudaError_t launch_x_m(const XArgs& a, cudaStream_t s) {
   using C = PassCfg<N>;
@@ -1239,30 +1253,35 @@ template <int N, int MODE> cudaError_t launch_x_m(const XArgs& a, cudaStream_t s
   const int acc = MODE == X_PK ? (C::XT / 32) * 5 * a.n_shells * 4
                   : (MODE == X_PKP || MODE == X_PKI) ? (C::XT / 32) * a.n_shells * 4
                                                      : (MODE == X_ADJ_SOURCE ? (C::XT / 32) * 8 : 0);
-  // bulk-tensor tiles where they measured faster at 512^3 (x_delta 0.91 -> 0.86 ms); the
-  // one-transform shell-sum modes keep the global-load kernel at twice the CTAs per SM, and
-  // the source multiplier, which also reads delta(k) per mode, measured 0.73 -> 0.76 ms
-  constexpr bool tma = LPT2_X_TMA && (MODE == X_DELTA || MODE == X_PHI);
-  if constexpr (tma) {
-    using Q = XTmaCfg<N>;
-    XArgs b = a;
-    if (!encode_x_tile_map(&b.tmap, a.in, N, C::W, a.g.batch)) return cudaErrorInvalidValue;
-    const int smem = Q::ACC_OFF + acc;
-    cudaError_t e = cudaFuncSetAttribute(k_x_tma<N, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e != cudaSuccess) return e;
-    int dev = 0, sms = 0, per_sm = 0;
-    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
-    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_x_tma<N, MODE>, C::XT, smem)) != cudaSuccess)
-      return e;
-    const long long tiles = (long long)Q::KZB * N * a.g.batch;
-    const int grid = (int)std::min<long long>(tiles, (long long)sms * std::max(per_sm, 1));
-    k_x_tma<N, MODE><<<grid, C::XT, smem, s>>>(b);
-  } else {
-    const int smem = C::XSMEM + acc;
-    cudaFuncSetAttribute(k_x<N, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    k_x<N, MODE><<<dim3(C::H / C::W, N, a.g.batch), C::XT, smem, s>>>(a);
+  // The delta and phi modes have two tile paths: bulk-tensor tiles (default where they
+  // measured faster at 512^3, x_delta 0.91 -> 0.86 ms) and global loads; Geo::xtile picks
+  // one per grid-size group (0 the build default, 1 bulk-tensor, 2 global) and the other
+  // modes ignore it.  The one-transform shell-sum modes keep the global-load kernel at twice
+  // the CTAs per SM, and the source multiplier, which also reads delta(k) per mode, measured
+  // 0.73 -> 0.76 ms with bulk-tensor tiles.
+  if (a.g.xtile < 0 || a.g.xtile > 2) return cudaErrorInvalidValue;
+  if constexpr (MODE == X_DELTA || MODE == X_PHI) {
+    if (a.g.xtile == 0 ? LPT2_X_TMA != 0 : a.g.xtile == 1) {
+      using Q = XTmaCfg<N>;
+      XArgs b = a;
+      if (!encode_x_tile_map(&b.tmap, a.in, N, C::W, a.g.batch)) return cudaErrorInvalidValue;
+      const int smem = Q::ACC_OFF + acc;
+      cudaError_t e = cudaFuncSetAttribute(k_x_tma<N, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+      if (e != cudaSuccess) return e;
+      int dev = 0, sms = 0, per_sm = 0;
+      if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+      if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+      if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_x_tma<N, MODE>, C::XT, smem)) != cudaSuccess)
+        return e;
+      const long long tiles = (long long)Q::KZB * N * a.g.batch;
+      const int grid = (int)std::min<long long>(tiles, (long long)sms * std::max(per_sm, 1));
+      k_x_tma<N, MODE><<<grid, C::XT, smem, s>>>(b);
+      return cudaGetLastError();
+    }
   }
+  const int smem = C::XSMEM + acc;
+  cudaFuncSetAttribute(k_x<N, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  k_x<N, MODE><<<dim3(C::H / C::W, N, a.g.batch), C::XT, smem, s>>>(a);
   return cudaGetLastError();
 }
 template <int N> cudaError_t launch_x_t(const XArgs& a, cudaStream_t s) {

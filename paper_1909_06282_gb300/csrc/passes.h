@@ -39,6 +39,10 @@ struct Geo {
   int tab_stride;       // floats per instance in the float growth tables
   int* err;             // device error word (0 = ok), may be null
   long long wait;       // cycle budget of the bounded consumer waits (0: give up at once)
+  // tile schedule of this grid-size group (0 = build default): y-pass pencils per CTA
+  // (8 or 16) and the x-pass tile path of the delta and phi modes (1 bulk-tensor, 2 global)
+  int ytile;
+  int xtile;
 };
 
 // Codes a kernel writes into Geo::err when a bounded wait gives up.

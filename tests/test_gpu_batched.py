@@ -117,3 +117,59 @@ def test_batched_96_workload_one_instance_per_size_against_oracle():
         ok = ref["n_modes"] > 0
         np.testing.assert_array_equal(pk["n_modes"][j].cpu().numpy(), ref["n_modes"])
         np.testing.assert_allclose(pk["pk"][j].cpu().numpy()[ok], ref["pk"][ok], rtol=1e-4)
+
+
+def test_tile_choices_are_bit_identical_and_autotuned():
+    """The y-pass pencils per CTA (8, 16) and the x-pass tile path of the phi potentials
+    (bulk-tensor tiles, global loads) change only how the same arithmetic is laid out on
+    the GPU: Psi1, Psi2 and positions of a mixed batched plan, and the adjoint of a
+    single-instance plan, are equal bit for bit under every choice; P(k) to 1e-6 (the
+    particles that leave their CIC tile's halo are deposited with float atomics, whose
+    order varies from run to run whatever the tiles).  Invalid choices are refused, and
+    the autotuner leaves a valid one per group."""
+    L = lp()
+    insts = instances()   # groups 32^3, 64^3, 96^3
+    plan = L.Plan(insts, n_steps=STEPS)
+    assert L.lpt2_tiles(plan) == ([0, 0, 0], [0, 0, 0])
+
+    def run():
+        out = L.lpt2_displace(plan, psi1=True, psi2=True, pos=True)
+        pk = L.lpt2_cic_pk(plan, pos=None, n_shells=16)
+        torch.cuda.synchronize()
+        return {k: v.clone() for k, v in out.items()}, pk["pk"].clone()
+
+    ref, ref_pk = run()
+    for yt in (8, 16):
+        for xt in (1, 2):
+            L.lpt2_set_tiles(plan, [yt] * 3, [xt] * 3)
+            assert L.lpt2_tiles(plan) == ([yt] * 3, [xt] * 3)
+            got, got_pk = run()
+            for key in ("psi1", "psi2", "pos"):
+                assert torch.equal(got[key], ref[key]), (yt, xt, key)
+            torch.testing.assert_close(got_pk, ref_pk, rtol=1e-6, atol=0)
+    for bad_y, bad_x in (([12, 8, 8], [0, 0, 0]), ([8, 8, 8], [0, 3, 0]), ([8, 8, 8], [-1, 0, 0])):
+        with pytest.raises(L.LPT2Error):
+            L.lpt2_set_tiles(plan, bad_y, bad_x)
+    with pytest.raises(L.LPT2Error):
+        L.lpt2_set_tiles(plan, [8, 8], [0, 0])                # one entry per group
+    small = L.Plan(W.Instance(16, 64.0, 3, W.COSMO), n_steps=STEPS)
+    with pytest.raises(L.LPT2Error):
+        L.lpt2_set_tiles(small, [16], [0])                     # 16 pencils need N >= 32
+    L.lpt2_set_tiles(small, [8], [2])
+    L.lpt2_set_tiles(plan, [0, 0, 0], [0, 0, 0])
+    L.lpt2_autotune(plan, n_shells=16, reps=1)
+    yt, xt = L.lpt2_tiles(plan)
+    assert all(v in (0, 8, 16) for v in yt) and all(v in (0, 1, 2) for v in xt)
+    got, got_pk = run()
+    for key in ("psi1", "psi2", "pos"):
+        assert torch.equal(got[key], ref[key]), key
+
+    single = L.Plan(W.Instance(64, 256.0, 5, W.COSMO), n_steps=STEPS)
+    vjps = []
+    for yt, xt in ((0, 0), (16, 2), (8, 1)):
+        L.lpt2_set_tiles(single, [yt], [xt])
+        g_noise, g_t = L.lpt2_displace_vjp(single, g_density=torch.full((64 ** 3,), 1e-3, device="cuda"))
+        torch.cuda.synchronize()
+        vjps.append((g_noise.clone(), g_t.clone()))
+    for g_noise, g_t in vjps[1:]:
+        assert torch.equal(g_noise, vjps[0][0]) and torch.equal(g_t, vjps[0][1])
