@@ -223,14 +223,15 @@ int x_blocks(int n) {
 
 // Workspace layout (byte offsets; every region 256-byte aligned):
 //   N_SLOTS slots of slot_sz bytes, the CIC density of every instance (sum of n^3 floats),
-//   P(k) block partials [xb_max][3][256] doubles, internal pk / k_mean / n_modes [256] each,
+//   sqrt(P N^3/V) per stored mode of every instance (sum of n^3 / 2 floats; filled by
+//   lpt2_set_workspace from the mode tables, read by the x passes of delta(k)), P(k) block partials [xb_max][3][256] doubles, internal pk / k_mean / n_modes [256] each,
 //   shell weights [256] floats, dL/dln|fR0| block partials [xb_max] doubles, P(k) per
 //   instance [n_inst][256] doubles (lpt2_autotune), then with LPT2_HOST_IO two buffer sets
 //   of lpt2_displace_host (noise n^3 floats, positions 3 n^3 floats, P(k) 256 doubles) and
 //   with LPT2_MAX_OUTPUTS(m) m output times' tables (growth [4][nk] doubles and floats,
 //   multiplier tables [mode_table_len] float4 and float2).
 struct WsLayout {
-  size_t slot_sz, rho, pk_part, pk, shw, theta, inst_pk, hio, hio_noise, hio_pos, hio_pk, hio_set, outs,
+  size_t slot_sz, rho, scf, pk_part, pk, shw, theta, inst_pk, hio, hio_noise, hio_pos, hio_pk, hio_set, outs,
       out_tab, out_tabf, out_mt0, out_mt1, out_each, total;
 };
 size_t up256(size_t b) { return (b + 255) / 256 * 256; }
@@ -239,7 +240,8 @@ WsLayout ws_layout(size_t slot_sz, size_t total_cells, int xb_max, int n_inst, i
   WsLayout w{};
   w.slot_sz = slot_sz;
   w.rho = N_SLOTS * slot_sz;
-  w.pk_part = up256(w.rho + total_cells * sizeof(float));
+  w.scf = up256(w.rho + total_cells * sizeof(float));
+  w.pk_part = up256(w.scf + total_cells / 2 * sizeof(float));
   w.pk = up256(w.pk_part + (size_t)xb_max * 3 * kMaxShells * 8);
   w.shw = up256(w.pk + 3 * kMaxShells * 8);
   w.theta = up256(w.shw + kMaxShells * 4);
@@ -268,6 +270,10 @@ size_t rho_all_off(const lpt2_plan_s* p) { return N_SLOTS * slot_bytes(p); }
 float* rho_group(const lpt2_plan_s* p) {
   return reinterpret_cast<float*>(p->ws + rho_all_off(p)) + p->cur_rho_off;
 }
+// sqrt(P N^3/V) per mode of the current instances (the scf field of XArgs)
+const float* scf_group(const lpt2_plan_s* p) {
+  return reinterpret_cast<const float*>(p->ws + ws_layout(p).scf) + p->cur_rho_off / 2;
+}
 size_t tail_pk_part(const lpt2_plan_s* p) { return ws_layout(p).pk_part; }
 size_t tail_shw(const lpt2_plan_s* p) { return ws_layout(p).shw; }
 size_t tail_theta(const lpt2_plan_s* p) { return ws_layout(p).theta; }
@@ -288,6 +294,7 @@ Geo make_geo(const lpt2_plan_s* p) {
   g.inv_cell = (float)(n / p->box);
   g.inv_n3 = (float)(1.0 / (n * n * n));
   g.sqrt_n3_over_v = (float)sqrt(n * n * n / (p->box * p->box * p->box));
+  g.kf2n3 = (float)(4.0 * M_PI * M_PI / (p->box * p->box) * n * n * n);
   g.batch = p->cur_batch;
   g.inst0 = p->cur_inst0;
   g.tab_stride = 4 * p->nk;
@@ -867,6 +874,11 @@ int lpt2_set_workspace(lpt2_plan_t p, void* dev_ptr, size_t bytes) {
   if (bytes < ws_need(p)) return fail(LPT2_ENOWORKSPACE, "workspace too small: %zu < %zu", bytes, ws_need(p));
   p->ws = (char*)dev_ptr;
   p->ws_bytes = bytes;
+  // the sqrt(P N^3/V) field of every group (P(k) only: no later call changes it)
+  for (const Group& g : p->groups)
+    LAUNCH(p, "sc_field", 2.0 * g.n * g.n * (double)g.n * g.count,
+           launch_sc_field(g.mt0, g.n, g.count,
+                           reinterpret_cast<float*>(p->ws + ws_layout(p).scf) + g.off / 2, p->stream));
   return p->n_out_a > 0 ? run_output_growth(p) : LPT2_OK;   // the output tables live in the workspace
 }
 
@@ -989,6 +1001,7 @@ int displace_prefix(lpt2_plan_t p, const FwdSlots& f, const float* noise, bool s
   x.mode = X_DELTA;
   x.split = split;
   x.in = f.A;
+  x.scf = scf_group(p);
   x.delta_out = f.D;
   for (int i = 0; i < 5; ++i) x.out[i] = f.X[i];
   x.cosmo = p->cosmo_dev;
@@ -1584,6 +1597,7 @@ int lpt2_source_ratio(lpt2_plan_t p, const float* noise, int n_bins, double* mea
     x.tw = p->tw;
     x.mode = X_DELTA;
     x.in = T;
+    x.scf = scf_group(p);
     x.delta_out = D;
     for (int i = 0; i < 3; ++i) x.out[i] = F[i];
     x.cosmo = p->cosmo_dev;
@@ -1947,6 +1961,7 @@ int lpt2_displace_vjp(lpt2_plan_t p, const float* noise, const float* g_pos, con
   xd.g = g;
   xd.tw = p->tw;
   xd.mode = X_ADJ_DELTA;
+  xd.scf = scf_group(p);
   xd.in2[0] = S[15];
   xd.in2[1] = S[16];
   xd.in2[2] = S[5];

@@ -456,7 +456,7 @@ cudaError_t launch_box_muller(const uint32_t* words, int64_t count, const float4
 
 // Bulk-tensor map of an x-pass input (see passes.h).  cuTensorMapEncodeTiled is a
 // host-only driver call, resolved through the runtime (no link against the driver).
-bool encode_x_tile_map(CUtensorMap* map, const void* base, int n, int w, int batch) {
+bool encode_x_tile_map(CUtensorMap* map, const void* base, int inner, int n, int box_inner, int batch) {
   typedef CUresult (*Encode)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
                              const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
                              CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
@@ -469,14 +469,37 @@ bool encode_x_tile_map(CUtensorMap* map, const void* base, int n, int w, int bat
       return false;
     encode = (Encode)f;
   }
-  const cuuint64_t nn = (cuuint64_t)n;
-  const cuuint64_t dims[4] = {nn, nn, nn, (cuuint64_t)batch};                  // kz floats, ky, kx, instance
-  const cuuint64_t strides[3] = {nn * 4, nn * nn * 4, nn * nn * nn * 4};       // bytes of dims 1..3
-  const cuuint32_t box[4] = {(cuuint32_t)(2 * w), 1u, (cuuint32_t)(n > 256 ? 256 : n), 1u};
+  const cuuint64_t nn = (cuuint64_t)n, in = (cuuint64_t)inner;
+  const cuuint64_t dims[4] = {in, nn, nn, (cuuint64_t)batch};                  // kz floats, ky, kx, instance
+  const cuuint64_t strides[3] = {in * 4, in * nn * 4, in * nn * nn * 4};       // bytes of dims 1..3
+  const cuuint32_t box[4] = {(cuuint32_t)box_inner, 1u, (cuuint32_t)(n > 256 ? 256 : n), 1u};
   const cuuint32_t estr[4] = {1u, 1u, 1u, 1u};
   return encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<void*>(base), dims, strides, box, estr,
                 CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                 CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// sqrt(P N^3/V) of every stored mode (kx, ky, kz < N/2) of `count` half spectra, from the
+// instances' mode tables; zero on the modes the x passes zero (a Nyquist kx or ky, and the
+// mean), so the field can stand in for the table entry with no test of its own.
+__global__ void k_sc_field(const float4* __restrict__ mt0, int n, float* __restrict__ scf) {
+  const int h = n / 2;
+  const size_t per = (size_t)n * n * h;
+  const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= per) return;
+  const int kz = (int)(e % h), ky = (int)((e / h) % n), kx = (int)(e / ((size_t)n * h));
+  const int mx = mode_of(kx, n), my = mode_of(ky, n), mz = kz;
+  const int n2 = mx * mx + my * my + mz * mz;
+  const bool zero = ky == h || kx == h || n2 == 0;
+  const size_t inst = blockIdx.y;
+  scf[inst * per + e] = zero ? 0.f : mt0[inst * mode_table_len(n) + n2].x;
+}
+
+cudaError_t launch_sc_field(const float4* mt0, int n, int count, float* scf, cudaStream_t s) {
+  const size_t per = (size_t)n * n * (n / 2);
+  if (count < 1 || count > 65535) return cudaErrorInvalidValue;
+  k_sc_field<<<dim3((unsigned)((per + 255) / 256), count), 256, 0, s>>>(mt0, n, scf);
+  return cudaGetLastError();
 }
 
 // Box-Muller tables (layout in boxmuller.cuh): FP64 values, each split into the float

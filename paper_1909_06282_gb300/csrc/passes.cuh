@@ -761,11 +761,13 @@ template <int N> constexpr int x_minb(int mode) {
 // One x-pass tile: kz block kzb (W consecutive kz), fixed ky, instance inst, all kx.
 // Thread tid = t * W + w; kx = elem(t, r).  v holds the tile's input (non-adjoint modes;
 // the adjoint modes load their x-order groups here), sm is the tile's exchange buffer,
-// s_acc the per-warp accumulators (zeroed by the caller), blk the tile's linear index.
+// s_acc the per-warp accumulators (zeroed by the caller), blk the tile's linear index,
+// s_sc the tile of the scf field staged in shared memory (element (kx, w) at kx W + w), or
+// null to read a.scf from global memory.
 template <int N, int MODE>
 __device__ __forceinline__ void x_tile(const XArgs& a, float2 (&v)[PassCfg<N>::RMAX], int kzb, int ky, int inst,
                                        size_t blk, const SmemCol<PassCfg<N>::W>& sm, const float2* s_tw,
-                                       double* s_acc) {
+                                       double* s_acc, const float* s_sc = nullptr) {
   using C = PassCfg<N>;
   const int w = threadIdx.x % C::W, t = threadIdx.x / C::W;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -986,7 +988,12 @@ __device__ __forceinline__ void x_tile(const XArgs& a, float2 (&v)[PassCfg<N>::R
   }
 
   // k-space multipliers from the per-|n|^2 tables.  g = potential to transform back along x.
+  // The modes of a warp hit scattered table entries (a sector each); where the multiplier is
+  // sqrt(P N^3/V) and 1/(k^2 N^3) only, the first comes from the scf field (coalesced, or
+  // staged with the tile) and the second is computed.
   const size_t toff = (size_t)inst * mode_table_len(N);
+  const bool field = (MODE == X_DELTA && !a.split && (s_sc || a.scf)) || (MODE == X_ADJ_DELTA && a.scf) ||
+                     MODE == X_PHI;
   float2 g[C::RMAX], hpot[C::RMAX];
   float theta = 0.f;
 #pragma unroll
@@ -995,9 +1002,17 @@ __device__ __forceinline__ void x_tile(const XArgs& a, float2 (&v)[PassCfg<N>::R
     const int mx = mode_of(kx, N);
     const bool zero = ny_nyq || kx == C::H || (mx == 0 && my == 0 && mz == 0);
     const int n2 = mx * mx + my * my + mz * mz;
-    const float4 mt = zero ? make_float4(0.f, 0.f, 0.f, 0.f) : __ldg(a.mt0 + toff + n2);
-    const float sc = mt.x, inv = mt.y, d1 = mt.z, d2 = mt.w;   // sqrt(P N^3/V), 1/(k^2 N^3), D1, D2
     const size_t e = base + (size_t)kx * stride;
+    float4 mt;
+    if (field) {
+      const float inv_c = zero ? 0.f : __frcp_rn((float)n2 * a.g.kf2n3);
+      float sc_f = 0.f;
+      if (MODE != X_PHI) sc_f = s_sc ? s_sc[kx * C::W + w] : __ldg(a.scf + e);
+      mt = make_float4(sc_f, inv_c, 0.f, 0.f);
+    } else {
+      mt = zero ? make_float4(0.f, 0.f, 0.f, 0.f) : __ldg(a.mt0 + toff + n2);
+    }
+    const float sc = mt.x, inv = mt.y, d1 = mt.z, d2 = mt.w;   // sqrt(P N^3/V), 1/(k^2 N^3), D1, D2
     if (MODE == X_DELTA) {
       const float2 d = cscale(v[r], sc);
       if (a.delta_out) a.delta_out[e] = d;
@@ -1096,21 +1111,26 @@ __global__ void __launch_bounds__(PassCfg<N>::XT, x_minb<N>(MODE)) k_x(XArgs a) 
 #ifndef LPT2_X_TMA
 #define LPT2_X_TMA 1
 #endif
-template <int N> struct XTmaCfg {
+// SC: each ring stage also holds the tile of the scf field (TILE floats after the TILE
+// float2 of the input).
+template <int N, bool SC = false> struct XTmaCfg {
   using C = PassCfg<N>;
   static constexpr int TILE = N * C::W;                 // float2 per tile
+  static constexpr int STAGE = TILE + (SC ? TILE / 2 : 0);   // float2 per ring stage
+  static constexpr unsigned STAGE_BYTES = STAGE * 8u;
   static constexpr int NBOX = N > 256 ? N / 256 : 1;    // bulk-tensor boxes per tile (<= 256 kx each)
   static constexpr int BOXROWS = N / NBOX;
   static constexpr int KZB = C::H / C::W;               // kz blocks per (ky, instance)
-  static constexpr int BAR_OFF = (N + 2 * TILE) * 8;    // bytes: twiddles, ring, then two barriers
+  static constexpr int BAR_OFF = (N + 2 * STAGE) * 8;   // bytes: twiddles, ring, then two barriers
   static constexpr int ACC_OFF = BAR_OFF + 16;
-  static_assert((2 * C::W * 4) % 16 == 0, "the box's innermost extent must be a multiple of 16 bytes");
+  static_assert((2 * C::W * 4) % 16 == 0 && (!SC || (C::W * 4) % 16 == 0),
+                "the boxes' innermost extents must be multiples of 16 bytes");
 };
 
-template <int N, int MODE>
+template <int N, int MODE, bool SC>
 __global__ void __launch_bounds__(PassCfg<N>::XT, x_minb<N>(MODE)) k_x_tma(const __grid_constant__ XArgs a) {
   using C = PassCfg<N>;
-  using Q = XTmaCfg<N>;
+  using Q = XTmaCfg<N, SC>;
   extern __shared__ __align__(128) unsigned char xs_raw[];
   float2* s_tw = reinterpret_cast<float2*>(xs_raw);
   float2* ring = s_tw + N;
@@ -1122,11 +1142,17 @@ __global__ void __launch_bounds__(PassCfg<N>::XT, x_minb<N>(MODE)) k_x_tma(const
   const int ntiles = Q::KZB * N * a.g.batch;
   auto issue = [&](int st, int tile) {   // one thread
     const int kzb = tile % Q::KZB, ky = (tile / Q::KZB) % N, inst = tile / (Q::KZB * N);
-    mbar_expect_tx(&bar[st], Q::TILE * 8u);
+    mbar_expect_tx(&bar[st], Q::STAGE_BYTES);
 #pragma unroll
     for (int j = 0; j < Q::NBOX; ++j)
-      tensor_load_4d(ring + st * Q::TILE + j * Q::BOXROWS * C::W, &a.tmap, 2 * kzb * C::W, ky, j * Q::BOXROWS,
+      tensor_load_4d(ring + st * Q::STAGE + j * Q::BOXROWS * C::W, &a.tmap, 2 * kzb * C::W, ky, j * Q::BOXROWS,
                      inst, &bar[st]);
+    if constexpr (SC) {
+      float* scs = reinterpret_cast<float*>(ring + st * Q::STAGE + Q::TILE);
+#pragma unroll
+      for (int j = 0; j < Q::NBOX; ++j)
+        tensor_load_4d(scs + j * Q::BOXROWS * C::W, &a.tmap_sc, kzb * C::W, ky, j * Q::BOXROWS, inst, &bar[st]);
+    }
   };
   if (threadIdx.x == 0) {
     s_fail = 0;
@@ -1147,7 +1173,7 @@ __global__ void __launch_bounds__(PassCfg<N>::XT, x_minb<N>(MODE)) k_x_tma(const
     const bool ok = mbar_wait(&bar[st], (i >> 1) & 1, a.g.wait);
     if (!ok) s_fail = 1;
     float2 v[C::RMAX];
-    const float2* tl = ring + st * Q::TILE;
+    const float2* tl = ring + st * Q::STAGE;
 #pragma unroll
     for (int r = 0; r < C::RMAX; ++r) v[r] = ok ? tl[elem<N>(t, r) * C::W + w] : make_float2(0.f, 0.f);
     __syncthreads();   // tile read by every thread before the transforms reuse the buffer
@@ -1160,8 +1186,9 @@ __global__ void __launch_bounds__(PassCfg<N>::XT, x_minb<N>(MODE)) k_x_tma(const
       return;
     }
     const int kzb = tile % Q::KZB, ky = (tile / Q::KZB) % N, inst = tile / (Q::KZB * N);
-    const SmemCol<C::W> sm{ring + st * Q::TILE + w};
-    x_tile<N, MODE>(a, v, kzb, ky, inst, (size_t)tile, sm, s_tw, s_acc);
+    const SmemCol<C::W> sm{ring + st * Q::STAGE + w};
+    const float* s_sc = SC ? reinterpret_cast<const float*>(ring + st * Q::STAGE + Q::TILE) : nullptr;
+    x_tile<N, MODE>(a, v, kzb, ky, inst, (size_t)tile, sm, s_tw, s_acc, s_sc);
     __syncthreads();   // ring stage and accumulators free
     if (threadIdx.x == 0 && tile + 2 * gridDim.x < ntiles) {
       fence_proxy_async_smem();
@@ -1247,6 +1274,26 @@ template <int N> cudaError_t launch_y_t(const YArgs& a, cudaStream_t s) {
   if (a.g.ytile != 0 && a.g.ytile != YCfg<N>::W) return cudaErrorInvalidValue;
   return launch_y_w<N, 0>(a, s);
 }
+// persistent bulk-tensor x pass: as many CTAs as fit on the GPU at once, or one per tile
+template <int N, int MODE, bool SC> cudaError_t launch_x_tma(const XArgs& a, int acc, cudaStream_t s) {
+  using C = PassCfg<N>;
+  using Q = XTmaCfg<N, SC>;
+  XArgs b = a;
+  if (!encode_x_tile_map(&b.tmap, a.in, N, N, 2 * C::W, a.g.batch)) return cudaErrorInvalidValue;
+  if (SC && !encode_x_tile_map(&b.tmap_sc, a.scf, N / 2, N, C::W, a.g.batch)) return cudaErrorInvalidValue;
+  const int smem = Q::ACC_OFF + acc;
+  cudaError_t e = cudaFuncSetAttribute(k_x_tma<N, MODE, SC>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  int dev = 0, sms = 0, per_sm = 0;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_x_tma<N, MODE, SC>, C::XT, smem)) != cudaSuccess)
+    return e;
+  const long long tiles = (long long)Q::KZB * N * a.g.batch;
+  const int grid = (int)std::min<long long>(tiles, (long long)sms * std::max(per_sm, 1));
+  k_x_tma<N, MODE, SC><<<grid, C::XT, smem, s>>>(b);
+  return cudaGetLastError();
+}
 template <int N, int MODE> cudaError_t launch_x_m(const XArgs& a, cudaStream_t s) {
   using C = PassCfg<N>;
   LPT2_CHECK_BATCH(a);
@@ -1262,21 +1309,10 @@ template <int N, int MODE> cudaError_t launch_x_m(const XArgs& a, cudaStream_t s
   if (a.g.xtile < 0 || a.g.xtile > 2) return cudaErrorInvalidValue;
   if constexpr (MODE == X_DELTA || MODE == X_PHI) {
     if (a.g.xtile == 0 ? LPT2_X_TMA != 0 : a.g.xtile == 1) {
-      using Q = XTmaCfg<N>;
-      XArgs b = a;
-      if (!encode_x_tile_map(&b.tmap, a.in, N, C::W, a.g.batch)) return cudaErrorInvalidValue;
-      const int smem = Q::ACC_OFF + acc;
-      cudaError_t e = cudaFuncSetAttribute(k_x_tma<N, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-      if (e != cudaSuccess) return e;
-      int dev = 0, sms = 0, per_sm = 0;
-      if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
-      if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-      if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_x_tma<N, MODE>, C::XT, smem)) != cudaSuccess)
-        return e;
-      const long long tiles = (long long)Q::KZB * N * a.g.batch;
-      const int grid = (int)std::min<long long>(tiles, (long long)sms * std::max(per_sm, 1));
-      k_x_tma<N, MODE><<<grid, C::XT, smem, s>>>(b);
-      return cudaGetLastError();
+      if constexpr (MODE == X_DELTA) {
+        if (a.scf && !a.split) return launch_x_tma<N, MODE, true>(a, acc, s);
+      }
+      return launch_x_tma<N, MODE, false>(a, acc, s);
     }
   }
   const int smem = C::XSMEM + acc;

@@ -32,6 +32,7 @@ struct Geo {
   float inv_cell;       // N / L
   float inv_n3;         // 1 / N^3 (inverse-transform normalisation)
   float sqrt_n3_over_v; // sqrt(N^3 / L^3)
+  float kf2n3;          // kf^2 N^3: a mode's 1/(k^2 N^3) is 1 / (|n|^2 kf2n3)
   // batching: grid z runs over `batch` instances of this grid size; instance z of
   // the launch is global instance inst0 + z (growth tables, seeds, outputs)
   int batch;
@@ -169,6 +170,11 @@ struct XArgs {
   // group, then |n|^2): {sqrt(P N^3/V), 1/(k^2 N^3), D1, D2} and {dD1, dD2}/dln|fR0|
   const float4* mt0;
   const float2* mt1;
+  // X_DELTA (without the split) and X_ADJ_DELTA: sqrt(P N^3/V) of every mode of the group's
+  // half spectra, float[batch][N][N][N/2] in the fields' layout (zero on the modes the
+  // passes zero), or null for the mode table; with it, and in X_PHI, 1/(k^2 N^3) is computed
+  // from |n|^2, so these modes read no table entry
+  const float* scf;
   double* theta_part;     // X_ADJ_SOURCE: per-block partial of dL/dln|fR0|
   // X_MUL: multiplier (i kx)^ord[0] (i ky)^ord[1] (i kz)^ord[2] g(|k|) / N^3, g one of MulG,
   // with m^2(a), 1/a^2 and D1_GR(a) for mu(k) and Pi(k)
@@ -176,13 +182,17 @@ struct XArgs {
   int mul_g;
   int mul_ord[3];
   float mul_m2a, mul_inv_a2, mul_d1gr;
-  CUtensorMap tmap;       // bulk-tensor map of `in` (set by the launcher; encode_x_tile_map)
+  CUtensorMap tmap;       // bulk-tensor maps of `in` and `scf` (set by the launcher)
+  CUtensorMap tmap_sc;
 };
 
-// Bulk-tensor map of a batch of half spectra float2[batch][N][N][N/2] seen as floats
-// (kz re/im: N floats, ky, kx, instance) whose box is one x-pass tile: 2w floats (w
-// consecutive kz) x 1 ky x min(N, 256) kx x 1 instance.  False if the driver refuses it.
-bool encode_x_tile_map(CUtensorMap* map, const void* base, int n, int w, int batch);
+// Bulk-tensor map of a batch of fields float[batch][N][N][inner] (inner floats along kz:
+// N for a half spectrum of float2, N/2 for the scf field; then ky, kx, instance) whose box
+// is one x-pass tile: box_inner floats x 1 ky x min(N, 256) kx x 1 instance.  False if the
+// driver refuses it.
+bool encode_x_tile_map(CUtensorMap* map, const void* base, int inner, int n, int box_inner, int batch);
+// Fills scf (XArgs) for `count` instances of an n^3 grid from their mode tables mt0.
+cudaError_t launch_sc_field(const float4* mt0, int n, int count, float* scf, cudaStream_t s);
 
 // Radial factors of the full-source diagnostic (Sec. 3, Eqs. s1-s4):
 enum MulG {

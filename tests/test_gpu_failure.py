@@ -10,6 +10,8 @@
 - Allocation failure: every device allocation is made by lpt2_plan; making the k-th one
   fail must return LPT2_ENOMEM, leave no plan and free every allocation already made.
 """
+import gc
+
 import numpy as np
 import pytest
 
@@ -63,6 +65,7 @@ def test_bounded_wait_timeout_in_the_adjoint_source_pass(L):
 
 def test_every_plan_allocation_failure_returns_enomem_and_frees(L):
     insts = [W.Instance(32, 64.0, 1, W.COSMO), W.Instance(64, 128.0, 2, W.COSMO)]
+    gc.collect()   # plans of earlier tests awaiting collection would free theirs mid-count
     base = L.lpt2_debug_alloc_hook(-1)
     ok = L.Plan(insts, n_steps=16, workspace=False)
     n_alloc = L.lpt2_debug_alloc_hook(-1) - base      # allocations a two-group plan makes
