@@ -297,6 +297,8 @@ __global__ void k_pk_finalize(const double* part, int n_blocks, int ns, double* 
   if (kmean) kmean += (size_t)blockIdx.y * ns;
   if (nmodes) nmodes += (size_t)blockIdx.y * ns;
   double sp = 0.0, sk = 0.0, sc = 0.0;
+  // unrolled: eight rows' loads in flight per thread; the adds keep their order
+#pragma unroll 8
   for (int i = threadIdx.x; i < n_blocks; i += blockDim.x) {
     const double* q = part + (size_t)i * 3 * ns;
     sp += q[b];
@@ -389,34 +391,57 @@ cudaError_t launch_shell_geometry(int n, double box, int n_shells, double* ksum,
   return cudaGetLastError();
 }
 
-__global__ void k_pk_finalize_p(const double* part, int n_blocks, int ns, const double* ksum,
-                                const unsigned long long* count, double* pk, double* kmean, int64_t* nmodes) {
-  const int b = blockIdx.x;
-  part += (size_t)blockIdx.y * n_blocks * ns;   // instance blockIdx.y
-  pk += (size_t)blockIdx.y * ns;
-  if (kmean) kmean += (size_t)blockIdx.y * ns;
-  if (nmodes) nmodes += (size_t)blockIdx.y * ns;
-  double sp = 0.0;
-  for (int i = threadIdx.x; i < n_blocks; i += blockDim.x) sp += part[(size_t)i * ns + b];
+// Shell sums of the per-block P partials in two fixed-order stages (the result does not
+// depend on scheduling).  Stage 1: CTA (g, instance) takes rows [g R, g R + R) of the
+// partials; thread (lane, b) = (tid / ns, tid % ns) sums rows lane, lane + L, ... of shell b
+// (L = 256 / ns lanes; a warp reads consecutive shells of a row, i.e. contiguous doubles),
+// then the lanes are summed in order into scratch[instance][g][b].  Stage 2 sums the G
+// rows of scratch per shell in order and divides by the shell's mode count.
+__global__ void k_pk_rows(const double* __restrict__ part, int n_blocks, int ns, int rows, double* __restrict__ scratch) {
+  const int g = blockIdx.x, inst = blockIdx.y;
+  part += (size_t)inst * n_blocks * ns;
+  const int L = blockDim.x / ns, lane = threadIdx.x / ns, b = threadIdx.x % ns;
+  const int r0 = g * rows, r1 = min(n_blocks, r0 + rows);
+  double acc = 0.0;
+  if (lane < L) {
+#pragma unroll 4
+    for (int r = r0 + lane; r < r1; r += L) acc += part[(size_t)r * ns + b];
+  }
   __shared__ double sh[256];
-  sh[threadIdx.x] = sp;
+  sh[threadIdx.x] = acc;
   __syncthreads();
-  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-    if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
-    __syncthreads();
+  if (threadIdx.x < ns) {
+    double sum = 0.0;
+    for (int l = 0; l < L; ++l) sum += sh[l * ns + threadIdx.x];
+    scratch[((size_t)inst * gridDim.x + g) * ns + threadIdx.x] = sum;
   }
-  if (threadIdx.x == 0) {
-    const double c = (double)count[b];
-    pk[b] = c > 0 ? sh[0] / c : 0.0;
-    if (kmean) kmean[b] = c > 0 ? ksum[b] / c : 0.0;
-    if (nmodes) nmodes[b] = (int64_t)count[b];
-  }
+}
+
+__global__ void k_pk_finalize_p(const double* __restrict__ scratch, int G, int ns, const double* ksum,
+                                const unsigned long long* count, double* pk, double* kmean, int64_t* nmodes) {
+  const int inst = blockIdx.x, b = threadIdx.x;
+  if (b >= ns) return;
+  double sp = 0.0;
+  for (int g = 0; g < G; ++g) sp += scratch[((size_t)inst * G + g) * ns + b];
+  const double c = (double)count[b];
+  pk[(size_t)inst * ns + b] = c > 0 ? sp / c : 0.0;
+  if (kmean) kmean[(size_t)inst * ns + b] = c > 0 ? ksum[b] / c : 0.0;
+  if (nmodes) nmodes[(size_t)inst * ns + b] = (int64_t)count[b];
 }
 
 cudaError_t launch_pk_finalize_p(const double* part, int n_blocks, int n_shells, const double* ksum,
                                  const unsigned long long* count, double* pk, double* k_mean, int64_t* n_modes,
                                  cudaStream_t s, int batch) {
-  k_pk_finalize_p<<<dim3(n_shells, batch), 256, 0, s>>>(part, n_blocks, n_shells, ksum, count, pk, k_mean, n_modes);
+  if (n_shells < 1 || n_shells > 256 || n_blocks < 1 || batch < 1 || batch > 65535) return cudaErrorInvalidValue;
+  // the stage-1 sums follow the partials in their buffer (sized for three quantities per
+  // row and shell, of which P uses one): batch * G * n_shells <= batch * n_blocks * n_shells
+  const int G = n_blocks < 128 ? n_blocks : 128;
+  const int rows = (n_blocks + G - 1) / G;
+  double* scratch = const_cast<double*>(part) + (size_t)batch * n_blocks * n_shells;
+  k_pk_rows<<<dim3(G, batch), 256, 0, s>>>(part, n_blocks, n_shells, rows, scratch);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_pk_finalize_p<<<batch, 256, 0, s>>>(scratch, G, n_shells, ksum, count, pk, k_mean, n_modes);
   return cudaGetLastError();
 }
 

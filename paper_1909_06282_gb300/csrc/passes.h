@@ -267,7 +267,9 @@ cudaError_t launch_src_t1(int n_bins, const double* ksum, const unsigned long lo
                           const double* tab_d1, int nk, double k_min, double k_max, const double* d1gr, double a,
                           double m2a, double M2a, double fpg, int gr, double* t1, cudaStream_t s);
 
-// P(k) from per-block |delta|^2 shell sums [n_blocks][n_shells] and the cached geometry.
+// P(k) from per-block |delta|^2 shell sums [batch][n_blocks][n_shells] and the cached
+// geometry; the buffer `part` must hold twice the partials (the first stage's sums follow
+// them), n_shells in [1, 256].
 cudaError_t launch_pk_finalize_p(const double* part, int n_blocks, int n_shells, const double* ksum,
                                  const unsigned long long* count, double* pk, double* k_mean, int64_t* n_modes,
                                  cudaStream_t s, int batch);
