@@ -758,6 +758,16 @@ template <int N> constexpr int x_minb(int mode) {
              : PassCfg<N>::XMINB;
 }
 
+// Tile inputs of the adjoint modes already in shared memory (element (kx, w) at kx W + w):
+// `summed` = v holds the sum of the transformed x-order groups; hpsi, delta, s replace the
+// global reads of hpsi_in, delta_in and s_in (null: read from global memory).
+struct XSmemIn {
+  bool summed = false;
+  const float2* hpsi = nullptr;
+  const float2* delta = nullptr;
+  const float2* s = nullptr;
+};
+
 // One x-pass tile: kz block kzb (W consecutive kz), fixed ky, instance inst, all kx.
 // Thread tid = t * W + w; kx = elem(t, r).  v holds the tile's input (non-adjoint modes;
 // the adjoint modes load their x-order groups here), sm is the tile's exchange buffer,
@@ -767,7 +777,7 @@ template <int N> constexpr int x_minb(int mode) {
 template <int N, int MODE>
 __device__ __forceinline__ void x_tile(const XArgs& a, float2 (&v)[PassCfg<N>::RMAX], int kzb, int ky, int inst,
                                        size_t blk, const SmemCol<PassCfg<N>::W>& sm, const float2* s_tw,
-                                       double* s_acc, const float* s_sc = nullptr) {
+                                       double* s_acc, const float* s_sc = nullptr, XSmemIn si = {}) {
   using C = PassCfg<N>;
   const int w = threadIdx.x % C::W, t = threadIdx.x / C::W;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -781,7 +791,7 @@ __device__ __forceinline__ void x_tile(const XArgs& a, float2 (&v)[PassCfg<N>::R
   (void)warp;
   (void)lane;
   const bool adjoint = (MODE == X_ADJ_SOURCE || MODE == X_ADJ_DELTA);
-  if (adjoint) {
+  if (adjoint && !si.summed) {
     // forward x transform of each x-order group, summed with conj((i kx)^m)
     const int ng = (MODE == X_ADJ_SOURCE) ? 2 : 3;
 #pragma unroll
@@ -797,7 +807,7 @@ __device__ __forceinline__ void x_tile(const XArgs& a, float2 (&v)[PassCfg<N>::R
         v[r] = cadd(v[r], dconj(u[r], kf * (float)mode_of(kx, N), gi));
       }
     }
-  } else {
+  } else if (!adjoint) {
     if (MODE == X_MUL) {   // full-source diagnostic: multiplier, then inverse x
       const size_t toff = (size_t)inst * mode_table_len(N);
 #pragma unroll
@@ -1033,12 +1043,13 @@ __device__ __forceinline__ void x_tile(const XArgs& a, float2 (&v)[PassCfg<N>::R
       g[r] = cscale(gu, -d2 * inv);                         // h_S = -D2 g_u / (k^2 N^3)
       if (!zero) {                                          // dL/dln|fR0| contribution
         const float2 tt = __ldg(a.mt1 + toff + n2);
-        const float2 dl = a.delta_in[e], sk = a.s_in[e];
+        const float2 dl = si.delta ? si.delta[kx * C::W + w] : a.delta_in[e];
+        const float2 sk = si.s ? si.s[kx * C::W + w] : a.s_in[e];
         const float cx = tt.x * dl.x - tt.y * sk.x, cy = tt.x * dl.y - tt.y * sk.y;
         theta += (cx * gu.x + cy * gu.y) * inv * (mz == 0 ? 1.f : 2.f);
       }
     } else {                                                // X_ADJ_DELTA: v = sum of h_phi groups
-      const float2 h = cadd(cscale(v[r], inv), a.hpsi_in[e]);
+      const float2 h = cadd(cscale(v[r], inv), si.hpsi ? si.hpsi[kx * C::W + w] : a.hpsi_in[e]);
       g[r] = cscale(h, sc);                                 // s(k) (h_Psi + h_phi)
     }
   }
@@ -1046,7 +1057,9 @@ __device__ __forceinline__ void x_tile(const XArgs& a, float2 (&v)[PassCfg<N>::R
     const float ws = warp_sum(theta);
     if (lane == 0) s_acc[warp] = (double)ws;
   }
-  // x-inverse transforms with x-derivative orders
+  // x-inverse transforms with x-derivative orders (the exchange buffer may hold the
+  // shared-memory inputs read above: every thread has read its own first)
+  if (si.summed) __syncthreads();
   int nout;
   if (MODE == X_DELTA) nout = a.split ? 5 : 3;
   else if (MODE == X_PHI) nout = 3;
@@ -1197,6 +1210,124 @@ __global__ void __launch_bounds__(PassCfg<N>::XT, x_minb<N>(MODE)) k_x_tma(const
   }
 }
 
+// Adjoint x modes with their tile inputs staged by the tensor-memory accelerator: a
+// persistent CTA walks the tiles blockIdx.x, blockIdx.x + gridDim.x, ... and streams each
+// tile's four inputs (X_ADJ_DELTA: the x-order groups 0, 1, 2 and h_Psi; X_ADJ_SOURCE: the
+// groups 0, 1, delta(k) and S(k)) through a three-stage shared-memory ring in that order:
+// input c sits in stage c mod 3.  A group's forward transform runs in place in its stage,
+// after which the stage takes input c + 3; the tile's last inputs are read by the
+// multiplier and the inverse transform runs in the last stage.  The loads of the next
+// tile's first groups overlap this tile's multiplier and inverse transform.  Every wait is
+// bounded; a CTA whose wait runs out waits (default budget) for its copies in flight, sets
+// the error word and returns.
+template <int N> struct XAdjCfg {
+  using C = PassCfg<N>;
+  static constexpr int TILE = N * C::W;
+  static constexpr int NBOX = N > 256 ? N / 256 : 1;
+  static constexpr int BOXROWS = N / NBOX;
+  static constexpr int KZB = C::H / C::W;
+  static constexpr int BAR_OFF = (N + 3 * TILE) * 8;   // twiddles, three stages, barriers
+  static constexpr int ACC_OFF = BAR_OFF + 32;
+};
+
+template <int N, int MODE>
+__global__ void __launch_bounds__(PassCfg<N>::XT, x_minb<N>(MODE)) k_x_tma_adj(const __grid_constant__ XArgs a) {
+  using C = PassCfg<N>;
+  using Q = XAdjCfg<N>;
+  constexpr int NG = MODE == X_ADJ_SOURCE ? 2 : 3;   // transformed groups per tile (then 4 - NG plain inputs)
+  constexpr int NWARP = C::XT / 32;
+  extern __shared__ __align__(128) unsigned char xa_raw[];
+  float2* s_tw = reinterpret_cast<float2*>(xa_raw);
+  float2* ring = s_tw + N;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(xa_raw + Q::BAR_OFF);
+  double* s_acc = reinterpret_cast<double*>(xa_raw + Q::ACC_OFF);
+  __shared__ int s_fail;
+  const int w = threadIdx.x % C::W, t = threadIdx.x / C::W;
+  const int ntiles = Q::KZB * N * a.g.batch;
+  const int mine = blockIdx.x < ntiles ? (ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+  const int nload = 4 * mine;
+  int issued = 0;                      // thread 0: inputs issued so far (0 .. nload)
+  auto issue = [&]() {                 // thread 0: the next input into its stage
+    const int c = issued++;
+    const int tile = blockIdx.x + (c >> 2) * gridDim.x, j = c & 3, st = c % 3;
+    const int kzb = tile % Q::KZB, ky = (tile / Q::KZB) % N, inst = tile / (Q::KZB * N);
+    mbar_expect_tx(&bar[st], Q::TILE * 8u);
+#pragma unroll
+    for (int b = 0; b < Q::NBOX; ++b)
+      tensor_load_4d(ring + st * Q::TILE + b * Q::BOXROWS * C::W, &a.tmap_l[j], 2 * kzb * C::W, ky, b * Q::BOXROWS,
+                     inst, &bar[st]);
+  };
+  auto drain = [&](int c) {            // thread 0: wait (default budget) for the copies in flight
+    for (int g = c; g < issued; ++g) mbar_wait(&bar[g % 3], (g / 3) & 1);
+    report_device_error(a.g.err, LPT2_DEV_ETIMEOUT_X);
+  };
+  if (threadIdx.x == 0) {
+    s_fail = 0;
+    for (int st = 0; st < 3; ++st) mbar_init(&bar[st], 1);
+    mbar_init_fence();
+    while (issued < 3 && issued < nload) issue();
+  }
+  load_twiddles(s_tw, a.tw, N);
+  __syncthreads();
+  int c = 0;                           // next input to wait for
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int kzb = tile % Q::KZB, ky = (tile / Q::KZB) % N, inst = tile / (Q::KZB * N);
+    if (MODE == X_ADJ_SOURCE)
+      for (int i = threadIdx.x; i < NWARP; i += blockDim.x) s_acc[i] = 0.0;
+    float2 v[C::RMAX];
+#pragma unroll
+    for (int r = 0; r < C::RMAX; ++r) v[r] = make_float2(0.f, 0.f);
+    for (int j = 0; j < NG; ++j, ++c) {
+      const int st = c % 3;
+      const bool ok = mbar_wait(&bar[st], (c / 3) & 1, a.g.wait);
+      if (!ok) s_fail = 1;
+      float2 u[C::RMAX];
+#pragma unroll
+      for (int r = 0; r < C::RMAX; ++r) u[r] = ok ? ring[st * Q::TILE + elem<N>(t, r) * C::W + w] : make_float2(0.f, 0.f);
+      __syncthreads();   // stage read by every thread before the transform reuses it (and s_fail seen)
+      if (s_fail) {
+        if (threadIdx.x == 0) drain(c);
+        return;
+      }
+      fft<N, false>(u, t, SmemCol<C::W>{ring + st * Q::TILE + w}, s_tw);   // ends past its last shared read
+#pragma unroll
+      for (int r = 0; r < C::RMAX; ++r) v[r] = cadd(v[r], dconj(u[r], a.g.kf * (float)mode_of(elem<N>(t, r), N), j));
+      __syncthreads();   // every warp is past the transform: the stage is free
+      if (threadIdx.x == 0 && issued < nload) {
+        fence_proxy_async_smem();
+        issue();
+      }
+    }
+    bool ok = true;
+    for (int j = 0; j < 4 - NG; ++j) ok = mbar_wait(&bar[(c + j) % 3], ((c + j) / 3) & 1, a.g.wait) && ok;
+    if (!ok) s_fail = 1;
+    __syncthreads();
+    if (s_fail) {
+      if (threadIdx.x == 0) drain(c);
+      return;
+    }
+    XSmemIn si;
+    si.summed = true;
+    const int s0 = c % 3, s1 = (c + 1) % 3;
+    float2* ex;
+    if (MODE == X_ADJ_DELTA) {
+      si.hpsi = ring + s0 * Q::TILE;
+      ex = ring + s0 * Q::TILE;
+    } else {
+      si.delta = ring + s0 * Q::TILE;
+      si.s = ring + s1 * Q::TILE;
+      ex = ring + s1 * Q::TILE;
+    }
+    x_tile<N, MODE>(a, v, kzb, ky, inst, (size_t)tile, SmemCol<C::W>{ex + w}, s_tw, s_acc, nullptr, si);
+    __syncthreads();   // stages and accumulators free
+    if (threadIdx.x == 0) {
+      fence_proxy_async_smem();
+      for (int j = 0; j < 4 - NG && issued < nload; ++j) issue();
+    }
+    c += 4 - NG;
+  }
+}
+
 // ================================================================ launchers
 // every launcher refuses a batch outside [1, 65535] (grid z) before launching
 #define LPT2_CHECK_BATCH(a) \
@@ -1294,6 +1425,30 @@ template <int N, int MODE, bool SC> cudaError_t launch_x_tma(const XArgs& a, int
   k_x_tma<N, MODE, SC><<<grid, C::XT, smem, s>>>(b);
   return cudaGetLastError();
 }
+#ifndef LPT2_X_TMA_ADJ
+#define LPT2_X_TMA_ADJ 1
+#endif
+template <int N, int MODE> cudaError_t launch_x_tma_adj(const XArgs& a, int acc, cudaStream_t s) {
+  using C = PassCfg<N>;
+  using Q = XAdjCfg<N>;
+  XArgs b = a;
+  const float2* src[4] = {a.in2[0], a.in2[1], MODE == X_ADJ_DELTA ? a.in2[2] : a.delta_in,
+                          MODE == X_ADJ_DELTA ? a.hpsi_in : a.s_in};
+  for (int j = 0; j < 4; ++j)
+    if (!src[j] || !encode_x_tile_map(&b.tmap_l[j], src[j], N, N, 2 * C::W, a.g.batch)) return cudaErrorInvalidValue;
+  const int smem = Q::ACC_OFF + acc;
+  cudaError_t e = cudaFuncSetAttribute(k_x_tma_adj<N, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  int dev = 0, sms = 0, per_sm = 0;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_x_tma_adj<N, MODE>, C::XT, smem)) != cudaSuccess)
+    return e;
+  const long long tiles = (long long)Q::KZB * N * a.g.batch;
+  const int grid = (int)std::min<long long>(tiles, (long long)sms * std::max(per_sm, 1));
+  k_x_tma_adj<N, MODE><<<grid, C::XT, smem, s>>>(b);
+  return cudaGetLastError();
+}
 template <int N, int MODE> cudaError_t launch_x_m(const XArgs& a, cudaStream_t s) {
   using C = PassCfg<N>;
   LPT2_CHECK_BATCH(a);
@@ -1307,6 +1462,9 @@ template <int N, int MODE> cudaError_t launch_x_m(const XArgs& a, cudaStream_t s
   // the CTAs per SM, and the source multiplier, which also reads delta(k) per mode, measured
   // 0.73 -> 0.76 ms with bulk-tensor tiles.
   if (a.g.xtile < 0 || a.g.xtile > 2) return cudaErrorInvalidValue;
+  if constexpr (MODE == X_ADJ_DELTA || MODE == X_ADJ_SOURCE) {
+    if (a.g.xtile == 0 ? LPT2_X_TMA_ADJ != 0 : a.g.xtile == 1) return launch_x_tma_adj<N, MODE>(a, acc, s);
+  }
   if constexpr (MODE == X_DELTA || MODE == X_PHI) {
     if (a.g.xtile == 0 ? LPT2_X_TMA != 0 : a.g.xtile == 1) {
       if constexpr (MODE == X_DELTA) {

@@ -184,6 +184,7 @@ struct XArgs {
   float mul_m2a, mul_inv_a2, mul_d1gr;
   CUtensorMap tmap;       // bulk-tensor maps of `in` and `scf` (set by the launcher)
   CUtensorMap tmap_sc;
+  CUtensorMap tmap_l[4];  // adjoint modes: the tile inputs in the order the ring takes them
 };
 
 // Bulk-tensor map of a batch of fields float[batch][N][N][inner] (inner floats along kz:
