@@ -642,6 +642,136 @@ __global__ void __launch_bounds__(PassCfg<N>::ZT, LPT2_Z_MINB) k_z_adj_source(ZA
   }
 }
 
+// Field-pair form of k_z_adj_source, for grids whose pencil is one warp (N / RMAX = 32,
+// N = 512).  A warp owns one real row; its six phi_ij arrive as three complex pencils
+// (xx + i yy, zz + i xy, xz + i yz).  After the first two inverse transforms the row holds
+// A = phi_xx, B = phi_yy, C = phi_zz, D = phi_xy, which give four of the cotangents,
+//   g_xx = g_S (B + C),  g_yy = g_S (A + C),  g_zz = g_S (A + B),  g_xy = -2 g_S D
+// (g_ii = g_S (Tr - phi_ii)), transformed forward two at a time (g_xx + i g_yy,
+// g_zz + i g_xy) and split into their half spectra; the third pencil gives g_xz, g_yz.
+// Per row: three inverse and three forward transforms, each phi_ij and g_S read once (the
+// paired-row form transforms 7.5 pencils per row and reads the diagonal fields twice).
+// Tiles as in the field-pair layout: a ring stage holds the two fields of a pencil for the
+// CTA's eight rows, each row in its warp's padded region, used in place as the exchange row.
+#ifndef LPT2_ZADJ_FIELD_PAIRS
+#define LPT2_ZADJ_FIELD_PAIRS 1
+#endif
+template <int N> struct ZAdjFpCfg {
+  static constexpr int RMAX = Cfg<N>::RMAX, TPP = N / RMAX, H = N / 2;
+  static constexpr int ROWS = 8;                               // rows (warps) per CTA
+  static constexpr int THREADS = ROWS * 32;
+  static constexpr int ROWW = SmemRow::words(N);               // float2 per warp region
+  static constexpr int STAGE_F2 = ROWS * ROWW;
+  static constexpr unsigned STAGE_BYTES = ROWS * 2 * H * 8u;   // bytes landing per stage
+  static constexpr int BAR_OFF = (N + 2 * STAGE_F2) * 8;       // twiddles, two stages, barriers
+  static constexpr int SMEM = BAR_OFF + 64;
+  static constexpr bool OK = TPP == 32;
+  static_assert(!OK || ((ROWW * 8) % 16 == 0 && (H * 8) % 16 == 0), "bulk copies need 16-byte alignment");
+};
+template <int N> constexpr bool zadj_field_pairs() { return LPT2_ZADJ_FIELD_PAIRS && ZAdjFpCfg<N>::OK; }
+
+template <int N>
+__global__ void __launch_bounds__(ZAdjFpCfg<N>::THREADS, 2) k_z_adj_source_fp(ZAdjSourceArgs a) {
+  using Q = ZAdjFpCfg<N>;
+  constexpr int RMAX = Q::RMAX, H = Q::H;
+  extern __shared__ __align__(128) unsigned char za_raw[];
+  float2* s_tw = reinterpret_cast<float2*>(za_raw);
+  float2* ring = s_tw + N;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(za_raw + Q::BAR_OFF);
+  __shared__ int s_fail;
+  const int warp = threadIdx.x >> 5, t = threadIdx.x & 31;
+  const size_t n3 = (size_t)N * N * N;
+  const size_t zs = blockIdx.z * (n3 / 2), zr = blockIdx.z * n3;   // instance blockIdx.z
+  const size_t row0 = (size_t)blockIdx.x * Q::ROWS, row = row0 + warp;
+  const float kf = a.g.kf;
+  auto issue = [&](int k) {   // pencil k's two fields -> stage k & 1
+    float2* st = ring + (k & 1) * Q::STAGE_F2;
+    mbar_expect_tx(&bar[k & 1], Q::STAGE_BYTES);
+    for (int r = 0; r < Q::ROWS; ++r) {
+      bulk_load(st + r * Q::ROWW, a.in[2 * k] + zs + (row0 + r) * H, H * 8u, &bar[k & 1]);
+      bulk_load(st + r * Q::ROWW + H, a.in[2 * k + 1] + zs + (row0 + r) * H, H * 8u, &bar[k & 1]);
+    }
+  };
+  if (threadIdx.x == 0) {
+    s_fail = 0;
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    mbar_init_fence();
+    issue(0);
+    issue(1);
+  }
+  const float* gsr = a.gs + zr + row * N;   // g_S of this row (read where used: registers are short)
+  load_twiddles(s_tw, a.tw, N);
+  __syncthreads();
+  // pencil k of this warp's row into v (Hermitian extension of both fields with their z
+  // derivative orders, Z = A + i B); false if a wait ran out (drained and reported)
+  auto fetch = [&](int k, float2 (&v)[RMAX]) -> bool {
+    const bool ok = mbar_wait(&bar[k & 1], (k >> 1) & 1, a.g.wait);
+    if (!ok) s_fail = 1;
+    __syncthreads();
+    if (s_fail) {
+      if (threadIdx.x == 0) {
+        for (int g = k; g < (k == 0 ? 2 : 3); ++g) mbar_wait(&bar[g & 1], (g >> 1) & 1);
+        report_device_error(a.g.err, LPT2_DEV_ETIMEOUT_ZADJSOURCE);
+      }
+      return false;
+    }
+    const float2* reg = ring + (k & 1) * Q::STAGE_F2 + warp * Q::ROWW;
+    const int ma = a.ord[2 * k], mb = a.ord[2 * k + 1];
+#pragma unroll
+    for (int r = 0; r < RMAX; ++r) {
+      const int n = elem<N>(t, r);
+      if (n == H) {
+        v[r] = make_float2(0.f, 0.f);
+      } else {
+        const bool lo = n < H;
+        const int j = lo ? n : N - n;
+        const float kz = kf * (float)j;
+        float2 A = deriv(reg[j], kz, ma), B = deriv(reg[H + j], kz, mb);
+        if (!lo) { A = cconj(A); B = cconj(B); }
+        v[r] = make_float2(A.x - B.y, A.y + B.x);
+      }
+    }
+    __syncwarp();   // the row is read before the transform's exchanges overwrite it
+    return true;
+  };
+  const SmemRowT<true> sm0{ring + warp * Q::ROWW}, sm1{ring + Q::STAGE_F2 + warp * Q::ROWW};
+  // pencil 0: phi_xx + i phi_yy
+  float2 ab[RMAX];
+  if (!fetch(0, ab)) return;
+  fft<N, true>(ab, t, sm0, s_tw);
+  __syncthreads();   // stage 0 free in every warp: the third pencil goes there
+  if (threadIdx.x == 0) {
+    fence_proxy_async_smem();
+    issue(2);
+  }
+  // pencil 1: phi_zz + i phi_xy; the cotangents of the diagonals and of xy
+  float2 v[RMAX], q[RMAX];
+  if (!fetch(1, v)) return;
+  fft<N, true>(v, t, sm1, s_tw);
+#pragma unroll
+  for (int r = 0; r < RMAX; ++r) {
+    const float A = ab[r].x, B = ab[r].y, Cz = v[r].x, D = v[r].y, g = __ldg(gsr + elem<N>(t, r));
+    q[r] = make_float2(g * (A + B), -2.f * g * D);    // g_zz + i g_xy
+    v[r] = make_float2(g * (B + Cz), g * (A + Cz));   // g_xx + i g_yy
+  }
+  fft<N, false>(v, t, sm1, s_tw);
+  z_store_pair_d<N>(v, t, sm1, a.out[0] + zs + row * H, a.out[1] + zs + row * H, kf, a.ord[0], a.ord[1]);
+  sm1.sync();
+  fft<N, false>(q, t, sm1, s_tw);
+  z_store_pair_d<N>(q, t, sm1, a.out[2] + zs + row * H, a.out[3] + zs + row * H, kf, a.ord[2], a.ord[3]);
+  // pencil 2: phi_xz + i phi_yz
+  if (!fetch(2, v)) return;
+  fft<N, true>(v, t, sm0, s_tw);
+#pragma unroll
+  for (int r = 0; r < RMAX; ++r) {
+    const float g = -2.f * __ldg(gsr + elem<N>(t, r));
+    v[r] = make_float2(g * v[r].x, g * v[r].y);
+  }
+  fft<N, false>(v, t, sm0, s_tw);
+  z_store_pair_d<N>(v, t, sm0, a.out[4] + zs + row * H, a.out[5] + zs + row * H, kf, a.ord[4], a.ord[5]);
+}
+
 // ===================================================================== y pass
 // CTA = (kz block of W, fixed x). Thread tid = t * W + w.
 // KIND: Y_MULTI  each output = transform of (i k_y)^ord times its input; the input
@@ -1377,6 +1507,12 @@ template <int N> cudaError_t launch_z_adj_source_t(const ZAdjSourceArgs& a, cuda
   using C = PassCfg<N>;
   using Q = ZSrcCfg<N>;
   LPT2_CHECK_BATCH(a);
+  if constexpr (zadj_field_pairs<N>()) {
+    using F = ZAdjFpCfg<N>;
+    cudaFuncSetAttribute(k_z_adj_source_fp<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, F::SMEM);
+    k_z_adj_source_fp<N><<<dim3(N * N / F::ROWS, 1, a.g.batch), F::THREADS, F::SMEM, s>>>(a);
+    return cudaGetLastError();
+  }
   cudaFuncSetAttribute(k_z_adj_source<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, Q::SMEM);
   k_z_adj_source<N><<<dim3(N * N / Q::ROWS, 1, a.g.batch), C::ZT, Q::SMEM, s>>>(a);
   return cudaGetLastError();
