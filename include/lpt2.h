@@ -291,8 +291,8 @@ int lpt2_displace_outputs(lpt2_plan_t plan, const float* noise, float* pos, doub
  * group's size); drops the plan's captured graphs (recaptured on the next call).
  * lpt2_tiles: the number of groups and, where the arrays are not NULL, up to max_groups
  * tile choices per group: ytile = pencils per CTA of the y passes (0 = build default, 8 or
- * 16) and xtile = tile path of the x passes that fill the phi potentials (0 = build
- * default, 1 = bulk-tensor tiles staged in shared memory, 2 = global loads).
+ * 16) and xtile = tile path of the x passes of delta(k) and of the adjoint's x transposes
+ * (0 = build default, 1 = bulk-tensor tiles staged in shared memory, 2 = global loads).
  * lpt2_set_tiles: sets them for every group (ytile 16 needs N >= 32); results are the
  * same bit for bit for every choice, only the speed differs.  Drops the captured graphs.
  * lpt2_autotune: times every group's forward step (Philox noise -> positions -> CIC ->
@@ -319,8 +319,10 @@ int lpt2_set_fr0(lpt2_plan_t plan, double fr0_abs);
  * lpt2_displace + lpt2_cic_pk, and of the particle positions (the paper has
  * no gradients: this is the transpose
  * of the steps of Sec. 2.1 Eq. second-ini and Sec. 2.4 taken in reverse order).
- * The forward map is recomputed inside (only delta(k) is kept; the six phi_ij
- * are recomputed from it for the source-term transpose), except on a plan made with
+ * The forward map is recomputed inside (delta(k), S(k), the positions and the six phi_ij
+ * stay in the workspace for the transposes: the forward's phi_ij are checkpointed in
+ * slots that nothing overwrites before the source-term transpose reads them), except on a
+ * plan made with
  * LPT2_KEEP_STATE whose last lpt2_displace (to the density only) used the same noise
  * pointer and whose workspace no call has overwritten since (lpt2_cic_pk of that density
  * keeps it too, and also leaves the density spectrum the adjoint needs): then the adjoint

@@ -86,7 +86,7 @@ struct Group {
   int geo_ns;                // 0: not computed yet
   int chunk = 0;             // instances per launch in lpt2_displace / lpt2_cic_pk (0: the whole group)
   int ytile = 0;             // y-pass pencils per CTA (0: build default, 8, 16)
-  int xtile = 0;             // x-pass tile path of the delta/phi modes (0: default, 1: bulk-tensor, 2: global)
+  int xtile = 0;             // x-pass tile path of the delta and adjoint modes (0: default, 1: bulk-tensor, 2: global)
 };
 
 struct GraphCache {  // one captured launch sequence per entry point (LPT2_GRAPH)
@@ -975,7 +975,13 @@ struct FwdSlots {
   float2* D;
   float2* X[5];
   float2* Y[9];
+  float2* P[6];   // the six phi_ij of the unsplit path (y-pass output order)
 };
+
+// Slots of the six phi_ij on the unsplit forward path: none of them is written again by the
+// rest of the forward, by lpt2_cic_pk, or by the adjoint before its source transpose, so
+// the adjoint reads the forward's phi_ij there instead of recomputing them from delta(k).
+constexpr int kPhiSlots[6] = {5, 6, 13, 14, 15, 16};
 
 FwdSlots fwd_slots(lpt2_plan_t p) {
   FwdSlots f;
@@ -983,6 +989,7 @@ FwdSlots fwd_slots(lpt2_plan_t p) {
   f.D = slot(p, S_DELTA);
   for (int i = 0; i < 5; ++i) f.X[i] = slot(p, S_X0 + i);
   for (int i = 0; i < 9; ++i) f.Y[i] = slot(p, S_Y0 + i);
+  for (int i = 0; i < 6; ++i) f.P[i] = slot(p, kPhiSlots[i]);
   return f;
 }
 
@@ -1024,7 +1031,7 @@ int displace_prefix(lpt2_plan_t p, const FwdSlots& f, const float* noise, bool s
   const int ord[9] = {0, 1, 2, 0, 1, 0, 0, 1, 0};
   y.job.n_out = split ? 9 : 6;
   for (int o = 0; o < 9; ++o) {
-    y.job.out[o] = f.Y[o];
+    y.job.out[o] = (split || o >= 6) ? f.Y[o] : f.P[o];   // split: Psi1 parts in Y[6..8]
     y.job.src[o] = src[o];
     y.job.ord[o] = ord[o];
   }
@@ -1034,7 +1041,8 @@ int displace_prefix(lpt2_plan_t p, const FwdSlots& f, const float* noise, bool s
   ZSourceArgs zs{};
   zs.g = g;
   zs.tw = p->tw;
-  const float2* phi[6] = {f.Y[5], f.Y[2], f.Y[0], f.Y[4], f.Y[3], f.Y[1]};   // xx yy zz xy xz yz
+  float2* const* ph = split ? f.Y : f.P;
+  const float2* phi[6] = {ph[5], ph[2], ph[0], ph[4], ph[3], ph[1]};   // xx yy zz xy xz yz
   const int zord[6] = {0, 0, 2, 0, 1, 1};
   for (int i = 0; i < 6; ++i) {
     zs.in[i] = phi[i];
@@ -1390,7 +1398,7 @@ int lpt2_set_tiles(lpt2_plan_t p, const int* ytile, const int* xtile, int n_grou
 // Times every group's forward step (Philox noise, positions, CIC, P(k)) at chunk sizes
 // count, ceil(count/2), ceil(count/4), ..., 1 and keeps the fastest per group; then, at
 // that chunk size, the y-pass pencils per CTA (8, 16) and the x-pass tile path of the
-// delta and phi modes (bulk-tensor, global loads), one after the other.
+// delta and adjoint modes (bulk-tensor, global loads), one after the other.
 int lpt2_autotune(lpt2_plan_t p, int n_shells, int reps) {
   if (p) drop_state(p);   // overwrites the state kept for the adjoint
   AbiRange nvtx_range("lpt2_autotune");
@@ -1459,7 +1467,7 @@ int lpt2_autotune(lpt2_plan_t p, int n_shells, int reps) {
       if (ms < best_ms) best_ms = ms;
       else gr.ytile = keep;
     }
-    for (int xt : {1, 2}) {    // x-pass tile path of the delta and phi modes
+    for (int xt : {1, 2}) {    // x-pass tile path of the delta and adjoint modes
       if (rc) break;
       const int keep = gr.xtile;
       gr.xtile = xt;
@@ -1869,7 +1877,9 @@ int lpt2_displace_vjp(lpt2_plan_t p, const float* noise, const float* g_pos, con
   ys.job.out[0] = S[10];
   ys.job.out[1] = S[11];
   LAUNCH(p, "y_adj_psi", 20.0 * V3(p), y_pass(n, ys, p->stream));
-  // 5-6. x transpose of the source step: h_Psi (slot 12), inverse x of h_S (slot 13), theta partials
+  // 5-6. x transpose of the source step: h_Psi (slot 12), inverse x of h_S (slot 3), theta
+  // partials; then h_S to real space (g_S, in the position slot: the positions are dead after
+  // the CIC transpose)
   XArgs xs{};
   xs.g = g;
   xs.tw = p->tw;
@@ -1879,7 +1889,7 @@ int lpt2_displace_vjp(lpt2_plan_t p, const float* noise, const float* g_pos, con
   xs.delta_in = S[S_DELTA];
   xs.s_in = S[S_SHAT];
   xs.hpsi_out = S[12];
-  xs.out[0] = S[13];
+  xs.out[0] = S[3];
   xs.cosmo = p->cosmo_dev;
   xs.mt0 = p->mt0;
   xs.mt1 = p->mt1;
@@ -1890,49 +1900,23 @@ int lpt2_displace_vjp(lpt2_plan_t p, const float* noise, const float* g_pos, con
   xs.theta_part = thp;
   LAUNCH(p, "x_adj_source", 28.0 * V3(p), x_pass(n, xs, p->stream));
   YArgs yh = yi;
-  yh.job.in[0] = S[13];
-  yh.job.out[0] = S[13];
+  yh.job.in[0] = S[3];
+  yh.job.out[0] = S[3];
   LAUNCH(p, "y_inv", 8.0 * V3(p), y_pass(n, yh, p->stream));
-  // 7. recompute the six phi_ij (checkpointed: from delta(k) in slot 1)
-  XArgs xph{};
-  xph.g = g;
-  xph.tw = p->tw;
-  xph.mode = X_PHI;
-  xph.in = S[S_DELTA];
-  xph.out[0] = S[2];
-  xph.out[1] = S[3];
-  xph.out[2] = S[4];
-  xph.cosmo = p->cosmo_dev;
-  xph.mt0 = p->mt0;
-  xph.mt1 = p->mt1;
-  LAUNCH(p, "x_phi", 16.0 * V3(p), x_pass(n, xph, p->stream));
-  YArgs yp{};
-  yp.g = g;
-  yp.tw = p->tw;
-  yp.inverse = 1;
-  yp.job.n_in = 3;
-  yp.job.n_out = 6;
-  const int psrc[6] = {0, 0, 0, 1, 1, 2}, pord[6] = {0, 1, 2, 0, 1, 0};
-  float2* pdst[6] = {S[5], S[6], S[7], S[8], S[9], S[10]};   // (x0y0) (x0y1) (x0y2) (x1y0) (x1y1) (x2y0)
-  for (int i = 0; i < 3; ++i) yp.job.in[i] = S[2 + i];
-  for (int o = 0; o < 6; ++o) {
-    yp.job.out[o] = pdst[o];
-    yp.job.src[o] = psrc[o];
-    yp.job.ord[o] = pord[o];
-  }
-  LAUNCH(p, "y_phi", 36.0 * V3(p), y_pass(n, yp, p->stream));
-  // 8. z transpose of the source term: outputs xx yy zz xy xz yz
+  float* gsr = reinterpret_cast<float*>(S[S_POS]);
+  ZC2RArgs zg{g, p->tw, S[3], gsr, nullptr};
+  LAUNCH(p, "z_c2r_gs", 8.0 * V3(p), z_c2r(n, zg, p->stream));
+  // 7-8. z transpose of the source term: the six phi_ij are the forward's (checkpointed in
+  // their slots: the forward above, or the kept one, wrote them and nothing since has);
+  // outputs xx yy zz xy xz yz
   ZAdjSourceArgs za{};
   za.g = g;
   za.tw = p->tw;
-  // g_S in real space (the positions of slots 18-20 are dead after the CIC transpose)
-  float* gsr = reinterpret_cast<float*>(S[S_POS]);
-  ZC2RArgs zg{g, p->tw, S[13], gsr, nullptr};
-  LAUNCH(p, "z_c2r_gs", 8.0 * V3(p), z_c2r(n, zg, p->stream));
   za.gs = gsr;
-  const float2* phi[6] = {S[10], S[7], S[5], S[9], S[8], S[6]};   // xx yy zz xy xz yz
+  const FwdSlots fs = fwd_slots(p);
+  const float2* phi[6] = {fs.P[5], fs.P[2], fs.P[0], fs.P[4], fs.P[3], fs.P[1]};   // xx yy zz xy xz yz
   const int zord[6] = {0, 0, 2, 0, 1, 1};
-  float2* gout[6] = {S[0], S[2], S[3], S[4], S[11], S[14]};
+  float2* gout[6] = {S[0], S[2], S[4], S[7], S[8], S[9]};
   for (int i = 0; i < 6; ++i) {
     za.in[i] = phi[i];
     za.ord[i] = zord[i];

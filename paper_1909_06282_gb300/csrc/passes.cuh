@@ -972,7 +972,7 @@ __device__ __forceinline__ void x_tile(const XArgs& a, float2 (&v)[PassCfg<N>::R
       for (int r = 0; r < C::RMAX; ++r) a.out[0][base + (size_t)(elem<N>(t, r)) * stride] = v[r];
       return;
     }
-    if (MODE != X_PHI) fft<N, false>(v, t, sm, s_tw);
+    fft<N, false>(v, t, sm, s_tw);
     if (MODE == X_FWD) {
 #pragma unroll
       for (int r = 0; r < C::RMAX; ++r) a.out[0][base + (size_t)(elem<N>(t, r)) * stride] = v[r];
@@ -1132,8 +1132,7 @@ __device__ __forceinline__ void x_tile(const XArgs& a, float2 (&v)[PassCfg<N>::R
   // sqrt(P N^3/V) and 1/(k^2 N^3) only, the first comes from the scf field (coalesced, or
   // staged with the tile) and the second is computed.
   const size_t toff = (size_t)inst * mode_table_len(N);
-  const bool field = (MODE == X_DELTA && !a.split && (s_sc || a.scf)) || (MODE == X_ADJ_DELTA && a.scf) ||
-                     MODE == X_PHI;
+  const bool field = (MODE == X_DELTA && !a.split && (s_sc || a.scf)) || (MODE == X_ADJ_DELTA && a.scf);
   float2 g[C::RMAX], hpot[C::RMAX];
   float theta = 0.f;
 #pragma unroll
@@ -1147,7 +1146,7 @@ __device__ __forceinline__ void x_tile(const XArgs& a, float2 (&v)[PassCfg<N>::R
     if (field) {
       const float inv_c = zero ? 0.f : __frcp_rn((float)n2 * a.g.kf2n3);
       float sc_f = 0.f;
-      if (MODE != X_PHI) sc_f = s_sc ? s_sc[kx * C::W + w] : __ldg(a.scf + e);
+      sc_f = s_sc ? s_sc[kx * C::W + w] : __ldg(a.scf + e);
       mt = make_float4(sc_f, inv_c, 0.f, 0.f);
     } else {
       mt = zero ? make_float4(0.f, 0.f, 0.f, 0.f) : __ldg(a.mt0 + toff + n2);
@@ -1158,8 +1157,6 @@ __device__ __forceinline__ void x_tile(const XArgs& a, float2 (&v)[PassCfg<N>::R
       if (a.delta_out) a.delta_out[e] = d;
       g[r] = cscale(d, inv);                                // phi1 = delta / k^2 (1/N^3 folded)
       if (a.split) hpot[r] = cscale(g[r], d1);
-    } else if (MODE == X_PHI) {                           // v = delta(k) already
-      g[r] = cscale(v[r], inv);
     } else if (MODE == X_SOURCE) {                        // v = S(k)
       float2 u = cscale(v[r], -d2 * inv);                   // phi2 = -S D2 / k^2
       if (!a.split) {
@@ -1192,12 +1189,11 @@ __device__ __forceinline__ void x_tile(const XArgs& a, float2 (&v)[PassCfg<N>::R
   if (si.summed) __syncthreads();
   int nout;
   if (MODE == X_DELTA) nout = a.split ? 5 : 3;
-  else if (MODE == X_PHI) nout = 3;
   else if (MODE == X_SOURCE) nout = 2;
   else nout = 1;
   for (int o = 0; o < nout; ++o) {
     const bool fromh = (MODE == X_DELTA) && o >= 3;
-    const int m = (MODE == X_DELTA || MODE == X_PHI) ? (o < 3 ? o : o - 3) : (MODE == X_SOURCE ? o : 0);
+    const int m = MODE == X_DELTA ? (o < 3 ? o : o - 3) : (MODE == X_SOURCE ? o : 0);
     float2 u[C::RMAX];
 #pragma unroll
     for (int r = 0; r < C::RMAX; ++r) {
@@ -1591,17 +1587,17 @@ template <int N, int MODE> cudaError_t launch_x_m(const XArgs& a, cudaStream_t s
   const int acc = MODE == X_PK ? (C::XT / 32) * 5 * a.n_shells * 4
                   : (MODE == X_PKP || MODE == X_PKI) ? (C::XT / 32) * a.n_shells * 4
                                                      : (MODE == X_ADJ_SOURCE ? (C::XT / 32) * 8 : 0);
-  // The delta and phi modes have two tile paths: bulk-tensor tiles (default where they
-  // measured faster at 512^3, x_delta 0.91 -> 0.86 ms) and global loads; Geo::xtile picks
-  // one per grid-size group (0 the build default, 1 bulk-tensor, 2 global) and the other
-  // modes ignore it.  The one-transform shell-sum modes keep the global-load kernel at twice
+  // The delta mode and the two adjoint modes have two tile paths: bulk-tensor tiles
+  // (default: measured faster at 512^3, x_delta 0.91 -> 0.86 ms, x_adj_delta 1.245 -> 1.113)
+  // and global loads; Geo::xtile picks one per grid-size group (0 the build default, 1
+  // bulk-tensor, 2 global) and the other modes ignore it.  The one-transform shell-sum modes keep the global-load kernel at twice
   // the CTAs per SM, and the source multiplier, which also reads delta(k) per mode, measured
   // 0.73 -> 0.76 ms with bulk-tensor tiles.
   if (a.g.xtile < 0 || a.g.xtile > 2) return cudaErrorInvalidValue;
   if constexpr (MODE == X_ADJ_DELTA || MODE == X_ADJ_SOURCE) {
     if (a.g.xtile == 0 ? LPT2_X_TMA_ADJ != 0 : a.g.xtile == 1) return launch_x_tma_adj<N, MODE>(a, acc, s);
   }
-  if constexpr (MODE == X_DELTA || MODE == X_PHI) {
+  if constexpr (MODE == X_DELTA) {
     if (a.g.xtile == 0 ? LPT2_X_TMA != 0 : a.g.xtile == 1) {
       if constexpr (MODE == X_DELTA) {
         if (a.scf && !a.split) return launch_x_tma<N, MODE, true>(a, acc, s);
@@ -1624,7 +1620,6 @@ template <int N> cudaError_t launch_x_t(const XArgs& a, cudaStream_t s) {
     case X_PKI: return launch_x_m<N, X_PKI>(a, s);
     case X_FWD: return launch_x_m<N, X_FWD>(a, s);
     case X_INV: return launch_x_m<N, X_INV>(a, s);
-    case X_PHI: return launch_x_m<N, X_PHI>(a, s);
     case X_PKADJ: return launch_x_m<N, X_PKADJ>(a, s);
     case X_ADJ_SOURCE: return launch_x_m<N, X_ADJ_SOURCE>(a, s);
     case X_ADJ_DELTA: return launch_x_m<N, X_ADJ_DELTA>(a, s);

@@ -41,7 +41,7 @@ struct Geo {
   int* err;             // device error word (0 = ok), may be null
   long long wait;       // cycle budget of the bounded consumer waits (0: give up at once)
   // tile schedule of this grid-size group (0 = build default): y-pass pencils per CTA
-  // (8 or 16) and the x-pass tile path of the delta and phi modes (1 bulk-tensor, 2 global)
+  // (8 or 16) and the x-pass tile path of the delta and adjoint modes (1 bulk-tensor, 2 global)
   int ytile;
   int xtile;
 };
@@ -136,7 +136,7 @@ enum XMode {
   X_PK = 2,         // fwd x, shell sums of |delta|^2
   X_FWD = 3,        // plain forward x
   X_INV = 4,        // plain inverse x
-  X_PHI = 5,        // phi potential from a stored delta(k) (no transform), inverse x orders 0, 1, 2
+  X_PHI = 5,        // (unused: the adjoint reads the forward's phi_ij)
   X_PKADJ = 6,      // fwd x, times per-shell weight, inverse x  (P(k) transpose)
   X_ADJ_SOURCE = 7, // transpose of X_SOURCE: h_Psi, h_S, dL/dln|fR0| partials
   X_ADJ_DELTA = 8,  // transpose of X_DELTA: s(k) (h_Psi + h_phi), inverse x
@@ -172,7 +172,7 @@ struct XArgs {
   const float2* mt1;
   // X_DELTA (without the split) and X_ADJ_DELTA: sqrt(P N^3/V) of every mode of the group's
   // half spectra, float[batch][N][N][N/2] in the fields' layout (zero on the modes the
-  // passes zero), or null for the mode table; with it, and in X_PHI, 1/(k^2 N^3) is computed
+  // passes zero), or null for the mode table; with it, 1/(k^2 N^3) is computed
   // from |n|^2, so these modes read no table entry
   const float* scf;
   double* theta_part;     // X_ADJ_SOURCE: per-block partial of dL/dln|fR0|
