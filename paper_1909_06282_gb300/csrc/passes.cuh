@@ -77,6 +77,19 @@ __device__ __forceinline__ float2 dconj(float2 v, float k, int m) {
   if (m == 1) return cscale(mul_mi(v), k);
   return cscale(v, -k * k);
 }
+// v + conj((i k)^m) u with every product and sum rounded on its own (the _rn intrinsics are
+// never contracted), so that the kernels that accumulate the x-order groups of the adjoint
+// (global-load and bulk-tensor tile paths) give the same bits
+__device__ __forceinline__ float2 acc_dconj(float2 v, float2 u, float k, int m) {
+  float2 w = u;
+  if (m == 1) {
+    w = make_float2(__fmul_rn(u.y, k), __fmul_rn(-u.x, k));
+  } else if (m == 2) {
+    const float kk = -__fmul_rn(k, k);
+    w = make_float2(__fmul_rn(u.x, kk), __fmul_rn(u.y, kk));
+  }
+  return make_float2(__fadd_rn(v.x, w.x), __fadd_rn(v.y, w.y));
+}
 
 // ===================================================================== z pass
 // Thread layout: tid = p * TPP + t (pencil pair p, lane t within the pencil).
@@ -934,7 +947,7 @@ __device__ __forceinline__ void x_tile(const XArgs& a, float2 (&v)[PassCfg<N>::R
 #pragma unroll
       for (int r = 0; r < C::RMAX; ++r) {
         const int kx = elem<N>(t, r);
-        v[r] = cadd(v[r], dconj(u[r], kf * (float)mode_of(kx, N), gi));
+        v[r] = acc_dconj(v[r], u[r], kf * (float)mode_of(kx, N), gi);
       }
     }
   } else if (!adjoint) {
@@ -1172,11 +1185,14 @@ __device__ __forceinline__ void x_tile(const XArgs& a, float2 (&v)[PassCfg<N>::R
         const float2 tt = __ldg(a.mt1 + toff + n2);
         const float2 dl = si.delta ? si.delta[kx * C::W + w] : a.delta_in[e];
         const float2 sk = si.s ? si.s[kx * C::W + w] : a.s_in[e];
-        const float cx = tt.x * dl.x - tt.y * sk.x, cy = tt.x * dl.y - tt.y * sk.y;
-        theta += (cx * gu.x + cy * gu.y) * inv * (mz == 0 ? 1.f : 2.f);
+        const float cx = __fmaf_rn(tt.x, dl.x, -__fmul_rn(tt.y, sk.x));
+        const float cy = __fmaf_rn(tt.x, dl.y, -__fmul_rn(tt.y, sk.y));
+        theta = __fmaf_rn(__fmul_rn(__fmaf_rn(cx, gu.x, __fmul_rn(cy, gu.y)), inv), mz == 0 ? 1.f : 2.f, theta);
       }
     } else {                                                // X_ADJ_DELTA: v = sum of h_phi groups
-      const float2 h = cadd(cscale(v[r], inv), si.hpsi ? si.hpsi[kx * C::W + w] : a.hpsi_in[e]);
+      const float2 hp = si.hpsi ? si.hpsi[kx * C::W + w] : a.hpsi_in[e];
+      // explicit FMAs: the same rounding in every kernel that inlines this tile
+      const float2 h = make_float2(__fmaf_rn(v[r].x, inv, hp.x), __fmaf_rn(v[r].y, inv, hp.y));
       g[r] = cscale(h, sc);                                 // s(k) (h_Psi + h_phi)
     }
   }
@@ -1417,7 +1433,7 @@ __global__ void __launch_bounds__(PassCfg<N>::XT, x_minb<N>(MODE)) k_x_tma_adj(c
       }
       fft<N, false>(u, t, SmemCol<C::W>{ring + st * Q::TILE + w}, s_tw);   // ends past its last shared read
 #pragma unroll
-      for (int r = 0; r < C::RMAX; ++r) v[r] = cadd(v[r], dconj(u[r], a.g.kf * (float)mode_of(elem<N>(t, r), N), j));
+      for (int r = 0; r < C::RMAX; ++r) v[r] = acc_dconj(v[r], u[r], a.g.kf * (float)mode_of(elem<N>(t, r), N), j);
       __syncthreads();   // every warp is past the transform: the stage is free
       if (threadIdx.x == 0 && issued < nload) {
         fence_proxy_async_smem();
