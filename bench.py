@@ -136,6 +136,7 @@ TRAFFIC_512 = {
     "z_source": (402.768896 + 52.556544) * 1e6 * 8,
     "cic": (270.255104 + 45.323008) * 1e6 * 8,
     "y_phi": (201.832704 + 345.711104) * 1e6 * 8,
+    "x_delta": (100.722944 + 207.546368) * 1e6 * 8,   # k_x_tma<256, 0, 1> (sqrt(P) field form)
     "x_source": (135.116288 + 84.932864) * 1e6 * 8,
     "z_final": (201.371392 + 152.319744) * 1e6 * 8,
 }

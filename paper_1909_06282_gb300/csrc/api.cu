@@ -1018,7 +1018,7 @@ int displace_prefix(lpt2_plan_t p, const FwdSlots& f, const float* noise, bool s
   x.d2f = p->tabf + p->nk;
   x.t1f = p->tabf + 2 * p->nk;
   x.t2f = p->tabf + 3 * p->nk;
-  LAUNCH(p, "x_delta", (split ? 28.0 : 20.0) * V3(p), x_pass(n, x, p->stream));
+  LAUNCH(p, "x_delta", (split ? 28.0 : 22.0) * V3(p), x_pass(n, x, p->stream));   // + the sqrt(P) field
 
   // 2. y inverse with y derivatives: the six phi_ij (+ Psi1)
   YArgs y{};
@@ -1615,7 +1615,7 @@ int lpt2_source_ratio(lpt2_plan_t p, const float* noise, int n_bins, double* mea
     x.d2f = p->tabf + p->nk;
     x.t1f = p->tabf + 2 * p->nk;
     x.t2f = p->tabf + 3 * p->nk;
-    LAUNCH(p, "x_delta", 20.0 * V3(p), x_pass(n, x, p->stream));
+    LAUNCH(p, "x_delta", 22.0 * V3(p), x_pass(n, x, p->stream));   // + the sqrt(P) field
   }
   // one real field: IDFT[(i k)^ord g(|k|) delta0(k)]
   auto field = [&](int gk, int ox, int oy, int oz, float* out) -> int {
@@ -1954,7 +1954,7 @@ int lpt2_displace_vjp(lpt2_plan_t p, const float* noise, const float* g_pos, con
   xd.cosmo = p->cosmo_dev;
   xd.mt0 = p->mt0;
   xd.mt1 = p->mt1;
-  LAUNCH(p, "x_adj_delta", 20.0 * V3(p), x_pass(n, xd, p->stream));
+  LAUNCH(p, "x_adj_delta", 22.0 * V3(p), x_pass(n, xd, p->stream));   // + the sqrt(P) field
   YArgs yg = yi;
   yg.job.in[0] = S[6];
   yg.job.out[0] = S[6];

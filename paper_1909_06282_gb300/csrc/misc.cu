@@ -396,7 +396,8 @@ cudaError_t launch_shell_geometry(int n, double box, int n_shells, double* ksum,
 // partials; thread (lane, b) = (tid / ns, tid % ns) sums rows lane, lane + L, ... of shell b
 // (L = 256 / ns lanes; a warp reads consecutive shells of a row, i.e. contiguous doubles),
 // then the lanes are summed in order into scratch[instance][g][b].  Stage 2 sums the G
-// rows of scratch per shell in order and divides by the shell's mode count.
+// rows of scratch per shell (a warp per shell: strided lane sums, then a fixed shuffle
+// tree) and divides by the shell's mode count.
 __global__ void k_pk_rows(const double* __restrict__ part, int n_blocks, int ns, int rows, double* __restrict__ scratch) {
   const int g = blockIdx.x, inst = blockIdx.y;
   part += (size_t)inst * n_blocks * ns;
@@ -419,14 +420,20 @@ __global__ void k_pk_rows(const double* __restrict__ part, int n_blocks, int ns,
 
 __global__ void k_pk_finalize_p(const double* __restrict__ scratch, int G, int ns, const double* ksum,
                                 const unsigned long long* count, double* pk, double* kmean, int64_t* nmodes) {
-  const int inst = blockIdx.x, b = threadIdx.x;
-  if (b >= ns) return;
-  double sp = 0.0;
-  for (int g = 0; g < G; ++g) sp += scratch[((size_t)inst * G + g) * ns + b];
-  const double c = (double)count[b];
-  pk[(size_t)inst * ns + b] = c > 0 ? sp / c : 0.0;
-  if (kmean) kmean[(size_t)inst * ns + b] = c > 0 ? ksum[b] / c : 0.0;
-  if (nmodes) nmodes[(size_t)inst * ns + b] = (int64_t)count[b];
+  const int inst = blockIdx.x, lane = threadIdx.x & 31;
+  // a warp per shell: lane l sums rows l, l + 32, ... in order, then a fixed shuffle tree
+  for (int b = threadIdx.x >> 5; b < ns; b += blockDim.x >> 5) {
+    double sp = 0.0;
+    for (int g = lane; g < G; g += 32) sp += scratch[((size_t)inst * G + g) * ns + b];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) sp += __shfl_xor_sync(0xffffffffu, sp, o);
+    if (lane == 0) {
+      const double c = (double)count[b];
+      pk[(size_t)inst * ns + b] = c > 0 ? sp / c : 0.0;
+      if (kmean) kmean[(size_t)inst * ns + b] = c > 0 ? ksum[b] / c : 0.0;
+      if (nmodes) nmodes[(size_t)inst * ns + b] = (int64_t)count[b];
+    }
+  }
 }
 
 cudaError_t launch_pk_finalize_p(const double* part, int n_blocks, int n_shells, const double* ksum,
