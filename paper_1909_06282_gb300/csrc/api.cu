@@ -520,6 +520,7 @@ int cic_pk_group(lpt2_plan_t p, int gi, const float* pos, float* density, double
   LAUNCH(p, "pk_finalize", 0.0,
          launch_pk_finalize_p(pk_part(p), x_blocks(n), n_shells, gr.geo_k, gr.geo_n, pk, k_mean, n_modes,
                               p->stream, p->cur_batch));
+  ++p->launches;   // two kernels: row-slice sums, then the shells
   return LPT2_OK;
 }
 
@@ -1537,6 +1538,7 @@ int lpt2_cic_pk_est(lpt2_plan_t p, const float* pos, float* density, double* pk,
            launch_pk_finalize_p(pk_part(p), x_blocks(n), n_shells, gr.geo_k, gr.geo_n, pk + (size_t)gr.inst0 * n_shells,
                                 k_mean ? k_mean + (size_t)gr.inst0 * n_shells : nullptr,
                                 n_modes ? n_modes + (size_t)gr.inst0 * n_shells : nullptr, p->stream, p->cur_batch));
+    ++p->launches;   // two kernels: row-slice sums, then the shells
   }
   return LPT2_OK;
 }
